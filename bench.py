@@ -1,0 +1,382 @@
+#!/usr/bin/env python
+"""Benchmark: MM iterations/s of distributed FastMNMF on one GB300.
+
+Workload (default): 4 subarrays x 4 microphones (M = 16), N = 5 sources,
+B = 16 bases, F = 513 bins, T = 626 frames, seeded synthetic mixtures.
+One timed step is the whole job of the paper on one mixture: reset to the
+initial state, 200 MM iterations (IP of every block, then the W, H, g
+multiplicative updates), the negative log-likelihood (read back to the host)
+and the per-subarray Wiener filter.  value = MM iterations/s over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank separates its own mixture on its own GPU (replicas:
+the mixture does not shard), timing is bracketed by a barrier and a device
+synchronise, and rank 0 prints one JSON line with the max time over ranks.
+L2 is flushed (a 256 MB write) before every timed step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MM iter/s at 4\u00d74 mics,N=5,F=513,T=626: BF16-TC vs FP32 plain, % roofline"
+UNIT = "MM iter/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="paper_4x4_n5")
+    ap.add_argument("--iters", type=int, default=None, help="MM iterations per step (default: the workload's)")
+    ap.add_argument("--ip", choices=["f32x2", "f64", "f32"], default="f32x2")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        try:
+            os.unlink(self.path)
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------- algorithmic bytes
+def kernel_bytes(F, T, M, N, B, K, MK):
+    """Algorithmic DRAM bytes of one launch of each kernel (each operand once)."""
+    q = F * K * MK * MK
+    return {
+        "k_cov": 8 * F * T * M + 4 * N * F * T + 4 * F * N * M + 8 * q * MK,
+        "k_ip": 8 * q * MK + 32 * q + 8 * q,
+        "k_pstats": 8 * F * T * M + 4 * N * F * T + 4 * F * N * M + 8 * q + 4 * F * T * M + 8 * N * F * T,
+        "k_wupd": 8 * N * F * T + 4 * N * B * T + 8 * N * F * B + 4 * N * F * T,
+        "k_stats": 4 * F * T * M + 4 * N * F * T + 4 * F * N * M + 8 * N * F * T,
+        "k_hupd": 8 * N * F * T + 4 * N * F * B + 8 * N * B * T + 4 * N * F * T,
+        "k_gupd": 4 * N * F * T + 4 * F * T * M + 8 * F * N * M,
+        "k_lambda": 4 * N * F * B + 4 * N * B * T + 4 * N * F * T,
+    }
+
+
+def iteration_bytes(F, T, M, N):
+    """B_alg = 28 F T M + 56 F T N: bytes of one MM iteration with each kernel's operands read once."""
+    return 28 * F * T * M + 56 * F * T * N
+
+
+# --------------------------------------------------------- CPU oracle arm
+def run_oracle_sample(workload: str, seconds: float, max_iters: int = 1000) -> dict:
+    """Time the FP64 oracle (single thread) for about `seconds` of MM iterations."""
+    code = f"""
+import os, sys, time, json
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+import oracle as O
+from paper_2605_19388_gb300 import synth
+p = synth.make_workload({workload!r}, seed=0)
+x = p.x.astype(np.complex128)
+st = O.state_from_arrays(p.Q0, p.W0, p.H0, p.g0, p.mics)
+t0 = time.perf_counter(); n = 0
+while True:
+    st = O.mm_iteration(x, p.mics, st); n += 1
+    el = time.perf_counter() - t0
+    if el >= {seconds} or n >= {max_iters}:
+        break
+print(json.dumps(dict(iters=n, seconds=el)))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               NUMEXPR_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    from paper_2605_19388_gb300 import synth
+    w = synth.WORKLOADS[args.workload]
+    F, T, M = w["F"], w["T"], sum(w["mics"])
+    per_step = max(2.0, min(args.cpu_seconds, 20.0))
+    for _ in range(args.warmup):
+        run_oracle_sample(args.workload, 0.0, max_iters=1)
+    times, iters = [], 0
+    for _ in range(args.steps):
+        s = run_oracle_sample(args.workload, per_step / 4, max_iters=1)
+        times.append(s["seconds"])
+        iters += s["iters"]
+    total = sum(times)
+    value = iters / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded STFT mixtures, stand-in for the paper's simulated JNAS rooms)",
+        "config": {"workload": args.workload, "F": F, "T": T, "mics": list(w["mics"]), "N": w["N"],
+                   "B": w["B"], "step": "one MM iteration of the FP64 oracle (bounded sample of the 200-iteration job)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{iters} MM iterations of the {args.workload} workload, one per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "tf_bin_mic_updates_per_s": F * T * M * value,
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+
+    import torch
+    from paper_2605_19388_gb300 import build as B
+    if rank == 0 or world == 1:
+        B.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+        dist.barrier()
+    from paper_2605_19388_gb300 import dfmnmf as D
+    from paper_2605_19388_gb300 import synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ip = {"f32x2": D.DFMNMF_IP_F32X2, "f64": D.DFMNMF_IP_F64, "f32": D.DFMNMF_IP_F32}[args.ip]
+    wl = synth.WORKLOADS[args.workload]
+    iters = args.iters or wl["iters"]
+    p = synth.make_workload(args.workload, seed=rank)
+    F, T, M, N, Bb, K, MK = p.F, p.T, p.M, p.N, p.B, p.K, p.mics[0]
+
+    x_d = torch.from_numpy(p.x).to(dev)
+    W0_d, H0_d, g0_d = (torch.from_numpy(a).to(dev) for a in (p.W0, p.H0, p.g0))
+    Q0_d = torch.from_numpy(p.Q0).to(dev)
+    c_out = torch.empty((N, F, T, M), dtype=torch.complex64, device=dev)
+    flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def make(ip_arith):
+        return D.dfmnmf_init(F, T, p.mics, N, Bb, x_d, W0_d, H0_d, g0_d, Q0_d, ip_arith=ip_arith)
+
+    ctx = make(ip)
+    nll_box = []
+
+    def step(c):
+        D.dfmnmf_set_params(c, Q0_d, W0_d, H0_d, g0_d)
+        D.dfmnmf_iterate(c, iters)
+        nll_box.append(D.dfmnmf_loglik(c))
+        D.dfmnmf_separate(c, c_out)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def timed(fn, c, nsteps):
+        tot = 0.0
+        for _ in range(nsteps):
+            flush_buf.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn(c)
+            e1.record()
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot
+
+    for _ in range(args.warmup):
+        step(ctx)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    total_ms = timed(step, ctx, args.steps)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * iters * args.steps / (total_ms / 1000.0)
+
+    launches_iter = D.dfmnmf_launches_per_iteration(ctx)
+    launches_step = iters * launches_iter + 2 + 3 + 2  # set_params, loglik, separate
+    gpu_launches = launches_step * args.steps
+
+    # per-kernel times inside the same steady state (events between launches)
+    D.dfmnmf_set_params(ctx, Q0_d, W0_d, H0_d, g0_d)
+    D.dfmnmf_iterate(ctx, 5)
+    kt = D.dfmnmf_kernel_times(ctx, 50)
+    iter_ms = sum(ms for _, ms in kt)
+    kb = kernel_bytes(F, T, M, N, Bb, K, MK)
+    peak, peak_kind = peaks()
+    dom_name, dom_ms = max(kt, key=lambda e: e[1])
+    ach = kb[dom_name] / (dom_ms * 1e-3) / 1e9
+    kernels = {n: {"ms": ms, "share": ms / iter_ms, "alg_bytes": kb.get(n),
+                   "GBps": (kb[n] / (ms * 1e-3) / 1e9) if n in kb else None} for n, ms in kt}
+    ib = iteration_bytes(F, T, M, N)
+    roofline = {"bound": "hbm", "kernel": dom_name, "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "traffic": None, "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
+                "alg_bytes_per_launch": kb[dom_name]}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (IP solves f32x2)" if args.ip == "f32x2" else f"f32 (IP solves {args.ip})",
+        "data": "synthetic (seeded STFT mixtures, stand-in for the paper's simulated JNAS rooms)",
+        "config": {"workload": args.workload, "F": F, "T": T, "mics": list(p.mics), "N": N, "B": Bb,
+                   "iters_per_step": iters, "form": "fp32-plain", "ip_arith": args.ip,
+                   "step": "reset state + iterations + loglik (D2H) + Wiener filter",
+                   "l2": "flushed before every timed step (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "tf_bin_mic_updates_per_s": F * T * M * value,
+        "roofline": roofline,
+        "iteration": {"ms": iter_ms, "alg_bytes": ib, "GBps": ib / (iter_ms * 1e-3) / 1e9,
+                      "frac_of_hbm_peak": ib / (iter_ms * 1e-3) / 1e9 / peak,
+                      "launches": launches_iter},
+        "kernels": kernels,
+        "clocks": clocks,
+        "gpu_launches": gpu_launches,
+        "nll_last": nll_box[-1] if nll_box else None,
+    }
+
+    # end to end through the public API with host buffers (pinned)
+    if not args.no_e2e:
+        xh = torch.from_numpy(p.x).pin_memory()
+        W0h, H0h, g0h = (torch.from_numpy(a).pin_memory() for a in (p.W0, p.H0, p.g0))
+        Q0h = torch.from_numpy(p.Q0).pin_memory()
+
+        def step_e2e(c):
+            D.dfmnmf_set_observation(c, xh)
+            D.dfmnmf_set_params(c, Q0h, W0h, H0h, g0h)
+            D.dfmnmf_iterate(c, iters)
+            D.dfmnmf_loglik(c)
+            D.dfmnmf_separate(c, c_out)
+
+        for _ in range(2):
+            step_e2e(ctx)
+        torch.cuda.synchronize()
+        barrier()
+        e2e_ms = timed(step_e2e, ctx, args.steps)
+        barrier()
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        h2d = xh.numel() * 8 + (W0h.numel() + H0h.numel() + g0h.numel()) * 4 + Q0h.numel() * 16
+        out["e2e"] = {"value": world * iters * args.steps / (e2e_ms / 1000.0), "unit": UNIT,
+                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8 + 16,
+                      "ms_per_step": e2e_ms / args.steps}
+
+    # variants on the same GPU: native-FP64 IP solves
+    if not args.no_variants:
+        var = {}
+        for name, ipv in (("ip_f64", D.DFMNMF_IP_F64), ("ip_f32", D.DFMNMF_IP_F32)):
+            if ipv == ip:
+                continue
+            c2 = make(ipv)
+            for _ in range(2):
+                step(c2)
+            ms = timed(step, c2, max(2, args.steps // 2))
+            n2 = max(2, args.steps // 2)
+            var[name] = {"value": world * iters * n2 / (ms / 1000.0), "unit": UNIT,
+                         "k_ip_ms": dict(D.dfmnmf_kernel_times(c2, 10)).get("k_ip")}
+            D.dfmnmf_destroy(c2)
+        out["variants"] = var
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        s = run_oracle_sample(args.workload, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": s["iters"] / s["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"{s['iters']} MM iterations of the FP64 oracle on the same workload "
+                                         f"({s['seconds']:.1f} s, one thread)"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,190 @@
+/*
+ * dfmnmf.h -- C ABI of the GB300 (sm_103a) distributed FastMNMF library.
+ *
+ * Distributed FastMNMF (arXiv 2605.19388) separates N sources observed by K
+ * subarrays of M_k microphones.  The spatial covariance of each source is
+ * block diagonal over subarrays and jointly diagonalised inside each block
+ * (Sec. III-B); the source PSDs follow an NMF model shared by all subarrays
+ * (Eq. 2).  One majorisation-minimisation (MM) iteration is the iterative
+ * projection of every diagonaliser block (Eqs. 13-15) followed by the
+ * multiplicative updates of the NMF bases, activations and diagonal SCM
+ * entries (Eqs. 8-10, with the microphone index taken over all subarrays as
+ * stated after Eq. 15).
+ *
+ * Symbols used in this header (paper symbol in brackets):
+ *   f < F frequency bin [i], t < T frame [j], k < K subarray [l],
+ *   m < M global microphone, mu < M_k microphone inside subarray k [mu],
+ *   o_k = M_0 + ... + M_{k-1} first global microphone of subarray k,
+ *   n < N source [n], b < B NMF basis [k],
+ *   W[n][f][b] spectral basis [t_ikn], H[n][b][t] activation [v_kjn],
+ *   lambda[n][f][t] = sum_b W H source PSD [h_ijn] (Eq. 2),
+ *   g[f][n][m] diagonal SCM entry [(Lambda_in)_mm] (Eq. 3, Eq. 10),
+ *   Q_f = blkdiag(Q_f0..Q_f,K-1) diagonaliser [W_i^H]; row mu of block k is
+ *   w_{i mu}^(l) H, so y_ftk = Q_fk x_ftk (Sec. III-B),
+ *   yhat[f][t][m] = max(sum_n lambda g, eps) model variance [eta_ijm],
+ *   P[f][t][m] = |y_ftm|^2 projected power [|y_ijm|^2],
+ *   V[f][k][mu] = (1/T) sum_t x_ftk x_ftk^H / yhat_ft(o_k+mu)  [Q_{i mu}^(l), Eq. 13].
+ *
+ * Memory conventions
+ *   - All pointers named *_dev are CUDA device pointers (or managed memory)
+ *     unless the comment says "host or device": those are copied with
+ *     cudaMemcpyAsync(cudaMemcpyDefault), so pinned or pageable host memory
+ *     works as well.  The caller owns every pointer it passes; the library
+ *     never keeps one after the call returns (x is copied at init).
+ *   - complex64 = interleaved float (re, im); complex128 = interleaved double.
+ *   - Arrays are C-contiguous in the index order written.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  All work is
+ *     enqueued on it; only dfmnmf_loglik and dfmnmf_get_params(host) block.
+ *
+ * Errors
+ *   Every entry point returns a dfmnmf_status; nothing throws or traps.  The
+ *   message of the last failure on the calling thread is returned by
+ *   dfmnmf_last_error().  A non-finite value produced by an update sets a
+ *   device flag that the next dfmnmf_loglik reports as DFMNMF_ENUMERIC.
+ *
+ * Limits of this release
+ *   All subarrays must have the same size M_k in 1..4 (the paper's layout is
+ *   three 4-microphone subarrays); other layouts return DFMNMF_EINVAL.
+ *   1 <= N <= 16, 1 <= B <= 64, 1 <= K <= 16, F >= 1, T >= 1.
+ */
+#ifndef DFMNMF_H
+#define DFMNMF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DFMNMF_VERSION 100
+
+typedef struct dfmnmf_ctx dfmnmf_ctx; /* opaque, owned by the library */
+
+typedef enum dfmnmf_status {
+  DFMNMF_OK = 0,
+  DFMNMF_EINVAL = 1,   /* bad argument, size or layout; nothing was enqueued */
+  DFMNMF_ENOMEM = 2,   /* device allocation failed */
+  DFMNMF_ECUDA = 3,    /* a CUDA runtime call failed (message has the detail) */
+  DFMNMF_ENUMERIC = 4, /* a NaN or Inf was produced by an update */
+  DFMNMF_ETIMEOUT = 5  /* a bounded device wait gave up (reserved) */
+} dfmnmf_status;
+
+/* Arithmetic of the weighted-covariance contraction and the NMF products. */
+typedef enum dfmnmf_precision {
+  DFMNMF_FP32 = 0,    /* CUDA-core FP32 everywhere except the IP solves   */
+  DFMNMF_BF16_TC = 1, /* tensor-core BF16 operands, FP32 accumulation     */
+  DFMNMF_TF32_TC = 2  /* tensor-core TF32 operands, FP32 accumulation     */
+} dfmnmf_precision;
+
+/* Arithmetic of the M_k x M_k iterative-projection solves (Eqs. 14-15). */
+typedef enum dfmnmf_ip_arith {
+  DFMNMF_IP_F64 = 0,   /* native IEEE binary64                            */
+  DFMNMF_IP_F32X2 = 1, /* float-float pairs (Dekker/Knuth), ~48-bit mantissa */
+  DFMNMF_IP_F32 = 2    /* plain binary32 (for precision studies only)     */
+} dfmnmf_ip_arith;
+
+typedef struct dfmnmf_desc {
+  int F, T, K;        /* bins, frames, subarrays                               */
+  const int* mics;    /* host array of K block sizes M_k; M = sum M_k          */
+  int N, B;           /* sources, NMF bases per source                          */
+  int precision;      /* dfmnmf_precision                                      */
+  int ip_arith;       /* dfmnmf_ip_arith                                       */
+  double floor_eps;   /* floor of yhat, MU denominators, IP normaliser (Sec. IV-A: 1e-6); <= 0 means 1e-6 */
+} dfmnmf_desc;
+
+/*
+ * Create a context and its state (Sec. III-B model, Eq. 2 and Eq. 3).
+ *   x       complex64 [F][T][M], host or device; copied, microphones of one
+ *           subarray contiguous (Sec. III-B).
+ *   W0      float32 [N][F][B] > 0, H0 float32 [N][B][T] > 0,
+ *   g0      float32 [F][N][M] > 0   (host or device; Sec. IV-A: strictly positive).
+ *   Q0      complex128 [F][sum_k M_k^2] (block k row-major M_k x M_k, blocks in
+ *           subarray order), host or device; NULL means identity blocks.
+ * On success *out owns all device state (about 8 F T M + 12 F T M + 16 F T N
+ * bytes); free it with dfmnmf_destroy.  EINVAL on a bad descriptor.
+ */
+int dfmnmf_init(dfmnmf_ctx** out, const dfmnmf_desc* desc, const void* x,
+                const float* W0, const float* H0, const float* g0, const void* Q0,
+                void* stream);
+
+/* Replace the observation x (same shape), host or device. */
+int dfmnmf_set_observation(dfmnmf_ctx* ctx, const void* x, void* stream);
+
+/*
+ * Run n_iter MM iterations (Sec. III-B: IP of every block by Eqs. 13-15 with
+ * rows mu in ascending order, then Eq. 8, Eq. 9, Eq. 10, the model refreshed
+ * after each rule).  Asynchronous; n_iter = 0 is a no-op; n_iter < 0 EINVAL.
+ */
+int dfmnmf_iterate(dfmnmf_ctx* ctx, int n_iter, void* stream);
+
+/* Stages of one iteration, for step-by-step checking.  Running the five in
+ * order equals one dfmnmf_iterate step. */
+typedef enum dfmnmf_stage {
+  DFMNMF_STAGE_COV = 1, /* yhat from the current model; V (Eq. 13)              */
+  DFMNMF_STAGE_IP = 2,  /* Q rows by Eqs. 14-15                                 */
+  DFMNMF_STAGE_W = 3,   /* P = |Q x|^2, W by Eq. 8, lambda refreshed           */
+  DFMNMF_STAGE_H = 4,   /* H by Eq. 9, lambda refreshed                         */
+  DFMNMF_STAGE_G = 5    /* g by Eq. 10                                          */
+} dfmnmf_stage;
+int dfmnmf_run_stage(dfmnmf_ctx* ctx, int stage, void* stream);
+
+/*
+ * Negative log-likelihood of Eq. (12) at the current state:
+ *   sum_{f,t,m} (P/yhat + ln yhat) - T sum_f sum_k ln |det Q_fk|^2
+ * (no F T M ln(pi) constant).  The data term is accumulated in FP64, the
+ * log-determinants by FP64 LU.  Synchronises `stream`.  ENUMERIC when a
+ * non-finite value was produced since init or the result is not finite.
+ */
+int dfmnmf_loglik(dfmnmf_ctx* ctx, double* nll_host, void* stream);
+
+/*
+ * Multichannel Wiener filter applied inside each subarray (Sec. III-B, last
+ * step): c_nft,(k) = Q_fk^{-1} diag(lambda_nft g_fn(o_k+mu) / yhat_ft(o_k+mu)) Q_fk x_ftk.
+ *   c_out   complex64 [N][F][T][M], device, caller-owned (8 N F T M bytes).
+ * Q_fk^{-1} is formed in FP64.
+ */
+int dfmnmf_separate(dfmnmf_ctx* ctx, void* c_out_dev, void* stream);
+
+/*
+ * Copy the state out / in (checkpoint and resume).  Any pointer may be NULL
+ * to skip that array; host or device.  Layouts as for dfmnmf_init; Q is
+ * complex128.  set_params refreshes lambda.  get_params synchronises `stream`
+ * when a destination is host memory.
+ */
+int dfmnmf_get_params(dfmnmf_ctx* ctx, void* Q, float* W, float* H, float* g, void* stream);
+int dfmnmf_set_params(dfmnmf_ctx* ctx, const void* Q, const float* W, const float* H,
+                      const float* g, void* stream);
+
+/* Intermediate buffers (for step-by-step checks), copied to host or device:
+ *   DFMNMF_BUF_V      complex64 [F][K][M_k][M_k][M_k]   (V[f][k][mu][a][b])
+ *   DFMNMF_BUF_P      float32   [F][T][M]
+ *   DFMNMF_BUF_LAMBDA float32   [N][F][T]
+ * Contents are those left by the last stage that wrote them. */
+typedef enum dfmnmf_buffer { DFMNMF_BUF_V = 1, DFMNMF_BUF_P = 2, DFMNMF_BUF_LAMBDA = 3 } dfmnmf_buffer;
+int dfmnmf_get_buffer(dfmnmf_ctx* ctx, int which, void* dst, size_t dst_bytes, void* stream);
+
+/* Number of kernel launches one dfmnmf_iterate step enqueues. */
+int dfmnmf_launches_per_iteration(const dfmnmf_ctx* ctx);
+
+/*
+ * Profiling aid: run n_iter >= 1 iterations launch by launch, with a CUDA
+ * event recorded on `stream` between consecutive kernels, and return the mean
+ * duration in milliseconds of each kernel of an iteration (avg_ms[i]) and its
+ * name (names[i], static strings; names may be NULL).  *count receives the
+ * number of kernels; cap is the capacity of both arrays (EINVAL if smaller).
+ * Advances the state by n_iter iterations.  Synchronises `stream`.
+ */
+int dfmnmf_kernel_times(dfmnmf_ctx* ctx, int n_iter, double* avg_ms, const char** names, int cap,
+                        int* count, void* stream);
+
+void dfmnmf_destroy(dfmnmf_ctx* ctx);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* dfmnmf_last_error(void);
+
+int dfmnmf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DFMNMF_H */

@@ -1,0 +1,378 @@
+// api.cu -- the C ABI of include/dfmnmf.h: argument checks, device state,
+// the iteration schedule and its CUDA graph.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+
+#include "../../include/dfmnmf.h"
+#include "common.cuh"
+#include "internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(DFMNMF_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+__global__ void k_identity_blocks(double2* Q, int F, int K, int MK) {
+  const size_t n = (size_t)F * K * MK * MK;
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int e = (int)(i % (size_t)(MK * MK));
+  Q[i] = make_double2((e / MK == e % MK) ? 1.0 : 0.0, 0.0);
+}
+
+void free_ctx(dfmnmf_ctx* c) {
+  if (!c) return;
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  void* ptrs[] = {c->x, c->Q64, c->Q32, c->Qinv32, c->V, c->W, c->H, c->g, c->lam,
+                  c->P, c->A, c->D, c->red, c->nll_dev, c->flags};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete c;
+}
+
+template <class T>
+int dalloc(T** p, size_t count, const char* what) {
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T) + 16);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(DFMNMF_ENOMEM, "cudaMalloc of %s (%zu bytes) failed: %s", what, count * sizeof(T),
+                cudaGetErrorString(e));
+  }
+  return DFMNMF_OK;
+}
+
+bool is_host_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
+}
+
+size_t nQ(const dfmnmf_ctx* c) { return (size_t)c->F * c->K * c->MK * c->MK; }
+size_t nW(const dfmnmf_ctx* c) { return (size_t)c->N * c->F * c->B; }
+size_t nH(const dfmnmf_ctx* c) { return (size_t)c->N * c->B * c->T; }
+size_t ng(const dfmnmf_ctx* c) { return (size_t)c->F * c->N * c->M; }
+size_t nx(const dfmnmf_ctx* c) { return (size_t)c->F * c->T * c->M; }
+
+// The launches of one iteration in order; stage s is the range of entries
+// with stage == s.
+struct Launch {
+  int stage;
+  const char* name;
+  cudaError_t (*fn)(const dfmnmf_ctx*, cudaStream_t);
+};
+
+int iteration_launches(const dfmnmf_ctx* c, Launch* out) {
+  int n = 0;
+  const bool fused = dfm::nmf_fused_lambda(c);
+  out[n++] = {DFMNMF_STAGE_COV, "k_cov", dfm::launch_cov};
+  out[n++] = {DFMNMF_STAGE_IP, "k_ip", dfm::launch_ip};
+  out[n++] = {DFMNMF_STAGE_W, "k_pstats", dfm::launch_power_stats};
+  out[n++] = {DFMNMF_STAGE_W, "k_wupd", dfm::launch_wupd};
+  if (!fused) out[n++] = {DFMNMF_STAGE_W, "k_lambda", dfm::launch_lambda};
+  out[n++] = {DFMNMF_STAGE_H, "k_stats", dfm::launch_stats};
+  out[n++] = {DFMNMF_STAGE_H, "k_hupd", dfm::launch_hupd};
+  if (!fused) out[n++] = {DFMNMF_STAGE_H, "k_lambda", dfm::launch_lambda};
+  out[n++] = {DFMNMF_STAGE_G, "k_gupd", dfm::launch_gupd};
+  return n;
+}
+constexpr int kMaxLaunches = 16;
+
+int enqueue_stage(dfmnmf_ctx* c, int stage, cudaStream_t s) {
+  if (stage < DFMNMF_STAGE_COV || stage > DFMNMF_STAGE_G) return fail(DFMNMF_EINVAL, "unknown stage %d", stage);
+  Launch L[kMaxLaunches];
+  const int n = iteration_launches(c, L);
+  for (int i = 0; i < n; ++i)
+    if (L[i].stage == stage) {
+      cudaError_t e = L[i].fn(c, s);
+      if (e != cudaSuccess) return fail(DFMNMF_ECUDA, "launch of %s failed: %s", L[i].name, cudaGetErrorString(e));
+    }
+  return DFMNMF_OK;
+}
+
+int enqueue_iteration(dfmnmf_ctx* c, cudaStream_t s) {
+  for (int st = DFMNMF_STAGE_COV; st <= DFMNMF_STAGE_G; ++st) {
+    int r = enqueue_stage(c, st, s);
+    if (r) return r;
+  }
+  return DFMNMF_OK;
+}
+
+int ensure_graph(dfmnmf_ctx* c) {
+  if (c->gexec) return DFMNMF_OK;
+  CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  int r = enqueue_iteration(c, c->cap_stream);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+  if (r) {
+    if (graph) cudaGraphDestroy(graph);
+    return r;
+  }
+  if (e != cudaSuccess) return fail(DFMNMF_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+  c->graph = graph;
+  CK(cudaGraphInstantiate(&c->gexec, c->graph, 0));
+  size_t nodes = 0;
+  CK(cudaGraphGetNodes(c->graph, nullptr, &nodes));
+  c->launches_per_iter = (int)nodes;
+  return DFMNMF_OK;
+}
+
+int refresh_derived(dfmnmf_ctx* c, cudaStream_t s) {
+  CK(dfm::launch_lambda(c, s));
+  CK(dfm::launch_q_convert(c, s));
+  return DFMNMF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dfmnmf_version(void) { return DFMNMF_VERSION; }
+
+const char* dfmnmf_last_error(void) { return g_last_error.c_str(); }
+
+int dfmnmf_init(dfmnmf_ctx** out, const dfmnmf_desc* d, const void* x, const float* W0, const float* H0,
+                const float* g0, const void* Q0, void* stream) {
+  g_last_error.clear();
+  if (!out || !d) return fail(DFMNMF_EINVAL, "null context or descriptor");
+  *out = nullptr;
+  if (!x || !W0 || !H0 || !g0) return fail(DFMNMF_EINVAL, "x, W0, H0 and g0 are required");
+  if (d->F < 1 || d->T < 1 || d->K < 1 || d->N < 1 || d->B < 1)
+    return fail(DFMNMF_EINVAL, "sizes must be positive (F=%d T=%d K=%d N=%d B=%d)", d->F, d->T, d->K, d->N, d->B);
+  if (d->F > 65535) return fail(DFMNMF_EINVAL, "F=%d exceeds 65535", d->F);
+  if (d->K > 16 || d->N > 16 || d->B > 64)
+    return fail(DFMNMF_EINVAL, "limits: K <= 16, N <= 16, B <= 64 (K=%d N=%d B=%d)", d->K, d->N, d->B);
+  if (!d->mics) return fail(DFMNMF_EINVAL, "mics is NULL");
+  const int MK = d->mics[0];
+  for (int k = 0; k < d->K; ++k) {
+    if (d->mics[k] < 1) return fail(DFMNMF_EINVAL, "mics[%d]=%d must be positive", k, d->mics[k]);
+    if (d->mics[k] != MK)
+      return fail(DFMNMF_EINVAL, "this release needs equal subarray sizes (mics[0]=%d, mics[%d]=%d)", MK, k,
+                  d->mics[k]);
+  }
+  if (MK > 4) return fail(DFMNMF_EINVAL, "subarray size M_k=%d exceeds 4", MK);
+  if (d->precision != DFMNMF_FP32)
+    return fail(DFMNMF_EINVAL, "precision %d is not built in this release", d->precision);
+  if (d->ip_arith < 0 || d->ip_arith > 2) return fail(DFMNMF_EINVAL, "unknown ip_arith %d", d->ip_arith);
+
+  dfmnmf_ctx* c = new dfmnmf_ctx;
+  memset(c, 0, sizeof *c);
+  c->F = d->F; c->T = d->T; c->K = d->K; c->MK = MK; c->M = d->K * MK; c->N = d->N; c->B = d->B;
+  c->precision = d->precision;
+  c->ip_arith = d->ip_arith;
+  c->eps = (float)(d->floor_eps > 0 ? d->floor_eps : 1e-6);
+  c->singular_rtol = 1e-6f;
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return fail(DFMNMF_ECUDA, "no CUDA device");
+  }
+  int r = 0;
+  const int ty = (c->T + 127) / 128;
+  c->red_len = (size_t)c->F * ty + (size_t)c->F * c->K;
+  if ((r = dalloc(&c->x, nx(c), "x")) || (r = dalloc(&c->Q64, nQ(c), "Q64")) ||
+      (r = dalloc(&c->Q32, nQ(c), "Q32")) || (r = dalloc(&c->Qinv32, nQ(c), "Qinv")) ||
+      (r = dalloc(&c->V, nQ(c) * MK, "V")) || (r = dalloc(&c->W, nW(c), "W")) ||
+      (r = dalloc(&c->H, nH(c), "H")) || (r = dalloc(&c->g, ng(c), "g")) ||
+      (r = dalloc(&c->lam, (size_t)c->N * c->F * c->T, "lambda")) || (r = dalloc(&c->P, nx(c), "P")) ||
+      (r = dalloc(&c->A, (size_t)c->N * c->F * c->T, "A")) ||
+      (r = dalloc(&c->D, (size_t)c->N * c->F * c->T, "D")) || (r = dalloc(&c->red, c->red_len, "red")) ||
+      (r = dalloc(&c->nll_dev, 1, "nll")) || (r = dalloc(&c->flags, dfm::FLAG_COUNT, "flags"))) {
+    free_ctx(c);
+    return r;
+  }
+  cudaStream_t s = as_stream(stream);
+  auto bail = [&](int code) { free_ctx(c); return code; };
+  if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(fail(DFMNMF_ECUDA, "stream creation failed"));
+#define CKI(call)                                                                                        \
+  do {                                                                                                   \
+    cudaError_t e_ = (call);                                                                             \
+    if (e_ != cudaSuccess) return bail(fail(DFMNMF_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_))); \
+  } while (0)
+  CKI(cudaMemcpyAsync(c->x, x, nx(c) * sizeof(float2), cudaMemcpyDefault, s));
+  CKI(cudaMemcpyAsync(c->W, W0, nW(c) * sizeof(float), cudaMemcpyDefault, s));
+  CKI(cudaMemcpyAsync(c->H, H0, nH(c) * sizeof(float), cudaMemcpyDefault, s));
+  CKI(cudaMemcpyAsync(c->g, g0, ng(c) * sizeof(float), cudaMemcpyDefault, s));
+  if (Q0) {
+    CKI(cudaMemcpyAsync(c->Q64, Q0, nQ(c) * sizeof(double2), cudaMemcpyDefault, s));
+  } else {
+    k_identity_blocks<<<(unsigned)((nQ(c) + 255) / 256), 256, 0, s>>>(c->Q64, c->F, c->K, MK);
+    CKI(cudaGetLastError());
+  }
+  CKI(cudaMemsetAsync(c->flags, 0, dfm::FLAG_COUNT * sizeof(unsigned), s));
+  CKI(cudaMemsetAsync(c->P, 0, nx(c) * sizeof(float), s));
+  if ((r = refresh_derived(c, s))) return bail(r);
+#undef CKI
+  *out = c;
+  return DFMNMF_OK;
+}
+
+int dfmnmf_set_observation(dfmnmf_ctx* c, const void* x, void* stream) {
+  if (!c || !x) return fail(DFMNMF_EINVAL, "null argument");
+  CK(cudaSetDevice(c->device));
+  CK(cudaMemcpyAsync(c->x, x, nx(c) * sizeof(float2), cudaMemcpyDefault, as_stream(stream)));
+  return DFMNMF_OK;
+}
+
+int dfmnmf_iterate(dfmnmf_ctx* c, int n_iter, void* stream) {
+  if (!c) return fail(DFMNMF_EINVAL, "null context");
+  if (n_iter < 0) return fail(DFMNMF_EINVAL, "n_iter=%d is negative", n_iter);
+  if (n_iter == 0) return DFMNMF_OK;
+  CK(cudaSetDevice(c->device));
+  int r = ensure_graph(c);
+  if (r) return r;
+  for (int i = 0; i < n_iter; ++i) CK(cudaGraphLaunch(c->gexec, as_stream(stream)));
+  return DFMNMF_OK;
+}
+
+int dfmnmf_run_stage(dfmnmf_ctx* c, int stage, void* stream) {
+  if (!c) return fail(DFMNMF_EINVAL, "null context");
+  if (stage < DFMNMF_STAGE_COV || stage > DFMNMF_STAGE_G) return fail(DFMNMF_EINVAL, "unknown stage %d", stage);
+  CK(cudaSetDevice(c->device));
+  return enqueue_stage(c, stage, as_stream(stream));
+}
+
+int dfmnmf_launches_per_iteration(const dfmnmf_ctx* c) {
+  if (!c) return -1;
+  Launch L[kMaxLaunches];
+  return iteration_launches(c, L);
+}
+
+int dfmnmf_kernel_times(dfmnmf_ctx* c, int n_iter, double* avg_ms, const char** names, int cap, int* count,
+                        void* stream) {
+  if (!c || !avg_ms || !count || n_iter < 1) return fail(DFMNMF_EINVAL, "bad argument");
+  CK(cudaSetDevice(c->device));
+  Launch L[kMaxLaunches];
+  const int n = iteration_launches(c, L);
+  *count = n;
+  if (cap < n) return fail(DFMNMF_EINVAL, "capacity %d < %d kernels", cap, n);
+  cudaStream_t s = as_stream(stream);
+  cudaEvent_t ev[kMaxLaunches + 1];
+  for (int i = 0; i <= n; ++i) CK(cudaEventCreate(&ev[i]));
+  for (int i = 0; i < n; ++i) avg_ms[i] = 0.0;
+  int rc = DFMNMF_OK;
+  for (int it = 0; it < n_iter && rc == DFMNMF_OK; ++it) {
+    cudaEventRecord(ev[0], s);
+    for (int i = 0; i < n; ++i) {
+      cudaError_t e = L[i].fn(c, s);
+      if (e != cudaSuccess) { rc = fail(DFMNMF_ECUDA, "%s: %s", L[i].name, cudaGetErrorString(e)); break; }
+      cudaEventRecord(ev[i + 1], s);
+    }
+    if (rc) break;
+    if (cudaEventSynchronize(ev[n]) != cudaSuccess) { rc = fail(DFMNMF_ECUDA, "event sync failed"); break; }
+    for (int i = 0; i < n; ++i) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+      avg_ms[i] += ms / n_iter;
+    }
+  }
+  for (int i = 0; i <= n; ++i) cudaEventDestroy(ev[i]);
+  if (names)
+    for (int i = 0; i < n; ++i) names[i] = L[i].name;
+  return rc;
+}
+
+int dfmnmf_loglik(dfmnmf_ctx* c, double* nll_host, void* stream) {
+  if (!c || !nll_host) return fail(DFMNMF_EINVAL, "null argument");
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = as_stream(stream);
+  CK(dfm::launch_loglik(c, s));
+  unsigned flags[dfm::FLAG_COUNT];
+  double v = 0.0;
+  CK(cudaMemcpyAsync(&v, c->nll_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(flags, c->flags, sizeof flags, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  *nll_host = v;
+  if (flags[dfm::FLAG_NONFINITE]) return fail(DFMNMF_ENUMERIC, "a non-finite value was produced (flags=%u)",
+                                              flags[dfm::FLAG_NONFINITE]);
+  return DFMNMF_OK;
+}
+
+int dfmnmf_separate(dfmnmf_ctx* c, void* c_out, void* stream) {
+  if (!c || !c_out) return fail(DFMNMF_EINVAL, "null argument");
+  if (is_host_ptr(c_out)) return fail(DFMNMF_EINVAL, "c_out must be device memory");
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = as_stream(stream);
+  CK(dfm::launch_qinv(c, s));
+  CK(dfm::launch_separate(c, reinterpret_cast<float2*>(c_out), s));
+  return DFMNMF_OK;
+}
+
+int dfmnmf_get_params(dfmnmf_ctx* c, void* Q, float* W, float* H, float* g, void* stream) {
+  if (!c) return fail(DFMNMF_EINVAL, "null context");
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = as_stream(stream);
+  bool host = false;
+  if (Q) { CK(cudaMemcpyAsync(Q, c->Q64, nQ(c) * sizeof(double2), cudaMemcpyDefault, s)); host |= is_host_ptr(Q); }
+  if (W) { CK(cudaMemcpyAsync(W, c->W, nW(c) * sizeof(float), cudaMemcpyDefault, s)); host |= is_host_ptr(W); }
+  if (H) { CK(cudaMemcpyAsync(H, c->H, nH(c) * sizeof(float), cudaMemcpyDefault, s)); host |= is_host_ptr(H); }
+  if (g) { CK(cudaMemcpyAsync(g, c->g, ng(c) * sizeof(float), cudaMemcpyDefault, s)); host |= is_host_ptr(g); }
+  if (host) CK(cudaStreamSynchronize(s));
+  return DFMNMF_OK;
+}
+
+int dfmnmf_set_params(dfmnmf_ctx* c, const void* Q, const float* W, const float* H, const float* g,
+                      void* stream) {
+  if (!c) return fail(DFMNMF_EINVAL, "null context");
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = as_stream(stream);
+  if (Q) CK(cudaMemcpyAsync(c->Q64, Q, nQ(c) * sizeof(double2), cudaMemcpyDefault, s));
+  if (W) CK(cudaMemcpyAsync(c->W, W, nW(c) * sizeof(float), cudaMemcpyDefault, s));
+  if (H) CK(cudaMemcpyAsync(c->H, H, nH(c) * sizeof(float), cudaMemcpyDefault, s));
+  if (g) CK(cudaMemcpyAsync(c->g, g, ng(c) * sizeof(float), cudaMemcpyDefault, s));
+  return refresh_derived(c, s);
+}
+
+int dfmnmf_get_buffer(dfmnmf_ctx* c, int which, void* dst, size_t dst_bytes, void* stream) {
+  if (!c || !dst) return fail(DFMNMF_EINVAL, "null argument");
+  const void* src = nullptr;
+  size_t bytes = 0;
+  switch (which) {
+    case DFMNMF_BUF_V: src = c->V; bytes = nQ(c) * c->MK * sizeof(float2); break;
+    case DFMNMF_BUF_P: src = c->P; bytes = nx(c) * sizeof(float); break;
+    case DFMNMF_BUF_LAMBDA: src = c->lam; bytes = (size_t)c->N * c->F * c->T * sizeof(float); break;
+    default: return fail(DFMNMF_EINVAL, "unknown buffer %d", which);
+  }
+  if (dst_bytes < bytes) return fail(DFMNMF_EINVAL, "buffer %d needs %zu bytes, got %zu", which, bytes, dst_bytes);
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = as_stream(stream);
+  CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
+  if (is_host_ptr(dst)) CK(cudaStreamSynchronize(s));
+  return DFMNMF_OK;
+}
+
+void dfmnmf_destroy(dfmnmf_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  free_ctx(c);
+}
+
+}  // extern "C"

@@ -1,0 +1,332 @@
+// kernels_ip.cu -- iterative projection of the diagonaliser blocks
+// (Eqs. 14-15) and the small dense FP64 block kernels (log-determinant,
+// inverse, precision conversion).
+//
+// Layout of the IP kernel: one diagonaliser block Q_fk (M_k <= 4) per
+// 16-lane half warp, one matrix element per lane (lane e -> row e / M_k,
+// column e % M_k).  For each mu in ascending order the half warp
+//   1. forms A = Q_fk V_fk,mu (each lane one entry, M_k complex FMAs),
+//   2. solves A q = e_mu by Gauss-Jordan elimination with partial pivoting,
+//      exchanging rows and pivots through warp shuffles,
+//   3. normalises q <- q / sqrt(max(Re q^H V q, eps)) (Eq. 15) and writes
+//      row mu of Q_fk = q^H.
+// Gauss-Jordan with partial pivoting selects the same pivots as Gaussian
+// elimination with partial pivoting, so the singularity test (smallest
+// |pivot| <= rtol * max|A_ij|) is the one of Sec. IV-A's pseudo-inverse rule;
+// a singular system is solved with the SVD pseudo-inverse (one-sided Jacobi,
+// FP64, one lane), which is the rare path.
+//
+// The arithmetic type R is a template parameter: IEEE double, float-float
+// pairs (dfm::dd) or float.
+#include "common.cuh"
+#include "internal.h"
+
+namespace dfm {
+
+// q = pinv(A) e_mu by one-sided (Hestenes) Jacobi on the columns of A.
+// Singular values <= rtol * s_max are dropped.  One thread, FP64.
+template <int MK>
+__device__ void pinv_column(cx<double> (&U)[MK][MK], int mu, double rtol, cx<double> (&q)[MK]) {
+  cx<double> Vm[MK][MK];
+#pragma unroll
+  for (int r = 0; r < MK; ++r)
+#pragma unroll
+    for (int c = 0; c < MK; ++c) Vm[r][c] = cmake(r == c ? 1.0 : 0.0, 0.0);
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < MK; ++p)
+      for (int qq = p + 1; qq < MK; ++qq) {
+        double al = 0.0, be = 0.0, gr = 0.0, gi = 0.0;
+        for (int r = 0; r < MK; ++r) {
+          al += U[r][p].re * U[r][p].re + U[r][p].im * U[r][p].im;
+          be += U[r][qq].re * U[r][qq].re + U[r][qq].im * U[r][qq].im;
+          gr += U[r][p].re * U[r][qq].re + U[r][p].im * U[r][qq].im;  // conj(u_p) u_q
+          gi += U[r][p].re * U[r][qq].im - U[r][p].im * U[r][qq].re;
+        }
+        const double gm = sqrt(gr * gr + gi * gi);
+        const double nrm = sqrt(al * be);
+        if (!(gm > 1e-300) || !(gm > 1e-15 * nrm)) continue;
+        off = fmax(off, gm / nrm);
+        const double pr = gr / gm, pi = -gi / gm;  // conj(gamma / |gamma|)
+        const double zeta = (be - al) / (2.0 * gm);
+        const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
+        for (int r = 0; r < MK; ++r) {
+          cx<double> up = U[r][p], uq = U[r][qq];
+          cx<double> uq2 = cmake(uq.re * pr - uq.im * pi, uq.re * pi + uq.im * pr);
+          U[r][p] = cmake(cs * up.re - sn * uq2.re, cs * up.im - sn * uq2.im);
+          U[r][qq] = cmake(sn * up.re + cs * uq2.re, sn * up.im + cs * uq2.im);
+          cx<double> vp = Vm[r][p], vq = Vm[r][qq];
+          cx<double> vq2 = cmake(vq.re * pr - vq.im * pi, vq.re * pi + vq.im * pr);
+          Vm[r][p] = cmake(cs * vp.re - sn * vq2.re, cs * vp.im - sn * vq2.im);
+          Vm[r][qq] = cmake(sn * vp.re + cs * vq2.re, sn * vp.im + cs * vq2.im);
+        }
+      }
+    if (off < 1e-15) break;
+  }
+  double sig2[MK], smax2 = 0.0;
+  for (int c = 0; c < MK; ++c) {
+    double s = 0.0;
+    for (int r = 0; r < MK; ++r) s += U[r][c].re * U[r][c].re + U[r][c].im * U[r][c].im;
+    sig2[c] = s;
+    smax2 = fmax(smax2, s);
+  }
+  for (int r = 0; r < MK; ++r) q[r] = cmake(0.0, 0.0);
+  for (int c = 0; c < MK; ++c) {
+    if (!(sig2[c] > rtol * rtol * smax2) || !(sig2[c] > 0.0)) continue;
+    // coefficient conj(U[mu][c]) / sigma_c^2
+    const double cr = U[mu][c].re / sig2[c], ci = -U[mu][c].im / sig2[c];
+    for (int r = 0; r < MK; ++r) {
+      q[r].re += Vm[r][c].re * cr - Vm[r][c].im * ci;
+      q[r].im += Vm[r][c].re * ci + Vm[r][c].im * cr;
+    }
+  }
+}
+
+template <int MK, class R>
+__global__ void __launch_bounds__(128) k_ip(const float2* __restrict__ V, double2* __restrict__ Q64,
+                                            float2* __restrict__ Q32, int nblocks, float eps, float rtol,
+                                            unsigned* __restrict__ flags) {
+  using O = RealOps<R>;
+  constexpr int E = MK * MK;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int seg = lane >> 4, e = lane & 15, sb = seg << 4;
+  const bool act = e < E;
+  const int i = act ? e / MK : 0, j = act ? e % MK : 0;
+  const int blk = (blockIdx.x * 4 + warp) * 2 + seg;
+  const bool valid = blk < nblocks;
+  const unsigned segmask = 0xffffu << sb;
+  __shared__ cx<R> Qs[4][2][E];
+  __shared__ cx<double> qfb[4][2][MK];
+  cx<R>* Qb = Qs[warp][seg];
+  if (act) {
+    if (valid) Qb[e] = cfrom_d2<R>(Q64[(size_t)blk * E + e]);
+    else Qb[e] = cmake(i == j ? O::one() : O::zero(), O::zero());
+  }
+  __syncwarp();
+  const float2* Vb = V + (size_t)(valid ? blk : 0) * E * MK;
+  auto L = [&](int r, int c) { return sb + r * MK + c; };
+
+  for (int mu = 0; mu < MK; ++mu) {
+    // 1. A = Q V_mu (lane (i, j)) and V_mu[i][j]
+    cx<R> a = czero<R>(), vij = czero<R>();
+#pragma unroll
+    for (int l = 0; l < MK; ++l) {
+      const cx<R> vlj = cfrom_f2<R>(Vb[mu * E + l * MK + j]);
+      a = cadd(a, cmul(Qb[i * MK + l], vlj));
+      if (l == i) vij = vlj;
+    }
+    float maxabs = act ? sqrtf(cabs2_f(a)) : 0.f;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) maxabs = fmaxf(maxabs, __shfl_xor_sync(DFM_FULL_MASK, maxabs, o));
+    cx<R> b = (act && i == mu) ? cmake(O::one(), O::zero()) : czero<R>();
+    float minpiv = INFINITY;
+    // 2. Gauss-Jordan with partial pivoting
+#pragma unroll
+    for (int c = 0; c < MK; ++c) {
+      float key = (act && j == c && i >= c) ? cabs2_f(a) : -1.f;
+      int prow = i;
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) {
+        const float ok = __shfl_xor_sync(DFM_FULL_MASK, key, o);
+        const int orow = __shfl_xor_sync(DFM_FULL_MASK, prow, o);
+        if (ok > key || (ok == key && orow < prow)) {
+          key = ok;
+          prow = orow;
+        }
+      }
+      int src = lane;
+      if (act && i == c) src = L(prow, j);
+      else if (act && i == prow) src = L(c, j);
+      a = cshfl(a, src);
+      b = cshfl(b, src);
+      const cx<R> piv = cshfl(a, L(c, c));
+      minpiv = fminf(minpiv, sqrtf(cabs2_f(piv)));
+      const cx<R> inv = crecip(piv);
+      const cx<R> rowc = cmul(cshfl(a, L(c, j)), inv);
+      const cx<R> bc = cmul(cshfl(b, L(c, 0)), inv);
+      const cx<R> m = cshfl(a, L(i, c));
+      if (i == c) {
+        a = rowc;
+        b = bc;
+      } else {
+        a = csub(a, cmul(m, rowc));
+        b = csub(b, cmul(m, bc));
+      }
+    }
+    const bool singular = !(minpiv > rtol * maxabs);
+    cx<R> qi = b;
+    if (singular) {
+      if (e == 0 && valid) {
+        cx<double> U[MK][MK], q[MK];
+        for (int r = 0; r < MK; ++r)
+          for (int c = 0; c < MK; ++c) {
+            double sr = 0.0, si = 0.0;
+            for (int l = 0; l < MK; ++l) {
+              const cx<R> qrl = Qb[r * MK + l];
+              const double qr = O::to_d(qrl.re), qim = O::to_d(qrl.im);
+              const float2 v = Vb[mu * E + l * MK + c];
+              sr += qr * (double)v.x - qim * (double)v.y;
+              si += qr * (double)v.y + qim * (double)v.x;
+            }
+            U[r][c] = cmake(sr, si);
+          }
+        pinv_column<MK>(U, mu, (double)rtol, q);
+        for (int r = 0; r < MK; ++r) qfb[warp][seg][r] = q[r];
+        atomicAdd(flags + FLAG_PINV, 1u);
+      }
+      __syncwarp(segmask);
+      qi = cfrom_d2<R>(make_double2(qfb[warp][seg][i].re, qfb[warp][seg][i].im));
+    }
+    // 3. normalisation (Eq. 15) and row update
+    const cx<R> qj = cshfl(qi, L(j, 0));
+    R term = O::zero();
+    if (act) {
+      const cx<R> vq = cmul(vij, qj);
+      term = O::add(O::mul(qi.re, vq.re), O::mul(qi.im, vq.im));  // Re(conj(q_i) V_ij q_j)
+    }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) term = O::add(term, O::shfl_xor(term, o));
+    R s = term;
+    if (!(O::to_f(s) > eps)) s = O::from_f(eps);
+    const R rs = O::div(O::one(), O::sqrt_(s));
+    __syncwarp();
+    if (act && i == mu) Qb[mu * MK + j] = cscale(cconj(qj), rs);
+    __syncwarp();
+  }
+  if (act && valid) {
+    const cx<R> v = Qb[e];
+    const double re = O::to_d(v.re), im = O::to_d(v.im);
+    if (!isfinite(re) || !isfinite(im)) atomicOr(flags + FLAG_NONFINITE, 1u);
+    Q64[(size_t)blk * E + e] = make_double2(re, im);
+    Q32[(size_t)blk * E + e] = make_float2((float)re, (float)im);
+  }
+}
+
+// ln |det Q_fk|^2 by FP64 Gaussian elimination with partial pivoting, one
+// thread per block.
+template <int MK>
+__global__ void k_logdet(const double2* __restrict__ Q64, double* __restrict__ out, int nblocks) {
+  const int blk = blockIdx.x * blockDim.x + threadIdx.x;
+  if (blk >= nblocks) return;
+  double ar[MK][MK], ai[MK][MK];
+  for (int r = 0; r < MK; ++r)
+    for (int c = 0; c < MK; ++c) {
+      const double2 v = Q64[(size_t)blk * MK * MK + r * MK + c];
+      ar[r][c] = v.x;
+      ai[r][c] = v.y;
+    }
+  double acc = 0.0;
+  for (int c = 0; c < MK; ++c) {
+    int p = c;
+    double best = ar[c][c] * ar[c][c] + ai[c][c] * ai[c][c];
+    for (int r = c + 1; r < MK; ++r) {
+      const double m = ar[r][c] * ar[r][c] + ai[r][c] * ai[r][c];
+      if (m > best) { best = m; p = r; }
+    }
+    if (p != c)
+      for (int q = 0; q < MK; ++q) {
+        double t = ar[c][q]; ar[c][q] = ar[p][q]; ar[p][q] = t;
+        t = ai[c][q]; ai[c][q] = ai[p][q]; ai[p][q] = t;
+      }
+    acc += log(best);
+    if (!(best > 0.0)) continue;
+    for (int r = c + 1; r < MK; ++r) {
+      // m = a[r][c] / a[c][c]
+      const double mr = (ar[r][c] * ar[c][c] + ai[r][c] * ai[c][c]) / best;
+      const double mi = (ai[r][c] * ar[c][c] - ar[r][c] * ai[c][c]) / best;
+      for (int q = c; q < MK; ++q) {
+        ar[r][q] -= mr * ar[c][q] - mi * ai[c][q];
+        ai[r][q] -= mr * ai[c][q] + mi * ar[c][q];
+      }
+    }
+  }
+  out[blk] = acc;
+}
+
+// Q_fk^{-1} by FP64 Gauss-Jordan with partial pivoting, one thread per block.
+template <int MK>
+__global__ void k_qinv(const double2* __restrict__ Q64, float2* __restrict__ Qinv, int nblocks,
+                       unsigned* __restrict__ flags) {
+  const int blk = blockIdx.x * blockDim.x + threadIdx.x;
+  if (blk >= nblocks) return;
+  double ar[MK][2 * MK], ai[MK][2 * MK];
+  for (int r = 0; r < MK; ++r)
+    for (int c = 0; c < MK; ++c) {
+      const double2 v = Q64[(size_t)blk * MK * MK + r * MK + c];
+      ar[r][c] = v.x;
+      ai[r][c] = v.y;
+      ar[r][MK + c] = (r == c) ? 1.0 : 0.0;
+      ai[r][MK + c] = 0.0;
+    }
+  for (int c = 0; c < MK; ++c) {
+    int p = c;
+    double best = ar[c][c] * ar[c][c] + ai[c][c] * ai[c][c];
+    for (int r = c + 1; r < MK; ++r) {
+      const double m = ar[r][c] * ar[r][c] + ai[r][c] * ai[r][c];
+      if (m > best) { best = m; p = r; }
+    }
+    if (!(best > 0.0)) { atomicOr(flags + FLAG_NONFINITE, 1u); best = 1.0; }
+    if (p != c)
+      for (int q = 0; q < 2 * MK; ++q) {
+        double t = ar[c][q]; ar[c][q] = ar[p][q]; ar[p][q] = t;
+        t = ai[c][q]; ai[c][q] = ai[p][q]; ai[p][q] = t;
+      }
+    const double ir = ar[c][c] / best, ii = -ai[c][c] / best;  // 1 / pivot
+    for (int q = 0; q < 2 * MK; ++q) {
+      const double xr = ar[c][q], xi = ai[c][q];
+      ar[c][q] = xr * ir - xi * ii;
+      ai[c][q] = xr * ii + xi * ir;
+    }
+    for (int r = 0; r < MK; ++r) {
+      if (r == c) continue;
+      const double mr = ar[r][c], mi = ai[r][c];
+      for (int q = 0; q < 2 * MK; ++q) {
+        ar[r][q] -= mr * ar[c][q] - mi * ai[c][q];
+        ai[r][q] -= mr * ai[c][q] + mi * ar[c][q];
+      }
+    }
+  }
+  for (int r = 0; r < MK; ++r)
+    for (int c = 0; c < MK; ++c)
+      Qinv[(size_t)blk * MK * MK + r * MK + c] = make_float2((float)ar[r][MK + c], (float)ai[r][MK + c]);
+}
+
+__global__ void k_q32(const double2* __restrict__ Q64, float2* __restrict__ Q32, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) Q32[i] = make_float2((float)Q64[i].x, (float)Q64[i].y);
+}
+
+
+cudaError_t launch_ip(const dfmnmf_ctx* c, cudaStream_t s) {
+  const int nblocks = c->F * c->K;
+  const int grid = (nblocks + 7) / 8;  // 4 warps x 2 blocks per CTA
+  DFM_MK_DISPATCH(c->MK, {
+    switch (c->ip_arith) {
+      case 0: k_ip<MK_, double><<<grid, 128, 0, s>>>(c->V, c->Q64, c->Q32, nblocks, c->eps, c->singular_rtol, c->flags); break;
+      case 1: k_ip<MK_, dd><<<grid, 128, 0, s>>>(c->V, c->Q64, c->Q32, nblocks, c->eps, c->singular_rtol, c->flags); break;
+      default: k_ip<MK_, float><<<grid, 128, 0, s>>>(c->V, c->Q64, c->Q32, nblocks, c->eps, c->singular_rtol, c->flags); break;
+    }
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_logdet(const dfmnmf_ctx* c, double* out, cudaStream_t s) {
+  const int nblocks = c->F * c->K;
+  DFM_MK_DISPATCH(c->MK, { k_logdet<MK_><<<(nblocks + 127) / 128, 128, 0, s>>>(c->Q64, out, nblocks); });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_qinv(const dfmnmf_ctx* c, cudaStream_t s) {
+  const int nblocks = c->F * c->K;
+  DFM_MK_DISPATCH(c->MK, { k_qinv<MK_><<<(nblocks + 127) / 128, 128, 0, s>>>(c->Q64, c->Qinv32, nblocks, c->flags); });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_q_convert(const dfmnmf_ctx* c, cudaStream_t s) {
+  const size_t n = (size_t)c->F * c->K * c->MK * c->MK;
+  k_q32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c->Q64, c->Q32, n);
+  return cudaGetLastError();
+}
+
+}  // namespace dfm

@@ -1,0 +1,72 @@
+"""The C-ABI library loads, exports every symbol include/dfmnmf.h declares,
+and rejects bad descriptors on the host (no GPU needed for these paths)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2605_19388_gb300 import build as B
+from paper_2605_19388_gb300 import dfmnmf as D
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return D.load_library()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "dfmnmf.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dfmnmf_[a-z_]+)\s*\(", text)))
+
+
+def test_header_symbols_exported(lib):
+    syms = declared_symbols()
+    assert len(syms) >= 12
+    for s in syms:
+        assert hasattr(lib, s), s
+    assert set(syms) == set(D.EXPORTED)
+
+
+def test_version(lib):
+    assert D.dfmnmf_version() == 100
+
+
+def _args(F=3, T=4, mics=(4, 4), N=2, B_=3):
+    M = sum(mics)
+    return dict(F=F, T=T, mics=mics, N=N, B=B_, x=np.zeros((F, T, M), np.complex64),
+                W0=np.ones((N, F, B_), np.float32), H0=np.ones((N, B_, T), np.float32),
+                g0=np.ones((F, N, M), np.float32))
+
+
+@pytest.mark.parametrize("bad", [dict(F=0), dict(T=0), dict(N=0), dict(B_=0), dict(mics=(4, 3)),
+                                 dict(mics=(5,)), dict(mics=(0,)), dict(N=17), dict(B_=65),
+                                 dict(mics=(1,) * 17)])
+def test_invalid_descriptor_rejected(lib, bad):
+    a = _args(**bad)
+    with pytest.raises(D.DfmnmfError) as ei:
+        D.dfmnmf_init(a["F"], a["T"], a["mics"], a["N"], a["B"], a["x"], a["W0"], a["H0"], a["g0"])
+    assert ei.value.code == D.DFMNMF_EINVAL
+
+
+def test_unknown_precision_rejected(lib):
+    a = _args()
+    for kw in (dict(precision=7), dict(ip_arith=9)):
+        with pytest.raises(D.DfmnmfError) as ei:
+            D.dfmnmf_init(a["F"], a["T"], a["mics"], a["N"], a["B"], a["x"], a["W0"], a["H0"], a["g0"], **kw)
+        assert ei.value.code == D.DFMNMF_EINVAL
+
+
+def test_null_arguments_rejected(lib):
+    import ctypes
+    assert lib.dfmnmf_iterate(None, 1, None) == D.DFMNMF_EINVAL
+    assert lib.dfmnmf_loglik(None, None, None) == D.DFMNMF_EINVAL
+    assert lib.dfmnmf_run_stage(None, 1, None) == D.DFMNMF_EINVAL
+    assert lib.dfmnmf_init(None, None, None, None, None, None, None, None) == D.DFMNMF_EINVAL
+    assert b"null" in lib.dfmnmf_last_error()
+    lib.dfmnmf_destroy(None)
+    assert lib.dfmnmf_launches_per_iteration(None) == -1
