@@ -156,7 +156,7 @@ int dfmnmf_set_params(dfmnmf_ctx* ctx, const void* Q, const float* W, const floa
                       const float* g, void* stream);
 
 /* Intermediate buffers (for step-by-step checks), copied to host or device:
- *   DFMNMF_BUF_V      complex64 [F][K][M_k][M_k][M_k]   (V[f][k][mu][a][b])
+ *   DFMNMF_BUF_V      complex128 [F][K][M_k][M_k][M_k]  (V[f][k][mu][a][b])
  *   DFMNMF_BUF_P      float32   [F][T][M]
  *   DFMNMF_BUF_LAMBDA float32   [N][F][T]
  * Contents are those left by the last stage that wrote them. */

@@ -187,7 +187,7 @@ int dfmnmf_init(dfmnmf_ctx** out, const dfmnmf_desc* d, const void* x, const flo
   c->precision = d->precision;
   c->ip_arith = d->ip_arith;
   c->eps = (float)(d->floor_eps > 0 ? d->floor_eps : 1e-6);
-  c->singular_rtol = 1e-6f;
+  c->singular_rtol = (d->ip_arith == DFMNMF_IP_F32) ? 1e-6f : 1e-12f;
   if (cudaGetDevice(&c->device) != cudaSuccess) {
     cudaGetLastError();
     delete c;
@@ -355,7 +355,7 @@ int dfmnmf_get_buffer(dfmnmf_ctx* c, int which, void* dst, size_t dst_bytes, voi
   const void* src = nullptr;
   size_t bytes = 0;
   switch (which) {
-    case DFMNMF_BUF_V: src = c->V; bytes = nQ(c) * c->MK * sizeof(float2); break;
+    case DFMNMF_BUF_V: src = c->V; bytes = nQ(c) * c->MK * sizeof(double2); break;
     case DFMNMF_BUF_P: src = c->P; bytes = nx(c) * sizeof(float); break;
     case DFMNMF_BUF_LAMBDA: src = c->lam; bytes = (size_t)c->N * c->F * c->T * sizeof(float); break;
     default: return fail(DFMNMF_EINVAL, "unknown buffer %d", which);

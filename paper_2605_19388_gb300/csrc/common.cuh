@@ -215,6 +215,64 @@ __device__ __forceinline__ void warp_reduce_scatter(float (&v)[C], int lane) {
 
 __device__ __forceinline__ bool finitef(float v) { return isfinite(v); }
 
+// Compensated complex dot product y = sum_nu q_nu x_nu with q = qh + ql a
+// float pair (the FP64 diagonaliser row split in two floats) and x single
+// precision: every product qh * x is exact (Dekker), the running sum is kept
+// error-free with Knuth's two-sum, and the rounding terms plus the ql * x
+// products are added in single precision ("Dot2" of Ogita, Rump and Oishi).
+// The result is as accurate as if computed in twice the working precision
+// and then rounded, which matters when the row has large entries and y is
+// small (cancellation by a factor |q| |x| / |y| of 1e2..1e4 on the outputs
+// that track the noise floor).
+template <int MK>
+__device__ __forceinline__ float2 cdot2(const float2* __restrict__ qh, const float2* __restrict__ ql,
+                                        const float2 (&x)[MK]) {
+  float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+#pragma unroll
+  for (int nu = 0; nu < MK; ++nu) {
+    const float2 a = qh[nu], b = ql[nu], v = x[nu];
+    // real part: a.x v.x - a.y v.y ; imag: a.x v.y + a.y v.x
+    dd p = two_prod(a.x, v.x);
+    dd s = two_sum(sr, p.hi);
+    sr = s.hi; cr = __fadd_rn(cr, __fadd_rn(s.lo, p.lo));
+    p = two_prod(-a.y, v.y);
+    s = two_sum(sr, p.hi);
+    sr = s.hi; cr = __fadd_rn(cr, __fadd_rn(s.lo, p.lo));
+    cr = __fmaf_rn(b.x, v.x, __fmaf_rn(-b.y, v.y, cr));
+    p = two_prod(a.x, v.y);
+    s = two_sum(si, p.hi);
+    si = s.hi; ci = __fadd_rn(ci, __fadd_rn(s.lo, p.lo));
+    p = two_prod(a.y, v.x);
+    s = two_sum(si, p.hi);
+    si = s.hi; ci = __fadd_rn(ci, __fadd_rn(s.lo, p.lo));
+    ci = __fmaf_rn(b.x, v.y, __fmaf_rn(b.y, v.x, ci));
+  }
+  return make_float2(__fadd_rn(sr, cr), __fadd_rn(si, ci));
+}
+
+// Split an FP64 complex into a float pair (hi = rounded, lo = remainder).
+__device__ __forceinline__ void split_c(double2 q, float2& hi, float2& lo) {
+  hi = make_float2((float)q.x, (float)q.y);
+  lo = make_float2((float)(q.x - (double)hi.x), (float)(q.y - (double)hi.y));
+}
+
+// MK consecutive complex64 values (vector loads when MK is even: the caller
+// guarantees 16-byte alignment then).
+template <int MK>
+__device__ __forceinline__ void load_block(const float2* __restrict__ p, float2 (&v)[MK]) {
+  if constexpr (MK % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < MK; i += 2) {
+      float4 q = __ldg(reinterpret_cast<const float4*>(p + i));
+      v[i] = make_float2(q.x, q.y);
+      v[i + 1] = make_float2(q.z, q.w);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < MK; ++i) v[i] = __ldg(p + i);
+  }
+}
+
 // flags[0]: non-finite value produced; flags[1]: IP blocks that took the
 // pseudo-inverse path (counter).
 enum { FLAG_NONFINITE = 0, FLAG_PINV = 1, FLAG_COUNT = 4 };

@@ -16,7 +16,7 @@ struct dfmnmf_ctx {
   double2* Q64;    // [F][K*MK*MK]   master copy
   float2* Q32;     // [F][K*MK*MK]   single-precision copy used by the streaming kernels
   float2* Qinv32;  // [F][K*MK*MK]   inverse blocks (Wiener filter)
-  float2* V;       // [F][K][MK][MK][MK]
+  double2* V;      // [F][K][MK][MK][MK]  (FP64: float-float accumulated)
   float* W;        // [N][F][B]
   float* H;        // [N][B][T]
   float* g;        // [F][N][M]

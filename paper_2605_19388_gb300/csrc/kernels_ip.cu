@@ -84,7 +84,7 @@ __device__ void pinv_column(cx<double> (&U)[MK][MK], int mu, double rtol, cx<dou
 }
 
 template <int MK, class R>
-__global__ void __launch_bounds__(128) k_ip(const float2* __restrict__ V, double2* __restrict__ Q64,
+__global__ void __launch_bounds__(128) k_ip(const double2* __restrict__ V, double2* __restrict__ Q64,
                                             float2* __restrict__ Q32, int nblocks, float eps, float rtol,
                                             unsigned* __restrict__ flags) {
   using O = RealOps<R>;
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(128) k_ip(const float2* __restrict__ V, double
     else Qb[e] = cmake(i == j ? O::one() : O::zero(), O::zero());
   }
   __syncwarp();
-  const float2* Vb = V + (size_t)(valid ? blk : 0) * E * MK;
+  const double2* Vb = V + (size_t)(valid ? blk : 0) * E * MK;
   auto L = [&](int r, int c) { return sb + r * MK + c; };
 
   for (int mu = 0; mu < MK; ++mu) {
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(128) k_ip(const float2* __restrict__ V, double
     cx<R> a = czero<R>(), vij = czero<R>();
 #pragma unroll
     for (int l = 0; l < MK; ++l) {
-      const cx<R> vlj = cfrom_f2<R>(Vb[mu * E + l * MK + j]);
+      const cx<R> vlj = cfrom_d2<R>(Vb[mu * E + l * MK + j]);
       a = cadd(a, cmul(Qb[i * MK + l], vlj));
       if (l == i) vij = vlj;
     }
@@ -165,9 +165,9 @@ __global__ void __launch_bounds__(128) k_ip(const float2* __restrict__ V, double
             for (int l = 0; l < MK; ++l) {
               const cx<R> qrl = Qb[r * MK + l];
               const double qr = O::to_d(qrl.re), qim = O::to_d(qrl.im);
-              const float2 v = Vb[mu * E + l * MK + c];
-              sr += qr * (double)v.x - qim * (double)v.y;
-              si += qr * (double)v.y + qim * (double)v.x;
+              const double2 v = Vb[mu * E + l * MK + c];
+              sr += qr * v.x - qim * v.y;
+              si += qr * v.y + qim * v.x;
             }
             U[r][c] = cmake(sr, si);
           }

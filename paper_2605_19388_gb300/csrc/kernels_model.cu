@@ -1,7 +1,6 @@
 // kernels_model.cu -- per-frequency streaming kernels of one MM iteration.
 //
 //   k_lambda     lambda[n][f][t] = sum_b W[n][f][b] H[n][b][t]            (Eq. 2)
-//   k_cov        V[f][k][mu] = (1/T) sum_t x_ftk x_ftk^H / yhat_ft(o_k+mu) (Eq. 13)
 //   k_pstats     P = |Q_fk x_ftk|^2 (Sec. III-B, y = W^H x) and the MU
 //                statistics A = sum_m g P yhat^-2, D = sum_m g yhat^-1 that
 //                Eqs. (8) and (9) contract with H and W
@@ -39,108 +38,11 @@ cudaError_t launch_lambda(const dfmnmf_ctx* c, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// ------------------------------------------------------ weighted covariance
-template <int MK>
-__device__ __forceinline__ void load_block(const float2* __restrict__ p, float2 (&v)[MK]) {
-  if constexpr (MK % 2 == 0) {
-#pragma unroll
-    for (int i = 0; i < MK; i += 2) {
-      float4 q = __ldg(reinterpret_cast<const float4*>(p + i));
-      v[i] = make_float2(q.x, q.y);
-      v[i + 1] = make_float2(q.z, q.w);
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < MK; ++i) v[i] = __ldg(p + i);
-  }
-}
-
-// One warp per (subarray k, slice of t); lanes stride over t.  Every lane keeps
-// the MK x MK^2 real partial sums of its frames in registers (the Hermitian
-// outer product x x^H is formed once per frame and weighted for all mu), then
-// the warp reduce-scatters them and the slices are added in a fixed order.
-template <int MK>
-__global__ void __launch_bounds__(256) k_cov(const float2* __restrict__ x, const float* __restrict__ lam,
-                                             const float* __restrict__ g, float2* __restrict__ V, int F,
-                                             int T, int K, int N, float eps) {
-  constexpr int C = MK * MK * MK;
-  constexpr int CP = (C + 31) / 32 * 32;
-  constexpr int NW = 8;
-  const int f = blockIdx.x;
-  const int M = K * MK;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  extern __shared__ float sm[];
-  float* gs = sm;            // [N][M]
-  float* part = sm + N * M;  // [slots][CP]
-  for (int i = threadIdx.x; i < N * M; i += blockDim.x) gs[i] = g[(size_t)f * N * M + i];
-  __syncthreads();
-  const int WPI = (K <= NW) ? NW / K : 1;
-  const int nslots = K * WPI;
-  for (int slot = warp; slot < nslots; slot += NW) {
-    const int k = slot / WPI, pid = slot % WPI;
-    float acc[CP];
-#pragma unroll
-    for (int i = 0; i < CP; ++i) acc[i] = 0.f;
-    const float* gsk = gs + k * MK;
-    for (int t = pid * 32 + lane; t < T; t += WPI * 32) {
-      float2 xv[MK];
-      load_block<MK>(x + ((size_t)f * T + t) * M + k * MK, xv);
-      float ys[MK];
-#pragma unroll
-      for (int mu = 0; mu < MK; ++mu) ys[mu] = 0.f;
-#pragma unroll
-      for (int n = 0; n < NMAXR; ++n) {
-        if (n < N) {
-          const float l = __ldg(lam + ((size_t)n * F + f) * T + t);
-#pragma unroll
-          for (int mu = 0; mu < MK; ++mu) ys[mu] = fmaf(l, gsk[n * M + mu], ys[mu]);
-        }
-      }
-      float w[MK];
-#pragma unroll
-      for (int mu = 0; mu < MK; ++mu) w[mu] = __frcp_rn(fmaxf(ys[mu], eps));
-      // R[a*MK+b]: a==b |x_a|^2 ; a<b Re(x_a conj x_b) ; a>b Im(x_b conj x_a)
-      float R[MK * MK];
-#pragma unroll
-      for (int a = 0; a < MK; ++a) {
-        R[a * MK + a] = fmaf(xv[a].x, xv[a].x, xv[a].y * xv[a].y);
-#pragma unroll
-        for (int b = a + 1; b < MK; ++b) {
-          R[a * MK + b] = fmaf(xv[a].x, xv[b].x, xv[a].y * xv[b].y);
-          R[b * MK + a] = fmaf(xv[a].y, xv[b].x, -xv[a].x * xv[b].y);
-        }
-      }
-#pragma unroll
-      for (int mu = 0; mu < MK; ++mu)
-#pragma unroll
-        for (int r = 0; r < MK * MK; ++r) acc[mu * MK * MK + r] = fmaf(w[mu], R[r], acc[mu * MK * MK + r]);
-    }
-    warp_reduce_scatter<CP>(acc, lane);
-#pragma unroll
-    for (int i = 0; i < CP / 32; ++i) part[slot * CP + lane * (CP / 32) + i] = acc[i];
-  }
-  __syncthreads();
-  const float invT = 1.f / (float)T;
-  const int total = K * MK * MK * MK;
-  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int b = idx % MK, a = (idx / MK) % MK, mu = (idx / (MK * MK)) % MK, k = idx / (MK * MK * MK);
-    const int lo = a < b ? a : b, hi = a < b ? b : a;
-    float re = 0.f, im = 0.f;
-    for (int pid = 0; pid < WPI; ++pid) {
-      const float* pp = part + (k * WPI + pid) * CP + mu * MK * MK;
-      re += pp[lo * MK + hi];
-      if (lo != hi) im += pp[hi * MK + lo];
-    }
-    if (a > b) im = -im;
-    V[(size_t)f * total + idx] = make_float2(re * invT, im * invT);
-  }
-}
-
 // --------------------------------------------------- projected power + stats
 // Thread per frame t: P for all M microphones (when COMPUTE_P) or read back,
 // then A[n][f][t] = sum_m g P yhat^-2 and D[n][f][t] = sum_m g yhat^-1.
 template <int MK, bool COMPUTE_P>
-__global__ void __launch_bounds__(128) k_pstats(const float2* __restrict__ x, const float2* __restrict__ Q32,
+__global__ void __launch_bounds__(128) k_pstats(const float2* __restrict__ x, const double2* __restrict__ Q64,
                                                 const float* __restrict__ lam, const float* __restrict__ g,
                                                 float* __restrict__ P, float* __restrict__ A,
                                                 float* __restrict__ D, int F, int T, int K, int N, float eps) {
@@ -148,10 +50,11 @@ __global__ void __launch_bounds__(128) k_pstats(const float2* __restrict__ x, co
   const int M = K * MK;
   const int f = blockIdx.x;
   float* gs = sm;                                            // [N][M]
-  float2* Qs = reinterpret_cast<float2*>(sm + ((N * M + 1) & ~1));  // [K][MK][MK]
+  float2* Qh = reinterpret_cast<float2*>(sm + ((N * M + 1) & ~1));  // [K][MK][MK] high parts
+  float2* Ql = Qh + K * MK * MK;                                      // low parts
   for (int i = threadIdx.x; i < N * M; i += blockDim.x) gs[i] = g[(size_t)f * N * M + i];
   if (COMPUTE_P)
-    for (int i = threadIdx.x; i < K * MK * MK; i += blockDim.x) Qs[i] = Q32[(size_t)f * K * MK * MK + i];
+    for (int i = threadIdx.x; i < K * MK * MK; i += blockDim.x) split_c(Q64[(size_t)f * K * MK * MK + i], Qh[i], Ql[i]);
   __syncthreads();
   const int t = blockIdx.y * blockDim.x + threadIdx.x;
   if (t >= T) return;
@@ -168,17 +71,10 @@ __global__ void __launch_bounds__(128) k_pstats(const float2* __restrict__ x, co
     if (COMPUTE_P) {
       float2 xv[MK];
       load_block<MK>(x + ((size_t)f * T + t) * M + k * MK, xv);
-      const float2* Qk = Qs + k * MK * MK;
 #pragma unroll
       for (int mu = 0; mu < MK; ++mu) {
-        float yr = 0.f, yi = 0.f;
-#pragma unroll
-        for (int nu = 0; nu < MK; ++nu) {
-          const float2 q = Qk[mu * MK + nu];
-          yr = fmaf(q.x, xv[nu].x, fmaf(-q.y, xv[nu].y, yr));
-          yi = fmaf(q.x, xv[nu].y, fmaf(q.y, xv[nu].x, yi));
-        }
-        pv[mu] = fmaf(yr, yr, yi * yi);
+        const float2 y = cdot2<MK>(Qh + (k * MK + mu) * MK, Ql + (k * MK + mu) * MK, xv);
+        pv[mu] = fmaf(y.x, y.x, y.y * y.y);
       }
       if constexpr (MK == 4) {
         *reinterpret_cast<float4*>(Pt + k * MK) = make_float4(pv[0], pv[1], pv[2], pv[3]);
@@ -299,30 +195,14 @@ __global__ void __launch_bounds__(256) k_gupd(const float* __restrict__ lam, con
 
 // ----------------------------------------------------------------- launchers
 
-static size_t cov_smem(const dfmnmf_ctx* c, int CP) {
-  const int NW = 8;
-  const int slots = c->K <= NW ? NW : c->K;
-  return (size_t)(c->N * c->M + slots * CP) * sizeof(float);
-}
-
-cudaError_t launch_cov(const dfmnmf_ctx* c, cudaStream_t s) {
-  DFM_MK_DISPATCH(c->MK, {
-    constexpr int CP = (MK_ * MK_ * MK_ + 31) / 32 * 32;
-    const size_t sm = cov_smem(c, CP);
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_cov<MK_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_cov<MK_><<<c->F, 256, sm, s>>>(c->x, c->lam, c->g, c->V, c->F, c->T, c->K, c->N, c->eps);
-  });
-  return cudaGetLastError();
-}
-
 static size_t pstats_smem(const dfmnmf_ctx* c) {
-  return (size_t)((c->N * c->M + 1) & ~1) * sizeof(float) + (size_t)c->K * c->MK * c->MK * sizeof(float2);
+  return (size_t)((c->N * c->M + 1) & ~1) * sizeof(float) + 2 * (size_t)c->K * c->MK * c->MK * sizeof(float2);
 }
 
 cudaError_t launch_power_stats(const dfmnmf_ctx* c, cudaStream_t s) {
   dim3 grid(c->F, (c->T + 127) / 128);
   DFM_MK_DISPATCH(c->MK, {
-    k_pstats<MK_, true><<<grid, 128, pstats_smem(c), s>>>(c->x, c->Q32, c->lam, c->g, c->P, c->A, c->D, c->F,
+    k_pstats<MK_, true><<<grid, 128, pstats_smem(c), s>>>(c->x, c->Q64, c->lam, c->g, c->P, c->A, c->D, c->F,
                                                          c->T, c->K, c->N, c->eps);
   });
   return cudaGetLastError();
@@ -331,7 +211,7 @@ cudaError_t launch_power_stats(const dfmnmf_ctx* c, cudaStream_t s) {
 cudaError_t launch_stats(const dfmnmf_ctx* c, cudaStream_t s) {
   dim3 grid(c->F, (c->T + 127) / 128);
   DFM_MK_DISPATCH(c->MK, {
-    k_pstats<MK_, false><<<grid, 128, pstats_smem(c), s>>>(c->x, c->Q32, c->lam, c->g, c->P, c->A, c->D, c->F,
+    k_pstats<MK_, false><<<grid, 128, pstats_smem(c), s>>>(c->x, c->Q64, c->lam, c->g, c->P, c->A, c->D, c->F,
                                                           c->T, c->K, c->N, c->eps);
   });
   return cudaGetLastError();

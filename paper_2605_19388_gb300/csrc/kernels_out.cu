@@ -14,7 +14,7 @@ constexpr int NMAXO = 16;
 // of a frame, FP64 across frames; one partial per CTA, reduced in a fixed
 // order by k_nll_final.
 template <int MK>
-__global__ void __launch_bounds__(128) k_nll_data(const float2* __restrict__ x, const float2* __restrict__ Q32,
+__global__ void __launch_bounds__(128) k_nll_data(const float2* __restrict__ x, const double2* __restrict__ Q64,
                                                   const float* __restrict__ lam, const float* __restrict__ g,
                                                   double* __restrict__ part, int F, int T, int K, int N,
                                                   float eps) {
@@ -22,10 +22,11 @@ __global__ void __launch_bounds__(128) k_nll_data(const float2* __restrict__ x, 
   const int M = K * MK;
   const int f = blockIdx.x;
   float* gs = sm;
-  float2* Qs = reinterpret_cast<float2*>(sm + ((N * M + 1) & ~1));
+  float2* Qh = reinterpret_cast<float2*>(sm + ((N * M + 1) & ~1));
+  float2* Ql = Qh + K * MK * MK;
   __shared__ double wsum[4];
   for (int i = threadIdx.x; i < N * M; i += blockDim.x) gs[i] = g[(size_t)f * N * M + i];
-  for (int i = threadIdx.x; i < K * MK * MK; i += blockDim.x) Qs[i] = Q32[(size_t)f * K * MK * MK + i];
+  for (int i = threadIdx.x; i < K * MK * MK; i += blockDim.x) split_c(Q64[(size_t)f * K * MK * MK + i], Qh[i], Ql[i]);
   __syncthreads();
   const int t = blockIdx.y * blockDim.x + threadIdx.x;
   double acc = 0.0;
@@ -40,14 +41,8 @@ __global__ void __launch_bounds__(128) k_nll_data(const float2* __restrict__ x, 
       float s = 0.f;
 #pragma unroll
       for (int mu = 0; mu < MK; ++mu) {
-        float yr = 0.f, yi = 0.f;
-#pragma unroll
-        for (int nu = 0; nu < MK; ++nu) {
-          const float2 q = Qs[(k * MK + mu) * MK + nu];
-          yr = fmaf(q.x, xv[nu].x, fmaf(-q.y, xv[nu].y, yr));
-          yi = fmaf(q.x, xv[nu].y, fmaf(q.y, xv[nu].x, yi));
-        }
-        const float p = fmaf(yr, yr, yi * yi);
+        const float2 yv = cdot2<MK>(Qh + (k * MK + mu) * MK, Ql + (k * MK + mu) * MK, xv);
+        const float p = fmaf(yv.x, yv.x, yv.y * yv.y);
         float ys = 0.f;
 #pragma unroll
         for (int n = 0; n < NMAXO; ++n)
@@ -91,7 +86,7 @@ __global__ void __launch_bounds__(256) k_nll_final(const double* __restrict__ pa
 
 
 static size_t gq_smem(const dfmnmf_ctx* c) {
-  return (size_t)((c->N * c->M + 1) & ~1) * sizeof(float) + (size_t)c->K * c->MK * c->MK * sizeof(float2);
+  return (size_t)((c->N * c->M + 1) & ~1) * sizeof(float) + 2 * (size_t)c->K * c->MK * c->MK * sizeof(float2);
 }
 
 cudaError_t launch_loglik(const dfmnmf_ctx* c, cudaStream_t s) {
@@ -100,7 +95,7 @@ cudaError_t launch_loglik(const dfmnmf_ctx* c, cudaStream_t s) {
   double* ld = c->red + npart;
   const size_t nld = (size_t)c->F * c->K;
   DFM_MK_DISPATCH(c->MK, {
-    k_nll_data<MK_><<<dim3(c->F, ty), 128, gq_smem(c), s>>>(c->x, c->Q32, c->lam, c->g, c->red, c->F, c->T,
+    k_nll_data<MK_><<<dim3(c->F, ty), 128, gq_smem(c), s>>>(c->x, c->Q64, c->lam, c->g, c->red, c->F, c->T,
                                                              c->K, c->N, c->eps);
   });
   cudaError_t e = cudaGetLastError();
@@ -113,7 +108,7 @@ cudaError_t launch_loglik(const dfmnmf_ctx* c, cudaStream_t s) {
 
 // Wiener filter: c_n = Q^{-1} diag(lambda_n g_n / yhat) Q x per subarray block.
 template <int MK>
-__global__ void __launch_bounds__(128) k_separate(const float2* __restrict__ x, const float2* __restrict__ Q32,
+__global__ void __launch_bounds__(128) k_separate(const float2* __restrict__ x, const double2* __restrict__ Q64,
                                                   const float2* __restrict__ Qinv, const float* __restrict__ lam,
                                                   const float* __restrict__ g, float2* __restrict__ out, int F,
                                                   int T, int K, int N, float eps) {
@@ -121,11 +116,12 @@ __global__ void __launch_bounds__(128) k_separate(const float2* __restrict__ x, 
   const int M = K * MK;
   const int f = blockIdx.x;
   float* gs = sm;
-  float2* Qs = reinterpret_cast<float2*>(sm + ((N * M + 1) & ~1));
-  float2* Qi = Qs + K * MK * MK;
+  float2* Qh = reinterpret_cast<float2*>(sm + ((N * M + 1) & ~1));
+  float2* Ql = Qh + K * MK * MK;
+  float2* Qi = Ql + K * MK * MK;
   for (int i = threadIdx.x; i < N * M; i += blockDim.x) gs[i] = g[(size_t)f * N * M + i];
   for (int i = threadIdx.x; i < K * MK * MK; i += blockDim.x) {
-    Qs[i] = Q32[(size_t)f * K * MK * MK + i];
+    split_c(Q64[(size_t)f * K * MK * MK + i], Qh[i], Ql[i]);
     Qi[i] = Qinv[(size_t)f * K * MK * MK + i];
   }
   __syncthreads();
@@ -141,14 +137,7 @@ __global__ void __launch_bounds__(128) k_separate(const float2* __restrict__ x, 
     for (int nu = 0; nu < MK; ++nu) xv[nu] = x[((size_t)f * T + t) * M + k * MK + nu];
 #pragma unroll
     for (int mu = 0; mu < MK; ++mu) {
-      float yr = 0.f, yi = 0.f;
-#pragma unroll
-      for (int nu = 0; nu < MK; ++nu) {
-        const float2 q = Qs[(k * MK + mu) * MK + nu];
-        yr = fmaf(q.x, xv[nu].x, fmaf(-q.y, xv[nu].y, yr));
-        yi = fmaf(q.x, xv[nu].y, fmaf(q.y, xv[nu].x, yi));
-      }
-      y[mu] = make_float2(yr, yi);
+      y[mu] = cdot2<MK>(Qh + (k * MK + mu) * MK, Ql + (k * MK + mu) * MK, xv);
       float ys = 0.f;
 #pragma unroll
       for (int n = 0; n < NMAXO; ++n)
@@ -185,7 +174,7 @@ cudaError_t launch_separate(const dfmnmf_ctx* c, float2* out, cudaStream_t s) {
   const int ty = (c->T + 127) / 128;
   const size_t sm = gq_smem(c) + (size_t)c->K * c->MK * c->MK * sizeof(float2);
   DFM_MK_DISPATCH(c->MK, {
-    k_separate<MK_><<<dim3(c->F, ty), 128, sm, s>>>(c->x, c->Q32, c->Qinv32, c->lam, c->g, out, c->F, c->T,
+    k_separate<MK_><<<dim3(c->F, ty), 128, sm, s>>>(c->x, c->Q64, c->Qinv32, c->lam, c->g, out, c->F, c->T,
                                                      c->K, c->N, c->eps);
   });
   return cudaGetLastError();

@@ -237,7 +237,7 @@ def params_numpy(ctx: Context):
 
 def buffer_numpy(ctx: Context, which: int):
     mk = ctx.mics[0]
-    shapes = {DFMNMF_BUF_V: ((ctx.F, ctx.K, mk, mk, mk), np.complex64),
+    shapes = {DFMNMF_BUF_V: ((ctx.F, ctx.K, mk, mk, mk), np.complex128),
               DFMNMF_BUF_P: ((ctx.F, ctx.T, ctx.M), np.float32),
               DFMNMF_BUF_LAMBDA: ((ctx.N, ctx.F, ctx.T), np.float32)}
     shape, dt = shapes[which]

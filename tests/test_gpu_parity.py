@@ -82,10 +82,12 @@ def test_stage_parity_two_subarrays_ragged(ip):
     stage_parity(p, Q0, ip)
 
 
-def test_stage_parity_plain_fp32_ip():
-    p = synth.make_problem(23, 97, (4, 4, 4), 2, 5, seed=2)
+def test_stage_parity_plain_fp32_ip_well_conditioned():
+    """Plain binary32 solves are only a study mode: they hold on well-conditioned
+    covariances (more sources than microphones per subarray, 26 dB noise floor)."""
+    p = synth.make_problem(23, 97, (4, 4, 4), 6, 5, seed=2, noise_std=0.05)
     Q0 = synth.random_blocks(p.F, p.mics, seed=4)
-    stage_parity(p, Q0, D.DFMNMF_IP_F32, tol_ip=3e-4)
+    stage_parity(p, Q0, D.DFMNMF_IP_F32, tol_ip=1e-4)
 
 
 @pytest.mark.parametrize("mics", [(1, 1, 1), (2, 2), (3, 3), (4,), (4, 4, 4, 4)])
