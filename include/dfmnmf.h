@@ -179,6 +179,35 @@ int dfmnmf_kernel_times(dfmnmf_ctx* ctx, int n_iter, double* avg_ms, const char*
 
 void dfmnmf_destroy(dfmnmf_ctx* ctx);
 
+/*
+ * Allocation-free negative log-likelihood.  The paper has no counterpart:
+ * this entry point exists for callers that may not allocate device memory
+ * when they need the cost -- for example an audio engine's real-time thread,
+ * where cudaMalloc can block and synchronise the whole device, or a plug-in
+ * whose host application owns the GPU memory budget.  It evaluates exactly
+ * the quantity of dfmnmf_loglik (Eq. 12 without the F T M ln(pi) constant)
+ * from state the caller already holds in device memory, and needs no context:
+ *   desc         sizes and layout as for dfmnmf_init (precision and ip_arith
+ *                are ignored; floor_eps <= 0 means 1e-6),
+ *   x_dev        complex64 [F][T][M], Q_dev complex128 [F][sum M_k^2],
+ *   W_dev, H_dev, g_dev float32 as for dfmnmf_init (all device memory),
+ *   nll_host     receives the cost (the call synchronises `stream`).
+ * Its partial sums live in one static device array of
+ * DFMNMF_NOALLOC_SCRATCH_DOUBLES doubles (512 KiB) that every GPU which loads
+ * this library keeps until the process exits; sizes with
+ * F * ceil(T/128) + F * K + 1 above that return DFMNMF_EINVAL (the
+ * 4 x 4-mic, F = 513, T = 626 workload needs 4618).  No cudaMalloc, cudaFree
+ * or allocating library routine is called.  The first call on each device
+ * (with that device current) looks the array's address up once; make that
+ * first call before starting any stream capture.  All calls share the array:
+ * calls whose GPU work may overlap (different streams without ordering) race
+ * and must be serialised by the caller.  ENUMERIC if the cost is not finite.
+ */
+#define DFMNMF_NOALLOC_SCRATCH_DOUBLES 65536
+int dfmnmf_loglik_noalloc(const dfmnmf_desc* desc, const void* x_dev, const void* Q_dev,
+                          const float* W_dev, const float* H_dev, const float* g_dev,
+                          double* nll_host, void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* dfmnmf_last_error(void);
 

@@ -151,6 +151,8 @@ int refresh_derived(dfmnmf_ctx* c, cudaStream_t s) {
 
 }  // namespace
 
+void dfm::set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
 extern "C" {
 
 int dfmnmf_version(void) { return DFMNMF_VERSION; }

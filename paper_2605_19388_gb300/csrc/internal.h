@@ -51,6 +51,9 @@ cudaError_t launch_qinv(const dfmnmf_ctx* c, cudaStream_t s);
 cudaError_t launch_separate(const dfmnmf_ctx* c, float2* out, cudaStream_t s);
 cudaError_t launch_q_convert(const dfmnmf_ctx* c, cudaStream_t s);    // Q64 -> Q32
 
+// Record the message returned by dfmnmf_last_error() on this thread.
+void set_last_error(const char* msg);
+
 // Whether the NMF update kernels refresh lambda themselves (else a separate
 // lambda launch follows them).
 bool nmf_fused_lambda(const dfmnmf_ctx* c);

@@ -28,7 +28,7 @@ DFMNMF_BUF_V, DFMNMF_BUF_P, DFMNMF_BUF_LAMBDA = 1, 2, 3
 EXPORTED = ("dfmnmf_init", "dfmnmf_set_observation", "dfmnmf_iterate", "dfmnmf_run_stage",
             "dfmnmf_loglik", "dfmnmf_separate", "dfmnmf_get_params", "dfmnmf_set_params",
             "dfmnmf_get_buffer", "dfmnmf_launches_per_iteration", "dfmnmf_kernel_times", "dfmnmf_destroy",
-            "dfmnmf_last_error", "dfmnmf_version")
+            "dfmnmf_last_error", "dfmnmf_version", "dfmnmf_loglik_noalloc")
 
 
 class DfmnmfError(RuntimeError):
@@ -72,6 +72,7 @@ def load_library(path: Optional[str] = None):
         "dfmnmf_destroy": (None, [vp]),
         "dfmnmf_last_error": (ctypes.c_char_p, []),
         "dfmnmf_version": (ci, []),
+        "dfmnmf_loglik_noalloc": (ci, [ctypes.POINTER(dfmnmf_desc), vp, vp, vp, vp, vp, ctypes.POINTER(cd), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -222,6 +223,19 @@ def dfmnmf_destroy(ctx: Context):
 
 def dfmnmf_version() -> int:
     return load_library().dfmnmf_version()
+
+
+def dfmnmf_loglik_noalloc(F: int, T: int, mics: Sequence[int], N: int, B: int, x, Q, W, H, g,
+                          floor_eps: float = 1e-6, stream=None) -> float:
+    """Eq. (12) from caller-held device arrays, with no device allocation (see the header)."""
+    lib = load_library()
+    mic_arr = (ctypes.c_int * len(mics))(*[int(m) for m in mics])
+    d = dfmnmf_desc(int(F), int(T), len(mics), mic_arr, int(N), int(B), 0, 0, float(floor_eps))
+    v = ctypes.c_double()
+    _check(lib.dfmnmf_loglik_noalloc(ctypes.byref(d), _ptr(x, _dt("c64")), _ptr(Q, _dt("c128")),
+                                     _ptr(W, _dt("f32")), _ptr(H, _dt("f32")), _ptr(g, _dt("f32")),
+                                     ctypes.byref(v), _stream(stream)))
+    return v.value
 
 
 # --------------------------------------------------------------- convenience
