@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--workload", default="paper_4x4_n5")
     ap.add_argument("--iters", type=int, default=None, help="MM iterations per step (default: the workload's)")
     ap.add_argument("--ip", choices=["f32x2", "f64", "f32"], default="f32x2")
+    ap.add_argument("--forms", default="bf16tc,fp32",
+                    help="comma list of forms to time; the first is the headline value")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
@@ -121,7 +123,9 @@ class ClockSampler:
 def kernel_bytes(F, T, M, N, B, K, MK):
     """Algorithmic DRAM bytes of one launch of each kernel (each operand once)."""
     q = F * K * MK * MK
+    Tr = (T + 63) // 64 * 64
     return {
+        "k_vtc": 2 * F * 16 * K * Tr * 2 + 4 * N * F * T + 4 * F * N * M + 16 * q * MK + 16 * q * MK,
         "k_cov": 8 * F * T * M + 4 * N * F * T + 4 * F * N * M + 8 * q * MK,
         "k_ip": 8 * q * MK + 32 * q + 8 * q,
         "k_pstats": 8 * F * T * M + 4 * N * F * T + 4 * F * N * M + 8 * q + 4 * F * T * M + 8 * N * F * T,
@@ -231,13 +235,12 @@ def main():
     c_out = torch.empty((N, F, T, M), dtype=torch.complex64, device=dev)
     flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def make(ip_arith):
-        return D.dfmnmf_init(F, T, p.mics, N, Bb, x_d, W0_d, H0_d, g0_d, Q0_d, ip_arith=ip_arith)
-
-    ctx = make(ip)
+    precisions = {"bf16tc": D.DFMNMF_BF16_TC, "fp32": D.DFMNMF_FP32}
+    forms = [f.strip() for f in args.forms.split(",") if f.strip()]
     nll_box = []
 
     def step(c):
+        D.dfmnmf_set_observation(c, x_d)          # observation in place (TC form: x x^H split anew)
         D.dfmnmf_set_params(c, Q0_d, W0_d, H0_d, g0_d)
         D.dfmnmf_iterate(c, iters)
         nll_box.append(D.dfmnmf_loglik(c))
@@ -261,65 +264,87 @@ def main():
             tot += e0.elapsed_time(e1)
         return tot
 
-    for _ in range(args.warmup):
-        step(ctx)
-    torch.cuda.synchronize()
-    sampler = ClockSampler(local if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
-    barrier()
-    torch.cuda.synchronize()
-    sampler.start()
-    total_ms = timed(step, ctx, args.steps)
-    torch.cuda.synchronize()
-    barrier()
-    clocks = sampler.stop()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
-    value = world * iters * args.steps / (total_ms / 1000.0)
+    def max_over_ranks(v):
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([v], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            return float(t.item())
+        return v
 
-    launches_iter = D.dfmnmf_launches_per_iteration(ctx)
-    launches_step = iters * launches_iter + 2 + 3 + 2  # set_params, loglik, separate
-    gpu_launches = launches_step * args.steps
-
-    # per-kernel times inside the same steady state (events between launches)
-    D.dfmnmf_set_params(ctx, Q0_d, W0_d, H0_d, g0_d)
-    D.dfmnmf_iterate(ctx, 5)
-    kt = D.dfmnmf_kernel_times(ctx, 50)
-    iter_ms = sum(ms for _, ms in kt)
     kb = kernel_bytes(F, T, M, N, Bb, K, MK)
     peak, peak_kind = peaks()
-    dom_name, dom_ms = max(kt, key=lambda e: e[1])
-    ach = kb[dom_name] / (dom_ms * 1e-3) / 1e9
-    kernels = {n: {"ms": ms, "share": ms / iter_ms, "alg_bytes": kb.get(n),
-                   "GBps": (kb[n] / (ms * 1e-3) / 1e9) if n in kb else None} for n, ms in kt}
     ib = iteration_bytes(F, T, M, N)
+    results = {}
+    ctxs = {}
+    clocks = None
+    for form in forms:
+        c = D.dfmnmf_init(F, T, p.mics, N, Bb, x_d, W0_d, H0_d, g0_d, Q0_d, ip_arith=ip,
+                          precision=precisions[form])
+        ctxs[form] = c
+        for _ in range(args.warmup):
+            step(c)
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
+        barrier()
+        torch.cuda.synchronize()
+        sampler.start()
+        total_ms = timed(step, c, args.steps)
+        torch.cuda.synchronize()
+        barrier()
+        ck = sampler.stop()
+        total_ms = max_over_ranks(total_ms)
+        launches_iter = D.dfmnmf_launches_per_iteration(c)
+        # per-kernel times inside the same steady state (events between launches)
+        D.dfmnmf_set_params(c, Q0_d, W0_d, H0_d, g0_d)
+        D.dfmnmf_iterate(c, 5)
+        kt = D.dfmnmf_kernel_times(c, 50)
+        iter_ms = sum(ms for _, ms in kt)
+        dom_name, dom_ms = max(kt, key=lambda e: e[1])
+        results[form] = dict(
+            value=world * iters * args.steps / (total_ms / 1000.0), ms_per_step=total_ms / args.steps,
+            launches_iter=launches_iter, kernels=kt, iter_ms=iter_ms, dominant=(dom_name, dom_ms),
+            nll=nll_box[-1], clocks=ck)
+        if clocks is None:
+            clocks = ck
+    head = results[forms[0]]
+    dom_name, dom_ms = head["dominant"]
+    ach = kb[dom_name] / (dom_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": dom_name, "achieved": ach, "peak": peak, "unit": "GB/s",
                 "frac": ach / peak, "traffic": None, "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
                 "alg_bytes_per_launch": kb[dom_name]}
 
+    def kernel_table(kt, iter_ms):
+        return {n: {"ms": ms, "share": ms / iter_ms, "alg_bytes": kb.get(n),
+                    "GBps": (kb[n] / (ms * 1e-3) / 1e9) if n in kb else None} for n, ms in kt}
+
+    launches_step = iters * head["launches_iter"] + 2 + 3 + 2 + (1 if forms[0] == "bf16tc" else 0)
     out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 (IP solves f32x2)" if args.ip == "f32x2" else f"f32 (IP solves {args.ip})",
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": ("bf16x3 tensor-core covariances, f32 updates, f32x2 IP" if forms[0] == "bf16tc"
+                  else "f32 (float-float covariances, f32x2 IP)"),
         "data": "synthetic (seeded STFT mixtures, stand-in for the paper's simulated JNAS rooms)",
         "config": {"workload": args.workload, "F": F, "T": T, "mics": list(p.mics), "N": N, "B": Bb,
-                   "iters_per_step": iters, "form": "fp32-plain", "ip_arith": args.ip,
-                   "step": "reset state + iterations + loglik (D2H) + Wiener filter",
+                   "iters_per_step": iters, "form": forms[0], "ip_arith": args.ip,
+                   "step": "observation + state reset, iterations, loglik (D2H), Wiener filter",
                    "l2": "flushed before every timed step (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "tf_bin_mic_updates_per_s": F * T * M * value,
+        "tf_bin_mic_updates_per_s": F * T * M * head["value"],
         "roofline": roofline,
-        "iteration": {"ms": iter_ms, "alg_bytes": ib, "GBps": ib / (iter_ms * 1e-3) / 1e9,
-                      "frac_of_hbm_peak": ib / (iter_ms * 1e-3) / 1e9 / peak,
-                      "launches": launches_iter},
-        "kernels": kernels,
+        "iteration": {"ms": head["iter_ms"], "alg_bytes": ib, "GBps": ib / (head["iter_ms"] * 1e-3) / 1e9,
+                      "frac_of_hbm_peak": ib / (head["iter_ms"] * 1e-3) / 1e9 / peak,
+                      "launches": head["launches_iter"]},
+        "kernels": kernel_table(head["kernels"], head["iter_ms"]),
+        "forms": {f: {"value": r["value"], "unit": UNIT, "ms_per_step": r["ms_per_step"], "iter_ms": r["iter_ms"],
+                      "kernels": kernel_table(r["kernels"], r["iter_ms"]), "nll_last": r["nll"],
+                      "clocks": r["clocks"]} for f, r in results.items()},
         "clocks": clocks,
-        "gpu_launches": gpu_launches,
-        "nll_last": nll_box[-1] if nll_box else None,
+        "gpu_launches": launches_step * args.steps,
+        "nll_last": head["nll"],
     }
+    ctx = ctxs[forms[0]]
 
     # end to end through the public API with host buffers (pinned)
     if not args.no_e2e:
@@ -328,7 +353,7 @@ def main():
         Q0h = torch.from_numpy(p.Q0).pin_memory()
 
         def step_e2e(c):
-            D.dfmnmf_set_observation(c, xh)
+            D.dfmnmf_set_observation(c, xh)           # pinned host -> device, inside the timed region
             D.dfmnmf_set_params(c, Q0h, W0h, H0h, g0h)
             D.dfmnmf_iterate(c, iters)
             D.dfmnmf_loglik(c)
@@ -350,13 +375,13 @@ def main():
                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8 + 16,
                       "ms_per_step": e2e_ms / args.steps}
 
-    # variants on the same GPU: native-FP64 IP solves
+    # variants on the same GPU: native-FP64 and plain-FP32 IP solves (FP32 form)
     if not args.no_variants:
         var = {}
         for name, ipv in (("ip_f64", D.DFMNMF_IP_F64), ("ip_f32", D.DFMNMF_IP_F32)):
             if ipv == ip:
                 continue
-            c2 = make(ipv)
+            c2 = D.dfmnmf_init(F, T, p.mics, N, Bb, x_d, W0_d, H0_d, g0_d, Q0_d, ip_arith=ipv)
             for _ in range(2):
                 step(c2)
             ms = timed(step, c2, max(2, args.steps // 2))

@@ -46,8 +46,8 @@ void free_ctx(dfmnmf_ctx* c) {
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   if (c->graph) cudaGraphDestroy(c->graph);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
-  void* ptrs[] = {c->x, c->Q64, c->Q32, c->Qinv32, c->V, c->W, c->H, c->g, c->lam,
-                  c->P, c->A, c->D, c->red, c->nll_dev, c->flags};
+  void* ptrs[] = {c->x, c->Q64, c->Q32, c->Qinv32, c->V, c->Vdd, c->W, c->H, c->g, c->lam,
+                  c->P, c->A, c->D, c->red, c->nll_dev, c->flags, c->nmf_part, c->nmf_ticket, c->Rhi, c->Rlo};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -76,7 +76,13 @@ bool is_host_ptr(const void* p) {
 
 size_t nQ(const dfmnmf_ctx* c) { return (size_t)c->F * c->K * c->MK * c->MK; }
 size_t nW(const dfmnmf_ctx* c) { return (size_t)c->N * c->F * c->B; }
-size_t nH(const dfmnmf_ctx* c) { return (size_t)c->N * c->B * c->T; }
+size_t nH(const dfmnmf_ctx* c) { return (size_t)c->N * c->B * c->Tp; }
+// copy H between the ABI layout [N][B][T] and the padded internal one
+cudaError_t copy_H(dfmnmf_ctx* c, void* dst, const void* src, bool to_internal, cudaStream_t s) {
+  const size_t w = (size_t)c->T * sizeof(float), pitch = (size_t)c->Tp * sizeof(float);
+  return to_internal ? cudaMemcpy2DAsync(dst, pitch, src, w, w, (size_t)c->N * c->B, cudaMemcpyDefault, s)
+                     : cudaMemcpy2DAsync(dst, w, src, pitch, w, (size_t)c->N * c->B, cudaMemcpyDefault, s);
+}
 size_t ng(const dfmnmf_ctx* c) { return (size_t)c->F * c->N * c->M; }
 size_t nx(const dfmnmf_ctx* c) { return (size_t)c->F * c->T * c->M; }
 
@@ -91,7 +97,8 @@ struct Launch {
 int iteration_launches(const dfmnmf_ctx* c, Launch* out) {
   int n = 0;
   const bool fused = dfm::nmf_fused_lambda(c);
-  out[n++] = {DFMNMF_STAGE_COV, "k_cov", dfm::launch_cov};
+  if (c->precision == DFMNMF_BF16_TC) out[n++] = {DFMNMF_STAGE_COV, "k_vtc", dfm::launch_vtc};
+  else out[n++] = {DFMNMF_STAGE_COV, "k_cov", dfm::launch_cov};
   out[n++] = {DFMNMF_STAGE_IP, "k_ip", dfm::launch_ip};
   out[n++] = {DFMNMF_STAGE_W, "k_pstats", dfm::launch_power_stats};
   out[n++] = {DFMNMF_STAGE_W, "k_wupd", dfm::launch_wupd};
@@ -179,13 +186,15 @@ int dfmnmf_init(dfmnmf_ctx** out, const dfmnmf_desc* d, const void* x, const flo
                   d->mics[k]);
   }
   if (MK > 4) return fail(DFMNMF_EINVAL, "subarray size M_k=%d exceeds 4", MK);
-  if (d->precision != DFMNMF_FP32)
+  if (d->precision != DFMNMF_FP32 && d->precision != DFMNMF_BF16_TC)
     return fail(DFMNMF_EINVAL, "precision %d is not built in this release", d->precision);
+  if (d->precision == DFMNMF_BF16_TC && !dfm::tc_supported(MK, d->K))
+    return fail(DFMNMF_EINVAL, "the tensor-core form needs M_k = 4 and K in {1, 2, 4, 8} (M_k=%d K=%d)", MK, d->K);
   if (d->ip_arith < 0 || d->ip_arith > 2) return fail(DFMNMF_EINVAL, "unknown ip_arith %d", d->ip_arith);
 
   dfmnmf_ctx* c = new dfmnmf_ctx;
   memset(c, 0, sizeof *c);
-  c->F = d->F; c->T = d->T; c->K = d->K; c->MK = MK; c->M = d->K * MK; c->N = d->N; c->B = d->B;
+  c->F = d->F; c->T = d->T; c->Tp = (d->T + 3) & ~3; c->Tr = (d->T + 63) & ~63; c->K = d->K; c->MK = MK; c->M = d->K * MK; c->N = d->N; c->B = d->B;
   c->precision = d->precision;
   c->ip_arith = d->ip_arith;
   c->eps = (float)(d->floor_eps > 0 ? d->floor_eps : 1e-6);
@@ -200,14 +209,32 @@ int dfmnmf_init(dfmnmf_ctx** out, const dfmnmf_desc* d, const void* x, const flo
   c->red_len = (size_t)c->F * ty + (size_t)c->F * c->K;
   if ((r = dalloc(&c->x, nx(c), "x")) || (r = dalloc(&c->Q64, nQ(c), "Q64")) ||
       (r = dalloc(&c->Q32, nQ(c), "Q32")) || (r = dalloc(&c->Qinv32, nQ(c), "Qinv")) ||
-      (r = dalloc(&c->V, nQ(c) * MK, "V")) || (r = dalloc(&c->W, nW(c), "W")) ||
+      (r = dalloc(&c->V, nQ(c) * MK, "V")) || (r = dalloc(&c->Vdd, nQ(c) * MK, "Vdd")) || (r = dalloc(&c->W, nW(c), "W")) ||
       (r = dalloc(&c->H, nH(c), "H")) || (r = dalloc(&c->g, ng(c), "g")) ||
-      (r = dalloc(&c->lam, (size_t)c->N * c->F * c->T, "lambda")) || (r = dalloc(&c->P, nx(c), "P")) ||
-      (r = dalloc(&c->A, (size_t)c->N * c->F * c->T, "A")) ||
-      (r = dalloc(&c->D, (size_t)c->N * c->F * c->T, "D")) || (r = dalloc(&c->red, c->red_len, "red")) ||
-      (r = dalloc(&c->nll_dev, 1, "nll")) || (r = dalloc(&c->flags, dfm::FLAG_COUNT, "flags"))) {
+      (r = dalloc(&c->lam, (size_t)c->N * c->F * c->Tp, "lambda")) || (r = dalloc(&c->P, nx(c), "P")) ||
+      (r = dalloc(&c->A, (size_t)c->N * c->F * c->Tp, "A")) ||
+      (r = dalloc(&c->D, (size_t)c->N * c->F * c->Tp, "D")) || (r = dalloc(&c->red, c->red_len, "red")) ||
+      (r = dalloc(&c->nll_dev, 1, "nll")) || (r = dalloc(&c->flags, dfm::FLAG_COUNT, "flags")) ||
+      (r = dalloc(&c->nmf_part, dfm::nmf_scratch_floats(c), "nmf partials")) ||
+      (r = dalloc(&c->nmf_ticket, dfm::nmf_ticket_count(c), "nmf tickets"))) {
     free_ctx(c);
     return r;
+  }
+  if (c->precision == DFMNMF_BF16_TC) {
+    const size_t nr = (size_t)c->F * 16 * c->K * c->Tr;
+    unsigned short *rh = nullptr, *rl = nullptr;
+    if ((r = dalloc(&rh, nr, "R hi")) || (r = dalloc(&rl, nr, "R lo"))) {
+      c->Rhi = rh;
+      c->Rlo = rl;
+      free_ctx(c);
+      return r;
+    }
+    c->Rhi = rh;
+    c->Rlo = rl;
+    if (dfm::tc_make_maps(c) != cudaSuccess) {
+      free_ctx(c);
+      return fail(DFMNMF_ECUDA, "tensor map creation failed (cuTensorMapEncodeTiled unavailable or rejected)");
+    }
   }
   cudaStream_t s = as_stream(stream);
   auto bail = [&](int code) { free_ctx(c); return code; };
@@ -220,7 +247,8 @@ int dfmnmf_init(dfmnmf_ctx** out, const dfmnmf_desc* d, const void* x, const flo
   } while (0)
   CKI(cudaMemcpyAsync(c->x, x, nx(c) * sizeof(float2), cudaMemcpyDefault, s));
   CKI(cudaMemcpyAsync(c->W, W0, nW(c) * sizeof(float), cudaMemcpyDefault, s));
-  CKI(cudaMemcpyAsync(c->H, H0, nH(c) * sizeof(float), cudaMemcpyDefault, s));
+  CKI(cudaMemsetAsync(c->H, 0, nH(c) * sizeof(float), s));
+  CKI(copy_H(c, c->H, H0, true, s));
   CKI(cudaMemcpyAsync(c->g, g0, ng(c) * sizeof(float), cudaMemcpyDefault, s));
   if (Q0) {
     CKI(cudaMemcpyAsync(c->Q64, Q0, nQ(c) * sizeof(double2), cudaMemcpyDefault, s));
@@ -229,8 +257,13 @@ int dfmnmf_init(dfmnmf_ctx** out, const dfmnmf_desc* d, const void* x, const flo
     CKI(cudaGetLastError());
   }
   CKI(cudaMemsetAsync(c->flags, 0, dfm::FLAG_COUNT * sizeof(unsigned), s));
+  CKI(cudaMemsetAsync(c->nmf_ticket, 0, dfm::nmf_ticket_count(c) * sizeof(unsigned), s));
   CKI(cudaMemsetAsync(c->P, 0, nx(c) * sizeof(float), s));
+  CKI(cudaMemsetAsync(c->lam, 0, (size_t)c->N * c->F * c->Tp * sizeof(float), s));
+  CKI(cudaMemsetAsync(c->A, 0, (size_t)c->N * c->F * c->Tp * sizeof(float), s));
+  CKI(cudaMemsetAsync(c->D, 0, (size_t)c->N * c->F * c->Tp * sizeof(float), s));
   if ((r = refresh_derived(c, s))) return bail(r);
+  if (c->precision == DFMNMF_BF16_TC) CKI(dfm::launch_rprep(c, s));
 #undef CKI
   *out = c;
   return DFMNMF_OK;
@@ -240,6 +273,7 @@ int dfmnmf_set_observation(dfmnmf_ctx* c, const void* x, void* stream) {
   if (!c || !x) return fail(DFMNMF_EINVAL, "null argument");
   CK(cudaSetDevice(c->device));
   CK(cudaMemcpyAsync(c->x, x, nx(c) * sizeof(float2), cudaMemcpyDefault, as_stream(stream)));
+  if (c->precision == DFMNMF_BF16_TC) CK(dfm::launch_rprep(c, as_stream(stream)));
   return DFMNMF_OK;
 }
 
@@ -312,6 +346,7 @@ int dfmnmf_loglik(dfmnmf_ctx* c, double* nll_host, void* stream) {
   CK(cudaMemcpyAsync(flags, c->flags, sizeof flags, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   *nll_host = v;
+  if (flags[dfm::FLAG_TIMEOUT]) return fail(DFMNMF_ETIMEOUT, "a bounded device wait gave up");
   if (flags[dfm::FLAG_NONFINITE]) return fail(DFMNMF_ENUMERIC, "a non-finite value was produced (flags=%u)",
                                               flags[dfm::FLAG_NONFINITE]);
   return DFMNMF_OK;
@@ -334,7 +369,7 @@ int dfmnmf_get_params(dfmnmf_ctx* c, void* Q, float* W, float* H, float* g, void
   bool host = false;
   if (Q) { CK(cudaMemcpyAsync(Q, c->Q64, nQ(c) * sizeof(double2), cudaMemcpyDefault, s)); host |= is_host_ptr(Q); }
   if (W) { CK(cudaMemcpyAsync(W, c->W, nW(c) * sizeof(float), cudaMemcpyDefault, s)); host |= is_host_ptr(W); }
-  if (H) { CK(cudaMemcpyAsync(H, c->H, nH(c) * sizeof(float), cudaMemcpyDefault, s)); host |= is_host_ptr(H); }
+  if (H) { CK(copy_H(c, H, c->H, false, s)); host |= is_host_ptr(H); }
   if (g) { CK(cudaMemcpyAsync(g, c->g, ng(c) * sizeof(float), cudaMemcpyDefault, s)); host |= is_host_ptr(g); }
   if (host) CK(cudaStreamSynchronize(s));
   return DFMNMF_OK;
@@ -347,7 +382,7 @@ int dfmnmf_set_params(dfmnmf_ctx* c, const void* Q, const float* W, const float*
   cudaStream_t s = as_stream(stream);
   if (Q) CK(cudaMemcpyAsync(c->Q64, Q, nQ(c) * sizeof(double2), cudaMemcpyDefault, s));
   if (W) CK(cudaMemcpyAsync(c->W, W, nW(c) * sizeof(float), cudaMemcpyDefault, s));
-  if (H) CK(cudaMemcpyAsync(c->H, H, nH(c) * sizeof(float), cudaMemcpyDefault, s));
+  if (H) CK(copy_H(c, c->H, H, true, s));
   if (g) CK(cudaMemcpyAsync(c->g, g, ng(c) * sizeof(float), cudaMemcpyDefault, s));
   return refresh_derived(c, s);
 }
@@ -365,7 +400,11 @@ int dfmnmf_get_buffer(dfmnmf_ctx* c, int which, void* dst, size_t dst_bytes, voi
   if (dst_bytes < bytes) return fail(DFMNMF_EINVAL, "buffer %d needs %zu bytes, got %zu", which, bytes, dst_bytes);
   CK(cudaSetDevice(c->device));
   cudaStream_t s = as_stream(stream);
-  CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
+  if (which == DFMNMF_BUF_LAMBDA)  // drop the padding of the row stride
+    CK(cudaMemcpy2DAsync(dst, (size_t)c->T * sizeof(float), src, (size_t)c->Tp * sizeof(float),
+                         (size_t)c->T * sizeof(float), (size_t)c->N * c->F, cudaMemcpyDefault, s));
+  else
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
   if (is_host_ptr(dst)) CK(cudaStreamSynchronize(s));
   return DFMNMF_OK;
 }

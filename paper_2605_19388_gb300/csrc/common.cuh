@@ -215,6 +215,14 @@ __device__ __forceinline__ void warp_reduce_scatter(float (&v)[C], int lane) {
 
 __device__ __forceinline__ bool finitef(float v) { return isfinite(v); }
 
+// Hardware reciprocal (rcp.approx.f32, relative error <= 2^-23): the weights
+// 1/yhat only ever enter as relative perturbations of positive terms.
+__device__ __forceinline__ float fast_rcp(float a) {
+  float r;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
+}
+
 // Compensated complex dot product y = sum_nu q_nu x_nu with q = qh + ql a
 // float pair (the FP64 diagonaliser row split in two floats) and x single
 // precision: every product qh * x is exact (Dekker), the running sum is kept
@@ -274,8 +282,25 @@ __device__ __forceinline__ void load_block(const float2* __restrict__ p, float2 
 }
 
 // flags[0]: non-finite value produced; flags[1]: IP blocks that took the
-// pseudo-inverse path (counter).
-enum { FLAG_NONFINITE = 0, FLAG_PINV = 1, FLAG_COUNT = 4 };
+// pseudo-inverse path (counter); flags[2]: a bounded device wait gave up.
+enum { FLAG_NONFINITE = 0, FLAG_PINV = 1, FLAG_TIMEOUT = 2, FLAG_COUNT = 4 };
+
+// ------------------------------------------------------------ async copies
+// cp.async (global -> shared, bypassing registers); groups are committed and
+// waited on explicitly.
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 // Dispatch on the subarray size M_k (1..4) as the compile-time constant MK_.
 #define DFM_MK_DISPATCH(MKV, ...)                          \

@@ -7,6 +7,8 @@
 struct dfmnmf_ctx {
   // sizes
   int F, T, K, MK, M, N, B;
+  int Tp;               // row stride of lambda, A and D: T rounded up to a multiple of 4 (zero tail)
+  int Tr;               // row length of the tensor-core operands: T rounded up to 64 (zero tail)
   int precision, ip_arith;
   float eps;            // floor of Sec. IV-A
   float singular_rtol;  // relative pivot / singular-value cut-off of the IP solve
@@ -17,16 +19,24 @@ struct dfmnmf_ctx {
   float2* Q32;     // [F][K*MK*MK]   single-precision copy used by the streaming kernels
   float2* Qinv32;  // [F][K*MK*MK]   inverse blocks (Wiener filter)
   double2* V;      // [F][K][MK][MK][MK]  (FP64: float-float accumulated)
+  float4* Vdd;     // same entries as float pairs (re hi, re lo, im hi, im lo) for the IP kernel
   float* W;        // [N][F][B]
-  float* H;        // [N][B][T]
+  float* H;        // [N][B][Tp]  (zero tail; the ABI layout [N][B][T] is converted on copy)
   float* g;        // [F][N][M]
-  float* lam;      // [N][F][T]
+  float* lam;      // [N][F][Tp]
   float* P;        // [F][T][M]
-  float* A;        // [N][F][T]
-  float* D;        // [N][F][T]
+  float* A;        // [N][F][Tp]
+  float* D;        // [N][F][Tp]
   double* red;     // loglik partial sums
+  float* nmf_part;       // split-reduction partials of the NMF updates
+  unsigned* nmf_ticket;  // per-tile tickets of the split reductions (self-resetting)
   double* nll_dev; // 1 double
   unsigned* flags; // dfm::FLAG_COUNT words
+  // tensor-core form: x x^H split in two bfloat16 parts, [F * 16 K][Tr] each, and their TMA descriptors
+  void* Rhi;
+  void* Rlo;
+  alignas(64) unsigned char tmap_hi[128];
+  alignas(64) unsigned char tmap_lo[128];
   size_t red_len;
   // CUDA graph of one iteration, captured on first use
   cudaStream_t cap_stream;
@@ -40,6 +50,10 @@ namespace dfm {
 // All launchers return cudaGetLastError() after enqueueing.
 cudaError_t launch_lambda(const dfmnmf_ctx* c, cudaStream_t s);
 cudaError_t launch_cov(const dfmnmf_ctx* c, cudaStream_t s);
+cudaError_t launch_vtc(const dfmnmf_ctx* c, cudaStream_t s);     // tensor-core covariances (BF16_TC form)
+cudaError_t launch_rprep(const dfmnmf_ctx* c, cudaStream_t s);   // split-bfloat16 x x^H for the TC form
+cudaError_t tc_make_maps(dfmnmf_ctx* c);
+bool tc_supported(int MK, int K);
 cudaError_t launch_ip(const dfmnmf_ctx* c, cudaStream_t s);
 cudaError_t launch_power_stats(const dfmnmf_ctx* c, cudaStream_t s);  // P + A/D (current lambda)
 cudaError_t launch_wupd(const dfmnmf_ctx* c, cudaStream_t s);         // Eq. 8 + lambda
@@ -57,5 +71,7 @@ void set_last_error(const char* msg);
 // Whether the NMF update kernels refresh lambda themselves (else a separate
 // lambda launch follows them).
 bool nmf_fused_lambda(const dfmnmf_ctx* c);
+size_t nmf_scratch_floats(const dfmnmf_ctx* c);
+size_t nmf_ticket_count(const dfmnmf_ctx* c);
 
 }  // namespace dfm

@@ -19,7 +19,6 @@
 
 namespace dfm {
 
-constexpr int NMAXC = 16;
 
 // Exact real/imag parts of x_a conj(x_b) as (hi, lo) float pairs.
 __device__ __forceinline__ void exact_re(float2 a, float2 b, float& hi, float& lo) {
@@ -57,106 +56,180 @@ __device__ __forceinline__ void warp_reduce_scatter_dd(float (&hi)[C], float (&l
   }
 }
 
-// One warp per (subarray k, group of G rows mu, slice of frames); every lane
-// keeps G x MK^2 float-pair partial sums.  x x^H is stored packed as MK^2
-// reals R[a*MK+b]: a == b |x_a|^2, a < b Re(x_a conj x_b), a > b Im(x_b conj x_a).
+// One warp per (subarray k, part of the MK^2 packed entries, slice of frames):
+// each lane forms only its part of the exact products x_a conj(x_b) and
+// accumulates them against all MK weights 1/yhat, so no product is formed
+// twice.  x x^H is packed as MK^2 reals R[a*MK+b]: a == b |x_a|^2,
+// a < b Re(x_a conj x_b), a > b Im(x_b conj x_a).  Diagonal entries only add
+// non-negative terms, so their running sum dominates every new term and the
+// cheaper fast two-sum is exact for them.
+template <int MK>
+struct CovCfg {
+  static constexpr int E = MK * MK;
+  static constexpr int PARTS = (MK == 4) ? 2 : 1;  // entry parts per subarray
+  static constexpr int EP = E / PARTS;              // entries per lane
+  static constexpr int C = MK * EP;                 // float-pair accumulators per lane
+  static constexpr int CP = (C + 31) / 32 * 32;
+};
+
+template <int MK>
+__device__ __forceinline__ void exact_entry(const float2 (&xv)[MK], int r, float& hi, float& lo) {
+  const int a = r / MK, b = r % MK;
+  if (a == b) exact_re(xv[a], xv[a], hi, lo);
+  else if (a < b) exact_re(xv[a], xv[b], hi, lo);
+  else exact_im(xv[b], xv[a], hi, lo);
+}
+
+// Accumulate w_q * R[E0 + j] (exact products) for q < MK, j < EP into the pairs.
+template <int MK, int E0, int EP, int CP>
+__device__ __forceinline__ void cov_accumulate_impl(const float2 (&xv)[MK], const float (&w)[MK], float (&ah)[CP],
+                                                    float (&al)[CP]) {
+#pragma unroll
+  for (int j = 0; j < EP; ++j) {
+    const int r = E0 + j;
+    float rh, rl;
+    exact_entry<MK>(xv, r, rh, rl);
+    const bool diag = (r / MK) == (r % MK);
+#pragma unroll
+    for (int q = 0; q < MK; ++q) {
+      const dd p = two_prod(w[q], rh);
+      const float e = __fmaf_rn(w[q], rl, p.lo);
+      const dd s = diag ? quick_two_sum(ah[q * EP + j], p.hi) : two_sum(ah[q * EP + j], p.hi);
+      ah[q * EP + j] = s.hi;
+      al[q * EP + j] = __fadd_rn(al[q * EP + j], __fadd_rn(s.lo, e));
+    }
+  }
+}
+template <int MK, int E0>
+__device__ __forceinline__ void cov_accumulate(const float2 (&xv)[MK], const float (&w)[MK],
+                                               float (&ah)[CovCfg<MK>::CP], float (&al)[CovCfg<MK>::CP]) {
+  cov_accumulate_impl<MK, E0, CovCfg<MK>::EP, CovCfg<MK>::CP>(xv, w, ah, al);
+}
+
+// Frames are staged through shared memory in chunks of CT (x rows and the
+// lambda rows of the frequency), double-buffered with cp.async so that the
+// float-float arithmetic never waits on global memory.
+constexpr int CT = 64;
+
 template <int MK>
 __global__ void __launch_bounds__(256, 2) k_cov(const float2* __restrict__ x, const float* __restrict__ lam,
-                                                const float* __restrict__ g, double2* __restrict__ V, int F,
-                                                int T, int K, int N, float eps) {
-  constexpr int G = (MK == 4) ? 2 : MK;
-  constexpr int NG = MK / G;
-  constexpr int E = MK * MK;
-  constexpr int C = G * E;
-  constexpr int CP = (C + 31) / 32 * 32;
+                                                const float* __restrict__ g, double2* __restrict__ V, float4* __restrict__ Vdd,
+                                                int F, int T, int Tp, int K, int N, float eps) {
+  using Cfg = CovCfg<MK>;
+  constexpr int E = Cfg::E, EP = Cfg::EP, CP = Cfg::CP, PARTS = Cfg::PARTS;
   constexpr int NW = 8;
-  const int f = blockIdx.x;
+  const int f = blockIdx.x, tid = threadIdx.x;
   const int M = K * MK;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int items = K * NG;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int items = K * PARTS;
   const int WPI = (items <= NW) ? NW / items : 1;
   const int nslots = items * WPI;
+  const int maxslots = items <= NW ? NW : items;
   extern __shared__ double smd[];
-  double* part = smd;                                                   // [nslots][CP]
-  float* gs = reinterpret_cast<float*>(smd + (size_t)(items <= NW ? NW : items) * CP);  // [N][M]
-  for (int i = threadIdx.x; i < N * M; i += blockDim.x) gs[i] = g[(size_t)f * N * M + i];
-  __syncthreads();
-  for (int slot = warp; slot < nslots; slot += NW) {
-    const int item = slot / WPI, pid = slot % WPI;
-    const int k = item / NG, mu0 = (item % NG) * G;
-    float ah[CP], al[CP];
+  double* part = smd;                                                      // [maxslots][CP]
+  float2* xs = reinterpret_cast<float2*>(smd + (size_t)maxslots * CP);     // [2][CT][M]
+  float* ls = reinterpret_cast<float*>(xs + 2 * CT * M);                   // [2][N][CT]
+  float* gs = ls + 2 * N * CT;                                             // [N][M]
+  for (int i = tid; i < N * M; i += blockDim.x) gs[i] = g[(size_t)f * N * M + i];
+  const bool vec = (M % 2) == 0;
+  auto issue = [&](int c) {
+    const int t0 = c * CT, nt = min(CT, T - t0), buf = c & 1;
+    const float2* src = x + ((size_t)f * T + t0) * M;
+    float2* dst = xs + (size_t)buf * CT * M;
+    if (vec)
+      for (int i = tid; i < nt * M / 2; i += blockDim.x) cp_async16(dst + 2 * i, src + 2 * i);
+    else
+      for (int i = tid; i < nt * M; i += blockDim.x) {
+        cp_async4(reinterpret_cast<float*>(dst + i), reinterpret_cast<const float*>(src + i));
+        cp_async4(reinterpret_cast<float*>(dst + i) + 1, reinterpret_cast<const float*>(src + i) + 1);
+      }
+    for (int i = tid; i < N * nt; i += blockDim.x) {
+      const int n = i / nt, tt = i % nt;
+      cp_async4(ls + (buf * N + n) * CT + tt, lam + ((size_t)n * F + f) * Tp + t0 + tt);
+    }
+    cp_async_commit();
+  };
+  // every warp owns slots warp, warp + NW, ...; with K <= NW/PARTS a warp owns one slot
+  float ah[CP], al[CP];
+  const int nchunk = (T + CT - 1) / CT;
+  for (int slot0 = 0; slot0 < nslots; slot0 += NW) {
+    const int slot = slot0 + warp;
+    const bool mine = slot < nslots;
+    const int item = mine ? slot / WPI : 0, pid = mine ? slot % WPI : 0;
+    const int k = item / PARTS, e0 = (item % PARTS) * EP;
 #pragma unroll
     for (int i = 0; i < CP; ++i) { ah[i] = 0.f; al[i] = 0.f; }
-    const float* gsk = gs + k * MK + mu0;
-    for (int t = pid * 32 + lane; t < T; t += WPI * 32) {
-      float2 xv[MK];
-      load_block<MK>(x + ((size_t)f * T + t) * M + k * MK, xv);
-      float ys[G];
+    const float* gsk = gs + k * MK;
+    __syncthreads();
+    issue(0);
+    for (int c = 0; c < nchunk; ++c) {
+      if (c + 1 < nchunk) {
+        issue(c + 1);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncthreads();
+      const int nt = min(CT, T - c * CT), buf = c & 1;
+      const float2* xb = xs + (size_t)buf * CT * M;
+      const float* lb = ls + buf * N * CT;
+      if (mine) {
+        for (int tt = pid * 32 + lane; tt < nt; tt += WPI * 32) {
+          float2 xv[MK];
 #pragma unroll
-      for (int q = 0; q < G; ++q) ys[q] = 0.f;
+          for (int q = 0; q < MK; ++q) xv[q] = xb[tt * M + k * MK + q];
+          float ys[MK];
 #pragma unroll
-      for (int n = 0; n < NMAXC; ++n) {
-        if (n < N) {
-          const float l = __ldg(lam + ((size_t)n * F + f) * T + t);
+          for (int q = 0; q < MK; ++q) ys[q] = 0.f;
+          for (int n = 0; n < N; ++n) {
+            const float l = lb[n * CT + tt];
 #pragma unroll
-          for (int q = 0; q < G; ++q) ys[q] = fmaf(l, gsk[n * M + q], ys[q]);
+            for (int q = 0; q < MK; ++q) ys[q] = fmaf(l, gsk[n * M + q], ys[q]);
+          }
+          float w[MK];
+#pragma unroll
+          for (int q = 0; q < MK; ++q) w[q] = fast_rcp(fmaxf(ys[q], eps));
+          if (e0 == 0) cov_accumulate<MK, 0>(xv, w, ah, al);
+          else cov_accumulate<MK, EP>(xv, w, ah, al);
         }
       }
-      float w[G];
-#pragma unroll
-      for (int q = 0; q < G; ++q) w[q] = __frcp_rn(fmaxf(ys[q], eps));
-      float rh[E], rl[E];
-#pragma unroll
-      for (int a = 0; a < MK; ++a) {
-        exact_re(xv[a], xv[a], rh[a * MK + a], rl[a * MK + a]);
-#pragma unroll
-        for (int b = a + 1; b < MK; ++b) {
-          exact_re(xv[a], xv[b], rh[a * MK + b], rl[a * MK + b]);
-          exact_im(xv[a], xv[b], rh[b * MK + a], rl[b * MK + a]);
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < G; ++q)
-#pragma unroll
-        for (int r = 0; r < E; ++r) {
-          const dd p = two_prod(w[q], rh[r]);
-          const float e = __fmaf_rn(w[q], rl[r], p.lo);
-          const dd s = two_sum(ah[q * E + r], p.hi);
-          ah[q * E + r] = s.hi;
-          al[q * E + r] = __fadd_rn(al[q * E + r], __fadd_rn(s.lo, e));
-        }
+      __syncthreads();
     }
     warp_reduce_scatter_dd<CP>(ah, al, lane);
+    if (mine)
 #pragma unroll
-    for (int i = 0; i < CP / 32; ++i)
-      part[slot * CP + lane * (CP / 32) + i] = (double)ah[i] + (double)al[i];
+      for (int i = 0; i < CP / 32; ++i)
+        part[slot * CP + lane * (CP / 32) + i] = (double)ah[i] + (double)al[i];
   }
   __syncthreads();
   const double invT = 1.0 / (double)T;
   const int total = K * MK * E;
-  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+  for (int idx = tid; idx < total; idx += blockDim.x) {
     const int b = idx % MK, a = (idx / MK) % MK, mu = (idx / E) % MK, k = idx / (MK * E);
     const int lo = a < b ? a : b, hi = a < b ? b : a;
-    const int item = k * NG + mu / G, q = mu % G;
+    const int rre = lo * MK + hi, rim = hi * MK + lo;
     double re = 0.0, im = 0.0;
     for (int pid = 0; pid < WPI; ++pid) {
-      const double* pp = part + (item * WPI + pid) * CP + q * E;
-      re += pp[lo * MK + hi];
-      if (lo != hi) im += pp[hi * MK + lo];
+      re += part[((k * PARTS + rre / EP) * WPI + pid) * CP + (rre % EP) + mu * EP];
+      if (lo != hi) im += part[((k * PARTS + rim / EP) * WPI + pid) * CP + (rim % EP) + mu * EP];
     }
     if (a > b) im = -im;
-    V[(size_t)f * total + idx] = make_double2(re * invT, im * invT);
+    re *= invT;
+    im *= invT;
+    V[(size_t)f * total + idx] = make_double2(re, im);
+    const float rh = (float)re, ih = (float)im;
+    Vdd[(size_t)f * total + idx] = make_float4(rh, (float)(re - (double)rh), ih, (float)(im - (double)ih));
   }
 }
 
 cudaError_t launch_cov(const dfmnmf_ctx* c, cudaStream_t s) {
   DFM_MK_DISPATCH(c->MK, {
-    constexpr int G = (MK_ == 4) ? 2 : MK_;
-    constexpr int CP = (G * MK_ * MK_ + 31) / 32 * 32;
-    const int items = c->K * (MK_ / G);
-    const size_t sm = (size_t)(items <= 8 ? 8 : items) * CP * sizeof(double) + (size_t)c->N * c->M * sizeof(float);
+    constexpr int CP = CovCfg<MK_>::CP;
+    const int items = c->K * CovCfg<MK_>::PARTS;
+    const size_t sm = (size_t)(items <= 8 ? 8 : items) * CP * sizeof(double) + 2 * (size_t)CT * c->M * sizeof(float2) +
+                      (2 * (size_t)c->N * CT + (size_t)c->N * c->M) * sizeof(float);
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_cov<MK_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_cov<MK_><<<c->F, 256, sm, s>>>(c->x, c->lam, c->g, c->V, c->F, c->T, c->K, c->N, c->eps);
+    k_cov<MK_><<<c->F, 256, sm, s>>>(c->x, c->lam, c->g, c->V, c->Vdd, c->F, c->T, c->Tp, c->K, c->N, c->eps);
   });
   return cudaGetLastError();
 }

@@ -83,8 +83,30 @@ __device__ void pinv_column(cx<double> (&U)[MK][MK], int mu, double rtol, cx<dou
   }
 }
 
+// V entry as the working type: float pairs come straight from the float-float
+// copy (no FP64 instructions), doubles from the FP64 copy.
+template <class R> struct VLoad;
+template <> struct VLoad<dd> {
+  static __device__ __forceinline__ cx<dd> get(const double2*, const float4* vd, size_t i) {
+    const float4 v = vd[i];
+    return cmake(dd_make(v.x, v.y), dd_make(v.z, v.w));
+  }
+};
+template <> struct VLoad<double> {
+  static __device__ __forceinline__ cx<double> get(const double2* v, const float4*, size_t i) {
+    return cfrom_d2<double>(v[i]);
+  }
+};
+template <> struct VLoad<float> {
+  static __device__ __forceinline__ cx<float> get(const double2*, const float4* vd, size_t i) {
+    const float4 v = vd[i];
+    return cmake(v.x, v.z);
+  }
+};
+
 template <int MK, class R>
-__global__ void __launch_bounds__(128) k_ip(const double2* __restrict__ V, double2* __restrict__ Q64,
+__global__ void __launch_bounds__(128) k_ip(const double2* __restrict__ V, const float4* __restrict__ Vdd,
+                                            double2* __restrict__ Q64,
                                             float2* __restrict__ Q32, int nblocks, float eps, float rtol,
                                             unsigned* __restrict__ flags) {
   using O = RealOps<R>;
@@ -104,7 +126,8 @@ __global__ void __launch_bounds__(128) k_ip(const double2* __restrict__ V, doubl
     else Qb[e] = cmake(i == j ? O::one() : O::zero(), O::zero());
   }
   __syncwarp();
-  const double2* Vb = V + (size_t)(valid ? blk : 0) * E * MK;
+  const size_t vbase = (size_t)(valid ? blk : 0) * E * MK;
+  const double2* Vb = V + vbase;
   auto L = [&](int r, int c) { return sb + r * MK + c; };
 
   for (int mu = 0; mu < MK; ++mu) {
@@ -112,7 +135,7 @@ __global__ void __launch_bounds__(128) k_ip(const double2* __restrict__ V, doubl
     cx<R> a = czero<R>(), vij = czero<R>();
 #pragma unroll
     for (int l = 0; l < MK; ++l) {
-      const cx<R> vlj = cfrom_d2<R>(Vb[mu * E + l * MK + j]);
+      const cx<R> vlj = VLoad<R>::get(V, Vdd, vbase + mu * E + l * MK + j);
       a = cadd(a, cmul(Qb[i * MK + l], vlj));
       if (l == i) vij = vlj;
     }
@@ -303,9 +326,9 @@ cudaError_t launch_ip(const dfmnmf_ctx* c, cudaStream_t s) {
   const int grid = (nblocks + 7) / 8;  // 4 warps x 2 blocks per CTA
   DFM_MK_DISPATCH(c->MK, {
     switch (c->ip_arith) {
-      case 0: k_ip<MK_, double><<<grid, 128, 0, s>>>(c->V, c->Q64, c->Q32, nblocks, c->eps, c->singular_rtol, c->flags); break;
-      case 1: k_ip<MK_, dd><<<grid, 128, 0, s>>>(c->V, c->Q64, c->Q32, nblocks, c->eps, c->singular_rtol, c->flags); break;
-      default: k_ip<MK_, float><<<grid, 128, 0, s>>>(c->V, c->Q64, c->Q32, nblocks, c->eps, c->singular_rtol, c->flags); break;
+      case 0: k_ip<MK_, double><<<grid, 128, 0, s>>>(c->V, c->Vdd, c->Q64, c->Q32, nblocks, c->eps, c->singular_rtol, c->flags); break;
+      case 1: k_ip<MK_, dd><<<grid, 128, 0, s>>>(c->V, c->Vdd, c->Q64, c->Q32, nblocks, c->eps, c->singular_rtol, c->flags); break;
+      default: k_ip<MK_, float><<<grid, 128, 0, s>>>(c->V, c->Vdd, c->Q64, c->Q32, nblocks, c->eps, c->singular_rtol, c->flags); break;
     }
   });
   return cudaGetLastError();

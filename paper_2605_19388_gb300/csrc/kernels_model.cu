@@ -12,221 +12,313 @@
 // round trip through memory.
 #include "common.cuh"
 #include "internal.h"
+#include "../../include/dfmnmf.h"
 
 namespace dfm {
 
-constexpr int NMAXR = 16;  // register bound on N in the per-frame kernels
 
 // ------------------------------------------------------------------ lambda
 __global__ void __launch_bounds__(256) k_lambda(const float* __restrict__ W, const float* __restrict__ H,
-                                                float* __restrict__ lam, int F, int T, int B) {
+                                                float* __restrict__ lam, int F, int T, int Tp, int B) {
   extern __shared__ float ws[];
   const int n = blockIdx.z, f = blockIdx.y;
   const int t = blockIdx.x * 256 + threadIdx.x;
   for (int b = threadIdx.x; b < B; b += 256) ws[b] = W[((size_t)n * F + f) * B + b];
   __syncthreads();
   if (t >= T) return;
-  const float* Hn = H + (size_t)n * B * T + t;
+  const float* Hn = H + (size_t)n * B * Tp + t;
   float s = 0.f;
-  for (int b = 0; b < B; ++b) s = fmaf(ws[b], Hn[(size_t)b * T], s);
-  lam[((size_t)n * F + f) * T + t] = s;
+  for (int b = 0; b < B; ++b) s = fmaf(ws[b], Hn[(size_t)b * Tp], s);
+  lam[((size_t)n * F + f) * Tp + t] = s;
 }
 
 cudaError_t launch_lambda(const dfmnmf_ctx* c, cudaStream_t s) {
   dim3 grid((c->T + 255) / 256, c->F, c->N);
-  k_lambda<<<grid, 256, c->B * sizeof(float), s>>>(c->W, c->H, c->lam, c->F, c->T, c->B);
+  k_lambda<<<grid, 256, c->B * sizeof(float), s>>>(c->W, c->H, c->lam, c->F, c->T, c->Tp, c->B);
   return cudaGetLastError();
 }
 
 // --------------------------------------------------- projected power + stats
-// Thread per frame t: P for all M microphones (when COMPUTE_P) or read back,
-// then A[n][f][t] = sum_m g P yhat^-2 and D[n][f][t] = sum_m g yhat^-1.
-template <int MK, bool COMPUTE_P>
-__global__ void __launch_bounds__(128) k_pstats(const float2* __restrict__ x, const double2* __restrict__ Q64,
+// Thread per (frame t, subarray k).  The thread projects x_ftk (when
+// COMPUTE_P: compensated dot products when COMP, plain FP32 otherwise) or
+// reads P back, rebuilds yhat for its M_k microphones, and forms its
+// subarray's share of A[n][f][t] = sum_m g P yhat^-2 and
+// D[n][f][t] = sum_m g yhat^-1 one source at a time (g rows as vector loads
+// from shared memory), so nothing is padded to a maximum source count.  The
+// K shares of a frame sit in adjacent lanes and are added by xor shuffles
+// (K a power of two) or through shared memory.
+template <int MK>
+__device__ __forceinline__ void load_row(const float* p, float (&v)[MK]) {
+  if constexpr (MK == 4) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2 % MK] = q.z; v[3 % MK] = q.w;
+  } else {
+#pragma unroll
+    for (int i = 0; i < MK; ++i) v[i] = p[i];
+  }
+}
+
+template <int MK, bool COMPUTE_P, bool COMP>
+__global__ void __launch_bounds__(256) k_pstats(const float2* __restrict__ x, const double2* __restrict__ Q64,
                                                 const float* __restrict__ lam, const float* __restrict__ g,
                                                 float* __restrict__ P, float* __restrict__ A,
-                                                float* __restrict__ D, int F, int T, int K, int N, float eps) {
-  extern __shared__ float sm[];
+                                                float* __restrict__ D, int F, int T, int Tp, int K, int N, float eps) {
+  extern __shared__ __align__(16) float sm[];
+  const int f = blockIdx.x, tid = threadIdx.x;
   const int M = K * MK;
-  const int f = blockIdx.x;
-  float* gs = sm;                                            // [N][M]
-  float2* Qh = reinterpret_cast<float2*>(sm + ((N * M + 1) & ~1));  // [K][MK][MK] high parts
-  float2* Ql = Qh + K * MK * MK;                                      // low parts
-  for (int i = threadIdx.x; i < N * M; i += blockDim.x) gs[i] = g[(size_t)f * N * M + i];
+  const int TB = blockDim.x / K;
+  const int k = tid % K, tl = tid / K;
+  const int t = blockIdx.y * TB + tl;
+  const bool valid = tl < TB && t < T;
+  const bool pow2 = (K & (K - 1)) == 0;
+  float* gs = sm;                                                  // [N][M]
+  const int qoff = (N * M + 3) & ~3;
+  float2* Qh = reinterpret_cast<float2*>(sm + qoff);               // [K][MK][MK] high parts
+  float2* Ql = Qh + K * MK * MK;                                   // low parts
+  float* red = sm + qoff + (COMPUTE_P ? 4 * K * MK * MK : 0);      // [TB][K][2] when K is not a power of two
+  for (int i = tid; i < N * M; i += blockDim.x) gs[i] = g[(size_t)f * N * M + i];
   if (COMPUTE_P)
-    for (int i = threadIdx.x; i < K * MK * MK; i += blockDim.x) split_c(Q64[(size_t)f * K * MK * MK + i], Qh[i], Ql[i]);
+    for (int i = tid; i < K * MK * MK; i += blockDim.x) split_c(Q64[(size_t)f * K * MK * MK + i], Qh[i], Ql[i]);
   __syncthreads();
-  const int t = blockIdx.y * blockDim.x + threadIdx.x;
-  if (t >= T) return;
-  float lr[NMAXR], accA[NMAXR], accD[NMAXR];
-#pragma unroll
-  for (int n = 0; n < NMAXR; ++n) {
-    lr[n] = (n < N) ? __ldg(lam + ((size_t)n * F + f) * T + t) : 0.f;
-    accA[n] = 0.f;
-    accD[n] = 0.f;
-  }
-  float* Pt = P + ((size_t)f * T + t) * M;
-  for (int k = 0; k < K; ++k) {
-    float pv[MK];
-    if (COMPUTE_P) {
-      float2 xv[MK];
-      load_block<MK>(x + ((size_t)f * T + t) * M + k * MK, xv);
-#pragma unroll
-      for (int mu = 0; mu < MK; ++mu) {
-        const float2 y = cdot2<MK>(Qh + (k * MK + mu) * MK, Ql + (k * MK + mu) * MK, xv);
-        pv[mu] = fmaf(y.x, y.x, y.y * y.y);
-      }
-      if constexpr (MK == 4) {
-        *reinterpret_cast<float4*>(Pt + k * MK) = make_float4(pv[0], pv[1], pv[2], pv[3]);
-      } else {
-#pragma unroll
-        for (int mu = 0; mu < MK; ++mu) Pt[k * MK + mu] = pv[mu];
-      }
-    } else {
-      if constexpr (MK == 4) {
-        const float4 q = *reinterpret_cast<const float4*>(Pt + k * MK);
-        pv[0] = q.x; pv[1] = q.y; pv[2] = q.z; pv[3] = q.w;
-      } else {
-#pragma unroll
-        for (int mu = 0; mu < MK; ++mu) pv[mu] = Pt[k * MK + mu];
-      }
-    }
+  const int tc = valid ? t : 0;
+  float pv[MK];
+  float* Pt = P + ((size_t)f * T + tc) * M + k * MK;
+  if (COMPUTE_P) {
+    float2 xv[MK];
+    load_block<MK>(x + ((size_t)f * T + tc) * M + k * MK, xv);
 #pragma unroll
     for (int mu = 0; mu < MK; ++mu) {
-      const int m = k * MK + mu;
-      float ys = 0.f;
+      const float2* qh = Qh + (k * MK + mu) * MK;
+      float2 y;
+      if (COMP) {
+        y = cdot2<MK>(qh, Ql + (k * MK + mu) * MK, xv);
+      } else {
+        float yr = 0.f, yi = 0.f;
 #pragma unroll
-      for (int n = 0; n < NMAXR; ++n)
-        if (n < N) ys = fmaf(lr[n], gs[n * M + m], ys);
-      const float w = __frcp_rn(fmaxf(ys, eps));
-      const float u = pv[mu] * w * w;
-#pragma unroll
-      for (int n = 0; n < NMAXR; ++n) {
-        if (n < N) {
-          const float gn = gs[n * M + m];
-          accA[n] = fmaf(gn, u, accA[n]);
-          accD[n] = fmaf(gn, w, accD[n]);
+        for (int nu = 0; nu < MK; ++nu) {
+          yr = fmaf(qh[nu].x, xv[nu].x, fmaf(-qh[nu].y, xv[nu].y, yr));
+          yi = fmaf(qh[nu].x, xv[nu].y, fmaf(qh[nu].y, xv[nu].x, yi));
         }
+        y = make_float2(yr, yi);
+      }
+      pv[mu] = fmaf(y.x, y.x, y.y * y.y);
+    }
+    if (valid) {
+      if constexpr (MK == 4) {
+        *reinterpret_cast<float4*>(Pt) = make_float4(pv[0], pv[1], pv[2], pv[3]);
+      } else {
+#pragma unroll
+        for (int mu = 0; mu < MK; ++mu) Pt[mu] = pv[mu];
       }
     }
+  } else {
+    load_row<MK>(Pt, pv);
   }
+  // yhat for the subarray's microphones
+  float ys[MK];
 #pragma unroll
-  for (int n = 0; n < NMAXR; ++n) {
-    if (n < N) {
-      A[((size_t)n * F + f) * T + t] = accA[n];
-      D[((size_t)n * F + f) * T + t] = accD[n];
+  for (int mu = 0; mu < MK; ++mu) ys[mu] = 0.f;
+  const float* lt = lam + (size_t)f * Tp + tc;
+  for (int n = 0; n < N; ++n) {
+    const float l = __ldg(lt + (size_t)n * F * Tp);
+    float gv[MK];
+    load_row<MK>(gs + n * M + k * MK, gv);
+#pragma unroll
+    for (int mu = 0; mu < MK; ++mu) ys[mu] = fmaf(l, gv[mu], ys[mu]);
+  }
+  float w[MK], u[MK];
+#pragma unroll
+  for (int mu = 0; mu < MK; ++mu) {
+    w[mu] = fast_rcp(fmaxf(ys[mu], eps));
+    u[mu] = pv[mu] * w[mu] * w[mu];
+  }
+  for (int n = 0; n < N; ++n) {
+    float gv[MK];
+    load_row<MK>(gs + n * M + k * MK, gv);
+    float a = 0.f, d = 0.f;
+#pragma unroll
+    for (int mu = 0; mu < MK; ++mu) {
+      a = fmaf(gv[mu], u[mu], a);
+      d = fmaf(gv[mu], w[mu], d);
+    }
+    const size_t o = ((size_t)n * F + f) * Tp + tc;
+    if (pow2) {
+      for (int s = 1; s < K; s <<= 1) {
+        a += __shfl_xor_sync(DFM_FULL_MASK, a, s);
+        d += __shfl_xor_sync(DFM_FULL_MASK, d, s);
+      }
+      if (valid && k == 0) {
+        A[o] = a;
+        D[o] = d;
+      }
+    } else {
+      __syncthreads();
+      if (tl < TB) {
+        red[(tl * K + k) * 2] = a;
+        red[(tl * K + k) * 2 + 1] = d;
+      }
+      __syncthreads();
+      if (valid && k == 0) {
+        float sa = 0.f, sd = 0.f;
+        for (int kk = 0; kk < K; ++kk) {
+          sa += red[(tl * K + kk) * 2];
+          sd += red[(tl * K + kk) * 2 + 1];
+        }
+        A[o] = sa;
+        D[o] = sd;
+      }
     }
   }
 }
 
 // ------------------------------------------------------------------ g update
-// One warp per (subarray k, n-chunk of NC sources, t slice); registers hold
-// the 2 x NC x MK partial numerators / denominators of Eq. (10).
-template <int MK>
+// One CTA per frequency.  Frames arrive in chunks of GT through a
+// double-buffered cp.async pipeline (lambda rows and the [t][m] block of P);
+// thread (slice s, microphone m) keeps g[f][:][m] and the 2 N partial sums of
+// Eq. (10) in registers, and the slices are added in a fixed order at the end.
+constexpr int GT = 128;
+
+// NM is N itself for N <= 8 (no padded work) and 16 (guarded) above.
+template <int NM>
 __global__ void __launch_bounds__(256) k_gupd(const float* __restrict__ lam, const float* __restrict__ P,
-                                              float* __restrict__ g, int F, int T, int K, int N, float eps,
+                                              float* __restrict__ g, int F, int T, int Tp, int M, int N, float eps,
                                               unsigned* __restrict__ flags) {
-  constexpr int NC = 8;
-  constexpr int C = 2 * NC * MK;
-  constexpr int CP = (C + 31) / 32 * 32;
-  constexpr int NW = 8;
-  const int f = blockIdx.x;
-  const int M = K * MK;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  extern __shared__ float sm[];
-  float* gs = sm;            // [N][M]
-  float* part = sm + N * M;  // [slots][CP]
-  for (int i = threadIdx.x; i < N * M; i += blockDim.x) gs[i] = g[(size_t)f * N * M + i];
-  __syncthreads();
-  const int nchunks = (N + NC - 1) / NC;
-  const int items = K * nchunks;
-  const int WPI = (items <= NW) ? NW / items : 1;
-  const int nslots = items * WPI;
-  for (int slot = warp; slot < nslots; slot += NW) {
-    const int item = slot / WPI, pid = slot % WPI;
-    const int k = item / nchunks;
-    const bool upper = (item % nchunks) != 0;
-    float acc[CP];
+  extern __shared__ __align__(16) float smg[];
+  const int f = blockIdx.x, tid = threadIdx.x;
+  const int S = blockDim.x / M;            // frame slices
+  const int m = tid % M, s = tid / M;
+  const bool active = s < S;
+  float* ls = smg;                         // [2][N][GT]
+  float* ps = ls + 2 * N * GT;             // [2][GT][M]
+  float* red = ps + 2 * GT * M;            // [S][M][2N]
+  const bool vec = (M % 4) == 0;
+  auto issue = [&](int c) {
+    const int t0 = c * GT, nt = min(GT, T - t0), buf = c & 1;
+    for (int i = tid; i < N * nt; i += blockDim.x) {
+      const int n = i / nt, tt = i % nt;
+      cp_async4(ls + (buf * N + n) * GT + tt, lam + ((size_t)n * F + f) * Tp + t0 + tt);
+    }
+    const float* src = P + ((size_t)f * T + t0) * M;
+    float* dst = ps + (size_t)buf * GT * M;
+    if (vec)
+      for (int i = tid; i < nt * M / 4; i += blockDim.x) cp_async16(dst + 4 * i, src + 4 * i);
+    else
+      for (int i = tid; i < nt * M; i += blockDim.x) cp_async4(dst + i, src + i);
+    cp_async_commit();
+  };
+  float gr[NM], num[NM], den[NM];
 #pragma unroll
-    for (int i = 0; i < CP; ++i) acc[i] = 0.f;
-    for (int t = pid * 32 + lane; t < T; t += WPI * 32) {
-      float lr[NMAXR];
-#pragma unroll
-      for (int n = 0; n < NMAXR; ++n) lr[n] = (n < N) ? __ldg(lam + ((size_t)n * F + f) * T + t) : 0.f;
-      const float* Pt = P + ((size_t)f * T + t) * M + k * MK;
-#pragma unroll
-      for (int mu = 0; mu < MK; ++mu) {
-        const int m = k * MK + mu;
+  for (int n = 0; n < NM; ++n) {
+    gr[n] = (active && n < N) ? g[((size_t)f * N + n) * M + m] : 0.f;
+    num[n] = 0.f;
+    den[n] = 0.f;
+  }
+  const int nchunk = (T + GT - 1) / GT;
+  issue(0);
+  for (int c = 0; c < nchunk; ++c) {
+    if (c + 1 < nchunk) {
+      issue(c + 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const int nt = min(GT, T - c * GT), buf = c & 1;
+    const float* lb = ls + buf * N * GT;
+    const float* pb = ps + (size_t)buf * GT * M;
+    if (active) {
+      for (int tt = s; tt < nt; tt += S) {
+        float l[NM];
         float ys = 0.f;
 #pragma unroll
-        for (int n = 0; n < NMAXR; ++n)
-          if (n < N) ys = fmaf(lr[n], gs[n * M + m], ys);
-        const float w = __frcp_rn(fmaxf(ys, eps));
-        const float u = __ldg(Pt + mu) * w * w;
+        for (int n = 0; n < NM; ++n) {
+          l[n] = (NM <= 8 || n < N) ? lb[n * GT + tt] : 0.f;
+          ys = fmaf(l[n], gr[n], ys);
+        }
+        const float w = fast_rcp(fmaxf(ys, eps));
+        const float u = pb[tt * M + m] * w * w;
 #pragma unroll
-        for (int j = 0; j < NC; ++j) {
-          // n0 is 0 or NC (N <= 2 NC): both branches index registers statically
-          const float l = upper ? lr[NC + j] : lr[j];
-          acc[(j * MK + mu) * 2 + 0] = fmaf(l, u, acc[(j * MK + mu) * 2 + 0]);
-          acc[(j * MK + mu) * 2 + 1] = fmaf(l, w, acc[(j * MK + mu) * 2 + 1]);
+        for (int n = 0; n < NM; ++n) {
+          num[n] = fmaf(l[n], u, num[n]);
+          den[n] = fmaf(l[n], w, den[n]);
         }
       }
     }
-    warp_reduce_scatter<CP>(acc, lane);
-#pragma unroll
-    for (int i = 0; i < CP / 32; ++i) part[slot * CP + lane * (CP / 32) + i] = acc[i];
+    __syncthreads();
   }
+  if (active)
+#pragma unroll
+    for (int n = 0; n < NM; ++n)
+      if (n < N) {
+        red[(s * M + m) * 2 * N + 2 * n] = num[n];
+        red[(s * M + m) * 2 * N + 2 * n + 1] = den[n];
+      }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < N * M; idx += blockDim.x) {
-    const int n = idx / M, m = idx % M;
-    const int k = m / MK, mu = m % MK;
-    const int item = k * nchunks + n / NC, j = n % NC;
-    float num = 0.f, den = 0.f;
-    for (int pid = 0; pid < WPI; ++pid) {
-      const float* pp = part + (item * WPI + pid) * CP;
-      num += pp[(j * MK + mu) * 2 + 0];
-      den += pp[(j * MK + mu) * 2 + 1];
+  for (int i = tid; i < N * M; i += blockDim.x) {
+    const int n = i / M, mm = i % M;
+    float a = 0.f, d = 0.f;
+    for (int q = 0; q < S; ++q) {
+      a += red[(q * M + mm) * 2 * N + 2 * n];
+      d += red[(q * M + mm) * 2 * N + 2 * n + 1];
     }
-    const float gnew = gs[idx] * sqrtf(num / fmaxf(den, eps));
+    const size_t gi = ((size_t)f * N + n) * M + mm;
+    const float gnew = g[gi] * sqrtf(a / fmaxf(d, eps));
     if (!finitef(gnew)) atomicOr(flags + FLAG_NONFINITE, 1u);
-    g[(size_t)f * N * M + idx] = gnew;
+    g[gi] = gnew;
   }
 }
 
 // ----------------------------------------------------------------- launchers
 
-static size_t pstats_smem(const dfmnmf_ctx* c) {
-  return (size_t)((c->N * c->M + 1) & ~1) * sizeof(float) + 2 * (size_t)c->K * c->MK * c->MK * sizeof(float2);
+// Dispatch on the register bound of N (4, 8 or 16) as NM_.
+#define DFM_NM_DISPATCH(NV, ...)                                  \
+  if ((NV) <= 4) { constexpr int NM_ = 4; __VA_ARGS__; }          \
+  else if ((NV) <= 8) { constexpr int NM_ = 8; __VA_ARGS__; }     \
+  else { constexpr int NM_ = 16; __VA_ARGS__; }
+
+template <bool COMPUTE_P, bool COMP>
+static cudaError_t launch_pstats_impl(const dfmnmf_ctx* c, cudaStream_t s) {
+  const int TB = 256 / c->K;
+  dim3 grid(c->F, (c->T + TB - 1) / TB);
+  const bool pow2 = (c->K & (c->K - 1)) == 0;
+  const size_t sm = (size_t)((c->N * c->M + 3) & ~3) * sizeof(float) +
+                    (COMPUTE_P ? 4 * (size_t)c->K * c->MK * c->MK * sizeof(float) : 0) +
+                    (pow2 ? 0 : (size_t)TB * c->K * 2 * sizeof(float));
+  DFM_MK_DISPATCH(c->MK, {
+    auto kern = k_pstats<MK_, COMPUTE_P, COMP>;
+    if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    kern<<<grid, 256, sm, s>>>(c->x, c->Q64, c->lam, c->g, c->P, c->A, c->D, c->F, c->T, c->Tp, c->K, c->N, c->eps);
+  });
+  return cudaGetLastError();
 }
 
 cudaError_t launch_power_stats(const dfmnmf_ctx* c, cudaStream_t s) {
-  dim3 grid(c->F, (c->T + 127) / 128);
-  DFM_MK_DISPATCH(c->MK, {
-    k_pstats<MK_, true><<<grid, 128, pstats_smem(c), s>>>(c->x, c->Q64, c->lam, c->g, c->P, c->A, c->D, c->F,
-                                                         c->T, c->K, c->N, c->eps);
-  });
-  return cudaGetLastError();
+  return c->precision == DFMNMF_FP32 ? launch_pstats_impl<true, true>(c, s) : launch_pstats_impl<true, false>(c, s);
 }
 
-cudaError_t launch_stats(const dfmnmf_ctx* c, cudaStream_t s) {
-  dim3 grid(c->F, (c->T + 127) / 128);
-  DFM_MK_DISPATCH(c->MK, {
-    k_pstats<MK_, false><<<grid, 128, pstats_smem(c), s>>>(c->x, c->Q64, c->lam, c->g, c->P, c->A, c->D, c->F,
-                                                          c->T, c->K, c->N, c->eps);
-  });
-  return cudaGetLastError();
-}
+cudaError_t launch_stats(const dfmnmf_ctx* c, cudaStream_t s) { return launch_pstats_impl<false, false>(c, s); }
 
 cudaError_t launch_gupd(const dfmnmf_ctx* c, cudaStream_t s) {
-  DFM_MK_DISPATCH(c->MK, {
-    constexpr int CP = (2 * 8 * MK_ + 31) / 32 * 32;
-    const int nchunks = (c->N + 7) / 8;
-    const int items = c->K * nchunks;
-    const int slots = items <= 8 ? 8 : items;
-    const size_t sm = (size_t)(c->N * c->M + slots * CP) * sizeof(float);
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_gupd<MK_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_gupd<MK_><<<c->F, 256, sm, s>>>(c->lam, c->P, c->g, c->F, c->T, c->K, c->N, c->eps, c->flags);
-  });
+  const int M = c->M, N = c->N;
+  const int S = 256 / M;
+  const size_t sm = (size_t)(2 * N * GT + 2 * GT * M + S * M * 2 * N) * sizeof(float);
+#define DFM_GUPD(NMV)                                                                                          \
+  {                                                                                                            \
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_gupd<NMV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+    k_gupd<NMV><<<c->F, 256, sm, s>>>(c->lam, c->P, c->g, c->F, c->T, c->Tp, M, N, c->eps, c->flags);                 \
+  }
+  switch (N) {
+    case 1: DFM_GUPD(1) break;
+    case 2: DFM_GUPD(2) break;
+    case 3: DFM_GUPD(3) break;
+    case 4: DFM_GUPD(4) break;
+    case 5: DFM_GUPD(5) break;
+    case 6: DFM_GUPD(6) break;
+    case 7: DFM_GUPD(7) break;
+    case 8: DFM_GUPD(8) break;
+    default: DFM_GUPD(16) break;
+  }
+#undef DFM_GUPD
   return cudaGetLastError();
 }
 

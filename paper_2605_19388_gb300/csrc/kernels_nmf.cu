@@ -17,45 +17,103 @@ namespace dfm {
 constexpr int TILE = 16;  // f (Eq. 8) or t (Eq. 9) per CTA, and b per CTA
 constexpr int NWARP = 8;
 constexpr int KCH = 64;   // reduction chunk staged in shared memory
+constexpr int NMF_MAX_SPLIT = 8;
+
+// Split-reduction epilogue shared by k_wupd / k_hupd.  Thread tid holds the
+// CTA's partial (num, den) of one output.  With S > 1 the partial is written
+// to part[tile][split][tid], and the CTA that takes the last ticket of the
+// tile returns true with the S partials summed in split order; the others
+// return false.  The ticket is reset for the next launch.
+__device__ __forceinline__ bool split_fixup(float& num, float& den, int S, int split, int tile,
+                                            float* __restrict__ part, unsigned* __restrict__ ticket) {
+  if (S == 1) return true;
+  __shared__ unsigned last;
+  float2* p = reinterpret_cast<float2*>(part) + ((size_t)tile * S) * 256;
+  p[(size_t)split * 256 + threadIdx.x] = make_float2(num, den);
+  __syncthreads();  // the CTA's partials are written ...
+  if (threadIdx.x == 0) {
+    __threadfence();  // ... and released at device scope before the ticket is taken
+    last = (atomicAdd(ticket + tile, 1u) == (unsigned)(S - 1));
+    if (last) __threadfence();  // acquire the other CTAs' partials
+  }
+  __syncthreads();
+  if (!last) return false;
+  num = 0.f;
+  den = 0.f;
+  for (int q = 0; q < S; ++q) {
+    const float2 v = __ldcg(p + (size_t)q * 256 + threadIdx.x);
+    num += v.x;
+    den += v.y;
+  }
+  if (threadIdx.x == 0) ticket[tile] = 0u;
+  return true;
+}
 
 // ------------------------------------------------------------------ Eq. (8)
-// grid (ceil(F/16), N, ceil(B/16)); 8 warps split T; lane = (f pair, b quad).
+// grid (ceil(F/16), N, ceil(B/16) * S); the S CTAs of a tile split the frames
+// (chunks of 64), 8 warps split each chunk; lane = (f pair, b quad).  A, D
+// and H tiles are read one chunk ahead into registers as float4 rows (the
+// padded row stride Tp is a multiple of 4) and stored transposed ([t][f],
+// [t][b]) after the current chunk is consumed.  Every CTA writes its partial
+// sums; the last CTA of a tile (counted with an atomic ticket) adds the S
+// partials in a fixed order, updates W and refreshes lambda.  Nothing waits
+// on another CTA.
 __global__ void __launch_bounds__(256) k_wupd(const float* __restrict__ A, const float* __restrict__ D,
                                               const float* __restrict__ H, float* __restrict__ W,
-                                              float* __restrict__ lam, int F, int T, int B, float eps,
-                                              int refresh, unsigned* __restrict__ flags) {
-  constexpr int AS = 18;  // padded row (floats) of the [t][f] staging tiles: 8-byte aligned pairs
-  constexpr int HS = 20;  // padded row of the [t][b] tile: 16-byte aligned quads
-  __shared__ __align__(16) float As[KCH * AS];
-  __shared__ __align__(16) float Ds[KCH * AS];
-  __shared__ __align__(16) float Hs[KCH * HS];
+                                              float* __restrict__ lam, int F, int T, int Tp, int B, float eps,
+                                              int refresh, unsigned* __restrict__ flags, int S, int cps,
+                                              float* __restrict__ part, unsigned* __restrict__ ticket) {
+  constexpr int TS = 20;  // padded row of the transposed tiles: conflict-free stores, 16-byte rows
+  constexpr int STAGE = 3 * KCH * TS;
+  __shared__ __align__(16) float stg[STAGE];
   __shared__ float red[NWARP * 32 * 16];
   __shared__ float Wn[TILE * TILE];
-  const int f0 = blockIdx.x * TILE, n = blockIdx.y, b0 = blockIdx.z * TILE;
+  const int nb = (B + TILE - 1) / TILE;
+  const int bt = blockIdx.z % nb, split = blockIdx.z / nb;
+  const int f0 = blockIdx.x * TILE, n = blockIdx.y, b0 = bt * TILE;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int fp = lane >> 2, bq = lane & 3;
-  const float* An = A + (size_t)n * F * T;
-  const float* Dn = D + (size_t)n * F * T;
-  const float* Hn = H + (size_t)n * B * T;
+  const float* An = A + (size_t)n * F * Tp;
+  const float* Dn = D + (size_t)n * F * Tp;
+  const float* Hn = H + (size_t)n * B * Tp;
+  float* As = stg;
+  float* Ds = As + KCH * TS;
+  float* Hs = Ds + KCH * TS;
+  const int r = tid % TILE, q = tid / TILE;  // row of the tile, float4 column of the chunk
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  auto fetch = [&](int c, float4& a4, float4& d4, float4& h4) {
+    const int t = c * KCH + 4 * q;
+    const int f = f0 + r, b = b0 + r;
+    const bool tin = t < Tp;
+    a4 = (tin && f < F) ? __ldg(reinterpret_cast<const float4*>(An + (size_t)f * Tp + t)) : z4;
+    d4 = (tin && f < F) ? __ldg(reinterpret_cast<const float4*>(Dn + (size_t)f * Tp + t)) : z4;
+    h4 = (tin && b < B) ? __ldg(reinterpret_cast<const float4*>(Hn + (size_t)b * Tp + t)) : z4;
+  };
+  auto store = [&](const float4& a4, const float4& d4, const float4& h4) {
+    const float av[4] = {a4.x, a4.y, a4.z, a4.w}, dv[4] = {d4.x, d4.y, d4.z, d4.w}, hv[4] = {h4.x, h4.y, h4.z, h4.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      As[(4 * q + j) * TS + r] = av[j];
+      Ds[(4 * q + j) * TS + r] = dv[j];
+      Hs[(4 * q + j) * TS + r] = hv[j];
+    }
+  };
   float acc[16];
 #pragma unroll
   for (int i = 0; i < 16; ++i) acc[i] = 0.f;
-  for (int t0 = 0; t0 < T; t0 += KCH) {
-    for (int idx = tid; idx < TILE * KCH; idx += 256) {
-      const int tt = idx % KCH, r = idx / KCH;
-      const int t = t0 + tt;
-      const int f = f0 + r, b = b0 + r;
-      As[tt * AS + r] = (t < T && f < F) ? An[(size_t)f * T + t] : 0.f;
-      Ds[tt * AS + r] = (t < T && f < F) ? Dn[(size_t)f * T + t] : 0.f;
-      Hs[tt * HS + r] = (t < T && b < B) ? Hn[(size_t)b * T + t] : 0.f;
-    }
+  const int c0 = split * cps, c1 = min((T + KCH - 1) / KCH, c0 + cps);
+  float4 pa, pd, ph;
+  if (c0 < c1) fetch(c0, pa, pd, ph);
+  for (int c = c0; c < c1; ++c) {
+    store(pa, pd, ph);
     __syncthreads();
+    if (c + 1 < c1) fetch(c + 1, pa, pd, ph);
 #pragma unroll
     for (int s = 0; s < KCH / NWARP; ++s) {
       const int tt = warp * (KCH / NWARP) + s;
-      const float2 a2 = *reinterpret_cast<const float2*>(As + tt * AS + 2 * fp);
-      const float2 d2 = *reinterpret_cast<const float2*>(Ds + tt * AS + 2 * fp);
-      const float4 h4 = *reinterpret_cast<const float4*>(Hs + tt * HS + 4 * bq);
+      const float2 a2 = *reinterpret_cast<const float2*>(As + tt * TS + 2 * fp);
+      const float2 d2 = *reinterpret_cast<const float2*>(Ds + tt * TS + 2 * fp);
+      const float4 h4 = *reinterpret_cast<const float4*>(Hs + tt * TS + 4 * bq);
       const float av[2] = {a2.x, a2.y}, dv[2] = {d2.x, d2.y}, hv[4] = {h4.x, h4.y, h4.z, h4.w};
 #pragma unroll
       for (int i = 0; i < 2; ++i)
@@ -80,6 +138,7 @@ __global__ void __launch_bounds__(256) k_wupd(const float* __restrict__ A, const
       num += red[(w * 32 + l) * 16 + slot + 0];
       den += red[(w * 32 + l) * 16 + slot + 1];
     }
+    if (!split_fixup(num, den, S, split, (n * gridDim.x + blockIdx.x) * nb + bt, part, ticket)) return;
     const int f = f0 + fi, b = b0 + bi;
     float wn = 0.f;
     if (f < F && b < B) {
@@ -92,52 +151,97 @@ __global__ void __launch_bounds__(256) k_wupd(const float* __restrict__ A, const
   }
   if (!refresh) return;
   __syncthreads();
-  // lambda[n][f][t] = sum_b Wn[f][b] H[b][t] for the 16 rows of this CTA (B <= 16 here)
-  for (int t = tid; t < T; t += 256) {
-    float hv[TILE];
+  // lambda[n][f][t] = sum_b Wn[f][b] H[b][t] for the 16 rows of this CTA (B <= 16 here), 4 frames per thread
+  for (int t = 4 * tid; t < T; t += 4 * 256) {
+    float4 hv[TILE];
 #pragma unroll
-    for (int b = 0; b < TILE; ++b) hv[b] = (b < B) ? __ldg(Hn + (size_t)b * T + t) : 0.f;
+    for (int b = 0; b < TILE; ++b) hv[b] = (b < B) ? __ldg(reinterpret_cast<const float4*>(Hn + (size_t)b * Tp + t)) : z4;
 #pragma unroll 4
     for (int fi = 0; fi < TILE; ++fi) {
       const int f = f0 + fi;
       if (f >= F) break;
-      float s = 0.f;
+      float4 s4 = z4;
 #pragma unroll
-      for (int b = 0; b < TILE; ++b) s = fmaf(Wn[fi * TILE + b], hv[b], s);
-      lam[((size_t)n * F + f) * T + t] = s;
+      for (int b = 0; b < TILE; ++b) {
+        const float wv = Wn[fi * TILE + b];
+        s4.x = fmaf(wv, hv[b].x, s4.x);
+        s4.y = fmaf(wv, hv[b].y, s4.y);
+        s4.z = fmaf(wv, hv[b].z, s4.z);
+        s4.w = fmaf(wv, hv[b].w, s4.w);
+      }
+      float* lp = lam + ((size_t)n * F + f) * Tp + t;
+      if (t + 3 < T) {
+        *reinterpret_cast<float4*>(lp) = s4;
+      } else {
+        const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
+        for (int j = 0; j < 4 && t + j < T; ++j) lp[j] = sv[j];
+      }
     }
   }
 }
 
 // ------------------------------------------------------------------ Eq. (9)
-// grid (ceil(T/16), N, ceil(B/16)); 8 warps split F; lane = (t pair, b quad).
+// grid (ceil(T/16), N, ceil(B/16) * S); the S CTAs of a tile split the
+// frequencies (chunks of 64) and finish as in k_wupd; lane = (t pair, b quad).
+// A, D (row stride Tp) and W (rows of B) tiles arrive by 16-byte cp.async in
+// their natural [f][t] / [f][b] layouts, double-buffered.
 __global__ void __launch_bounds__(256) k_hupd(const float* __restrict__ A, const float* __restrict__ D,
                                               const float* __restrict__ W, float* __restrict__ H,
-                                              float* __restrict__ lam, int F, int T, int B, float eps,
-                                              int refresh, unsigned* __restrict__ flags) {
-  __shared__ __align__(16) float As[KCH * TILE];
-  __shared__ __align__(16) float Ds[KCH * TILE];
-  __shared__ __align__(16) float Ws[KCH * TILE];
+                                              float* __restrict__ lam, int F, int T, int Tp, int B, float eps,
+                                              int refresh, unsigned* __restrict__ flags, int S, int cps,
+                                              float* __restrict__ part, unsigned* __restrict__ ticket) {
+  constexpr int STAGE = 3 * KCH * TILE;
+  __shared__ __align__(16) float stg[2 * STAGE];
   __shared__ float red[NWARP * 32 * 16];
   __shared__ float Hn_s[TILE * TILE];  // [b][t]
-  const int t0 = blockIdx.x * TILE, n = blockIdx.y, b0 = blockIdx.z * TILE;
+  const int nb = (B + TILE - 1) / TILE;
+  const int bt = blockIdx.z % nb, split = blockIdx.z / nb;
+  const int t0 = blockIdx.x * TILE, n = blockIdx.y, b0 = bt * TILE;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tp = lane >> 2, bq = lane & 3;
-  const float* An = A + (size_t)n * F * T;
-  const float* Dn = D + (size_t)n * F * T;
+  const float* An = A + (size_t)n * F * Tp;
+  const float* Dn = D + (size_t)n * F * Tp;
   const float* Wg = W + (size_t)n * F * B;
+  const bool wvec = (B % 4) == 0;
+  auto issue = [&](int ch) {
+    float* As = stg + (ch & 1) * STAGE;
+    float* Ds = As + KCH * TILE;
+    float* Ws = Ds + KCH * TILE;
+    const int fc = ch * KCH;
+    const int fi = tid / 4, q = tid % 4;  // 64 rows x 4 float4
+    const int f = fc + fi, t = t0 + 4 * q, b = b0 + 4 * q;
+    if (f < F && t < Tp) {
+      cp_async16(As + fi * TILE + 4 * q, An + (size_t)f * Tp + t);
+      cp_async16(Ds + fi * TILE + 4 * q, Dn + (size_t)f * Tp + t);
+    } else {
+      *reinterpret_cast<float4*>(As + fi * TILE + 4 * q) = make_float4(0.f, 0.f, 0.f, 0.f);
+      *reinterpret_cast<float4*>(Ds + fi * TILE + 4 * q) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (wvec && f < F && b + 3 < B) {
+      cp_async16(Ws + fi * TILE + 4 * q, Wg + (size_t)f * B + b);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        Ws[fi * TILE + 4 * q + j] = (f < F && b + j < B) ? Wg[(size_t)f * B + b + j] : 0.f;
+    }
+    cp_async_commit();
+  };
   float acc[16];
 #pragma unroll
   for (int i = 0; i < 16; ++i) acc[i] = 0.f;
-  for (int fc = 0; fc < F; fc += KCH) {
-    for (int idx = tid; idx < KCH * TILE; idx += 256) {
-      const int c = idx % TILE, fi = idx / TILE;
-      const int f = fc + fi, t = t0 + c, b = b0 + c;
-      As[fi * TILE + c] = (f < F && t < T) ? An[(size_t)f * T + t] : 0.f;
-      Ds[fi * TILE + c] = (f < F && t < T) ? Dn[(size_t)f * T + t] : 0.f;
-      Ws[fi * TILE + c] = (f < F && b < B) ? Wg[(size_t)f * B + b] : 0.f;
+  const int c0 = split * cps, c1 = min((F + KCH - 1) / KCH, c0 + cps);
+  if (c0 < c1) issue(c0);
+  for (int ch = c0; ch < c1; ++ch) {
+    if (ch + 1 < c1) {
+      issue(ch + 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
     __syncthreads();
+    const float* As = stg + (ch & 1) * STAGE;
+    const float* Ds = As + KCH * TILE;
+    const float* Ws = Ds + KCH * TILE;
 #pragma unroll
     for (int s = 0; s < KCH / NWARP; ++s) {
       const int fi = warp * (KCH / NWARP) + s;
@@ -168,10 +272,11 @@ __global__ void __launch_bounds__(256) k_hupd(const float* __restrict__ A, const
       num += red[(w * 32 + l) * 16 + slot + 0];
       den += red[(w * 32 + l) * 16 + slot + 1];
     }
+    if (!split_fixup(num, den, S, split, (n * gridDim.x + blockIdx.x) * nb + bt, part, ticket)) return;
     const int b = b0 + bi, t = t0 + ti;
     float hn = 0.f;
     if (b < B && t < T) {
-      float* hp = H + ((size_t)n * B + b) * T + t;
+      float* hp = H + ((size_t)n * B + b) * Tp + t;
       hn = *hp * sqrtf(num / fmaxf(den, eps));
       if (!finitef(hn)) atomicOr(flags + FLAG_NONFINITE, 1u);
       *hp = hn;
@@ -186,29 +291,56 @@ __global__ void __launch_bounds__(256) k_hupd(const float* __restrict__ A, const
   float hcol[TILE];
 #pragma unroll
   for (int b = 0; b < TILE; ++b) hcol[b] = Hn_s[b * TILE + ti];
+#pragma unroll 8
   for (int f = fl; f < F; f += 256 / TILE) {
     const float* wr = Wg + (size_t)f * B;
     float s = 0.f;
 #pragma unroll
     for (int b = 0; b < TILE; ++b)
       if (b < B) s = fmaf(__ldg(wr + b), hcol[b], s);
-    if (t < T) lam[((size_t)n * F + f) * T + t] = s;
+    if (t < T) lam[((size_t)n * F + f) * Tp + t] = s;
   }
 }
 
 bool nmf_fused_lambda(const dfmnmf_ctx* c) { return c->B <= TILE; }
 
+// Number of splits of the reduction: enough CTAs for about four per SM, at
+// most NMF_MAX_SPLIT, never more than the number of 64-wide chunks.
+static void split_plan(int tiles, int nch, int* S, int* cps) {
+  int s = (4 * 152 + tiles - 1) / tiles;
+  s = s < 1 ? 1 : (s > NMF_MAX_SPLIT ? NMF_MAX_SPLIT : s);
+  s = s > nch ? nch : s;
+  *cps = (nch + s - 1) / s;
+  *S = (nch + *cps - 1) / *cps;
+}
+
+size_t nmf_scratch_floats(const dfmnmf_ctx* c) {
+  const int nb = (c->B + TILE - 1) / TILE;
+  const size_t tw = (size_t)c->N * ((c->F + TILE - 1) / TILE) * nb;
+  const size_t th = (size_t)c->N * ((c->T + TILE - 1) / TILE) * nb;
+  return (tw > th ? tw : th) * NMF_MAX_SPLIT * 512;
+}
+size_t nmf_ticket_count(const dfmnmf_ctx* c) { return nmf_scratch_floats(c) / (NMF_MAX_SPLIT * 512); }
+
 cudaError_t launch_wupd(const dfmnmf_ctx* c, cudaStream_t s) {
   const int nb = (c->B + TILE - 1) / TILE;
-  dim3 grid((c->F + TILE - 1) / TILE, c->N, nb);
-  k_wupd<<<grid, 256, 0, s>>>(c->A, c->D, c->H, c->W, c->lam, c->F, c->T, c->B, c->eps, nb == 1, c->flags);
+  const int tiles = ((c->F + TILE - 1) / TILE) * c->N * nb;
+  int S, cps;
+  split_plan(tiles, (c->T + KCH - 1) / KCH, &S, &cps);
+  dim3 grid((c->F + TILE - 1) / TILE, c->N, nb * S);
+  k_wupd<<<grid, 256, 0, s>>>(c->A, c->D, c->H, c->W, c->lam, c->F, c->T, c->Tp, c->B, c->eps, nb == 1, c->flags, S, cps,
+                              c->nmf_part, c->nmf_ticket);
   return cudaGetLastError();
 }
 
 cudaError_t launch_hupd(const dfmnmf_ctx* c, cudaStream_t s) {
   const int nb = (c->B + TILE - 1) / TILE;
-  dim3 grid((c->T + TILE - 1) / TILE, c->N, nb);
-  k_hupd<<<grid, 256, 0, s>>>(c->A, c->D, c->W, c->H, c->lam, c->F, c->T, c->B, c->eps, nb == 1, c->flags);
+  const int tiles = ((c->T + TILE - 1) / TILE) * c->N * nb;
+  int S, cps;
+  split_plan(tiles, (c->F + KCH - 1) / KCH, &S, &cps);
+  dim3 grid((c->T + TILE - 1) / TILE, c->N, nb * S);
+  k_hupd<<<grid, 256, 0, s>>>(c->A, c->D, c->W, c->H, c->lam, c->F, c->T, c->Tp, c->B, c->eps, nb == 1, c->flags, S, cps,
+                              c->nmf_part, c->nmf_ticket);
   return cudaGetLastError();
 }
 

@@ -16,7 +16,7 @@ constexpr int NMAXO = 16;
 template <int MK>
 __global__ void __launch_bounds__(128) k_nll_data(const float2* __restrict__ x, const double2* __restrict__ Q64,
                                                   const float* __restrict__ lam, const float* __restrict__ g,
-                                                  double* __restrict__ part, int F, int T, int K, int N,
+                                                  double* __restrict__ part, int F, int T, int Tp, int K, int N,
                                                   float eps) {
   extern __shared__ float sm[];
   const int M = K * MK;
@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(128) k_nll_data(const float2* __restrict__ x, 
   if (t < T) {
     float lr[NMAXO];
 #pragma unroll
-    for (int n = 0; n < NMAXO; ++n) lr[n] = (n < N) ? lam[((size_t)n * F + f) * T + t] : 0.f;
+    for (int n = 0; n < NMAXO; ++n) lr[n] = (n < N) ? lam[((size_t)n * F + f) * Tp + t] : 0.f;
     for (int k = 0; k < K; ++k) {
       float2 xv[MK];
 #pragma unroll
@@ -96,7 +96,7 @@ cudaError_t launch_loglik(const dfmnmf_ctx* c, cudaStream_t s) {
   const size_t nld = (size_t)c->F * c->K;
   DFM_MK_DISPATCH(c->MK, {
     k_nll_data<MK_><<<dim3(c->F, ty), 128, gq_smem(c), s>>>(c->x, c->Q64, c->lam, c->g, c->red, c->F, c->T,
-                                                             c->K, c->N, c->eps);
+                                                             c->Tp, c->K, c->N, c->eps);
   });
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -111,7 +111,7 @@ template <int MK>
 __global__ void __launch_bounds__(128) k_separate(const float2* __restrict__ x, const double2* __restrict__ Q64,
                                                   const float2* __restrict__ Qinv, const float* __restrict__ lam,
                                                   const float* __restrict__ g, float2* __restrict__ out, int F,
-                                                  int T, int K, int N, float eps) {
+                                                  int T, int Tp, int K, int N, float eps) {
   extern __shared__ float sm[];
   const int M = K * MK;
   const int f = blockIdx.x;
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(128) k_separate(const float2* __restrict__ x, 
   if (t >= T) return;
   float lr[NMAXO];
 #pragma unroll
-  for (int n = 0; n < NMAXO; ++n) lr[n] = (n < N) ? lam[((size_t)n * F + f) * T + t] : 0.f;
+  for (int n = 0; n < NMAXO; ++n) lr[n] = (n < N) ? lam[((size_t)n * F + f) * Tp + t] : 0.f;
   for (int k = 0; k < K; ++k) {
     float2 xv[MK], y[MK];
     float iy[MK];
@@ -175,7 +175,7 @@ cudaError_t launch_separate(const dfmnmf_ctx* c, float2* out, cudaStream_t s) {
   const size_t sm = gq_smem(c) + (size_t)c->K * c->MK * c->MK * sizeof(float2);
   DFM_MK_DISPATCH(c->MK, {
     k_separate<MK_><<<dim3(c->F, ty), 128, sm, s>>>(c->x, c->Q64, c->Qinv32, c->lam, c->g, out, c->F, c->T,
-                                                     c->K, c->N, c->eps);
+                                                     c->Tp, c->K, c->N, c->eps);
   });
   return cudaGetLastError();
 }

@@ -1,0 +1,418 @@
+// kernels_tc.cu -- tensor-core form of the weighted covariances (Eq. 13).
+//
+//   V[f][k][mu][a][b] = (1/T) sum_t R[f][k][a,b](t) * w[f][t][k,mu],
+//   R = x_ftk x_ftk^H packed as M_k^2 = 16 reals, w = 1/yhat.
+//
+// For every frequency this is an (16 K x T) by (T x 4 K) product.  The
+// operands are split into two bfloat16 parts, R = R_hi + R_lo and
+// w = w_hi + w_lo, and three products R_hi w_hi + R_hi w_lo + R_lo w_hi are
+// accumulated in FP32 (the dropped R_lo w_lo term is below 2^-16 relative).
+// A plain bfloat16 contraction loses too much: on the paper-sized workload
+// it moves the IP update by 6e-2 relative, the split form by 1.5e-4.
+//
+// R depends only on the observation, so it is formed once (k_rprep) into
+// two bfloat16 arrays [F * 16K][Tr] (Tr = T rounded up to 64, zero tail).
+// k_vtc then streams them with TMA (128-byte swizzled tiles of 128 rows x 64
+// frames) into a 2-stage shared-memory ring (two CTAs per SM), six warps stage
+// lambda for the same frames and form w_hi / w_lo directly in the swizzled
+// operand layout, one thread issues
+// tcgen05.mma (M = 128 rows = 128 / (16 K) frequencies, N = 32 weights,
+// K = 16 frames per instruction, FP32 accumulators in tensor memory) and the
+// first four warps read the accumulators back with tcgen05.ld.
+//
+// Supported layouts: M_k = 4 and K in {1, 2, 4, 8} (M = 128 / (16 K) * 16 K
+// rows per tile, N = 32 columns).  Every mbarrier wait is bounded; a wait
+// that gives up sets FLAG_TIMEOUT and the CTA skips the rest of its work.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "../../include/dfmnmf.h"
+#include "common.cuh"
+#include "internal.h"
+
+namespace dfm {
+
+constexpr int TC_KC = 64;       // frames per chunk (128 bytes of bfloat16 per row)
+constexpr int TC_ROWS = 128;    // MMA M
+constexpr int TC_COLS = 32;     // MMA N
+constexpr int TC_STAGES = 2;
+constexpr int TC_PRODUCERS = 192;  // warps 2..7 form the weight operand
+constexpr int TC_A_BYTES = TC_ROWS * TC_KC * 2;   // 16 KB per operand part
+constexpr int TC_B_BYTES = TC_COLS * TC_KC * 2;   // 4 KB per operand part
+constexpr int TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_B_BYTES;
+constexpr unsigned long long TC_WAIT_CYCLES = 2000000000ull;  // ~1 s at 2 GHz
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// Wait for the phase with the given parity to complete; false on timeout.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  const unsigned addr = smem_u32(bar);
+  const unsigned long long start = clock64();
+  while (true) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - start > TC_WAIT_CYCLES) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand tile with 128-byte
+// swizzle, 8-row groups 1024 bytes apart (stride byte offset), descriptor
+// version 1, base offset 0.
+__device__ __forceinline__ unsigned long long smem_desc_sw128(unsigned addr) {
+  unsigned long long d = 0;
+  d |= (unsigned long long)((addr >> 4) & 0x3FFF);
+  d |= (unsigned long long)(1) << 16;              // leading byte offset (unused by swizzled K-major)
+  d |= (unsigned long long)((1024 >> 4) & 0x3FFF) << 32;
+  d |= 1ull << 46;                                 // version
+  d |= 2ull << 61;                                 // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D FP32, A and B bfloat16, both K-major,
+// N = 32, M = 128.
+constexpr unsigned TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((TC_COLS >> 3) << 17) | ((TC_ROWS >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16(unsigned tmem_d, unsigned long long a, unsigned long long b, unsigned acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+          tmem_d),
+      "l"(a), "l"(b), "r"(TC_IDESC), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(unsigned long long* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// ------------------------------------------------------------- R prepare
+// Rhi/Rlo[(f * K + k) * 16 + r][t] for t < Tr (zero beyond T).
+__global__ void __launch_bounds__(128) k_rprep(const float2* __restrict__ x, __nv_bfloat16* __restrict__ Rhi,
+                                               __nv_bfloat16* __restrict__ Rlo, int F, int T, int Tr, int K) {
+  const int f = blockIdx.y;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= Tr) return;
+  const int M = K * 4;
+  for (int k = 0; k < K; ++k) {
+    float R[16];
+    if (t < T) {
+      float2 xv[4];
+      load_block<4>(x + ((size_t)f * T + t) * M + k * 4, xv);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        R[a * 4 + a] = fmaf(xv[a].x, xv[a].x, xv[a].y * xv[a].y);
+#pragma unroll
+        for (int b = a + 1; b < 4; ++b) {
+          R[a * 4 + b] = fmaf(xv[a].x, xv[b].x, xv[a].y * xv[b].y);
+          R[b * 4 + a] = fmaf(xv[a].y, xv[b].x, -xv[a].x * xv[b].y);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < 16; ++r) R[r] = 0.f;
+    }
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(R[r]);
+      const __nv_bfloat16 l = __float2bfloat16_rn(R[r] - __bfloat162float(h));
+      const size_t o = ((size_t)(f * K + k) * 16 + r) * Tr + t;
+      Rhi[o] = h;
+      Rlo[o] = l;
+    }
+  }
+}
+
+// ------------------------------------------------------------ contraction
+struct TcSmem {
+  unsigned long long full[TC_STAGES];
+  unsigned long long empty[TC_STAGES];
+  unsigned long long done;
+  unsigned tmem_base;
+  unsigned abort;
+};
+
+// Shared memory: [1024-aligned operand ring][control][g of the CTA's
+// frequencies][lambda chunk of the CTA's frequencies].
+__host__ __device__ constexpr size_t tc_ring_bytes() { return (size_t)TC_STAGES * TC_STAGE_BYTES; }
+
+__global__ void __launch_bounds__(256, 2) k_vtc(const __grid_constant__ CUtensorMap map_hi,
+                                                const __grid_constant__ CUtensorMap map_lo,
+                                                const float* __restrict__ lam, const float* __restrict__ g,
+                                                double2* __restrict__ V, float4* __restrict__ Vdd, int F, int T,
+                                                int Tp, int Tr, int K, int N, float eps,
+                                                unsigned* __restrict__ flags) {
+  extern __shared__ __align__(1024) unsigned char tc_raw[];
+  unsigned char* ring = reinterpret_cast<unsigned char*>(((unsigned long long)tc_raw + 1023) & ~1023ull);
+  TcSmem* ctl = reinterpret_cast<TcSmem*>(ring + tc_ring_bytes());
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int FPC = TC_ROWS / (16 * K);  // frequencies per CTA
+  const int f0 = blockIdx.x * FPC;
+  const int M = 4 * K;
+  const int nch = Tr / TC_KC;
+  float* gsh = reinterpret_cast<float*>(ctl + 1);  // [FPC][N][M]
+  float* lsh = gsh + ((FPC * N * M + 3) & ~3);    // [FPC][N][TC_KC]
+
+  if (tid == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(&ctl->full[s], 1 + TC_PRODUCERS);
+      mbar_init(&ctl->empty[s], 1);
+    }
+    mbar_init(&ctl->done, 1);
+    ctl->abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int i = tid; i < FPC * N * M; i += blockDim.x) {
+    const int fj = i / (N * M), rem = i % (N * M);
+    const int f = f0 + fj;
+    gsh[i] = (f < F) ? g[(size_t)f * N * M + rem] : 0.f;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(&ctl->tmem_base))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const unsigned tmem = ctl->tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer: R_hi / R_lo tiles (rows f0 * 16K .., frames chunk * 64 ..)
+    for (int c = 0; c < nch; ++c) {
+      const int s = c % TC_STAGES;
+      if (c >= TC_STAGES && !mbar_wait(&ctl->empty[s], ((c / TC_STAGES) + 1) & 1)) {
+        atomicOr(&ctl->abort, 1u);
+        break;
+      }
+      if (ctl->abort) break;
+      unsigned char* st = ring + s * TC_STAGE_BYTES;
+      mbar_arrive_expect_tx(&ctl->full[s], 2 * TC_A_BYTES);
+      tma_load_2d(st, &map_hi, c * TC_KC, f0 * 16 * K, &ctl->full[s]);
+      tma_load_2d(st + TC_A_BYTES, &map_lo, c * TC_KC, f0 * 16 * K, &ctl->full[s]);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    for (int c = 0; c < nch; ++c) {
+      const int s = c % TC_STAGES;
+      if (!mbar_wait(&ctl->full[s], (c / TC_STAGES) & 1)) {
+        atomicOr(&ctl->abort, 1u);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const unsigned base = smem_u32(ring + s * TC_STAGE_BYTES);
+      const unsigned a_hi = base, a_lo = base + TC_A_BYTES;
+      const unsigned b_hi = base + 2 * TC_A_BYTES, b_lo = b_hi + TC_B_BYTES;
+#pragma unroll
+      for (int kk = 0; kk < TC_KC / 16; ++kk) {
+        const unsigned off = kk * 32;  // 16 bfloat16 along K inside the 128-byte swizzle atom
+        umma_bf16(tmem, smem_desc_sw128(a_hi + off), smem_desc_sw128(b_hi + off), (c > 0 || kk > 0) ? 1u : 0u);
+        umma_bf16(tmem, smem_desc_sw128(a_hi + off), smem_desc_sw128(b_lo + off), 1u);
+        umma_bf16(tmem, smem_desc_sw128(a_lo + off), smem_desc_sw128(b_hi + off), 1u);
+      }
+      umma_commit(&ctl->empty[s]);
+    }
+    umma_commit(&ctl->done);
+  } else if (warp >= 2) {
+    // ---- weight producers: stage lambda for the chunk, then w_hi / w_lo rows
+    //      (fj, k, mu) x 64 frames, swizzled like the TMA tiles
+    const int p = tid - 64;  // 0 .. TC_PRODUCERS-1
+    for (int c = 0; c < nch; ++c) {
+      const int s = c % TC_STAGES;
+      const int tc0 = c * TC_KC;
+      // lambda rows of the chunk: FPC x N rows of 16 float4 (Tp is a multiple of 4)
+      for (int i = p; i < FPC * N * (TC_KC / 4); i += TC_PRODUCERS) {
+        const int row = i / (TC_KC / 4), q = i % (TC_KC / 4);
+        const int fj = row / N, n = row % N, f = f0 + fj, t = tc0 + 4 * q;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (f < F && t < Tp) v = __ldg(reinterpret_cast<const float4*>(lam + ((size_t)n * F + f) * Tp + t));
+        *reinterpret_cast<float4*>(lsh + row * TC_KC + 4 * q) = v;
+      }
+      asm volatile("bar.sync 1, %0;" ::"n"(TC_PRODUCERS) : "memory");
+      if (c >= TC_STAGES && !mbar_wait(&ctl->empty[s], ((c / TC_STAGES) + 1) & 1)) atomicOr(&ctl->abort, 1u);
+      unsigned char* bh = ring + s * TC_STAGE_BYTES + 2 * TC_A_BYTES;
+      unsigned char* bl = bh + TC_B_BYTES;
+      for (int item = p; item < TC_COLS * 8; item += TC_PRODUCERS) {
+        const int row = item >> 3, j = item & 7;
+        const int fj = row / M, m = row % M;  // row = fj * 4K + k * 4 + mu = fj * M + m
+        const int f = f0 + fj;
+        const int t0 = tc0 + j * 8;
+        float ys[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) ys[q] = 0.f;
+        for (int n = 0; n < N; ++n) {
+          const float gv = gsh[(fj * N + n) * M + m];
+          const float4 l0 = *reinterpret_cast<const float4*>(lsh + (fj * N + n) * TC_KC + j * 8);
+          const float4 l1 = *reinterpret_cast<const float4*>(lsh + (fj * N + n) * TC_KC + j * 8 + 4);
+          ys[0] = fmaf(l0.x, gv, ys[0]); ys[1] = fmaf(l0.y, gv, ys[1]);
+          ys[2] = fmaf(l0.z, gv, ys[2]); ys[3] = fmaf(l0.w, gv, ys[3]);
+          ys[4] = fmaf(l1.x, gv, ys[4]); ys[5] = fmaf(l1.y, gv, ys[5]);
+          ys[6] = fmaf(l1.z, gv, ys[6]); ys[7] = fmaf(l1.w, gv, ys[7]);
+        }
+        unsigned hw[4], lw[4];
+#pragma unroll
+        for (int q = 0; q < 8; q += 2) {
+          const bool v0 = f < F && t0 + q < T, v1 = f < F && t0 + q + 1 < T;
+          const float w0 = v0 ? fast_rcp(fmaxf(ys[q], eps)) : 0.f;
+          const float w1 = v1 ? fast_rcp(fmaxf(ys[q + 1], eps)) : 0.f;
+          const __nv_bfloat162 h = __floats2bfloat162_rn(w0, w1);
+          const float2 hf = __bfloat1622float2(h);
+          const __nv_bfloat162 l = __floats2bfloat162_rn(w0 - hf.x, w1 - hf.y);
+          hw[q / 2] = *reinterpret_cast<const unsigned*>(&h);
+          lw[q / 2] = *reinterpret_cast<const unsigned*>(&l);
+        }
+        const int off = row * 128 + ((j ^ (row & 7)) << 4);
+        *reinterpret_cast<uint4*>(bh + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4*>(bl + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(&ctl->full[s]);
+      asm volatile("bar.sync 1, %0;" ::"n"(TC_PRODUCERS) : "memory");  // lsh reused by the next chunk
+    }
+  }
+
+  // ---- epilogue: warps 0-3 read the accumulators (lane = row)
+  if (warp < 4) {
+    __syncwarp();
+    const bool ok = mbar_wait(&ctl->done, 0);
+    if (!ok) atomicOr(&ctl->abort, 1u);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    unsigned r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(tmem + ((unsigned)(warp * 32) << 16)));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const int row = tid;                      // 0..127
+    const int fj = row / (16 * K), rk = row % (16 * K);
+    const int k = rk / 16, e = rk % 16;       // packed entry e = a * 4 + b
+    const int f = f0 + fj;
+    if (ok && !ctl->abort && f < F) {
+      const int a = e / 4, b = e % 4;
+      const double invT = 1.0 / (double)T;
+      const size_t blk = (size_t)f * K + k;
+#pragma unroll
+      for (int mu = 0; mu < 4; ++mu) {
+        const float v = __uint_as_float(r[fj * M + k * 4 + mu]);
+        const double dv = (double)v * invT;
+        double2* Vb = V + (blk * 4 + mu) * 16;
+        float4* Vd = Vdd + (blk * 4 + mu) * 16;
+        double* vdbl = reinterpret_cast<double*>(Vb);
+        float* vflt = reinterpret_cast<float*>(Vd);
+        const float fv = (float)dv;
+        if (a == b) {
+          Vb[a * 4 + a] = make_double2(dv, 0.0);
+          Vd[a * 4 + a] = make_float4(fv, 0.f, 0.f, 0.f);
+        } else if (a < b) {  // real part of V[a][b] and V[b][a]
+          vdbl[2 * (a * 4 + b)] = dv;
+          vdbl[2 * (b * 4 + a)] = dv;
+          vflt[4 * (a * 4 + b)] = fv; vflt[4 * (a * 4 + b) + 1] = 0.f;
+          vflt[4 * (b * 4 + a)] = fv; vflt[4 * (b * 4 + a) + 1] = 0.f;
+        } else {  // e = a*4+b with a > b holds Im(x_b conj x_a) = Im V[b][a]
+          vdbl[2 * (b * 4 + a) + 1] = dv;
+          vdbl[2 * (a * 4 + b) + 1] = -dv;
+          vflt[4 * (b * 4 + a) + 2] = fv; vflt[4 * (b * 4 + a) + 3] = 0.f;
+          vflt[4 * (a * 4 + b) + 2] = -fv; vflt[4 * (a * 4 + b) + 3] = 0.f;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (ctl->abort && tid == 0) atomicOr(flags + FLAG_TIMEOUT, 1u);
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+  }
+}
+
+// ------------------------------------------------------------- host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+bool tc_supported(int MK, int K) { return MK == 4 && (K == 1 || K == 2 || K == 4 || K == 8); }
+
+size_t tc_smem_bytes(const dfmnmf_ctx* c) {
+  const int FPC = TC_ROWS / (16 * c->K);
+  return 1024 + tc_ring_bytes() + sizeof(TcSmem) +
+         ((size_t)((FPC * c->N * c->M + 3) & ~3) + (size_t)FPC * c->N * TC_KC) * sizeof(float);
+}
+
+cudaError_t tc_make_maps(dfmnmf_ctx* c) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  const cuuint64_t dims[2] = {(cuuint64_t)c->Tr, (cuuint64_t)c->F * 16 * c->K};
+  const cuuint64_t strides[1] = {(cuuint64_t)c->Tr * 2};
+  const cuuint32_t box[2] = {TC_KC, TC_ROWS};
+  const cuuint32_t estr[2] = {1, 1};
+  CUtensorMap* maps[2] = {reinterpret_cast<CUtensorMap*>(c->tmap_hi), reinterpret_cast<CUtensorMap*>(c->tmap_lo)};
+  void* bases[2] = {c->Rhi, c->Rlo};
+  for (int i = 0; i < 2; ++i) {
+    const CUresult r = fn(maps[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, bases[i], dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_rprep(const dfmnmf_ctx* c, cudaStream_t s) {
+  dim3 grid((c->Tr + 127) / 128, c->F);
+  k_rprep<<<grid, 128, 0, s>>>(c->x, reinterpret_cast<__nv_bfloat16*>(c->Rhi),
+                               reinterpret_cast<__nv_bfloat16*>(c->Rlo), c->F, c->T, c->Tr, c->K);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vtc(const dfmnmf_ctx* c, cudaStream_t s) {
+  const size_t sm = tc_smem_bytes(c);
+  cudaFuncSetAttribute(k_vtc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const int FPC = TC_ROWS / (16 * c->K);
+  const int grid = (c->F + FPC - 1) / FPC;
+  const CUtensorMap* mh = reinterpret_cast<const CUtensorMap*>(c->tmap_hi);
+  const CUtensorMap* ml = reinterpret_cast<const CUtensorMap*>(c->tmap_lo);
+  k_vtc<<<grid, 256, sm, s>>>(*mh, *ml, c->lam, c->g, c->V, c->Vdd, c->F, c->T, c->Tp, c->Tr, c->K, c->N,
+                                      c->eps, c->flags);
+  return cudaGetLastError();
+}
+
+}  // namespace dfm

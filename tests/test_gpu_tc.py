@@ -1,0 +1,108 @@
+"""Tensor-core form (split-bfloat16 weighted covariances on tcgen05) against
+the FP32 form and the FP64 oracle.
+
+Tolerances are those of the acceptance bar for the tensor-core form: every
+single update within 3e-3 normwise relative error, the cost of Eq. (12) after
+50 iterations within 1e-2 relative and the SDR within 0.2 dB.  The form is
+meant for mixtures with at least as many sources as microphones per subarray
+(the 4 x 4-mic, N = 5 workload): its covariances keep condition numbers
+below ~1e4 there, which split bfloat16 resolves.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2605_19388_gb300 import synth
+from tests._helpers import rel_err, v_oracle_layout, sdr_db, oracle_state
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2605_19388_gb300 import dfmnmf as D  # noqa: E402
+
+TOL_TC = 3e-3
+
+
+def ctx_for(p, precision, Q0=None):
+    return D.dfmnmf_init(p.F, p.T, p.mics, p.N, p.B, p.x, p.W0, p.H0, p.g0,
+                         Q0 if Q0 is not None else p.Q0, precision=precision)
+
+
+def state(ctx):
+    Q, W, H, g = D.params_numpy(ctx)
+    return O.state_from_arrays(Q, W, H, g, ctx.mics)
+
+
+@pytest.mark.parametrize("shape", [dict(F=37, T=150, mics=(4, 4, 4, 4), N=5, B=8),
+                                   dict(F=20, T=64, mics=(4, 4), N=6, B=4),
+                                   dict(F=9, T=200, mics=(4,), N=5, B=3),
+                                   dict(F=11, T=77, mics=(4,) * 8, N=9, B=5)])
+def test_tc_covariances_match_oracle(shape):
+    """k_vtc's V against the oracle's Eq. (13) on the same state (ragged T, odd F)."""
+    p = synth.make_problem(shape["F"], shape["T"], shape["mics"], shape["N"], shape["B"], seed=31)
+    ctx = ctx_for(p, D.DFMNMF_BF16_TC)
+    st = state(ctx)
+    D.dfmnmf_run_stage(ctx, D.DFMNMF_STAGE_COV)
+    V = D.buffer_numpy(ctx, D.DFMNMF_BUF_V)
+    y = O.model_variance(O.source_psd(st.W, st.H), st.g)
+    V_ref = v_oracle_layout(O.weighted_covariances(p.x.astype(np.complex128), y, p.mics))
+    err = rel_err(V, V_ref)
+    assert err < 1e-4, err
+
+
+def test_tc_stage_parity_paper_shaped():
+    """Every update of one iteration within 3e-3 (oracle fed the GPU's inputs)."""
+    p = synth.make_problem(41, 120, (4, 4, 4, 4), 5, 16, seed=32)
+    x = p.x.astype(np.complex128)
+    ctx = ctx_for(p, D.DFMNMF_BF16_TC)
+    st = state(ctx)
+    errs = {}
+    D.dfmnmf_run_stage(ctx, D.DFMNMF_STAGE_COV)
+    V = D.buffer_numpy(ctx, D.DFMNMF_BUF_V)
+    y = O.model_variance(O.source_psd(st.W, st.H), st.g)
+    errs["V"] = rel_err(V, v_oracle_layout(O.weighted_covariances(x, y, p.mics)))
+    D.dfmnmf_run_stage(ctx, D.DFMNMF_STAGE_IP)
+    st2 = state(ctx)
+    Q_ref = O.ip_update(st.Q, [V[:, k] for k in range(p.K)])
+    errs["Q"] = max(rel_err(st2.Q[k], Q_ref[k]) for k in range(p.K))
+    D.dfmnmf_run_stage(ctx, D.DFMNMF_STAGE_W)
+    st3 = state(ctx)
+    P = O.projected_power(x, st2.Q, p.mics)
+    errs["P"] = rel_err(D.buffer_numpy(ctx, D.DFMNMF_BUF_P), P)
+    errs["W"] = rel_err(st3.W, O.update_W(st2.W, st2.H, st2.g, P))
+    D.dfmnmf_run_stage(ctx, D.DFMNMF_STAGE_H)
+    st4 = state(ctx)
+    errs["H"] = rel_err(st4.H, O.update_H(st3.W, st3.H, st3.g, P))
+    D.dfmnmf_run_stage(ctx, D.DFMNMF_STAGE_G)
+    st5 = state(ctx)
+    errs["g"] = rel_err(st5.g, O.update_g(st4.W, st4.H, st4.g, P))
+    assert max(errs.values()) < TOL_TC, errs
+
+
+def test_tc_trajectory_50_iterations_paper_workload():
+    """50 iterations on the 4 x 4-mic, N = 5, F = 513, T = 626 workload."""
+    p = synth.make_workload("paper_4x4_n5", seed=0, with_images=True)
+    x = p.x.astype(np.complex128)
+    ctx = ctx_for(p, D.DFMNMF_BF16_TC)
+    D.dfmnmf_iterate(ctx, 50)
+    nll = D.dfmnmf_loglik(ctx)
+    c = torch.empty((p.N, p.F, p.T, p.M), dtype=torch.complex64, device="cuda")
+    D.dfmnmf_separate(ctx, c)
+    st = oracle_state(p)
+    for _ in range(50):
+        st = O.mm_iteration(x, p.mics, st)
+    ref = O.neg_loglik(x, p.mics, st)
+    assert abs(nll - ref) <= 1e-2 * abs(ref), (nll, ref)
+    s_gpu, _ = sdr_db(c.cpu().numpy(), p.c)
+    s_ref, _ = sdr_db(O.wiener_filter(x, p.mics, st), p.c)
+    assert np.max(np.abs(np.sort(s_gpu) - np.sort(s_ref))) <= 0.2, (s_gpu, s_ref)
+
+
+def test_tc_form_rejects_unsupported_layouts():
+    p = synth.make_problem(5, 20, (2, 2), 2, 3, seed=1)
+    with pytest.raises(D.DfmnmfError) as ei:
+        ctx_for(p, D.DFMNMF_BF16_TC)
+    assert ei.value.code == D.DFMNMF_EINVAL
