@@ -46,6 +46,9 @@ void free_ctx(dfmnmf_ctx* c) {
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   if (c->graph) cudaGraphDestroy(c->graph);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->side_stream) cudaStreamDestroy(c->side_stream);
+  if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+  if (c->join_ev) cudaEventDestroy(c->join_ev);
   void* ptrs[] = {c->x, c->Q64, c->Q32, c->Qinv32, c->V, c->Vdd, c->W, c->H, c->g, c->lam,
                   c->P, c->A, c->D, c->red, c->nll_dev, c->flags, c->nmf_part, c->nmf_ticket, c->Rhi, c->Rlo};
   for (void* p : ptrs)
@@ -87,26 +90,33 @@ size_t ng(const dfmnmf_ctx* c) { return (size_t)c->F * c->N * c->M; }
 size_t nx(const dfmnmf_ctx* c) { return (size_t)c->F * c->T * c->M; }
 
 // The launches of one iteration in order; stage s is the range of entries
-// with stage == s.
+// with stage == s.  `ranged` launches are per frequency and take a frequency
+// range; the captured iteration runs them for two halves of the band on two
+// branches so that the latency-bound IP of one half overlaps the streaming
+// kernels of the other.
+typedef cudaError_t (*LaunchFn)(const dfmnmf_ctx*, cudaStream_t, int, int);
 struct Launch {
   int stage;
   const char* name;
-  cudaError_t (*fn)(const dfmnmf_ctx*, cudaStream_t);
+  LaunchFn fn;
+  bool ranged;
 };
 
 int iteration_launches(const dfmnmf_ctx* c, Launch* out) {
   int n = 0;
   const bool fused = dfm::nmf_fused_lambda(c);
-  if (c->precision == DFMNMF_BF16_TC) out[n++] = {DFMNMF_STAGE_COV, "k_vtc", dfm::launch_vtc};
-  else out[n++] = {DFMNMF_STAGE_COV, "k_cov", dfm::launch_cov};
-  out[n++] = {DFMNMF_STAGE_IP, "k_ip", dfm::launch_ip};
-  out[n++] = {DFMNMF_STAGE_W, "k_pstats", dfm::launch_power_stats};
-  out[n++] = {DFMNMF_STAGE_W, "k_wupd", dfm::launch_wupd};
-  if (!fused) out[n++] = {DFMNMF_STAGE_W, "k_lambda", dfm::launch_lambda};
-  out[n++] = {DFMNMF_STAGE_H, "k_stats", dfm::launch_stats};
-  out[n++] = {DFMNMF_STAGE_H, "k_hupd", dfm::launch_hupd};
-  if (!fused) out[n++] = {DFMNMF_STAGE_H, "k_lambda", dfm::launch_lambda};
-  out[n++] = {DFMNMF_STAGE_G, "k_gupd", dfm::launch_gupd};
+  if (c->precision == DFMNMF_BF16_TC) out[n++] = {DFMNMF_STAGE_COV, "k_vtc", dfm::launch_vtc, true};
+  else out[n++] = {DFMNMF_STAGE_COV, "k_cov", dfm::launch_cov, true};
+  out[n++] = {DFMNMF_STAGE_IP, "k_ip", dfm::launch_ip, true};
+  out[n++] = {DFMNMF_STAGE_W, "k_pstats", dfm::launch_power_stats, true};
+  out[n++] = {DFMNMF_STAGE_W, "k_wupd", [](const dfmnmf_ctx* c, cudaStream_t s, int, int) { return dfm::launch_wupd(c, s); }, false};
+  if (!fused)
+    out[n++] = {DFMNMF_STAGE_W, "k_lambda", [](const dfmnmf_ctx* c, cudaStream_t s, int, int) { return dfm::launch_lambda(c, s); }, false};
+  out[n++] = {DFMNMF_STAGE_H, "k_stats", [](const dfmnmf_ctx* c, cudaStream_t s, int, int) { return dfm::launch_stats(c, s); }, false};
+  out[n++] = {DFMNMF_STAGE_H, "k_hupd", [](const dfmnmf_ctx* c, cudaStream_t s, int, int) { return dfm::launch_hupd(c, s); }, false};
+  if (!fused)
+    out[n++] = {DFMNMF_STAGE_H, "k_lambda", [](const dfmnmf_ctx* c, cudaStream_t s, int, int) { return dfm::launch_lambda(c, s); }, false};
+  out[n++] = {DFMNMF_STAGE_G, "k_gupd", [](const dfmnmf_ctx* c, cudaStream_t s, int, int) { return dfm::launch_gupd(c, s); }, false};
   return n;
 }
 constexpr int kMaxLaunches = 16;
@@ -117,16 +127,39 @@ int enqueue_stage(dfmnmf_ctx* c, int stage, cudaStream_t s) {
   const int n = iteration_launches(c, L);
   for (int i = 0; i < n; ++i)
     if (L[i].stage == stage) {
-      cudaError_t e = L[i].fn(c, s);
+      cudaError_t e = L[i].fn(c, s, 0, c->F);
       if (e != cudaSuccess) return fail(DFMNMF_ECUDA, "launch of %s failed: %s", L[i].name, cudaGetErrorString(e));
     }
   return DFMNMF_OK;
 }
 
+// Split point of the band: a multiple of 8 frequencies (whole tensor-core tiles).
+int band_split(const dfmnmf_ctx* c) {
+  const int h = ((c->F / 2) + 7) & ~7;
+  return (h > 0 && h < c->F) ? h : 0;
+}
+
+// One iteration for capture: ranged launches for both halves on two branches,
+// joined before the first band-wide launch.
 int enqueue_iteration(dfmnmf_ctx* c, cudaStream_t s) {
-  for (int st = DFMNMF_STAGE_COV; st <= DFMNMF_STAGE_G; ++st) {
-    int r = enqueue_stage(c, st, s);
-    if (r) return r;
+  Launch L[kMaxLaunches];
+  const int n = iteration_launches(c, L);
+  const int h = band_split(c);
+  int i = 0;
+  if (h > 0) {
+    CK(cudaEventRecord(c->fork_ev, s));
+    CK(cudaStreamWaitEvent(c->side_stream, c->fork_ev, 0));
+    for (; i < n && L[i].ranged; ++i) {
+      cudaError_t e = L[i].fn(c, s, 0, h);
+      if (e == cudaSuccess) e = L[i].fn(c, c->side_stream, h, c->F - h);
+      if (e != cudaSuccess) return fail(DFMNMF_ECUDA, "launch of %s failed: %s", L[i].name, cudaGetErrorString(e));
+    }
+    CK(cudaEventRecord(c->join_ev, c->side_stream));
+    CK(cudaStreamWaitEvent(s, c->join_ev, 0));
+  }
+  for (; i < n; ++i) {
+    cudaError_t e = L[i].fn(c, s, 0, c->F);
+    if (e != cudaSuccess) return fail(DFMNMF_ECUDA, "launch of %s failed: %s", L[i].name, cudaGetErrorString(e));
   }
   return DFMNMF_OK;
 }
@@ -238,8 +271,11 @@ int dfmnmf_init(dfmnmf_ctx** out, const dfmnmf_desc* d, const void* x, const flo
   }
   cudaStream_t s = as_stream(stream);
   auto bail = [&](int code) { free_ctx(c); return code; };
-  if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
-    return bail(fail(DFMNMF_ECUDA, "stream creation failed"));
+  if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming) != cudaSuccess)
+    return bail(fail(DFMNMF_ECUDA, "stream or event creation failed"));
 #define CKI(call)                                                                                        \
   do {                                                                                                   \
     cudaError_t e_ = (call);                                                                             \
@@ -298,7 +334,10 @@ int dfmnmf_run_stage(dfmnmf_ctx* c, int stage, void* stream) {
 int dfmnmf_launches_per_iteration(const dfmnmf_ctx* c) {
   if (!c) return -1;
   Launch L[kMaxLaunches];
-  return iteration_launches(c, L);
+  const int n = iteration_launches(c, L);
+  int ranged = 0;
+  for (int i = 0; i < n; ++i) ranged += L[i].ranged ? 1 : 0;
+  return band_split(c) > 0 ? n + ranged : n;
 }
 
 int dfmnmf_kernel_times(dfmnmf_ctx* c, int n_iter, double* avg_ms, const char** names, int cap, int* count,
@@ -317,7 +356,7 @@ int dfmnmf_kernel_times(dfmnmf_ctx* c, int n_iter, double* avg_ms, const char** 
   for (int it = 0; it < n_iter && rc == DFMNMF_OK; ++it) {
     cudaEventRecord(ev[0], s);
     for (int i = 0; i < n; ++i) {
-      cudaError_t e = L[i].fn(c, s);
+      cudaError_t e = L[i].fn(c, s, 0, c->F);
       if (e != cudaSuccess) { rc = fail(DFMNMF_ECUDA, "%s: %s", L[i].name, cudaGetErrorString(e)); break; }
       cudaEventRecord(ev[i + 1], s);
     }

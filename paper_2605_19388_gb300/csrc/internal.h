@@ -43,19 +43,22 @@ struct dfmnmf_ctx {
   cudaGraph_t graph;
   cudaGraphExec_t gexec;
   int launches_per_iter;
+  cudaStream_t side_stream;   // second branch of the captured iteration
+  cudaEvent_t fork_ev, join_ev;
 };
 
 namespace dfm {
 
 // All launchers return cudaGetLastError() after enqueueing.
 cudaError_t launch_lambda(const dfmnmf_ctx* c, cudaStream_t s);
-cudaError_t launch_cov(const dfmnmf_ctx* c, cudaStream_t s);
-cudaError_t launch_vtc(const dfmnmf_ctx* c, cudaStream_t s);     // tensor-core covariances (BF16_TC form)
+// Launchers of the per-frequency kernels take a frequency range [fb, fb + fc).
+cudaError_t launch_cov(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc);
+cudaError_t launch_vtc(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc);  // tensor-core covariances (BF16_TC form)
 cudaError_t launch_rprep(const dfmnmf_ctx* c, cudaStream_t s);   // split-bfloat16 x x^H for the TC form
 cudaError_t tc_make_maps(dfmnmf_ctx* c);
 bool tc_supported(int MK, int K);
-cudaError_t launch_ip(const dfmnmf_ctx* c, cudaStream_t s);
-cudaError_t launch_power_stats(const dfmnmf_ctx* c, cudaStream_t s);  // P + A/D (current lambda)
+cudaError_t launch_ip(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc);
+cudaError_t launch_power_stats(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc);  // P + A/D (current lambda)
 cudaError_t launch_wupd(const dfmnmf_ctx* c, cudaStream_t s);         // Eq. 8 + lambda
 cudaError_t launch_stats(const dfmnmf_ctx* c, cudaStream_t s);        // A/D from stored P
 cudaError_t launch_hupd(const dfmnmf_ctx* c, cudaStream_t s);         // Eq. 9 + lambda

@@ -114,11 +114,11 @@ constexpr int CT = 64;
 template <int MK>
 __global__ void __launch_bounds__(256, 2) k_cov(const float2* __restrict__ x, const float* __restrict__ lam,
                                                 const float* __restrict__ g, double2* __restrict__ V, float4* __restrict__ Vdd,
-                                                int F, int T, int Tp, int K, int N, float eps) {
+                                                int F, int T, int Tp, int K, int N, float eps, int fb) {
   using Cfg = CovCfg<MK>;
   constexpr int E = Cfg::E, EP = Cfg::EP, CP = Cfg::CP, PARTS = Cfg::PARTS;
   constexpr int NW = 8;
-  const int f = blockIdx.x, tid = threadIdx.x;
+  const int f = fb + blockIdx.x, tid = threadIdx.x;
   const int M = K * MK;
   const int warp = tid >> 5, lane = tid & 31;
   const int items = K * PARTS;
@@ -222,14 +222,14 @@ __global__ void __launch_bounds__(256, 2) k_cov(const float2* __restrict__ x, co
   }
 }
 
-cudaError_t launch_cov(const dfmnmf_ctx* c, cudaStream_t s) {
+cudaError_t launch_cov(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
   DFM_MK_DISPATCH(c->MK, {
     constexpr int CP = CovCfg<MK_>::CP;
     const int items = c->K * CovCfg<MK_>::PARTS;
     const size_t sm = (size_t)(items <= 8 ? 8 : items) * CP * sizeof(double) + 2 * (size_t)CT * c->M * sizeof(float2) +
                       (2 * (size_t)c->N * CT + (size_t)c->N * c->M) * sizeof(float);
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_cov<MK_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_cov<MK_><<<c->F, 256, sm, s>>>(c->x, c->lam, c->g, c->V, c->Vdd, c->F, c->T, c->Tp, c->K, c->N, c->eps);
+    k_cov<MK_><<<fc, 256, sm, s>>>(c->x, c->lam, c->g, c->V, c->Vdd, c->F, c->T, c->Tp, c->K, c->N, c->eps, fb);
   });
   return cudaGetLastError();
 }

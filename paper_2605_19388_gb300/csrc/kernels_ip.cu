@@ -321,14 +321,15 @@ __global__ void k_q32(const double2* __restrict__ Q64, float2* __restrict__ Q32,
 }
 
 
-cudaError_t launch_ip(const dfmnmf_ctx* c, cudaStream_t s) {
-  const int nblocks = c->F * c->K;
+cudaError_t launch_ip(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
+  const int nblocks = fc * c->K;
+  const size_t o = (size_t)fb * c->K;  // first block of the range
   const int grid = (nblocks + 7) / 8;  // 4 warps x 2 blocks per CTA
   DFM_MK_DISPATCH(c->MK, {
     switch (c->ip_arith) {
-      case 0: k_ip<MK_, double><<<grid, 128, 0, s>>>(c->V, c->Vdd, c->Q64, c->Q32, nblocks, c->eps, c->singular_rtol, c->flags); break;
-      case 1: k_ip<MK_, dd><<<grid, 128, 0, s>>>(c->V, c->Vdd, c->Q64, c->Q32, nblocks, c->eps, c->singular_rtol, c->flags); break;
-      default: k_ip<MK_, float><<<grid, 128, 0, s>>>(c->V, c->Vdd, c->Q64, c->Q32, nblocks, c->eps, c->singular_rtol, c->flags); break;
+      case 0: k_ip<MK_, double><<<grid, 128, 0, s>>>(c->V + o * MK_ * MK_ * MK_, c->Vdd + o * MK_ * MK_ * MK_, c->Q64 + o * MK_ * MK_, c->Q32 + o * MK_ * MK_, nblocks, c->eps, c->singular_rtol, c->flags); break;
+      case 1: k_ip<MK_, dd><<<grid, 128, 0, s>>>(c->V + o * MK_ * MK_ * MK_, c->Vdd + o * MK_ * MK_ * MK_, c->Q64 + o * MK_ * MK_, c->Q32 + o * MK_ * MK_, nblocks, c->eps, c->singular_rtol, c->flags); break;
+      default: k_ip<MK_, float><<<grid, 128, 0, s>>>(c->V + o * MK_ * MK_ * MK_, c->Vdd + o * MK_ * MK_ * MK_, c->Q64 + o * MK_ * MK_, c->Q32 + o * MK_ * MK_, nblocks, c->eps, c->singular_rtol, c->flags); break;
     }
   });
   return cudaGetLastError();

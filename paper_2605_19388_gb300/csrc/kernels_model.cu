@@ -62,9 +62,10 @@ template <int MK, bool COMPUTE_P, bool COMP>
 __global__ void __launch_bounds__(256) k_pstats(const float2* __restrict__ x, const double2* __restrict__ Q64,
                                                 const float* __restrict__ lam, const float* __restrict__ g,
                                                 float* __restrict__ P, float* __restrict__ A,
-                                                float* __restrict__ D, int F, int T, int Tp, int K, int N, float eps) {
+                                                float* __restrict__ D, int F, int T, int Tp, int K, int N, float eps,
+                                                int fb) {
   extern __shared__ __align__(16) float sm[];
-  const int f = blockIdx.x, tid = threadIdx.x;
+  const int f = fb + blockIdx.x, tid = threadIdx.x;
   const int M = K * MK;
   const int TB = blockDim.x / K;
   const int k = tid % K, tl = tid / K;
@@ -277,9 +278,9 @@ __global__ void __launch_bounds__(256) k_gupd(const float* __restrict__ lam, con
   else { constexpr int NM_ = 16; __VA_ARGS__; }
 
 template <bool COMPUTE_P, bool COMP>
-static cudaError_t launch_pstats_impl(const dfmnmf_ctx* c, cudaStream_t s) {
+static cudaError_t launch_pstats_impl(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
   const int TB = 256 / c->K;
-  dim3 grid(c->F, (c->T + TB - 1) / TB);
+  dim3 grid(fc, (c->T + TB - 1) / TB);
   const bool pow2 = (c->K & (c->K - 1)) == 0;
   const size_t sm = (size_t)((c->N * c->M + 3) & ~3) * sizeof(float) +
                     (COMPUTE_P ? 4 * (size_t)c->K * c->MK * c->MK * sizeof(float) : 0) +
@@ -287,16 +288,18 @@ static cudaError_t launch_pstats_impl(const dfmnmf_ctx* c, cudaStream_t s) {
   DFM_MK_DISPATCH(c->MK, {
     auto kern = k_pstats<MK_, COMPUTE_P, COMP>;
     if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    kern<<<grid, 256, sm, s>>>(c->x, c->Q64, c->lam, c->g, c->P, c->A, c->D, c->F, c->T, c->Tp, c->K, c->N, c->eps);
+    kern<<<grid, 256, sm, s>>>(c->x, c->Q64, c->lam, c->g, c->P, c->A, c->D, c->F, c->T, c->Tp, c->K, c->N, c->eps,
+                               fb);
   });
   return cudaGetLastError();
 }
 
-cudaError_t launch_power_stats(const dfmnmf_ctx* c, cudaStream_t s) {
-  return c->precision == DFMNMF_FP32 ? launch_pstats_impl<true, true>(c, s) : launch_pstats_impl<true, false>(c, s);
+cudaError_t launch_power_stats(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
+  return c->precision == DFMNMF_FP32 ? launch_pstats_impl<true, true>(c, s, fb, fc)
+                                     : launch_pstats_impl<true, false>(c, s, fb, fc);
 }
 
-cudaError_t launch_stats(const dfmnmf_ctx* c, cudaStream_t s) { return launch_pstats_impl<false, false>(c, s); }
+cudaError_t launch_stats(const dfmnmf_ctx* c, cudaStream_t s) { return launch_pstats_impl<false, false>(c, s, 0, c->F); }
 
 cudaError_t launch_gupd(const dfmnmf_ctx* c, cudaStream_t s) {
   const int M = c->M, N = c->N;

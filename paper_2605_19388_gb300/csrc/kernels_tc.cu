@@ -41,6 +41,7 @@ constexpr int TC_A_BYTES = TC_ROWS * TC_KC * 2;   // 16 KB per operand part
 constexpr int TC_B_BYTES = TC_COLS * TC_KC * 2;   // 4 KB per operand part
 constexpr int TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_B_BYTES;
 constexpr unsigned long long TC_WAIT_CYCLES = 2000000000ull;  // ~1 s at 2 GHz
+constexpr size_t TC_LAMBDA_WHOLE_BYTES = 32 * 1024;  // lambda of the CTA kept whole in shared memory up to this size
 
 // ------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -165,17 +166,19 @@ __global__ void __launch_bounds__(256, 2) k_vtc(const __grid_constant__ CUtensor
                                                 const float* __restrict__ lam, const float* __restrict__ g,
                                                 double2* __restrict__ V, float4* __restrict__ Vdd, int F, int T,
                                                 int Tp, int Tr, int K, int N, float eps,
-                                                unsigned* __restrict__ flags) {
+                                                unsigned* __restrict__ flags, int fb, int fe) {
   extern __shared__ __align__(1024) unsigned char tc_raw[];
   unsigned char* ring = reinterpret_cast<unsigned char*>(((unsigned long long)tc_raw + 1023) & ~1023ull);
   TcSmem* ctl = reinterpret_cast<TcSmem*>(ring + tc_ring_bytes());
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int FPC = TC_ROWS / (16 * K);  // frequencies per CTA
-  const int f0 = blockIdx.x * FPC;
+  const int f0 = fb + blockIdx.x * FPC;  // frequencies f0 .. min(f0 + FPC, fe) - 1 are this CTA's
   const int M = 4 * K;
   const int nch = Tr / TC_KC;
   float* gsh = reinterpret_cast<float*>(ctl + 1);  // [FPC][N][M]
-  float* lsh = gsh + ((FPC * N * M + 3) & ~3);    // [FPC][N][TC_KC]
+  float* lsh = gsh + ((FPC * N * M + 3) & ~3);    // [FPC][N][LW] lambda rows (LW = Tr or TC_KC)
+  const bool whole = (size_t)FPC * N * Tr * sizeof(float) <= TC_LAMBDA_WHOLE_BYTES;
+  const int LW = whole ? Tr : TC_KC;
 
   if (tid == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
@@ -189,7 +192,19 @@ __global__ void __launch_bounds__(256, 2) k_vtc(const __grid_constant__ CUtensor
   for (int i = tid; i < FPC * N * M; i += blockDim.x) {
     const int fj = i / (N * M), rem = i % (N * M);
     const int f = f0 + fj;
-    gsh[i] = (f < F) ? g[(size_t)f * N * M + rem] : 0.f;
+    gsh[i] = (f < fe) ? g[(size_t)f * N * M + rem] : 0.f;
+  }
+  if (whole) {
+    // lambda rows of the CTA's frequencies for every frame, once (cp.async; zero beyond Tp)
+    for (int i = tid; i < FPC * N * (Tr / 4); i += blockDim.x) {
+      const int row = i / (Tr / 4), q = i % (Tr / 4);
+      const int fj = row / N, n = row % N, f = f0 + fj, t = 4 * q;
+      float* dst = lsh + (size_t)row * Tr + t;
+      if (f < fe && t < Tp) cp_async16(dst, lam + ((size_t)n * F + f) * Tp + t);
+      else *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(&ctl->tmem_base))
@@ -244,15 +259,18 @@ __global__ void __launch_bounds__(256, 2) k_vtc(const __grid_constant__ CUtensor
     for (int c = 0; c < nch; ++c) {
       const int s = c % TC_STAGES;
       const int tc0 = c * TC_KC;
-      // lambda rows of the chunk: FPC x N rows of 16 float4 (Tp is a multiple of 4)
-      for (int i = p; i < FPC * N * (TC_KC / 4); i += TC_PRODUCERS) {
-        const int row = i / (TC_KC / 4), q = i % (TC_KC / 4);
-        const int fj = row / N, n = row % N, f = f0 + fj, t = tc0 + 4 * q;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (f < F && t < Tp) v = __ldg(reinterpret_cast<const float4*>(lam + ((size_t)n * F + f) * Tp + t));
-        *reinterpret_cast<float4*>(lsh + row * TC_KC + 4 * q) = v;
+      const int lo = whole ? tc0 : 0;  // column of this chunk inside the lambda rows
+      if (!whole) {
+        // lambda rows of the chunk: FPC x N rows of 16 float4 (Tp is a multiple of 4)
+        for (int i = p; i < FPC * N * (TC_KC / 4); i += TC_PRODUCERS) {
+          const int row = i / (TC_KC / 4), q = i % (TC_KC / 4);
+          const int fj = row / N, n = row % N, f = f0 + fj, t = tc0 + 4 * q;
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (f < fe && t < Tp) v = __ldg(reinterpret_cast<const float4*>(lam + ((size_t)n * F + f) * Tp + t));
+          *reinterpret_cast<float4*>(lsh + row * TC_KC + 4 * q) = v;
+        }
+        asm volatile("bar.sync 1, %0;" ::"n"(TC_PRODUCERS) : "memory");
       }
-      asm volatile("bar.sync 1, %0;" ::"n"(TC_PRODUCERS) : "memory");
       if (c >= TC_STAGES && !mbar_wait(&ctl->empty[s], ((c / TC_STAGES) + 1) & 1)) atomicOr(&ctl->abort, 1u);
       unsigned char* bh = ring + s * TC_STAGE_BYTES + 2 * TC_A_BYTES;
       unsigned char* bl = bh + TC_B_BYTES;
@@ -266,8 +284,8 @@ __global__ void __launch_bounds__(256, 2) k_vtc(const __grid_constant__ CUtensor
         for (int q = 0; q < 8; ++q) ys[q] = 0.f;
         for (int n = 0; n < N; ++n) {
           const float gv = gsh[(fj * N + n) * M + m];
-          const float4 l0 = *reinterpret_cast<const float4*>(lsh + (fj * N + n) * TC_KC + j * 8);
-          const float4 l1 = *reinterpret_cast<const float4*>(lsh + (fj * N + n) * TC_KC + j * 8 + 4);
+          const float4 l0 = *reinterpret_cast<const float4*>(lsh + (size_t)(fj * N + n) * LW + lo + j * 8);
+          const float4 l1 = *reinterpret_cast<const float4*>(lsh + (size_t)(fj * N + n) * LW + lo + j * 8 + 4);
           ys[0] = fmaf(l0.x, gv, ys[0]); ys[1] = fmaf(l0.y, gv, ys[1]);
           ys[2] = fmaf(l0.z, gv, ys[2]); ys[3] = fmaf(l0.w, gv, ys[3]);
           ys[4] = fmaf(l1.x, gv, ys[4]); ys[5] = fmaf(l1.y, gv, ys[5]);
@@ -276,7 +294,7 @@ __global__ void __launch_bounds__(256, 2) k_vtc(const __grid_constant__ CUtensor
         unsigned hw[4], lw[4];
 #pragma unroll
         for (int q = 0; q < 8; q += 2) {
-          const bool v0 = f < F && t0 + q < T, v1 = f < F && t0 + q + 1 < T;
+          const bool v0 = f < fe && t0 + q < T, v1 = f < fe && t0 + q + 1 < T;
           const float w0 = v0 ? fast_rcp(fmaxf(ys[q], eps)) : 0.f;
           const float w1 = v1 ? fast_rcp(fmaxf(ys[q + 1], eps)) : 0.f;
           const __nv_bfloat162 h = __floats2bfloat162_rn(w0, w1);
@@ -291,7 +309,7 @@ __global__ void __launch_bounds__(256, 2) k_vtc(const __grid_constant__ CUtensor
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(&ctl->full[s]);
-      asm volatile("bar.sync 1, %0;" ::"n"(TC_PRODUCERS) : "memory");  // lsh reused by the next chunk
+      if (!whole) asm volatile("bar.sync 1, %0;" ::"n"(TC_PRODUCERS) : "memory");  // lsh reused by the next chunk
     }
   }
 
@@ -315,7 +333,7 @@ __global__ void __launch_bounds__(256, 2) k_vtc(const __grid_constant__ CUtensor
     const int fj = row / (16 * K), rk = row % (16 * K);
     const int k = rk / 16, e = rk % 16;       // packed entry e = a * 4 + b
     const int f = f0 + fj;
-    if (ok && !ctl->abort && f < F) {
+    if (ok && !ctl->abort && f < fe) {
       const int a = e / 4, b = e % 4;
       const double invT = 1.0 / (double)T;
       const size_t blk = (size_t)f * K + k;
@@ -374,8 +392,9 @@ bool tc_supported(int MK, int K) { return MK == 4 && (K == 1 || K == 2 || K == 4
 
 size_t tc_smem_bytes(const dfmnmf_ctx* c) {
   const int FPC = TC_ROWS / (16 * c->K);
-  return 1024 + tc_ring_bytes() + sizeof(TcSmem) +
-         ((size_t)((FPC * c->N * c->M + 3) & ~3) + (size_t)FPC * c->N * TC_KC) * sizeof(float);
+  const bool whole = (size_t)FPC * c->N * c->Tr * sizeof(float) <= TC_LAMBDA_WHOLE_BYTES;
+  return 1024 + tc_ring_bytes() + sizeof(TcSmem) + 16 +
+         ((size_t)((FPC * c->N * c->M + 3) & ~3) + (size_t)FPC * c->N * (whole ? c->Tr : TC_KC)) * sizeof(float);
 }
 
 cudaError_t tc_make_maps(dfmnmf_ctx* c) {
@@ -403,15 +422,15 @@ cudaError_t launch_rprep(const dfmnmf_ctx* c, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_vtc(const dfmnmf_ctx* c, cudaStream_t s) {
+cudaError_t launch_vtc(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
   const size_t sm = tc_smem_bytes(c);
   cudaFuncSetAttribute(k_vtc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   const int FPC = TC_ROWS / (16 * c->K);
-  const int grid = (c->F + FPC - 1) / FPC;
+  const int grid = (fc + FPC - 1) / FPC;
   const CUtensorMap* mh = reinterpret_cast<const CUtensorMap*>(c->tmap_hi);
   const CUtensorMap* ml = reinterpret_cast<const CUtensorMap*>(c->tmap_lo);
   k_vtc<<<grid, 256, sm, s>>>(*mh, *ml, c->lam, c->g, c->V, c->Vdd, c->F, c->T, c->Tp, c->Tr, c->K, c->N,
-                                      c->eps, c->flags);
+                                      c->eps, c->flags, fb, fb + fc);
   return cudaGetLastError();
 }
 
