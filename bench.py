@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--concurrent", type=int, default=8,
+                    help="also time this many independent mixtures run concurrently on separate streams (0: skip)")
     return ap.parse_args()
 
 
@@ -374,6 +376,46 @@ def main():
         out["e2e"] = {"value": world * iters * args.steps / (e2e_ms / 1000.0), "unit": UNIT,
                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8 + 16,
                       "ms_per_step": e2e_ms / args.steps}
+
+    # independent mixtures of the same shape run concurrently, one stream and one context each
+    if args.concurrent > 1:
+        nmix = args.concurrent
+        cctx, cstreams, couts = [], [], []
+        for _ in range(nmix):
+            cctx.append(D.dfmnmf_init(F, T, p.mics, N, Bb, x_d, W0_d, H0_d, g0_d, Q0_d, ip_arith=ip,
+                                      precision=precisions[forms[0]]))
+            cstreams.append(torch.cuda.Stream(device=dev))
+            couts.append(torch.empty((N, F, T, M), dtype=torch.complex64, device=dev))
+
+        def step_many(_):
+            cur = torch.cuda.current_stream()
+            start = torch.cuda.Event()
+            start.record(cur)
+            for c, st in zip(cctx, cstreams):
+                st.wait_event(start)
+                D.dfmnmf_set_observation(c, x_d, stream=st)
+                D.dfmnmf_set_params(c, Q0_d, W0_d, H0_d, g0_d, stream=st)
+                D.dfmnmf_iterate(c, iters, stream=st)
+            for c, st, co in zip(cctx, cstreams, couts):
+                D.dfmnmf_loglik(c, stream=st)
+                D.dfmnmf_separate(c, co, stream=st)
+                ev = torch.cuda.Event()
+                ev.record(st)
+                cur.wait_event(ev)
+
+        for _ in range(2):
+            step_many(None)
+        torch.cuda.synchronize()
+        barrier()
+        many_ms = max_over_ranks(timed(step_many, None, max(2, args.steps // 2)))
+        n_many = max(2, args.steps // 2)
+        val = world * nmix * iters * n_many / (many_ms / 1000.0)
+        out["concurrent"] = {"mixtures": nmix, "value": val, "unit": UNIT, "ms_per_step": many_ms / n_many,
+                             "tf_bin_mic_updates_per_s": F * T * M * val,
+                             "alg_GBps_per_iteration_bytes": ib * val / world / 1e9,
+                             "frac_of_hbm_peak": ib * val / world / 1e9 / peak}
+        for c in cctx:
+            D.dfmnmf_destroy(c)
 
     # variants on the same GPU: native-FP64 and plain-FP32 IP solves (FP32 form)
     if not args.no_variants:

@@ -172,6 +172,106 @@ __global__ void __launch_bounds__(256) k_pstats(const float2* __restrict__ x, co
   }
 }
 
+// Frame-per-thread variant for the common layouts (compile-time K and M_k):
+// every thread owns whole frames of one frequency, keeps P, yhat, w and u of
+// all M microphones in registers, reads g[f] rows from shared memory as
+// broadcast vector loads and writes A, D for every source -- no shuffles and
+// no per-subarray redundancy.  Q (split in two floats) is read from shared
+// memory when P is formed here.
+template <int K, int MK, bool COMPUTE_P, bool COMP>
+__global__ void __launch_bounds__(256) k_pstats_ft(const float2* __restrict__ x, const double2* __restrict__ Q64,
+                                                   const float* __restrict__ lam, const float* __restrict__ g,
+                                                   float* __restrict__ P, float* __restrict__ A,
+                                                   float* __restrict__ D, int F, int T, int Tp, int N, float eps,
+                                                   int fb, int tpc) {
+  constexpr int M = K * MK;
+  extern __shared__ __align__(16) float sm[];
+  const int f = fb + blockIdx.x, tid = threadIdx.x;
+  float* gs = sm;                                                       // [N][M]
+  float2* Qh = reinterpret_cast<float2*>(sm + ((N * M + 3) & ~3));      // [K][MK][MK] high parts
+  float2* Ql = Qh + K * MK * MK;                                        // low parts
+  for (int i = tid; i < N * M; i += blockDim.x) gs[i] = g[(size_t)f * N * M + i];
+  if (COMPUTE_P)
+    for (int i = tid; i < K * MK * MK; i += blockDim.x) split_c(Q64[(size_t)f * K * MK * MK + i], Qh[i], Ql[i]);
+  __syncthreads();
+  const int t0 = blockIdx.y * tpc, t1 = min(T, t0 + tpc);
+  const float* lt = lam + (size_t)f * Tp;
+  for (int t = t0 + tid; t < t1; t += blockDim.x) {
+    float pv[M];
+    float* Pt = P + ((size_t)f * T + t) * M;
+    if (COMPUTE_P) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        float2 xv[MK];
+        load_block<MK>(x + ((size_t)f * T + t) * M + k * MK, xv);
+#pragma unroll
+        for (int mu = 0; mu < MK; ++mu) {
+          const float2* qh = Qh + (k * MK + mu) * MK;
+          float2 y;
+          if (COMP) {
+            y = cdot2<MK>(qh, Ql + (k * MK + mu) * MK, xv);
+          } else {
+            float yr = 0.f, yi = 0.f;
+#pragma unroll
+            for (int nu = 0; nu < MK; ++nu) {
+              yr = fmaf(qh[nu].x, xv[nu].x, fmaf(-qh[nu].y, xv[nu].y, yr));
+              yi = fmaf(qh[nu].x, xv[nu].y, fmaf(qh[nu].y, xv[nu].x, yi));
+            }
+            y = make_float2(yr, yi);
+          }
+          pv[k * MK + mu] = fmaf(y.x, y.x, y.y * y.y);
+        }
+      }
+      if constexpr (M % 4 == 0) {
+#pragma unroll
+        for (int m = 0; m < M; m += 4)
+          *reinterpret_cast<float4*>(Pt + m) = make_float4(pv[m], pv[m + 1], pv[m + 2], pv[m + 3]);
+      } else {
+#pragma unroll
+        for (int m = 0; m < M; ++m) Pt[m] = pv[m];
+      }
+    } else {
+      if constexpr (M % 4 == 0) {
+#pragma unroll
+        for (int m = 0; m < M; m += 4) {
+          const float4 q = *reinterpret_cast<const float4*>(Pt + m);
+          pv[m] = q.x; pv[m + 1] = q.y; pv[m + 2] = q.z; pv[m + 3] = q.w;
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < M; ++m) pv[m] = Pt[m];
+      }
+    }
+    float ys[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) ys[m] = 0.f;
+    for (int n = 0; n < N; ++n) {
+      const float l = __ldg(lt + (size_t)n * F * Tp + t);
+      const float* gr = gs + n * M;
+#pragma unroll
+      for (int m = 0; m < M; ++m) ys[m] = fmaf(l, gr[m], ys[m]);
+    }
+    float w[M], u[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      w[m] = fast_rcp(fmaxf(ys[m], eps));
+      u[m] = pv[m] * w[m] * w[m];
+    }
+    for (int n = 0; n < N; ++n) {
+      const float* gr = gs + n * M;
+      float a = 0.f, d = 0.f;
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        a = fmaf(gr[m], u[m], a);
+        d = fmaf(gr[m], w[m], d);
+      }
+      const size_t o = ((size_t)n * F + f) * Tp + t;
+      A[o] = a;
+      D[o] = d;
+    }
+  }
+}
+
 // ------------------------------------------------------------------ g update
 // One CTA per frequency.  Frames arrive in chunks of GT through a
 // double-buffered cp.async pipeline (lambda rows and the [t][m] block of P);
@@ -277,8 +377,23 @@ __global__ void __launch_bounds__(256) k_gupd(const float* __restrict__ lam, con
   else if ((NV) <= 8) { constexpr int NM_ = 8; __VA_ARGS__; }     \
   else { constexpr int NM_ = 16; __VA_ARGS__; }
 
+template <int K, int MK, bool COMPUTE_P, bool COMP>
+static cudaError_t launch_pstats_ft(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
+  const int tpc = 512;  // frames per CTA (two per thread)
+  dim3 grid(fc, (c->T + tpc - 1) / tpc);
+  const size_t sm = ((size_t)((c->N * c->M + 3) & ~3) + (COMPUTE_P ? 4 * (size_t)K * MK * MK : 0)) * sizeof(float);
+  auto kern = k_pstats_ft<K, MK, COMPUTE_P, COMP>;
+  if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  kern<<<grid, 256, sm, s>>>(c->x, c->Q64, c->lam, c->g, c->P, c->A, c->D, c->F, c->T, c->Tp, c->N, c->eps, fb, tpc);
+  return cudaGetLastError();
+}
+
 template <bool COMPUTE_P, bool COMP>
 static cudaError_t launch_pstats_impl(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
+  if (c->MK == 4 && c->K == 4) return launch_pstats_ft<4, 4, COMPUTE_P, COMP>(c, s, fb, fc);
+  if (c->MK == 4 && c->K == 2) return launch_pstats_ft<2, 4, COMPUTE_P, COMP>(c, s, fb, fc);
+  if (c->MK == 4 && c->K == 1) return launch_pstats_ft<1, 4, COMPUTE_P, COMP>(c, s, fb, fc);
+  if (c->MK == 4 && c->K == 3) return launch_pstats_ft<3, 4, COMPUTE_P, COMP>(c, s, fb, fc);
   const int TB = 256 / c->K;
   dim3 grid(fc, (c->T + TB - 1) / TB);
   const bool pow2 = (c->K & (c->K - 1)) == 0;
