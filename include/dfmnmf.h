@@ -167,12 +167,15 @@ int dfmnmf_get_buffer(dfmnmf_ctx* ctx, int which, void* dst, size_t dst_bytes, v
 int dfmnmf_launches_per_iteration(const dfmnmf_ctx* ctx);
 
 /*
- * Profiling aid: run n_iter >= 1 iterations launch by launch, with a CUDA
- * event recorded on `stream` between consecutive kernels, and return the mean
- * duration in milliseconds of each kernel of an iteration (avg_ms[i]) and its
- * name (names[i], static strings; names may be NULL).  *count receives the
- * number of kernels; cap is the capacity of both arrays (EINVAL if smaller).
- * Advances the state by n_iter iterations.  Synchronises `stream`.
+ * Profiling aid: run n_iter >= 1 iterations, each one CUDA graph of the
+ * iteration's kernels launched band-wide one after another with a timing
+ * event after every kernel (so host launch latency is not counted), and
+ * return the mean duration in milliseconds of each kernel of an iteration
+ * (avg_ms[i], including the launch gap before it) and its name (names[i],
+ * static strings; names may be NULL; a kernel launched twice per iteration
+ * appears twice).  *count receives the number of kernels; cap is the
+ * capacity of both arrays (EINVAL if smaller).  Advances the state by n_iter
+ * iterations.  Synchronises `stream`.
  */
 int dfmnmf_kernel_times(dfmnmf_ctx* ctx, int n_iter, double* avg_ms, const char** names, int cap,
                         int* count, void* stream);

@@ -50,7 +50,7 @@ void free_ctx(dfmnmf_ctx* c) {
   if (c->fork_ev) cudaEventDestroy(c->fork_ev);
   if (c->join_ev) cudaEventDestroy(c->join_ev);
   void* ptrs[] = {c->x, c->Q64, c->Q32, c->Qinv32, c->V, c->Vdd, c->W, c->H, c->g, c->lam,
-                  c->P, c->A, c->D, c->red, c->nll_dev, c->flags, c->nmf_part, c->nmf_ticket, c->Rhi, c->Rlo};
+                  c->P, c->A, c->D, c->red, c->nll_dev, c->flags, c->nmf_part, c->nmf_ticket, c->Rhi, c->Rlo, c->wy_hi, c->wy_lo};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -104,18 +104,17 @@ struct Launch {
 
 int iteration_launches(const dfmnmf_ctx* c, Launch* out) {
   int n = 0;
-  const bool fused = dfm::nmf_fused_lambda(c);
-  if (c->precision == DFMNMF_BF16_TC) out[n++] = {DFMNMF_STAGE_COV, "k_vtc", dfm::launch_vtc, true};
-  else out[n++] = {DFMNMF_STAGE_COV, "k_cov", dfm::launch_cov, true};
+  if (c->precision == DFMNMF_BF16_TC) {
+    out[n++] = {DFMNMF_STAGE_COV, "k_wprep", dfm::launch_wprep, true};
+    out[n++] = {DFMNMF_STAGE_COV, "k_vtc", dfm::launch_vtc, true};
+  } else out[n++] = {DFMNMF_STAGE_COV, "k_cov", dfm::launch_cov, true};
   out[n++] = {DFMNMF_STAGE_IP, "k_ip", dfm::launch_ip, true};
   out[n++] = {DFMNMF_STAGE_W, "k_pstats", dfm::launch_power_stats, true};
   out[n++] = {DFMNMF_STAGE_W, "k_wupd", [](const dfmnmf_ctx* c, cudaStream_t s, int, int) { return dfm::launch_wupd(c, s); }, false};
-  if (!fused)
-    out[n++] = {DFMNMF_STAGE_W, "k_lambda", [](const dfmnmf_ctx* c, cudaStream_t s, int, int) { return dfm::launch_lambda(c, s); }, false};
+  out[n++] = {DFMNMF_STAGE_W, "k_lambda", [](const dfmnmf_ctx* c, cudaStream_t s, int, int) { return dfm::launch_lambda(c, s); }, false};
   out[n++] = {DFMNMF_STAGE_H, "k_stats", [](const dfmnmf_ctx* c, cudaStream_t s, int, int) { return dfm::launch_stats(c, s); }, false};
   out[n++] = {DFMNMF_STAGE_H, "k_hupd", [](const dfmnmf_ctx* c, cudaStream_t s, int, int) { return dfm::launch_hupd(c, s); }, false};
-  if (!fused)
-    out[n++] = {DFMNMF_STAGE_H, "k_lambda", [](const dfmnmf_ctx* c, cudaStream_t s, int, int) { return dfm::launch_lambda(c, s); }, false};
+  out[n++] = {DFMNMF_STAGE_H, "k_lambda", [](const dfmnmf_ctx* c, cudaStream_t s, int, int) { return dfm::launch_lambda(c, s); }, false};
   out[n++] = {DFMNMF_STAGE_G, "k_gupd", [](const dfmnmf_ctx* c, cudaStream_t s, int, int) { return dfm::launch_gupd(c, s); }, false};
   return n;
 }
@@ -254,16 +253,20 @@ int dfmnmf_init(dfmnmf_ctx** out, const dfmnmf_desc* d, const void* x, const flo
     return r;
   }
   if (c->precision == DFMNMF_BF16_TC) {
-    const size_t nr = (size_t)c->F * 16 * c->K * c->Tr;
-    unsigned short *rh = nullptr, *rl = nullptr;
-    if ((r = dalloc(&rh, nr, "R hi")) || (r = dalloc(&rl, nr, "R lo"))) {
-      c->Rhi = rh;
-      c->Rlo = rl;
+    const size_t nr = (size_t)c->F * 16 * c->K * c->Tr, nw = (size_t)c->F * c->M * c->Tr;
+    unsigned short *rh = nullptr, *rl = nullptr, *wh = nullptr, *wl = nullptr;
+    r = dalloc(&rh, nr, "R hi");
+    if (!r) r = dalloc(&rl, nr, "R lo");
+    if (!r) r = dalloc(&wh, nw, "w hi");
+    if (!r) r = dalloc(&wl, nw, "w lo");
+    c->Rhi = rh;
+    c->Rlo = rl;
+    c->wy_hi = wh;
+    c->wy_lo = wl;
+    if (r) {
       free_ctx(c);
       return r;
     }
-    c->Rhi = rh;
-    c->Rlo = rl;
     if (dfm::tc_make_maps(c) != cudaSuccess) {
       free_ctx(c);
       return fail(DFMNMF_ECUDA, "tensor map creation failed (cuTensorMapEncodeTiled unavailable or rejected)");
@@ -349,26 +352,44 @@ int dfmnmf_kernel_times(dfmnmf_ctx* c, int n_iter, double* avg_ms, const char** 
   *count = n;
   if (cap < n) return fail(DFMNMF_EINVAL, "capacity %d < %d kernels", cap, n);
   cudaStream_t s = as_stream(stream);
-  cudaEvent_t ev[kMaxLaunches + 1];
-  for (int i = 0; i <= n; ++i) CK(cudaEventCreate(&ev[i]));
-  for (int i = 0; i < n; ++i) avg_ms[i] = 0.0;
-  int rc = DFMNMF_OK;
-  for (int it = 0; it < n_iter && rc == DFMNMF_OK; ++it) {
-    cudaEventRecord(ev[0], s);
-    for (int i = 0; i < n; ++i) {
-      cudaError_t e = L[i].fn(c, s, 0, c->F);
-      if (e != cudaSuccess) { rc = fail(DFMNMF_ECUDA, "%s: %s", L[i].name, cudaGetErrorString(e)); break; }
-      cudaEventRecord(ev[i + 1], s);
+  // One iteration, band-wide launches in order, captured into a graph with a
+  // timing event after every launch: replays run back to back on the device,
+  // so host launch latency does not enter the per-kernel times.
+  cudaEvent_t ev[kMaxLaunches + 1] = {};
+  int nev = 0;
+  for (; nev <= n; ++nev)
+    if (cudaEventCreate(&ev[nev]) != cudaSuccess) break;
+  int rc = nev <= n ? fail(DFMNMF_ECUDA, "event creation failed") : DFMNMF_OK;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  if (!rc && cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    rc = fail(DFMNMF_ECUDA, "capture failed");
+  if (!rc) {
+    cudaError_t e = cudaEventRecordWithFlags(ev[0], c->cap_stream, cudaEventRecordExternal);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+      e = L[i].fn(c, c->cap_stream, 0, c->F);
+      if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[i + 1], c->cap_stream, cudaEventRecordExternal);
     }
-    if (rc) break;
-    if (cudaEventSynchronize(ev[n]) != cudaSuccess) { rc = fail(DFMNMF_ECUDA, "event sync failed"); break; }
+    const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) rc = fail(DFMNMF_ECUDA, "capture of the timed iteration failed: %s",
+                                                         cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  if (!rc && cudaGraphInstantiate(&gexec, graph, 0) != cudaSuccess) rc = fail(DFMNMF_ECUDA, "graph instantiation failed");
+  for (int i = 0; i < n; ++i) avg_ms[i] = 0.0;
+  for (int it = 0; it < n_iter && !rc; ++it) {
+    if (cudaGraphLaunch(gexec, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+      rc = fail(DFMNMF_ECUDA, "timed iteration failed");
+      break;
+    }
     for (int i = 0; i < n; ++i) {
       float ms = 0.f;
       cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
       avg_ms[i] += ms / n_iter;
     }
   }
-  for (int i = 0; i <= n; ++i) cudaEventDestroy(ev[i]);
+  if (gexec) cudaGraphExecDestroy(gexec);
+  if (graph) cudaGraphDestroy(graph);
+  for (int i = 0; i < nev; ++i) cudaEventDestroy(ev[i]);
   if (names)
     for (int i = 0; i < n; ++i) names[i] = L[i].name;
   return rc;

@@ -35,8 +35,12 @@ struct dfmnmf_ctx {
   // tensor-core form: x x^H split in two bfloat16 parts, [F * 16 K][Tr] each, and their TMA descriptors
   void* Rhi;
   void* Rlo;
+  void* wy_hi;  // 1/yhat split in two bfloat16 parts, [F * M][Tr] each (k_wprep)
+  void* wy_lo;
   alignas(64) unsigned char tmap_hi[128];
   alignas(64) unsigned char tmap_lo[128];
+  alignas(64) unsigned char tmap_whi[128];
+  alignas(64) unsigned char tmap_wlo[128];
   size_t red_len;
   // CUDA graph of one iteration, captured on first use
   cudaStream_t cap_stream;
@@ -55,13 +59,14 @@ cudaError_t launch_lambda(const dfmnmf_ctx* c, cudaStream_t s);
 cudaError_t launch_cov(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc);
 cudaError_t launch_vtc(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc);  // tensor-core covariances (BF16_TC form)
 cudaError_t launch_rprep(const dfmnmf_ctx* c, cudaStream_t s);   // split-bfloat16 x x^H for the TC form
+cudaError_t launch_wprep(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc);  // split-bfloat16 1/yhat for the TC form
 cudaError_t tc_make_maps(dfmnmf_ctx* c);
 bool tc_supported(int MK, int K);
 cudaError_t launch_ip(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc);
 cudaError_t launch_power_stats(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc);  // P + A/D (current lambda)
-cudaError_t launch_wupd(const dfmnmf_ctx* c, cudaStream_t s);         // Eq. 8 + lambda
+cudaError_t launch_wupd(const dfmnmf_ctx* c, cudaStream_t s);         // Eq. 8
 cudaError_t launch_stats(const dfmnmf_ctx* c, cudaStream_t s);        // A/D from stored P
-cudaError_t launch_hupd(const dfmnmf_ctx* c, cudaStream_t s);         // Eq. 9 + lambda
+cudaError_t launch_hupd(const dfmnmf_ctx* c, cudaStream_t s);         // Eq. 9
 cudaError_t launch_gupd(const dfmnmf_ctx* c, cudaStream_t s);         // Eq. 10
 cudaError_t launch_loglik(const dfmnmf_ctx* c, cudaStream_t s);       // Eq. 12 -> c->nll_dev
 cudaError_t launch_qinv(const dfmnmf_ctx* c, cudaStream_t s);
@@ -71,9 +76,6 @@ cudaError_t launch_q_convert(const dfmnmf_ctx* c, cudaStream_t s);    // Q64 -> 
 // Record the message returned by dfmnmf_last_error() on this thread.
 void set_last_error(const char* msg);
 
-// Whether the NMF update kernels refresh lambda themselves (else a separate
-// lambda launch follows them).
-bool nmf_fused_lambda(const dfmnmf_ctx* c);
 size_t nmf_scratch_floats(const dfmnmf_ctx* c);
 size_t nmf_ticket_count(const dfmnmf_ctx* c);
 

@@ -18,23 +18,56 @@ namespace dfm {
 
 
 // ------------------------------------------------------------------ lambda
-__global__ void __launch_bounds__(256) k_lambda(const float* __restrict__ W, const float* __restrict__ H,
-                                                float* __restrict__ lam, int F, int T, int Tp, int B) {
-  extern __shared__ float ws[];
-  const int n = blockIdx.z, f = blockIdx.y;
-  const int t = blockIdx.x * 256 + threadIdx.x;
-  for (int b = threadIdx.x; b < B; b += 256) ws[b] = W[((size_t)n * F + f) * B + b];
+// lambda[n][f][t] = sum_b W[n][f][b] H[n][b][t] (Eq. 2) for a tile of
+// LAM_F frequencies x 128 frames of one source.  The W rows of the tile sit
+// in shared memory (read as broadcast float4 loads); each thread holds H of
+// its frame for 16 bases at a time in registers and writes LAM_F outputs,
+// coalesced along t.  Frames T .. Tp-1 are written too: H is zero there, so
+// the zero tail of lambda is kept.
+constexpr int LAM_F = 16;
+
+__global__ void __launch_bounds__(128) k_lambda(const float* __restrict__ W, const float* __restrict__ H,
+                                                float* __restrict__ lam, int F, int Tp, int B) {
+  extern __shared__ __align__(16) float ws[];  // [LAM_F][Bq], Bq = B rounded up to 16, zero padded
+  const int n = blockIdx.z, f0 = blockIdx.y * LAM_F;
+  const int Bq = (B + 15) & ~15;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int i = threadIdx.x; i < LAM_F * Bq; i += blockDim.x) {
+    const int fi = i / Bq, b = i % Bq, f = f0 + fi;
+    ws[i] = (f < F && b < B) ? W[((size_t)n * F + f) * B + b] : 0.f;
+  }
   __syncthreads();
-  if (t >= T) return;
+  if (t >= Tp) return;
   const float* Hn = H + (size_t)n * B * Tp + t;
-  float s = 0.f;
-  for (int b = 0; b < B; ++b) s = fmaf(ws[b], Hn[(size_t)b * Tp], s);
-  lam[((size_t)n * F + f) * Tp + t] = s;
+  float acc[LAM_F];
+#pragma unroll
+  for (int fi = 0; fi < LAM_F; ++fi) acc[fi] = 0.f;
+  for (int b0 = 0; b0 < Bq; b0 += 16) {
+    float h[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) h[j] = (b0 + j < B) ? __ldg(Hn + (size_t)(b0 + j) * Tp) : 0.f;
+#pragma unroll
+    for (int fi = 0; fi < LAM_F; ++fi) {
+      const float4* wr = reinterpret_cast<const float4*>(ws + fi * Bq + b0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 w4 = wr[q];
+        acc[fi] = fmaf(w4.x, h[4 * q + 0], acc[fi]);
+        acc[fi] = fmaf(w4.y, h[4 * q + 1], acc[fi]);
+        acc[fi] = fmaf(w4.z, h[4 * q + 2], acc[fi]);
+        acc[fi] = fmaf(w4.w, h[4 * q + 3], acc[fi]);
+      }
+    }
+  }
+#pragma unroll
+  for (int fi = 0; fi < LAM_F; ++fi)
+    if (f0 + fi < F) lam[((size_t)n * F + f0 + fi) * Tp + t] = acc[fi];
 }
 
 cudaError_t launch_lambda(const dfmnmf_ctx* c, cudaStream_t s) {
-  dim3 grid((c->T + 255) / 256, c->F, c->N);
-  k_lambda<<<grid, 256, c->B * sizeof(float), s>>>(c->W, c->H, c->lam, c->F, c->T, c->Tp, c->B);
+  dim3 grid((c->Tp + 127) / 128, (c->F + LAM_F - 1) / LAM_F, c->N);
+  const size_t sm = (size_t)LAM_F * ((c->B + 15) & ~15) * sizeof(float);
+  k_lambda<<<grid, 128, sm, s>>>(c->W, c->H, c->lam, c->F, c->Tp, c->B);
   return cudaGetLastError();
 }
 
@@ -273,14 +306,15 @@ __global__ void __launch_bounds__(256) k_pstats_ft(const float2* __restrict__ x,
 }
 
 // ------------------------------------------------------------------ g update
-// One CTA per frequency.  Frames arrive in chunks of GT through a
-// double-buffered cp.async pipeline (lambda rows and the [t][m] block of P);
-// thread (slice s, microphone m) keeps g[f][:][m] and the 2 N partial sums of
-// Eq. (10) in registers, and the slices are added in a fixed order at the end.
+// One CTA per frequency.  Frames arrive in chunks of GT through an NST-stage
+// cp.async ring (lambda rows and the [t][m] block of P), NST - 1 chunks
+// ahead of the one being used; thread (slice s, microphone m) keeps
+// g[f][:][m] and the 2 N partial sums of Eq. (10) in registers, and the
+// slices are added in a fixed order at the end.
 constexpr int GT = 128;
 
 // NM is N itself for N <= 8 (no padded work) and 16 (guarded) above.
-template <int NM>
+template <int NM, int NST>
 __global__ void __launch_bounds__(256) k_gupd(const float* __restrict__ lam, const float* __restrict__ P,
                                               float* __restrict__ g, int F, int T, int Tp, int M, int N, float eps,
                                               unsigned* __restrict__ flags) {
@@ -289,23 +323,26 @@ __global__ void __launch_bounds__(256) k_gupd(const float* __restrict__ lam, con
   const int S = blockDim.x / M;            // frame slices
   const int m = tid % M, s = tid / M;
   const bool active = s < S;
-  float* ls = smg;                         // [2][N][GT]
-  float* ps = ls + 2 * N * GT;             // [2][GT][M]
-  float* red = ps + 2 * GT * M;            // [S][M][2N]
+  float* ls = smg;                         // [NST][N][GT]
+  float* ps = ls + NST * N * GT;           // [NST][GT][M]
+  float* red = ps + NST * GT * M;          // [S][M][2N]
   const bool vec = (M % 4) == 0;
+  const int nchunk = (T + GT - 1) / GT;
   auto issue = [&](int c) {
-    const int t0 = c * GT, nt = min(GT, T - t0), buf = c & 1;
-    for (int i = tid; i < N * nt; i += blockDim.x) {
-      const int n = i / nt, tt = i % nt;
-      cp_async4(ls + (buf * N + n) * GT + tt, lam + ((size_t)n * F + f) * Tp + t0 + tt);
+    if (c < nchunk) {
+      const int t0 = c * GT, nt = min(GT, T - t0), buf = c % NST;
+      for (int i = tid; i < N * nt; i += blockDim.x) {
+        const int n = i / nt, tt = i % nt;
+        cp_async4(ls + (buf * N + n) * GT + tt, lam + ((size_t)n * F + f) * Tp + t0 + tt);
+      }
+      const float* src = P + ((size_t)f * T + t0) * M;
+      float* dst = ps + (size_t)buf * GT * M;
+      if (vec)
+        for (int i = tid; i < nt * M / 4; i += blockDim.x) cp_async16(dst + 4 * i, src + 4 * i);
+      else
+        for (int i = tid; i < nt * M; i += blockDim.x) cp_async4(dst + i, src + i);
     }
-    const float* src = P + ((size_t)f * T + t0) * M;
-    float* dst = ps + (size_t)buf * GT * M;
-    if (vec)
-      for (int i = tid; i < nt * M / 4; i += blockDim.x) cp_async16(dst + 4 * i, src + 4 * i);
-    else
-      for (int i = tid; i < nt * M; i += blockDim.x) cp_async4(dst + i, src + i);
-    cp_async_commit();
+    cp_async_commit();  // an empty group past the end keeps the group count uniform
   };
   float gr[NM], num[NM], den[NM];
 #pragma unroll
@@ -314,17 +351,13 @@ __global__ void __launch_bounds__(256) k_gupd(const float* __restrict__ lam, con
     num[n] = 0.f;
     den[n] = 0.f;
   }
-  const int nchunk = (T + GT - 1) / GT;
-  issue(0);
+#pragma unroll
+  for (int c = 0; c < NST - 1; ++c) issue(c);
   for (int c = 0; c < nchunk; ++c) {
-    if (c + 1 < nchunk) {
-      issue(c + 1);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
+    issue(c + NST - 1);
+    cp_async_wait<NST - 1>();
     __syncthreads();
-    const int nt = min(GT, T - c * GT), buf = c & 1;
+    const int nt = min(GT, T - c * GT), buf = c % NST;
     const float* lb = ls + buf * N * GT;
     const float* pb = ps + (size_t)buf * GT * M;
     if (active) {
@@ -416,15 +449,24 @@ cudaError_t launch_power_stats(const dfmnmf_ctx* c, cudaStream_t s, int fb, int 
 
 cudaError_t launch_stats(const dfmnmf_ctx* c, cudaStream_t s) { return launch_pstats_impl<false, false>(c, s, 0, c->F); }
 
+// Four stages while they fit in 64 KB of shared memory (several CTAs per SM),
+// else two.
 cudaError_t launch_gupd(const dfmnmf_ctx* c, cudaStream_t s) {
   const int M = c->M, N = c->N;
   const int S = 256 / M;
-  const size_t sm = (size_t)(2 * N * GT + 2 * GT * M + S * M * 2 * N) * sizeof(float);
-#define DFM_GUPD(NMV)                                                                                          \
-  {                                                                                                            \
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_gupd<NMV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
-    k_gupd<NMV><<<c->F, 256, sm, s>>>(c->lam, c->P, c->g, c->F, c->T, c->Tp, M, N, c->eps, c->flags);                 \
+  const size_t stage = (size_t)(N * GT + GT * M) * sizeof(float);
+  const size_t red = (size_t)S * M * 2 * N * sizeof(float);
+  const bool deep = 4 * stage + red <= 64 * 1024;
+  const size_t sm = (deep ? 4 : 2) * stage + red;
+#define DFM_GUPD_K(NMV, NSTV)                                                                                    \
+  {                                                                                                              \
+    if (sm > 48 * 1024)                                                                                          \
+      cudaFuncSetAttribute(k_gupd<NMV, NSTV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);             \
+    k_gupd<NMV, NSTV><<<c->F, 256, sm, s>>>(c->lam, c->P, c->g, c->F, c->T, c->Tp, M, N, c->eps, c->flags);      \
   }
+#define DFM_GUPD(NMV)           \
+  if (deep) DFM_GUPD_K(NMV, 4)  \
+  else DFM_GUPD_K(NMV, 2)
   switch (N) {
     case 1: DFM_GUPD(1) break;
     case 2: DFM_GUPD(2) break;
@@ -437,6 +479,7 @@ cudaError_t launch_gupd(const dfmnmf_ctx* c, cudaStream_t s) {
     default: DFM_GUPD(16) break;
   }
 #undef DFM_GUPD
+#undef DFM_GUPD_K
   return cudaGetLastError();
 }
 

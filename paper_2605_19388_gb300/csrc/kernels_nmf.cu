@@ -6,9 +6,10 @@
 //   Eq. (8)  num_W[f][b] = sum_t A[f][t] H[b][t]   (F x T)(T x B)
 //   Eq. (9)  num_H[b][t] = sum_f W[f][b] A[f][t]   (B x F)(F x T)
 // (same with D for the denominators), followed by the square-root ratio.  The
-// updated factor is then multiplied back into lambda = W H for the rows (or
-// columns) the CTA owns, so the refresh of the model that the paper asks for
-// after every rule costs no extra pass over W or H.
+// refresh of the model lambda = W H that the paper asks for after every rule
+// is the separate tiled k_lambda launch: done here, by the CTA that finishes
+// a tile, it serialised an O(F) (Eq. 9) or register-heavy (Eq. 8) tail
+// behind the split reduction.
 #include "common.cuh"
 #include "internal.h"
 
@@ -56,18 +57,17 @@ __device__ __forceinline__ bool split_fixup(float& num, float& den, int S, int s
 // padded row stride Tp is a multiple of 4) and stored transposed ([t][f],
 // [t][b]) after the current chunk is consumed.  Every CTA writes its partial
 // sums; the last CTA of a tile (counted with an atomic ticket) adds the S
-// partials in a fixed order, updates W and refreshes lambda.  Nothing waits
+// partials in a fixed order and updates W.  Nothing waits
 // on another CTA.
 __global__ void __launch_bounds__(256) k_wupd(const float* __restrict__ A, const float* __restrict__ D,
                                               const float* __restrict__ H, float* __restrict__ W,
-                                              float* __restrict__ lam, int F, int T, int Tp, int B, float eps,
-                                              int refresh, unsigned* __restrict__ flags, int S, int cps,
+                                              int F, int T, int Tp, int B, float eps,
+                                              unsigned* __restrict__ flags, int S, int cps,
                                               float* __restrict__ part, unsigned* __restrict__ ticket) {
   constexpr int TS = 20;  // padded row of the transposed tiles: conflict-free stores, 16-byte rows
   constexpr int STAGE = 3 * KCH * TS;
   __shared__ __align__(16) float stg[STAGE];
   __shared__ float red[NWARP * 32 * 16];
-  __shared__ float Wn[TILE * TILE];
   const int nb = (B + TILE - 1) / TILE;
   const int bt = blockIdx.z % nb, split = blockIdx.z / nb;
   const int f0 = blockIdx.x * TILE, n = blockIdx.y, b0 = bt * TILE;
@@ -140,42 +140,11 @@ __global__ void __launch_bounds__(256) k_wupd(const float* __restrict__ A, const
     }
     if (!split_fixup(num, den, S, split, (n * gridDim.x + blockIdx.x) * nb + bt, part, ticket)) return;
     const int f = f0 + fi, b = b0 + bi;
-    float wn = 0.f;
     if (f < F && b < B) {
       float* wp = W + ((size_t)n * F + f) * B + b;
-      wn = *wp * sqrtf(num / fmaxf(den, eps));
+      const float wn = *wp * sqrtf(num / fmaxf(den, eps));
       if (!finitef(wn)) atomicOr(flags + FLAG_NONFINITE, 1u);
       *wp = wn;
-    }
-    Wn[fi * TILE + bi] = wn;
-  }
-  if (!refresh) return;
-  __syncthreads();
-  // lambda[n][f][t] = sum_b Wn[f][b] H[b][t] for the 16 rows of this CTA (B <= 16 here), 4 frames per thread
-  for (int t = 4 * tid; t < T; t += 4 * 256) {
-    float4 hv[TILE];
-#pragma unroll
-    for (int b = 0; b < TILE; ++b) hv[b] = (b < B) ? __ldg(reinterpret_cast<const float4*>(Hn + (size_t)b * Tp + t)) : z4;
-#pragma unroll 4
-    for (int fi = 0; fi < TILE; ++fi) {
-      const int f = f0 + fi;
-      if (f >= F) break;
-      float4 s4 = z4;
-#pragma unroll
-      for (int b = 0; b < TILE; ++b) {
-        const float wv = Wn[fi * TILE + b];
-        s4.x = fmaf(wv, hv[b].x, s4.x);
-        s4.y = fmaf(wv, hv[b].y, s4.y);
-        s4.z = fmaf(wv, hv[b].z, s4.z);
-        s4.w = fmaf(wv, hv[b].w, s4.w);
-      }
-      float* lp = lam + ((size_t)n * F + f) * Tp + t;
-      if (t + 3 < T) {
-        *reinterpret_cast<float4*>(lp) = s4;
-      } else {
-        const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
-        for (int j = 0; j < 4 && t + j < T; ++j) lp[j] = sv[j];
-      }
     }
   }
 }
@@ -187,13 +156,12 @@ __global__ void __launch_bounds__(256) k_wupd(const float* __restrict__ A, const
 // their natural [f][t] / [f][b] layouts, double-buffered.
 __global__ void __launch_bounds__(256) k_hupd(const float* __restrict__ A, const float* __restrict__ D,
                                               const float* __restrict__ W, float* __restrict__ H,
-                                              float* __restrict__ lam, int F, int T, int Tp, int B, float eps,
-                                              int refresh, unsigned* __restrict__ flags, int S, int cps,
+                                              int F, int T, int Tp, int B, float eps,
+                                              unsigned* __restrict__ flags, int S, int cps,
                                               float* __restrict__ part, unsigned* __restrict__ ticket) {
   constexpr int STAGE = 3 * KCH * TILE;
   __shared__ __align__(16) float stg[2 * STAGE];
   __shared__ float red[NWARP * 32 * 16];
-  __shared__ float Hn_s[TILE * TILE];  // [b][t]
   const int nb = (B + TILE - 1) / TILE;
   const int bt = blockIdx.z % nb, split = blockIdx.z / nb;
   const int t0 = blockIdx.x * TILE, n = blockIdx.y, b0 = bt * TILE;
@@ -274,35 +242,14 @@ __global__ void __launch_bounds__(256) k_hupd(const float* __restrict__ A, const
     }
     if (!split_fixup(num, den, S, split, (n * gridDim.x + blockIdx.x) * nb + bt, part, ticket)) return;
     const int b = b0 + bi, t = t0 + ti;
-    float hn = 0.f;
     if (b < B && t < T) {
       float* hp = H + ((size_t)n * B + b) * Tp + t;
-      hn = *hp * sqrtf(num / fmaxf(den, eps));
+      const float hn = *hp * sqrtf(num / fmaxf(den, eps));
       if (!finitef(hn)) atomicOr(flags + FLAG_NONFINITE, 1u);
       *hp = hn;
     }
-    Hn_s[bi * TILE + ti] = hn;
-  }
-  if (!refresh) return;
-  __syncthreads();
-  // lambda[n][f][t0..t0+16) = sum_b W[n][f][b] Hn[b][t] for every f (B <= 16 here)
-  const int ti = tid % TILE, fl = tid / TILE;
-  const int t = t0 + ti;
-  float hcol[TILE];
-#pragma unroll
-  for (int b = 0; b < TILE; ++b) hcol[b] = Hn_s[b * TILE + ti];
-#pragma unroll 8
-  for (int f = fl; f < F; f += 256 / TILE) {
-    const float* wr = Wg + (size_t)f * B;
-    float s = 0.f;
-#pragma unroll
-    for (int b = 0; b < TILE; ++b)
-      if (b < B) s = fmaf(__ldg(wr + b), hcol[b], s);
-    if (t < T) lam[((size_t)n * F + f) * Tp + t] = s;
   }
 }
-
-bool nmf_fused_lambda(const dfmnmf_ctx* c) { return c->B <= TILE; }
 
 // Number of splits of the reduction: enough CTAs for about four per SM, at
 // most NMF_MAX_SPLIT, never more than the number of 64-wide chunks.
@@ -328,7 +275,7 @@ cudaError_t launch_wupd(const dfmnmf_ctx* c, cudaStream_t s) {
   int S, cps;
   split_plan(tiles, (c->T + KCH - 1) / KCH, &S, &cps);
   dim3 grid((c->F + TILE - 1) / TILE, c->N, nb * S);
-  k_wupd<<<grid, 256, 0, s>>>(c->A, c->D, c->H, c->W, c->lam, c->F, c->T, c->Tp, c->B, c->eps, nb == 1, c->flags, S, cps,
+  k_wupd<<<grid, 256, 0, s>>>(c->A, c->D, c->H, c->W, c->F, c->T, c->Tp, c->B, c->eps, c->flags, S, cps,
                               c->nmf_part, c->nmf_ticket);
   return cudaGetLastError();
 }
@@ -339,7 +286,7 @@ cudaError_t launch_hupd(const dfmnmf_ctx* c, cudaStream_t s) {
   int S, cps;
   split_plan(tiles, (c->F + KCH - 1) / KCH, &S, &cps);
   dim3 grid((c->T + TILE - 1) / TILE, c->N, nb * S);
-  k_hupd<<<grid, 256, 0, s>>>(c->A, c->D, c->W, c->H, c->lam, c->F, c->T, c->Tp, c->B, c->eps, nb == 1, c->flags, S, cps,
+  k_hupd<<<grid, 256, 0, s>>>(c->A, c->D, c->W, c->H, c->F, c->T, c->Tp, c->B, c->eps, c->flags, S, cps,
                               c->nmf_part, c->nmf_ticket);
   return cudaGetLastError();
 }

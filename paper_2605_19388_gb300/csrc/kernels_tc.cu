@@ -12,13 +12,16 @@
 //
 // R depends only on the observation, so it is formed once (k_rprep) into
 // two bfloat16 arrays [F * 16K][Tr] (Tr = T rounded up to 64, zero tail).
-// k_vtc then streams them with TMA (128-byte swizzled tiles of 128 rows x 64
-// frames) into a 2-stage shared-memory ring (two CTAs per SM), six warps stage
-// lambda for the same frames and form w_hi / w_lo directly in the swizzled
-// operand layout, one thread issues
+// The weights change every iteration: k_wprep forms w_hi / w_lo [F * M][Tr]
+// from lambda and g in one streaming pass.  k_vtc then only moves and
+// multiplies: one thread streams the four operand tiles of each 64-frame
+// chunk with TMA (128-byte swizzled, 128 rows of R and 32 rows of w) into a
+// 2-stage shared-memory ring (two CTAs per SM), one thread issues
 // tcgen05.mma (M = 128 rows = 128 / (16 K) frequencies, N = 32 weights,
 // K = 16 frames per instruction, FP32 accumulators in tensor memory) and the
-// first four warps read the accumulators back with tcgen05.ld.
+// four warps read the accumulators back with tcgen05.ld.  (Forming w inside
+// k_vtc, by warps beside the TMA and MMA threads, left the tensor pipe
+// waiting on them for most of every chunk.)
 //
 // Supported layouts: M_k = 4 and K in {1, 2, 4, 8} (M = 128 / (16 K) * 16 K
 // rows per tile, N = 32 columns).  Every mbarrier wait is bounded; a wait
@@ -36,12 +39,10 @@ constexpr int TC_KC = 64;       // frames per chunk (128 bytes of bfloat16 per r
 constexpr int TC_ROWS = 128;    // MMA M
 constexpr int TC_COLS = 32;     // MMA N
 constexpr int TC_STAGES = 2;
-constexpr int TC_PRODUCERS = 192;  // warps 2..7 form the weight operand
 constexpr int TC_A_BYTES = TC_ROWS * TC_KC * 2;   // 16 KB per operand part
 constexpr int TC_B_BYTES = TC_COLS * TC_KC * 2;   // 4 KB per operand part
 constexpr int TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_B_BYTES;
 constexpr unsigned long long TC_WAIT_CYCLES = 2000000000ull;  // ~1 s at 2 GHz
-constexpr size_t TC_LAMBDA_WHOLE_BYTES = 32 * 1024;  // lambda of the CTA kept whole in shared memory up to this size
 
 // ------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -148,6 +149,50 @@ __global__ void __launch_bounds__(128) k_rprep(const float2* __restrict__ x, __n
   }
 }
 
+// ------------------------------------------------------------- weights
+// w = 1 / max(yhat, eps), yhat[f][t][m] = sum_n lambda[n][f][t] g[f][n][m]
+// (Eq. 2 with the floor of Sec. IV-A), split into two bfloat16 parts and
+// stored as rows (f, m) of Tr frames, zero beyond T: the B operand of the
+// contraction, read by TMA in the same 128-byte swizzled tiles as R.  Each
+// thread forms two adjacent frames of one frequency for every microphone
+// (g[f] is broadcast from shared memory; stores are 4-byte bfloat16 pairs,
+// coalesced along t).
+__global__ void __launch_bounds__(128) k_wprep(const float* __restrict__ lam, const float* __restrict__ g,
+                                               __nv_bfloat16* __restrict__ whi, __nv_bfloat16* __restrict__ wlo,
+                                               int F, int T, int Tp, int Tr, int M, int N, float eps, int fb) {
+  extern __shared__ float gw[];  // [N][M]
+  const int f = fb + blockIdx.y;
+  for (int i = threadIdx.x; i < N * M; i += blockDim.x) gw[i] = g[(size_t)f * N * M + i];
+  __syncthreads();
+  const int t = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (t >= Tr) return;
+  float2 lv[16];
+#pragma unroll
+  for (int n = 0; n < 16; ++n) {
+    lv[n] = make_float2(0.f, 0.f);
+    if (n < N && t < Tp) lv[n] = *reinterpret_cast<const float2*>(lam + ((size_t)n * F + f) * Tp + t);
+  }
+  const bool v0 = t < T, v1 = t + 1 < T;
+  for (int m = 0; m < M; ++m) {
+    float y0 = 0.f, y1 = 0.f;
+#pragma unroll
+    for (int n = 0; n < 16; ++n)
+      if (n < N) {
+        const float gv = gw[n * M + m];
+        y0 = fmaf(lv[n].x, gv, y0);
+        y1 = fmaf(lv[n].y, gv, y1);
+      }
+    const float w0 = v0 ? fast_rcp(fmaxf(y0, eps)) : 0.f;
+    const float w1 = v1 ? fast_rcp(fmaxf(y1, eps)) : 0.f;
+    const __nv_bfloat162 h = __floats2bfloat162_rn(w0, w1);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(w0 - hf.x, w1 - hf.y);
+    const size_t o = ((size_t)f * M + m) * Tr + t;
+    *reinterpret_cast<__nv_bfloat162*>(whi + o) = h;
+    *reinterpret_cast<__nv_bfloat162*>(wlo + o) = l;
+  }
+}
+
 // ------------------------------------------------------------ contraction
 struct TcSmem {
   unsigned long long full[TC_STAGES];
@@ -157,54 +202,35 @@ struct TcSmem {
   unsigned abort;
 };
 
-// Shared memory: [1024-aligned operand ring][control][g of the CTA's
-// frequencies][lambda chunk of the CTA's frequencies].
 __host__ __device__ constexpr size_t tc_ring_bytes() { return (size_t)TC_STAGES * TC_STAGE_BYTES; }
 
-__global__ void __launch_bounds__(256, 2) k_vtc(const __grid_constant__ CUtensorMap map_hi,
-                                                const __grid_constant__ CUtensorMap map_lo,
-                                                const float* __restrict__ lam, const float* __restrict__ g,
-                                                double2* __restrict__ V, float4* __restrict__ Vdd, int F, int T,
-                                                int Tp, int Tr, int K, int N, float eps,
-                                                unsigned* __restrict__ flags, int fb, int fe) {
+// One CTA per tile of TC_ROWS / (16 K) frequencies, four warps: lane 0 of
+// warp 0 streams the four operand tiles of every 64-frame chunk (R_hi, R_lo,
+// w_hi, w_lo) into the shared-memory ring, lane 0 of warp 1 issues the three
+// split products per 16 frames, and all four warps read the accumulators back.
+__global__ void __launch_bounds__(128, 2) k_vtc(const __grid_constant__ CUtensorMap map_rhi,
+                                                const __grid_constant__ CUtensorMap map_rlo,
+                                                const __grid_constant__ CUtensorMap map_whi,
+                                                const __grid_constant__ CUtensorMap map_wlo,
+                                                double2* __restrict__ V, float4* __restrict__ Vdd, int T, int Tr,
+                                                int K, unsigned* __restrict__ flags, int fb, int fe) {
   extern __shared__ __align__(1024) unsigned char tc_raw[];
   unsigned char* ring = reinterpret_cast<unsigned char*>(((unsigned long long)tc_raw + 1023) & ~1023ull);
   TcSmem* ctl = reinterpret_cast<TcSmem*>(ring + tc_ring_bytes());
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int FPC = TC_ROWS / (16 * K);  // frequencies per CTA
+  const int FPC = TC_ROWS / (16 * K);    // frequencies per CTA
   const int f0 = fb + blockIdx.x * FPC;  // frequencies f0 .. min(f0 + FPC, fe) - 1 are this CTA's
   const int M = 4 * K;
   const int nch = Tr / TC_KC;
-  float* gsh = reinterpret_cast<float*>(ctl + 1);  // [FPC][N][M]
-  float* lsh = gsh + ((FPC * N * M + 3) & ~3);    // [FPC][N][LW] lambda rows (LW = Tr or TC_KC)
-  const bool whole = (size_t)FPC * N * Tr * sizeof(float) <= TC_LAMBDA_WHOLE_BYTES;
-  const int LW = whole ? Tr : TC_KC;
 
   if (tid == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
-      mbar_init(&ctl->full[s], 1 + TC_PRODUCERS);
+      mbar_init(&ctl->full[s], 1);
       mbar_init(&ctl->empty[s], 1);
     }
     mbar_init(&ctl->done, 1);
     ctl->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  for (int i = tid; i < FPC * N * M; i += blockDim.x) {
-    const int fj = i / (N * M), rem = i % (N * M);
-    const int f = f0 + fj;
-    gsh[i] = (f < fe) ? g[(size_t)f * N * M + rem] : 0.f;
-  }
-  if (whole) {
-    // lambda rows of the CTA's frequencies for every frame, once (cp.async; zero beyond Tp)
-    for (int i = tid; i < FPC * N * (Tr / 4); i += blockDim.x) {
-      const int row = i / (Tr / 4), q = i % (Tr / 4);
-      const int fj = row / N, n = row % N, f = f0 + fj, t = 4 * q;
-      float* dst = lsh + (size_t)row * Tr + t;
-      if (f < fe && t < Tp) cp_async16(dst, lam + ((size_t)n * F + f) * Tp + t);
-      else *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    cp_async_commit();
-    cp_async_wait<0>();
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(&ctl->tmem_base))
@@ -217,7 +243,7 @@ __global__ void __launch_bounds__(256, 2) k_vtc(const __grid_constant__ CUtensor
   const unsigned tmem = ctl->tmem_base;
 
   if (warp == 0 && lane == 0) {
-    // ---- TMA producer: R_hi / R_lo tiles (rows f0 * 16K .., frames chunk * 64 ..)
+    // ---- TMA producer: rows f0 * 16K .. of R, rows f0 * M .. of w, frames chunk * 64 ..
     for (int c = 0; c < nch; ++c) {
       const int s = c % TC_STAGES;
       if (c >= TC_STAGES && !mbar_wait(&ctl->empty[s], ((c / TC_STAGES) + 1) & 1)) {
@@ -226,9 +252,11 @@ __global__ void __launch_bounds__(256, 2) k_vtc(const __grid_constant__ CUtensor
       }
       if (ctl->abort) break;
       unsigned char* st = ring + s * TC_STAGE_BYTES;
-      mbar_arrive_expect_tx(&ctl->full[s], 2 * TC_A_BYTES);
-      tma_load_2d(st, &map_hi, c * TC_KC, f0 * 16 * K, &ctl->full[s]);
-      tma_load_2d(st + TC_A_BYTES, &map_lo, c * TC_KC, f0 * 16 * K, &ctl->full[s]);
+      mbar_arrive_expect_tx(&ctl->full[s], TC_STAGE_BYTES);
+      tma_load_2d(st, &map_rhi, c * TC_KC, f0 * 16 * K, &ctl->full[s]);
+      tma_load_2d(st + TC_A_BYTES, &map_rlo, c * TC_KC, f0 * 16 * K, &ctl->full[s]);
+      tma_load_2d(st + 2 * TC_A_BYTES, &map_whi, c * TC_KC, f0 * M, &ctl->full[s]);
+      tma_load_2d(st + 2 * TC_A_BYTES + TC_B_BYTES, &map_wlo, c * TC_KC, f0 * M, &ctl->full[s]);
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer
@@ -252,83 +280,24 @@ __global__ void __launch_bounds__(256, 2) k_vtc(const __grid_constant__ CUtensor
       umma_commit(&ctl->empty[s]);
     }
     umma_commit(&ctl->done);
-  } else if (warp >= 2) {
-    // ---- weight producers: stage lambda for the chunk, then w_hi / w_lo rows
-    //      (fj, k, mu) x 64 frames, swizzled like the TMA tiles
-    const int p = tid - 64;  // 0 .. TC_PRODUCERS-1
-    for (int c = 0; c < nch; ++c) {
-      const int s = c % TC_STAGES;
-      const int tc0 = c * TC_KC;
-      const int lo = whole ? tc0 : 0;  // column of this chunk inside the lambda rows
-      if (!whole) {
-        // lambda rows of the chunk: FPC x N rows of 16 float4 (Tp is a multiple of 4)
-        for (int i = p; i < FPC * N * (TC_KC / 4); i += TC_PRODUCERS) {
-          const int row = i / (TC_KC / 4), q = i % (TC_KC / 4);
-          const int fj = row / N, n = row % N, f = f0 + fj, t = tc0 + 4 * q;
-          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (f < fe && t < Tp) v = __ldg(reinterpret_cast<const float4*>(lam + ((size_t)n * F + f) * Tp + t));
-          *reinterpret_cast<float4*>(lsh + row * TC_KC + 4 * q) = v;
-        }
-        asm volatile("bar.sync 1, %0;" ::"n"(TC_PRODUCERS) : "memory");
-      }
-      if (c >= TC_STAGES && !mbar_wait(&ctl->empty[s], ((c / TC_STAGES) + 1) & 1)) atomicOr(&ctl->abort, 1u);
-      unsigned char* bh = ring + s * TC_STAGE_BYTES + 2 * TC_A_BYTES;
-      unsigned char* bl = bh + TC_B_BYTES;
-      for (int item = p; item < TC_COLS * 8; item += TC_PRODUCERS) {
-        const int row = item >> 3, j = item & 7;
-        const int fj = row / M, m = row % M;  // row = fj * 4K + k * 4 + mu = fj * M + m
-        const int f = f0 + fj;
-        const int t0 = tc0 + j * 8;
-        float ys[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) ys[q] = 0.f;
-        for (int n = 0; n < N; ++n) {
-          const float gv = gsh[(fj * N + n) * M + m];
-          const float4 l0 = *reinterpret_cast<const float4*>(lsh + (size_t)(fj * N + n) * LW + lo + j * 8);
-          const float4 l1 = *reinterpret_cast<const float4*>(lsh + (size_t)(fj * N + n) * LW + lo + j * 8 + 4);
-          ys[0] = fmaf(l0.x, gv, ys[0]); ys[1] = fmaf(l0.y, gv, ys[1]);
-          ys[2] = fmaf(l0.z, gv, ys[2]); ys[3] = fmaf(l0.w, gv, ys[3]);
-          ys[4] = fmaf(l1.x, gv, ys[4]); ys[5] = fmaf(l1.y, gv, ys[5]);
-          ys[6] = fmaf(l1.z, gv, ys[6]); ys[7] = fmaf(l1.w, gv, ys[7]);
-        }
-        unsigned hw[4], lw[4];
-#pragma unroll
-        for (int q = 0; q < 8; q += 2) {
-          const bool v0 = f < fe && t0 + q < T, v1 = f < fe && t0 + q + 1 < T;
-          const float w0 = v0 ? fast_rcp(fmaxf(ys[q], eps)) : 0.f;
-          const float w1 = v1 ? fast_rcp(fmaxf(ys[q + 1], eps)) : 0.f;
-          const __nv_bfloat162 h = __floats2bfloat162_rn(w0, w1);
-          const float2 hf = __bfloat1622float2(h);
-          const __nv_bfloat162 l = __floats2bfloat162_rn(w0 - hf.x, w1 - hf.y);
-          hw[q / 2] = *reinterpret_cast<const unsigned*>(&h);
-          lw[q / 2] = *reinterpret_cast<const unsigned*>(&l);
-        }
-        const int off = row * 128 + ((j ^ (row & 7)) << 4);
-        *reinterpret_cast<uint4*>(bh + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-        *reinterpret_cast<uint4*>(bl + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive(&ctl->full[s]);
-      if (!whole) asm volatile("bar.sync 1, %0;" ::"n"(TC_PRODUCERS) : "memory");  // lsh reused by the next chunk
-    }
   }
 
-  // ---- epilogue: warps 0-3 read the accumulators (lane = row)
-  if (warp < 4) {
-    __syncwarp();
-    const bool ok = mbar_wait(&ctl->done, 0);
-    if (!ok) atomicOr(&ctl->abort, 1u);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    unsigned r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(tmem + ((unsigned)(warp * 32) << 16)));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  // ---- epilogue: the four warps read the accumulators (lane = row)
+  __syncwarp();
+  const bool ok = mbar_wait(&ctl->done, 0);
+  if (!ok) atomicOr(&ctl->abort, 1u);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  unsigned r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(tmem + ((unsigned)(warp * 32) << 16)));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  {
     const int row = tid;                      // 0..127
     const int fj = row / (16 * K), rk = row % (16 * K);
     const int k = rk / 16, e = rk % 16;       // packed entry e = a * 4 + b
@@ -390,25 +359,26 @@ static EncodeTiledFn encode_fn() {
 
 bool tc_supported(int MK, int K) { return MK == 4 && (K == 1 || K == 2 || K == 4 || K == 8); }
 
-size_t tc_smem_bytes(const dfmnmf_ctx* c) {
-  const int FPC = TC_ROWS / (16 * c->K);
-  const bool whole = (size_t)FPC * c->N * c->Tr * sizeof(float) <= TC_LAMBDA_WHOLE_BYTES;
-  return 1024 + tc_ring_bytes() + sizeof(TcSmem) + 16 +
-         ((size_t)((FPC * c->N * c->M + 3) & ~3) + (size_t)FPC * c->N * (whole ? c->Tr : TC_KC)) * sizeof(float);
-}
+size_t tc_smem_bytes(const dfmnmf_ctx*) { return 1024 + tc_ring_bytes() + sizeof(TcSmem); }
 
+// Four 2-D bfloat16 maps with 128-byte swizzle: R_hi / R_lo ([F * 16K][Tr],
+// boxes of 128 rows x 64 frames) and w_hi / w_lo ([F * M][Tr], boxes of 32
+// rows x 64 frames).  Rows past the end read as zeros.
 cudaError_t tc_make_maps(dfmnmf_ctx* c) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
-  const cuuint64_t dims[2] = {(cuuint64_t)c->Tr, (cuuint64_t)c->F * 16 * c->K};
   const cuuint64_t strides[1] = {(cuuint64_t)c->Tr * 2};
-  const cuuint32_t box[2] = {TC_KC, TC_ROWS};
   const cuuint32_t estr[2] = {1, 1};
-  CUtensorMap* maps[2] = {reinterpret_cast<CUtensorMap*>(c->tmap_hi), reinterpret_cast<CUtensorMap*>(c->tmap_lo)};
-  void* bases[2] = {c->Rhi, c->Rlo};
-  for (int i = 0; i < 2; ++i) {
-    const CUresult r = fn(maps[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, bases[i], dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+  struct { unsigned char* map; void* base; cuuint64_t rows; cuuint32_t box_rows; } m[4] = {
+      {c->tmap_hi, c->Rhi, (cuuint64_t)c->F * 16 * c->K, TC_ROWS},
+      {c->tmap_lo, c->Rlo, (cuuint64_t)c->F * 16 * c->K, TC_ROWS},
+      {c->tmap_whi, c->wy_hi, (cuuint64_t)c->F * c->M, TC_COLS},
+      {c->tmap_wlo, c->wy_lo, (cuuint64_t)c->F * c->M, TC_COLS}};
+  for (int i = 0; i < 4; ++i) {
+    const cuuint64_t dims[2] = {(cuuint64_t)c->Tr, m[i].rows};
+    const cuuint32_t box[2] = {TC_KC, m[i].box_rows};
+    const CUresult r = fn(reinterpret_cast<CUtensorMap*>(m[i].map), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, m[i].base,
+                          dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
   }
@@ -422,15 +392,22 @@ cudaError_t launch_rprep(const dfmnmf_ctx* c, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_wprep(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
+  dim3 grid((c->Tr / 2 + 127) / 128, fc);
+  k_wprep<<<grid, 128, (size_t)c->N * c->M * sizeof(float), s>>>(
+      c->lam, c->g, reinterpret_cast<__nv_bfloat16*>(c->wy_hi), reinterpret_cast<__nv_bfloat16*>(c->wy_lo), c->F,
+      c->T, c->Tp, c->Tr, c->M, c->N, c->eps, fb);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_vtc(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
   const size_t sm = tc_smem_bytes(c);
   cudaFuncSetAttribute(k_vtc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   const int FPC = TC_ROWS / (16 * c->K);
   const int grid = (fc + FPC - 1) / FPC;
-  const CUtensorMap* mh = reinterpret_cast<const CUtensorMap*>(c->tmap_hi);
-  const CUtensorMap* ml = reinterpret_cast<const CUtensorMap*>(c->tmap_lo);
-  k_vtc<<<grid, 256, sm, s>>>(*mh, *ml, c->lam, c->g, c->V, c->Vdd, c->F, c->T, c->Tp, c->Tr, c->K, c->N,
-                                      c->eps, c->flags, fb, fb + fc);
+  auto map = [](const unsigned char* p) { return *reinterpret_cast<const CUtensorMap*>(p); };
+  k_vtc<<<grid, 128, sm, s>>>(map(c->tmap_hi), map(c->tmap_lo), map(c->tmap_whi), map(c->tmap_wlo), c->V, c->Vdd,
+                              c->T, c->Tr, c->K, c->flags, fb, fb + fc);
   return cudaGetLastError();
 }
 
