@@ -19,55 +19,58 @@ namespace dfm {
 
 // ------------------------------------------------------------------ lambda
 // lambda[n][f][t] = sum_b W[n][f][b] H[n][b][t] (Eq. 2) for a tile of
-// LAM_F frequencies x 128 frames of one source.  The W rows of the tile sit
-// in shared memory (read as broadcast float4 loads); each thread holds H of
-// its frame for 16 bases at a time in registers and writes LAM_F outputs,
-// coalesced along t.  Frames T .. Tp-1 are written too: H is zero there, so
-// the zero tail of lambda is kept.
-constexpr int LAM_F = 16;
+// LAM_F frequencies x 256 frames of one source.  The W rows of the tile sit
+// in shared memory; each thread keeps H of four adjacent frames for 16 bases
+// at a time in registers (float4 loads; the row stride Tp is a multiple of 4)
+// and writes four frames of each frequency as one float4, so every W value
+// read from shared memory serves four FMAs.  Frames T .. Tp-1 are written
+// too: H is zero there, so the zero tail of lambda is kept.
+constexpr int LAM_F = 8;
+constexpr int LAM_THREADS = 64;
 
-__global__ void __launch_bounds__(128) k_lambda(const float* __restrict__ W, const float* __restrict__ H,
-                                                float* __restrict__ lam, int F, int Tp, int B) {
+__global__ void __launch_bounds__(LAM_THREADS) k_lambda(const float* __restrict__ W, const float* __restrict__ H,
+                                                        float* __restrict__ lam, int F, int Tp, int B) {
   extern __shared__ __align__(16) float ws[];  // [LAM_F][Bq], Bq = B rounded up to 16, zero padded
   const int n = blockIdx.z, f0 = blockIdx.y * LAM_F;
   const int Bq = (B + 15) & ~15;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  for (int i = threadIdx.x; i < LAM_F * Bq; i += blockDim.x) {
-    const int fi = i / Bq, b = i % Bq, f = f0 + fi;
-    ws[i] = (f < F && b < B) ? W[((size_t)n * F + f) * B + b] : 0.f;
-  }
+  const int t = 4 * (blockIdx.x * LAM_THREADS + threadIdx.x);
+  for (int fi = 0; fi < LAM_F; ++fi)
+    for (int b = threadIdx.x; b < Bq; b += LAM_THREADS)
+      ws[fi * Bq + b] = (f0 + fi < F && b < B) ? W[((size_t)n * F + f0 + fi) * B + b] : 0.f;
   __syncthreads();
   if (t >= Tp) return;
   const float* Hn = H + (size_t)n * B * Tp + t;
-  float acc[LAM_F];
+  const int nf = min(LAM_F, F - f0);
+  float4 acc[LAM_F];
 #pragma unroll
-  for (int fi = 0; fi < LAM_F; ++fi) acc[fi] = 0.f;
+  for (int fi = 0; fi < LAM_F; ++fi) acc[fi] = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int b0 = 0; b0 < Bq; b0 += 16) {
-    float h[16];
+    float4 h[16];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) h[j] = (b0 + j < B) ? __ldg(Hn + (size_t)(b0 + j) * Tp) : 0.f;
+    for (int j = 0; j < 16; ++j)
+      h[j] = (b0 + j < B) ? __ldg(reinterpret_cast<const float4*>(Hn + (size_t)(b0 + j) * Tp))
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int fi = 0; fi < LAM_F; ++fi) {
-      const float4* wr = reinterpret_cast<const float4*>(ws + fi * Bq + b0);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float4 w4 = wr[q];
-        acc[fi] = fmaf(w4.x, h[4 * q + 0], acc[fi]);
-        acc[fi] = fmaf(w4.y, h[4 * q + 1], acc[fi]);
-        acc[fi] = fmaf(w4.z, h[4 * q + 2], acc[fi]);
-        acc[fi] = fmaf(w4.w, h[4 * q + 3], acc[fi]);
+      for (int j = 0; j < 16; ++j) {
+        const float wv = ws[fi * Bq + b0 + j];
+        acc[fi].x = fmaf(wv, h[j].x, acc[fi].x);
+        acc[fi].y = fmaf(wv, h[j].y, acc[fi].y);
+        acc[fi].z = fmaf(wv, h[j].z, acc[fi].z);
+        acc[fi].w = fmaf(wv, h[j].w, acc[fi].w);
       }
     }
   }
 #pragma unroll
   for (int fi = 0; fi < LAM_F; ++fi)
-    if (f0 + fi < F) lam[((size_t)n * F + f0 + fi) * Tp + t] = acc[fi];
+    if (fi < nf) *reinterpret_cast<float4*>(lam + ((size_t)n * F + f0 + fi) * Tp + t) = acc[fi];
 }
 
 cudaError_t launch_lambda(const dfmnmf_ctx* c, cudaStream_t s) {
-  dim3 grid((c->Tp + 127) / 128, (c->F + LAM_F - 1) / LAM_F, c->N);
+  dim3 grid((c->Tp / 4 + LAM_THREADS - 1) / LAM_THREADS, (c->F + LAM_F - 1) / LAM_F, c->N);
   const size_t sm = (size_t)LAM_F * ((c->B + 15) & ~15) * sizeof(float);
-  k_lambda<<<grid, 128, sm, s>>>(c->W, c->H, c->lam, c->F, c->Tp, c->B);
+  k_lambda<<<grid, LAM_THREADS, sm, s>>>(c->W, c->H, c->lam, c->F, c->Tp, c->B);
   return cudaGetLastError();
 }
 
@@ -331,10 +334,12 @@ __global__ void __launch_bounds__(256) k_gupd(const float* __restrict__ lam, con
   auto issue = [&](int c) {
     if (c < nchunk) {
       const int t0 = c * GT, nt = min(GT, T - t0), buf = c % NST;
-      for (int i = tid; i < N * nt; i += blockDim.x) {
-        const int n = i / nt, tt = i % nt;
-        cp_async4(ls + (buf * N + n) * GT + tt, lam + ((size_t)n * F + f) * Tp + t0 + tt);
-      }
+      // lambda rows: warp w copies rows w, w + 8, ... as 16-byte pieces (rows are
+      // 16-byte aligned and zero up to Tp, so the last piece may run past T)
+      const int nq = (nt + 3) / 4, q = tid & 31;
+      if (q < nq)
+        for (int n = tid >> 5; n < N; n += 8)
+          cp_async16(ls + (buf * N + n) * GT + 4 * q, lam + ((size_t)n * F + f) * Tp + t0 + 4 * q);
       const float* src = P + ((size_t)f * T + t0) * M;
       float* dst = ps + (size_t)buf * GT * M;
       if (vec)

@@ -19,6 +19,7 @@ constexpr int TILE = 16;  // f (Eq. 8) or t (Eq. 9) per CTA, and b per CTA
 constexpr int NWARP = 8;
 constexpr int KCH = 64;   // reduction chunk staged in shared memory
 constexpr int NMF_MAX_SPLIT = 8;
+constexpr int RS = 17;    // row stride of the cross-warp reduction array (odd: no bank conflicts)
 
 // Split-reduction epilogue shared by k_wupd / k_hupd.  Thread tid holds the
 // CTA's partial (num, den) of one output.  With S > 1 the partial is written
@@ -67,7 +68,7 @@ __global__ void __launch_bounds__(256) k_wupd(const float* __restrict__ A, const
   constexpr int TS = 20;  // padded row of the transposed tiles: conflict-free stores, 16-byte rows
   constexpr int STAGE = 3 * KCH * TS;
   __shared__ __align__(16) float stg[STAGE];
-  __shared__ float red[NWARP * 32 * 16];
+  __shared__ float red[NWARP * 32 * RS];
   const int nb = (B + TILE - 1) / TILE;
   const int bt = blockIdx.z % nb, split = blockIdx.z / nb;
   const int f0 = blockIdx.x * TILE, n = blockIdx.y, b0 = bt * TILE;
@@ -126,7 +127,7 @@ __global__ void __launch_bounds__(256) k_wupd(const float* __restrict__ A, const
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 16; ++i) red[(warp * 32 + lane) * 16 + i] = acc[i];
+  for (int i = 0; i < 16; ++i) red[(warp * 32 + lane) * RS + i] = acc[i];
   __syncthreads();
   {
     const int fi = tid / TILE, bi = tid % TILE;  // 256 threads = 16 x 16 outputs
@@ -135,8 +136,8 @@ __global__ void __launch_bounds__(256) k_wupd(const float* __restrict__ A, const
     float num = 0.f, den = 0.f;
 #pragma unroll
     for (int w = 0; w < NWARP; ++w) {
-      num += red[(w * 32 + l) * 16 + slot + 0];
-      den += red[(w * 32 + l) * 16 + slot + 1];
+      num += red[(w * 32 + l) * RS + slot + 0];
+      den += red[(w * 32 + l) * RS + slot + 1];
     }
     if (!split_fixup(num, den, S, split, (n * gridDim.x + blockIdx.x) * nb + bt, part, ticket)) return;
     const int f = f0 + fi, b = b0 + bi;
@@ -161,7 +162,7 @@ __global__ void __launch_bounds__(256) k_hupd(const float* __restrict__ A, const
                                               float* __restrict__ part, unsigned* __restrict__ ticket) {
   constexpr int STAGE = 3 * KCH * TILE;
   __shared__ __align__(16) float stg[2 * STAGE];
-  __shared__ float red[NWARP * 32 * 16];
+  __shared__ float red[NWARP * 32 * RS];
   const int nb = (B + TILE - 1) / TILE;
   const int bt = blockIdx.z % nb, split = blockIdx.z / nb;
   const int t0 = blockIdx.x * TILE, n = blockIdx.y, b0 = bt * TILE;
@@ -228,7 +229,7 @@ __global__ void __launch_bounds__(256) k_hupd(const float* __restrict__ A, const
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 16; ++i) red[(warp * 32 + lane) * 16 + i] = acc[i];
+  for (int i = 0; i < 16; ++i) red[(warp * 32 + lane) * RS + i] = acc[i];
   __syncthreads();
   {
     const int bi = tid / TILE, ti = tid % TILE;
@@ -237,8 +238,8 @@ __global__ void __launch_bounds__(256) k_hupd(const float* __restrict__ A, const
     float num = 0.f, den = 0.f;
 #pragma unroll
     for (int w = 0; w < NWARP; ++w) {
-      num += red[(w * 32 + l) * 16 + slot + 0];
-      den += red[(w * 32 + l) * 16 + slot + 1];
+      num += red[(w * 32 + l) * RS + slot + 0];
+      den += red[(w * 32 + l) * RS + slot + 1];
     }
     if (!split_fixup(num, den, S, split, (n * gridDim.x + blockIdx.x) * nb + bt, part, ticket)) return;
     const int b = b0 + bi, t = t0 + ti;

@@ -154,9 +154,10 @@ __global__ void __launch_bounds__(128) k_rprep(const float2* __restrict__ x, __n
 // (Eq. 2 with the floor of Sec. IV-A), split into two bfloat16 parts and
 // stored as rows (f, m) of Tr frames, zero beyond T: the B operand of the
 // contraction, read by TMA in the same 128-byte swizzled tiles as R.  Each
-// thread forms two adjacent frames of one frequency for every microphone
-// (g[f] is broadcast from shared memory; stores are 4-byte bfloat16 pairs,
-// coalesced along t).
+// thread forms four adjacent frames of one frequency for every microphone
+// (float4 lambda loads, g[f] broadcast from shared memory, 8-byte stores
+// coalesced along t).  NM is N itself for N <= 8 and 16 (guarded) above.
+template <int NM>
 __global__ void __launch_bounds__(128) k_wprep(const float* __restrict__ lam, const float* __restrict__ g,
                                                __nv_bfloat16* __restrict__ whi, __nv_bfloat16* __restrict__ wlo,
                                                int F, int T, int Tp, int Tr, int M, int N, float eps, int fb) {
@@ -164,32 +165,39 @@ __global__ void __launch_bounds__(128) k_wprep(const float* __restrict__ lam, co
   const int f = fb + blockIdx.y;
   for (int i = threadIdx.x; i < N * M; i += blockDim.x) gw[i] = g[(size_t)f * N * M + i];
   __syncthreads();
-  const int t = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int t = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
   if (t >= Tr) return;
-  float2 lv[16];
+  float4 lv[NM];
 #pragma unroll
-  for (int n = 0; n < 16; ++n) {
-    lv[n] = make_float2(0.f, 0.f);
-    if (n < N && t < Tp) lv[n] = *reinterpret_cast<const float2*>(lam + ((size_t)n * F + f) * Tp + t);
+  for (int n = 0; n < NM; ++n) {
+    lv[n] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if ((NM <= 8 || n < N) && t < Tp) lv[n] = *reinterpret_cast<const float4*>(lam + ((size_t)n * F + f) * Tp + t);
   }
-  const bool v0 = t < T, v1 = t + 1 < T;
+  const bool v0 = t < T, v1 = t + 1 < T, v2 = t + 2 < T, v3 = t + 3 < T;
   for (int m = 0; m < M; ++m) {
-    float y0 = 0.f, y1 = 0.f;
+    float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-    for (int n = 0; n < 16; ++n)
-      if (n < N) {
+    for (int n = 0; n < NM; ++n)
+      if (NM <= 8 || n < N) {
         const float gv = gw[n * M + m];
-        y0 = fmaf(lv[n].x, gv, y0);
-        y1 = fmaf(lv[n].y, gv, y1);
+        y.x = fmaf(lv[n].x, gv, y.x);
+        y.y = fmaf(lv[n].y, gv, y.y);
+        y.z = fmaf(lv[n].z, gv, y.z);
+        y.w = fmaf(lv[n].w, gv, y.w);
       }
-    const float w0 = v0 ? fast_rcp(fmaxf(y0, eps)) : 0.f;
-    const float w1 = v1 ? fast_rcp(fmaxf(y1, eps)) : 0.f;
-    const __nv_bfloat162 h = __floats2bfloat162_rn(w0, w1);
-    const float2 hf = __bfloat1622float2(h);
-    const __nv_bfloat162 l = __floats2bfloat162_rn(w0 - hf.x, w1 - hf.y);
+    const float w0 = v0 ? fast_rcp(fmaxf(y.x, eps)) : 0.f;
+    const float w1 = v1 ? fast_rcp(fmaxf(y.y, eps)) : 0.f;
+    const float w2 = v2 ? fast_rcp(fmaxf(y.z, eps)) : 0.f;
+    const float w3 = v3 ? fast_rcp(fmaxf(y.w, eps)) : 0.f;
+    const __nv_bfloat162 h01 = __floats2bfloat162_rn(w0, w1), h23 = __floats2bfloat162_rn(w2, w3);
+    const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+    const __nv_bfloat162 l01 = __floats2bfloat162_rn(w0 - f01.x, w1 - f01.y);
+    const __nv_bfloat162 l23 = __floats2bfloat162_rn(w2 - f23.x, w3 - f23.y);
     const size_t o = ((size_t)f * M + m) * Tr + t;
-    *reinterpret_cast<__nv_bfloat162*>(whi + o) = h;
-    *reinterpret_cast<__nv_bfloat162*>(wlo + o) = l;
+    *reinterpret_cast<uint2*>(whi + o) =
+        make_uint2(*reinterpret_cast<const unsigned*>(&h01), *reinterpret_cast<const unsigned*>(&h23));
+    *reinterpret_cast<uint2*>(wlo + o) =
+        make_uint2(*reinterpret_cast<const unsigned*>(&l01), *reinterpret_cast<const unsigned*>(&l23));
   }
 }
 
@@ -393,10 +401,24 @@ cudaError_t launch_rprep(const dfmnmf_ctx* c, cudaStream_t s) {
 }
 
 cudaError_t launch_wprep(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
-  dim3 grid((c->Tr / 2 + 127) / 128, fc);
-  k_wprep<<<grid, 128, (size_t)c->N * c->M * sizeof(float), s>>>(
-      c->lam, c->g, reinterpret_cast<__nv_bfloat16*>(c->wy_hi), reinterpret_cast<__nv_bfloat16*>(c->wy_lo), c->F,
-      c->T, c->Tp, c->Tr, c->M, c->N, c->eps, fb);
+  dim3 grid((c->Tr / 4 + 127) / 128, fc);
+  const size_t sm = (size_t)c->N * c->M * sizeof(float);
+  auto whi = reinterpret_cast<__nv_bfloat16*>(c->wy_hi);
+  auto wlo = reinterpret_cast<__nv_bfloat16*>(c->wy_lo);
+#define DFM_WPREP(NMV) \
+  k_wprep<NMV><<<grid, 128, sm, s>>>(c->lam, c->g, whi, wlo, c->F, c->T, c->Tp, c->Tr, c->M, c->N, c->eps, fb)
+  switch (c->N) {
+    case 1: DFM_WPREP(1); break;
+    case 2: DFM_WPREP(2); break;
+    case 3: DFM_WPREP(3); break;
+    case 4: DFM_WPREP(4); break;
+    case 5: DFM_WPREP(5); break;
+    case 6: DFM_WPREP(6); break;
+    case 7: DFM_WPREP(7); break;
+    case 8: DFM_WPREP(8); break;
+    default: DFM_WPREP(16); break;
+  }
+#undef DFM_WPREP
   return cudaGetLastError();
 }
 
