@@ -34,9 +34,20 @@ __global__ void __launch_bounds__(LAM_THREADS) k_lambda(const float* __restrict_
   const int n = blockIdx.z, f0 = blockIdx.y * LAM_F;
   const int Bq = (B + 15) & ~15;
   const int t = 4 * (blockIdx.x * LAM_THREADS + threadIdx.x);
-  for (int fi = 0; fi < LAM_F; ++fi)
-    for (int b = threadIdx.x; b < Bq; b += LAM_THREADS)
-      ws[fi * Bq + b] = (f0 + fi < F && b < B) ? W[((size_t)n * F + f0 + fi) * B + b] : 0.f;
+  {
+    // W tile: all loads issued before any store (B <= 64: at most 8 per thread)
+    float v[LAM_F * 64 / LAM_THREADS];
+#pragma unroll
+    for (int k = 0; k < LAM_F * 64 / LAM_THREADS; ++k) {
+      const int i = threadIdx.x + k * LAM_THREADS, fi = i / Bq, b = i % Bq;
+      v[k] = (i < LAM_F * Bq && f0 + fi < F && b < B) ? __ldg(W + ((size_t)n * F + f0 + fi) * B + b) : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < LAM_F * 64 / LAM_THREADS; ++k) {
+      const int i = threadIdx.x + k * LAM_THREADS;
+      if (i < LAM_F * Bq) ws[i] = v[k];
+    }
+  }
   __syncthreads();
   if (t >= Tp) return;
   const float* Hn = H + (size_t)n * B * Tp + t;
@@ -215,7 +226,7 @@ __global__ void __launch_bounds__(256) k_pstats(const float2* __restrict__ x, co
 // no per-subarray redundancy.  Q (split in two floats) is read from shared
 // memory when P is formed here.
 template <int K, int MK, bool COMPUTE_P, bool COMP>
-__global__ void __launch_bounds__(256) k_pstats_ft(const float2* __restrict__ x, const double2* __restrict__ Q64,
+__global__ void __launch_bounds__(128) k_pstats_ft(const float2* __restrict__ x, const double2* __restrict__ Q64,
                                                    const float* __restrict__ lam, const float* __restrict__ g,
                                                    float* __restrict__ P, float* __restrict__ A,
                                                    float* __restrict__ D, int F, int T, int Tp, int N, float eps,
@@ -417,12 +428,12 @@ __global__ void __launch_bounds__(256) k_gupd(const float* __restrict__ lam, con
 
 template <int K, int MK, bool COMPUTE_P, bool COMP>
 static cudaError_t launch_pstats_ft(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
-  const int tpc = 512;  // frames per CTA (two per thread)
+  const int tpc = 128;  // one frame per thread: every load of the CTA is in flight at once
   dim3 grid(fc, (c->T + tpc - 1) / tpc);
   const size_t sm = ((size_t)((c->N * c->M + 3) & ~3) + (COMPUTE_P ? 4 * (size_t)K * MK * MK : 0)) * sizeof(float);
   auto kern = k_pstats_ft<K, MK, COMPUTE_P, COMP>;
   if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  kern<<<grid, 256, sm, s>>>(c->x, c->Q64, c->lam, c->g, c->P, c->A, c->D, c->F, c->T, c->Tp, c->N, c->eps, fb, tpc);
+  kern<<<grid, tpc, sm, s>>>(c->x, c->Q64, c->lam, c->g, c->P, c->A, c->D, c->F, c->T, c->Tp, c->N, c->eps, fb, tpc);
   return cudaGetLastError();
 }
 
