@@ -140,6 +140,40 @@ def kernel_bytes(F, T, M, N, B, K, MK):
     }
 
 
+# DRAM bytes (read + write) of one band-wide launch, from the full-section ncu
+# captures summarised in profiles/kernels_paper_4x4_n5_{bf16tc,fp32}.md (the
+# per-half launches of the two-branch iteration added up).  A figure holds
+# only while the kernel's sources are the ones captured: the digest is the
+# first 16 hex digits of sha256 over csrc/<file>, csrc/common.cuh and
+# csrc/internal.h, and `traffic` is null when it no longer matches.
+NCU_TRAFFIC = {
+    "paper_4x4_n5": {
+        "k_pstats": (24.100352e6 + 24.195072e6 + 3840 + 1536, "kernels_model.cu", "6b319bc11fdfb3bd"),
+        "k_stats": (27.179008e6 + 1024, "kernels_model.cu", "6b319bc11fdfb3bd"),
+        "k_gupd": (27.183872e6, "kernels_model.cu", "6b319bc11fdfb3bd"),
+        "k_lambda": (0.388096e6, "kernels_model.cu", "6b319bc11fdfb3bd"),
+        "k_vtc": (52.44672e6 + 52.818688e6 + 154624 + 58880, "kernels_tc.cu", "5927cbffefb4c3ad"),
+        "k_wprep": (3.308288e6 + 3.322112e6, "kernels_tc.cu", "5927cbffefb4c3ad"),
+        "k_ip": (1.385984e6 + 1.391104e6, "kernels_ip.cu", "0d0af64a8e52ca52"),
+        "k_hupd": (13.26976e6, "kernels_nmf.cu", "e6322cff36f663d3"),
+        "k_cov": (23.854592e6 + 23.947776e6, "kernels_cov.cu", "bd8b5880fbb35ec6"),
+    },
+}
+
+
+def ncu_traffic(workload, kernel, form):
+    import hashlib
+    ent = NCU_TRAFFIC.get(workload, {}).get(kernel)
+    if ent is None or (kernel == "k_pstats" and form != "bf16tc"):  # the capture is of the plain projections
+        return None
+    nbytes, src, digest = ent
+    h = hashlib.sha256()
+    for name in (src, "common.cuh", "internal.h"):
+        with open(os.path.join(ROOT, "paper_2605_19388_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return nbytes if h.hexdigest()[:16] == digest else None
+
+
 def iteration_bytes(F, T, M, N):
     """B_alg = 28 F T M + 56 F T N: bytes of one MM iteration with each kernel's operands read once."""
     return 28 * F * T * M + 56 * F * T * N
@@ -330,7 +364,7 @@ def main():
     base = lambda n: n.split("#")[0]
     ach = kb[base(dom_name)] / (dom_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": dom_name, "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "traffic": None, "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
+                "frac": ach / peak, "traffic": ncu_traffic(args.workload, base(dom_name), forms[0]), "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
                 "alg_bytes_per_launch": kb[base(dom_name)]}
 
     def kernel_table(kt, iter_ms):
