@@ -42,8 +42,9 @@ def parse():
     ap.add_argument("--workload", default="paper_4x4_n5")
     ap.add_argument("--iters", type=int, default=None, help="MM iterations per step (default: the workload's)")
     ap.add_argument("--ip", choices=["f32x2", "f64", "f32"], default="f32x2")
-    ap.add_argument("--forms", default="bf16tc,fp32",
-                    help="comma list of forms to time; the first is the headline value")
+    ap.add_argument("--forms", default="bf16tc,fp32,allmic",
+                    help="comma list of forms to time (allmic: conventional FastMNMF with one full M x M "
+                         "diagonaliser, the comparator); the first is the headline value")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
@@ -272,13 +273,19 @@ def main():
     c_out = torch.empty((N, F, T, M), dtype=torch.complex64, device=dev)
     flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    precisions = {"bf16tc": D.DFMNMF_BF16_TC, "fp32": D.DFMNMF_FP32}
+    precisions = {"bf16tc": D.DFMNMF_BF16_TC, "fp32": D.DFMNMF_FP32, "allmic": D.DFMNMF_FP32}
+    # conventional all-microphone FastMNMF on the same observation: one 16 x 16 block per bin
+    allmic = (M,)
+    Q0_all_d = torch.from_numpy(synth.identity_blocks(F, allmic)).to(dev)
+    form_mics = {"bf16tc": p.mics, "fp32": p.mics, "allmic": allmic}
+    form_q0 = {"bf16tc": Q0_d, "fp32": Q0_d, "allmic": Q0_all_d}
+    ctx_q0 = {}
     forms = [f.strip() for f in args.forms.split(",") if f.strip()]
     nll_box = []
 
     def step(c):
         D.dfmnmf_set_observation(c, x_d)          # observation in place (TC form: x x^H split anew)
-        D.dfmnmf_set_params(c, Q0_d, W0_d, H0_d, g0_d)
+        D.dfmnmf_set_params(c, ctx_q0.get(id(c), Q0_d), W0_d, H0_d, g0_d)
         D.dfmnmf_iterate(c, iters)
         nll_box.append(D.dfmnmf_loglik(c))
         D.dfmnmf_separate(c, c_out)
@@ -309,15 +316,18 @@ def main():
             return float(t.item())
         return v
 
-    kb = kernel_bytes(F, T, M, N, Bb, K, MK)
+    kb_form = {f: (kernel_bytes(F, T, M, N, Bb, 1, M) if f == "allmic" else kernel_bytes(F, T, M, N, Bb, K, MK))
+               for f in forms}
+    kb = kb_form[forms[0]]
     peak, peak_kind = peaks()
     ib = iteration_bytes(F, T, M, N)
     results = {}
     ctxs = {}
     clocks = None
     for form in forms:
-        c = D.dfmnmf_init(F, T, p.mics, N, Bb, x_d, W0_d, H0_d, g0_d, Q0_d, ip_arith=ip,
+        c = D.dfmnmf_init(F, T, form_mics[form], N, Bb, x_d, W0_d, H0_d, g0_d, form_q0[form], ip_arith=ip,
                           precision=precisions[form])
+        ctx_q0[id(c)] = form_q0[form]
         ctxs[form] = c
         for _ in range(args.warmup):
             step(c)
@@ -333,7 +343,7 @@ def main():
         total_ms = max_over_ranks(total_ms)
         launches_iter = D.dfmnmf_launches_per_iteration(c)
         # steady-state iteration time of the captured graph (back-to-back launches)
-        D.dfmnmf_set_params(c, Q0_d, W0_d, H0_d, g0_d)
+        D.dfmnmf_set_params(c, form_q0[form], W0_d, H0_d, g0_d)
         D.dfmnmf_iterate(c, 5)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -367,9 +377,10 @@ def main():
                 "frac": ach / peak, "traffic": ncu_traffic(args.workload, base(dom_name), forms[0]), "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
                 "alg_bytes_per_launch": kb[base(dom_name)]}
 
-    def kernel_table(kt, iter_ms):
-        return {n: {"ms": ms, "share": ms / iter_ms, "alg_bytes": kb.get(base(n)),
-                    "GBps": (kb[base(n)] / (ms * 1e-3) / 1e9) if base(n) in kb else None} for n, ms in kt}
+    def kernel_table(kt, iter_ms, kbf=None):
+        kbf = kb if kbf is None else kbf
+        return {n: {"ms": ms, "share": ms / iter_ms, "alg_bytes": kbf.get(base(n)),
+                    "GBps": (kbf[base(n)] / (ms * 1e-3) / 1e9) if base(n) in kbf else None} for n, ms in kt}
 
     launches_step = iters * head["launches_iter"] + 2 + 3 + 2 + (1 if forms[0] == "bf16tc" else 0)
     out = {
@@ -395,9 +406,10 @@ def main():
         "kernels": kernel_table(head["kernels"], head["iter_ms"]),
         "forms": {f: {"value": r["value"], "unit": UNIT, "ms_per_step": r["ms_per_step"],
                       "iter_ms": r["graph_iter_ms"], "kernel_sum_ms": r["iter_ms"],
-                      "kernels": kernel_table(r["kernels"], r["iter_ms"]), "nll_last": r["nll"],
+                      "kernels": kernel_table(r["kernels"], r["iter_ms"], kb_form[f]), "nll_last": r["nll"],
                       "clocks": r["clocks"]} for f, r in results.items()},
         "clocks": clocks,
+        "distributed_vs_allmic": (results[forms[0]]["value"] / results["allmic"]["value"]) if "allmic" in results else None,
         "gpu_launches": launches_step * args.steps,
         "nll_last": head["nll"],
     }

@@ -44,7 +44,10 @@
  *
  * Limits of this release
  *   All subarrays must have the same size M_k in 1..4 (the paper's layout is
- *   three 4-microphone subarrays); other layouts return DFMNMF_EINVAL.
+ *   three 4-microphone subarrays), or K = 1 with M_k = 16: conventional
+ *   all-microphone FastMNMF with a full 16 x 16 diagonaliser (Sec. II-A),
+ *   which the distributed form reduces to at K = 1 and which is its
+ *   comparator (FP32 form only); other layouts return DFMNMF_EINVAL.
  *   1 <= N <= 16, 1 <= B <= 64, 1 <= K <= 16, F >= 1, T >= 1.
  */
 #ifndef DFMNMF_H

@@ -217,7 +217,9 @@ int dfmnmf_init(dfmnmf_ctx** out, const dfmnmf_desc* d, const void* x, const flo
       return fail(DFMNMF_EINVAL, "this release needs equal subarray sizes (mics[0]=%d, mics[%d]=%d)", MK, k,
                   d->mics[k]);
   }
-  if (MK > 4) return fail(DFMNMF_EINVAL, "subarray size M_k=%d exceeds 4", MK);
+  if (MK > 4 && !(MK == 16 && d->K == 1))
+    return fail(DFMNMF_EINVAL, "subarray size M_k=%d: this release supports 1..4, or 16 with K = 1 (all-microphone form)",
+                MK);
   if (d->precision != DFMNMF_FP32 && d->precision != DFMNMF_BF16_TC)
     return fail(DFMNMF_EINVAL, "precision %d is not built in this release", d->precision);
   if (d->precision == DFMNMF_BF16_TC && !dfm::tc_supported(MK, d->K))

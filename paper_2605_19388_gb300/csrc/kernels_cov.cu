@@ -222,7 +222,132 @@ __global__ void __launch_bounds__(256, 2) k_cov(const float2* __restrict__ x, co
   }
 }
 
+// ------------------------------------------------------------------------
+// One 16-microphone block per frequency (conventional all-microphone
+// FastMNMF, K = 1, M_k = 16: the comparator of the distributed form).
+// Thread r of the CTA owns packed entry r of x x^H (r = a * 16 + b: a == b
+// |x_a|^2, a < b Re(x_a conj x_b), a > b Im(x_b conj x_a)) and keeps the
+// float-float sums of that entry against all 16 weights 1/yhat_mu in
+// registers.  Frames arrive in chunks of CT through a double-buffered
+// cp.async ring (x rows and lambda rows); the weights of a chunk are formed
+// once into shared memory and read as broadcasts.
+template <int NM>
+__global__ void __launch_bounds__(256) k_cov16(const float2* __restrict__ x, const float* __restrict__ lam,
+                                               const float* __restrict__ g, double2* __restrict__ V,
+                                               float4* __restrict__ Vdd, int F, int T, int Tp, int N, float eps,
+                                               int fb) {
+  constexpr int MK = 16, E = MK * MK;
+  const int f = fb + blockIdx.x, tid = threadIdx.x;
+  extern __shared__ __align__(16) float smc[];
+  float2* xs = reinterpret_cast<float2*>(smc);     // [2][CT][16]
+  float* ls = smc + 2 * 2 * CT * MK;               // [2][N][CT]
+  float* ws = ls + 2 * NM * CT;                    // [CT][16] weights of the current chunk
+  float* gs = ws + CT * MK;                        // [N][16]
+  for (int i = tid; i < N * MK; i += blockDim.x) gs[i] = g[(size_t)f * N * MK + i];
+  const int nchunk = (T + CT - 1) / CT;
+  auto issue = [&](int c) {
+    const int t0 = c * CT, nt = min(CT, T - t0), buf = c & 1;
+    const float2* src = x + ((size_t)f * T + t0) * MK;
+    float2* dst = xs + (size_t)buf * CT * MK;
+    for (int i = tid; i < nt * MK / 2; i += blockDim.x) cp_async16(dst + 2 * i, src + 2 * i);
+    // lambda rows: warp w copies rows w, w + 8, ... in 16-byte pieces (rows are zero up to Tp)
+    const int nq = (nt + 3) / 4, q = tid & 31;
+    if (q < nq && q < CT / 4)
+      for (int n = tid >> 5; n < N; n += 8) cp_async16(ls + (buf * NM + n) * CT + 4 * q, lam + ((size_t)n * F + f) * Tp + t0 + 4 * q);
+    cp_async_commit();
+  };
+  const int a = tid / MK, b = tid % MK;
+  const bool diag = a == b;
+  float ah[MK], al[MK];
+#pragma unroll
+  for (int q = 0; q < MK; ++q) { ah[q] = 0.f; al[q] = 0.f; }
+  __syncthreads();
+  issue(0);
+  for (int c = 0; c < nchunk; ++c) {
+    if (c + 1 < nchunk) {
+      issue(c + 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const int nt = min(CT, T - c * CT), buf = c & 1;
+    const float2* xb = xs + (size_t)buf * CT * MK;
+    const float* lb = ls + buf * NM * CT;
+    // weights w[tt][mu] = 1 / max(sum_n lambda g, eps) of the chunk's frames
+    for (int i = tid; i < CT * MK; i += blockDim.x) {
+      const int tt = i / MK, mu = i % MK;
+      float y = 0.f;
+#pragma unroll
+      for (int n = 0; n < NM; ++n)  // NM is a register bound (8 or 16), not N itself
+        if (n < N) y = fmaf(lb[n * CT + tt], gs[n * MK + mu], y);
+      ws[i] = tt < nt ? fast_rcp(fmaxf(y, eps)) : 0.f;
+    }
+    __syncthreads();
+    for (int tt = 0; tt < nt; ++tt) {
+      const float2 xa = xb[tt * MK + (a < b ? a : b)], xo = xb[tt * MK + (a < b ? b : a)];
+      float rh, rl;
+      if (a <= b) exact_re(xa, xo, rh, rl);
+      else exact_im(xa, xo, rh, rl);
+      const float4* wr = reinterpret_cast<const float4*>(ws + tt * MK);
+#pragma unroll
+      for (int q4 = 0; q4 < MK / 4; ++q4) {
+        const float4 w4 = wr[q4];
+        const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int q = q4 * 4 + u;
+          const dd p = two_prod(wv[u], rh);
+          const float e = __fmaf_rn(wv[u], rl, p.lo);
+          const dd s = diag ? quick_two_sum(ah[q], p.hi) : two_sum(ah[q], p.hi);
+          ah[q] = s.hi;
+          al[q] = __fadd_rn(al[q], __fadd_rn(s.lo, e));
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // V[f][mu][a][b] (this thread's real or imaginary part, both halves of the Hermitian pair)
+  const double invT = 1.0 / (double)T;
+#pragma unroll
+  for (int q = 0; q < MK; ++q) {
+    const double v = ((double)ah[q] + (double)al[q]) * invT;
+    const float vh = (float)v, vl = (float)(v - (double)vh);
+    double* Vd = reinterpret_cast<double*>(V + ((size_t)f * MK + q) * E);
+    float* Vf = reinterpret_cast<float*>(Vdd + ((size_t)f * MK + q) * E);
+    if (diag) {
+      Vd[2 * (a * MK + a)] = v;
+      Vd[2 * (a * MK + a) + 1] = 0.0;
+      Vf[4 * (a * MK + a)] = vh; Vf[4 * (a * MK + a) + 1] = vl; Vf[4 * (a * MK + a) + 2] = 0.f; Vf[4 * (a * MK + a) + 3] = 0.f;
+    } else if (a < b) {  // Re V[a][b] = Re V[b][a]
+      Vd[2 * (a * MK + b)] = v;
+      Vd[2 * (b * MK + a)] = v;
+      Vf[4 * (a * MK + b)] = vh; Vf[4 * (a * MK + b) + 1] = vl;
+      Vf[4 * (b * MK + a)] = vh; Vf[4 * (b * MK + a) + 1] = vl;
+    } else {  // a > b: Im(x_b conj x_a) = Im V[b][a] = -Im V[a][b]
+      Vd[2 * (b * MK + a) + 1] = v;
+      Vd[2 * (a * MK + b) + 1] = -v;
+      Vf[4 * (b * MK + a) + 2] = vh; Vf[4 * (b * MK + a) + 3] = vl;
+      Vf[4 * (a * MK + b) + 2] = -vh; Vf[4 * (a * MK + b) + 3] = -vl;
+    }
+  }
+}
+
+static cudaError_t launch_cov16(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
+  const int NM = c->N <= 8 ? 8 : 16;
+  const size_t sm = ((size_t)2 * 2 * CT * 16 + 2 * (size_t)NM * CT + (size_t)CT * 16 + (size_t)c->N * 16) * sizeof(float);
+  if (NM == 8) {
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_cov16<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_cov16<8><<<fc, 256, sm, s>>>(c->x, c->lam, c->g, c->V, c->Vdd, c->F, c->T, c->Tp, c->N, c->eps, fb);
+  } else {
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_cov16<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_cov16<16><<<fc, 256, sm, s>>>(c->x, c->lam, c->g, c->V, c->Vdd, c->F, c->T, c->Tp, c->N, c->eps, fb);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_cov(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
+  if (c->MK == 16) return launch_cov16(c, s, fb, fc);
   DFM_MK_DISPATCH(c->MK, {
     constexpr int CP = CovCfg<MK_>::CP;
     const int items = c->K * CovCfg<MK_>::PARTS;

@@ -226,6 +226,132 @@ __global__ void __launch_bounds__(128) k_ip(const double2* __restrict__ V, const
   }
 }
 
+// One 16 x 16 block per CTA of 256 threads (conventional all-microphone
+// FastMNMF, M_k = 16): thread e owns entry (i, j) = (e / 16, e % 16).  For
+// mu ascending: V_mu is staged in shared memory, A = Q V_mu formed entry by
+// entry, A q = e_mu solved by Gauss-Jordan elimination with partial pivoting
+// (the pivot column's magnitudes and the rows exchanged through shared
+// memory, first maximum taken on ties), then Eq. (15) with a block reduction
+// of Re q^H V q.  The singularity test and the pseudo-inverse fallback are
+// those of k_ip.
+// Pseudo-inverse path of k_ip16 (rare): q = pinv(Q V_mu) e_mu in FP64 by one
+// thread, kept out of line so that its local arrays do not weigh on the
+// registers of the main path.
+template <class R>
+__device__ __noinline__ void ip16_pinv(const cx<R>* Qs, const double2* Vmu, int mu, float rtol, cx<double>* qout) {
+  using O = RealOps<R>;
+  constexpr int MK = 16;
+  cx<double> U[MK][MK], q[MK];
+  for (int r = 0; r < MK; ++r)
+    for (int cc = 0; cc < MK; ++cc) {
+      double sr = 0.0, si = 0.0;
+      for (int l = 0; l < MK; ++l) {
+        const cx<R> qrl = Qs[r * MK + l];
+        const double qr = O::to_d(qrl.re), qim = O::to_d(qrl.im);
+        const double2 v = Vmu[l * MK + cc];
+        sr += qr * v.x - qim * v.y;
+        si += qr * v.y + qim * v.x;
+      }
+      U[r][cc] = cmake(sr, si);
+    }
+  pinv_column<MK>(U, mu, (double)rtol, q);
+  for (int r = 0; r < MK; ++r) qout[r] = q[r];
+}
+
+template <class R>
+__global__ void __launch_bounds__(256, 2) k_ip16(const double2* __restrict__ V, const float4* __restrict__ Vdd,
+                                              double2* __restrict__ Q64, float2* __restrict__ Q32, float eps,
+                                              float rtol, unsigned* __restrict__ flags) {
+  using O = RealOps<R>;
+  constexpr int MK = 16, E = MK * MK;
+  const int blk = blockIdx.x;
+  const int e = threadIdx.x, i = e / MK, j = e % MK, lane = e & 31, warp = e >> 5;
+  __shared__ cx<R> Qs[E], As[E], Vs[E];
+  __shared__ cx<R> bs[MK];
+  __shared__ float keys[MK], wmax[8];
+  __shared__ R wred[8];
+  __shared__ cx<double> qfb[MK];
+  Qs[e] = cfrom_d2<R>(Q64[(size_t)blk * E + e]);
+  const size_t vbase = (size_t)blk * E * MK;
+  const double2* Vb = V + vbase;
+  for (int mu = 0; mu < MK; ++mu) {
+    Vs[e] = VLoad<R>::get(V, Vdd, vbase + (size_t)mu * E + e);
+    __syncthreads();
+    // 1. A = Q V_mu
+    cx<R> a = czero<R>();
+    for (int l = 0; l < MK; ++l) a = cadd(a, cmul(Qs[i * MK + l], Vs[l * MK + j]));
+    float m = sqrtf(cabs2_f(a));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(DFM_FULL_MASK, m, o));
+    if (lane == 0) wmax[warp] = m;
+    cx<R> bv = (i == mu) ? cmake(O::one(), O::zero()) : czero<R>();
+    float minpiv = INFINITY;
+    // 2. Gauss-Jordan with partial pivoting (b held by the threads of column 0)
+    for (int c = 0; c < MK; ++c) {
+      As[e] = a;
+      if (j == 0) bs[i] = bv;
+      if (j == c) keys[i] = (i >= c) ? cabs2_f(a) : -1.f;
+      __syncthreads();
+      int prow = c;
+      float best = keys[c];
+      for (int r = c + 1; r < MK; ++r)
+        if (keys[r] > best) {
+          best = keys[r];
+          prow = r;
+        }
+      const int ri = (i == c) ? prow : (i == prow ? c : i);  // this thread's row after the exchange
+      const cx<R> piv = As[prow * MK + c];
+      minpiv = fminf(minpiv, sqrtf(cabs2_f(piv)));
+      const cx<R> inv = crecip(piv);
+      const cx<R> rowc = cmul(As[prow * MK + j], inv);
+      const cx<R> bc = cmul(bs[prow], inv);
+      if (i == c) {
+        a = rowc;
+        bv = bc;
+      } else {
+        const cx<R> mi = As[ri * MK + c];
+        a = csub(As[ri * MK + j], cmul(mi, rowc));
+        bv = csub(bs[ri], cmul(mi, bc));
+      }
+      __syncthreads();
+    }
+    float maxabs = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) maxabs = fmaxf(maxabs, wmax[w]);
+    const bool singular = !(minpiv > rtol * maxabs);
+    if (singular) {
+      if (e == 0) {
+        ip16_pinv<R>(Qs, Vb + (size_t)mu * E, mu, rtol, qfb);
+        atomicAdd(flags + FLAG_PINV, 1u);
+      }
+    } else if (j == 0) {
+      qfb[i] = cmake(O::to_d(bv.re), O::to_d(bv.im));  // float pairs are exact in FP64
+    }
+    __syncthreads();
+    // 3. normalisation (Eq. 15): s = Re q^H V q over the block
+    const cx<R> qi = cfrom_d2<R>(make_double2(qfb[i].re, qfb[i].im));
+    const cx<R> qj = cfrom_d2<R>(make_double2(qfb[j].re, qfb[j].im));
+    const cx<R> vq = cmul(Vs[e], qj);
+    R term = O::add(O::mul(qi.re, vq.re), O::mul(qi.im, vq.im));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) term = O::add(term, O::shfl_xor(term, o));
+    if (lane == 0) wred[warp] = term;
+    __syncthreads();
+    R sum = O::zero();
+#pragma unroll
+    for (int w = 0; w < 8; ++w) sum = O::add(sum, wred[w]);
+    if (!(O::to_f(sum) > eps)) sum = O::from_f(eps);
+    const R rs = O::div(O::one(), O::sqrt_(sum));
+    if (i == mu) Qs[mu * MK + j] = cscale(cconj(qj), rs);
+    __syncthreads();
+  }
+  const cx<R> v = Qs[e];
+  const double re = O::to_d(v.re), im = O::to_d(v.im);
+  if (!isfinite(re) || !isfinite(im)) atomicOr(flags + FLAG_NONFINITE, 1u);
+  Q64[(size_t)blk * E + e] = make_double2(re, im);
+  Q32[(size_t)blk * E + e] = make_float2((float)re, (float)im);
+}
+
 // ln |det Q_fk|^2 by FP64 Gaussian elimination with partial pivoting, one
 // thread per block.
 template <int MK>
@@ -324,6 +450,15 @@ __global__ void k_q32(const double2* __restrict__ Q64, float2* __restrict__ Q32,
 cudaError_t launch_ip(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
   const int nblocks = fc * c->K;
   const size_t o = (size_t)fb * c->K;  // first block of the range
+  if (c->MK == 16) {
+    const size_t ov = o * 16 * 16 * 16, oq = o * 16 * 16;
+    switch (c->ip_arith) {
+      case 0: k_ip16<double><<<nblocks, 256, 0, s>>>(c->V + ov, c->Vdd + ov, c->Q64 + oq, c->Q32 + oq, c->eps, c->singular_rtol, c->flags); break;
+      case 1: k_ip16<dd><<<nblocks, 256, 0, s>>>(c->V + ov, c->Vdd + ov, c->Q64 + oq, c->Q32 + oq, c->eps, c->singular_rtol, c->flags); break;
+      default: k_ip16<float><<<nblocks, 256, 0, s>>>(c->V + ov, c->Vdd + ov, c->Q64 + oq, c->Q32 + oq, c->eps, c->singular_rtol, c->flags); break;
+    }
+    return cudaGetLastError();
+  }
   const int grid = (nblocks + 7) / 8;  // 4 warps x 2 blocks per CTA
   DFM_MK_DISPATCH(c->MK, {
     switch (c->ip_arith) {
@@ -337,12 +472,20 @@ cudaError_t launch_ip(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
 
 cudaError_t launch_logdet(const dfmnmf_ctx* c, double* out, cudaStream_t s) {
   const int nblocks = c->F * c->K;
+  if (c->MK == 16) {
+    k_logdet<16><<<(nblocks + 127) / 128, 128, 0, s>>>(c->Q64, out, nblocks);
+    return cudaGetLastError();
+  }
   DFM_MK_DISPATCH(c->MK, { k_logdet<MK_><<<(nblocks + 127) / 128, 128, 0, s>>>(c->Q64, out, nblocks); });
   return cudaGetLastError();
 }
 
 cudaError_t launch_qinv(const dfmnmf_ctx* c, cudaStream_t s) {
   const int nblocks = c->F * c->K;
+  if (c->MK == 16) {
+    k_qinv<16><<<(nblocks + 127) / 128, 128, 0, s>>>(c->Q64, c->Qinv32, nblocks, c->flags);
+    return cudaGetLastError();
+  }
   DFM_MK_DISPATCH(c->MK, { k_qinv<MK_><<<(nblocks + 127) / 128, 128, 0, s>>>(c->Q64, c->Qinv32, nblocks, c->flags); });
   return cudaGetLastError();
 }

@@ -94,10 +94,15 @@ cudaError_t launch_loglik(const dfmnmf_ctx* c, cudaStream_t s) {
   const size_t npart = (size_t)c->F * ty;
   double* ld = c->red + npart;
   const size_t nld = (size_t)c->F * c->K;
-  DFM_MK_DISPATCH(c->MK, {
-    k_nll_data<MK_><<<dim3(c->F, ty), 128, gq_smem(c), s>>>(c->x, c->Q64, c->lam, c->g, c->red, c->F, c->T,
-                                                             c->Tp, c->K, c->N, c->eps);
-  });
+  if (c->MK == 16) {
+    k_nll_data<16><<<dim3(c->F, ty), 128, gq_smem(c), s>>>(c->x, c->Q64, c->lam, c->g, c->red, c->F, c->T, c->Tp,
+                                                            c->K, c->N, c->eps);
+  } else {
+    DFM_MK_DISPATCH(c->MK, {
+      k_nll_data<MK_><<<dim3(c->F, ty), 128, gq_smem(c), s>>>(c->x, c->Q64, c->lam, c->g, c->red, c->F, c->T,
+                                                               c->Tp, c->K, c->N, c->eps);
+    });
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = launch_logdet(c, ld, s);
@@ -173,10 +178,15 @@ __global__ void __launch_bounds__(128) k_separate(const float2* __restrict__ x, 
 cudaError_t launch_separate(const dfmnmf_ctx* c, float2* out, cudaStream_t s) {
   const int ty = (c->T + 127) / 128;
   const size_t sm = gq_smem(c) + (size_t)c->K * c->MK * c->MK * sizeof(float2);
-  DFM_MK_DISPATCH(c->MK, {
-    k_separate<MK_><<<dim3(c->F, ty), 128, sm, s>>>(c->x, c->Q64, c->Qinv32, c->lam, c->g, out, c->F, c->T,
-                                                     c->Tp, c->K, c->N, c->eps);
-  });
+  if (c->MK == 16) {
+    k_separate<16><<<dim3(c->F, ty), 128, sm, s>>>(c->x, c->Q64, c->Qinv32, c->lam, c->g, out, c->F, c->T, c->Tp,
+                                                    c->K, c->N, c->eps);
+  } else {
+    DFM_MK_DISPATCH(c->MK, {
+      k_separate<MK_><<<dim3(c->F, ty), 128, sm, s>>>(c->x, c->Q64, c->Qinv32, c->lam, c->g, out, c->F, c->T,
+                                                       c->Tp, c->K, c->N, c->eps);
+    });
+  }
   return cudaGetLastError();
 }
 

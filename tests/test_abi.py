@@ -45,7 +45,7 @@ def _args(F=3, T=4, mics=(4, 4), N=2, B_=3):
 
 @pytest.mark.parametrize("bad", [dict(F=0), dict(T=0), dict(N=0), dict(B_=0), dict(mics=(4, 3)),
                                  dict(mics=(5,)), dict(mics=(0,)), dict(N=17), dict(B_=65),
-                                 dict(mics=(1,) * 17)])
+                                 dict(mics=(1,) * 17), dict(mics=(16, 16)), dict(mics=(8,))])
 def test_invalid_descriptor_rejected(lib, bad):
     a = _args(**bad)
     with pytest.raises(D.DfmnmfError) as ei:
@@ -56,6 +56,11 @@ def test_invalid_descriptor_rejected(lib, bad):
 def test_unknown_precision_rejected(lib):
     a = _args()
     for kw in (dict(precision=7), dict(ip_arith=9)):
+        with pytest.raises(D.DfmnmfError) as ei:
+            D.dfmnmf_init(a["F"], a["T"], a["mics"], a["N"], a["B"], a["x"], a["W0"], a["H0"], a["g0"], **kw)
+        assert ei.value.code == D.DFMNMF_EINVAL
+    a = _args(mics=(16,))  # the all-microphone block is built in the FP32 form only
+    for kw in (dict(precision=D.DFMNMF_BF16_TC),):
         with pytest.raises(D.DfmnmfError) as ei:
             D.dfmnmf_init(a["F"], a["T"], a["mics"], a["N"], a["B"], a["x"], a["W0"], a["H0"], a["g0"], **kw)
         assert ei.value.code == D.DFMNMF_EINVAL
