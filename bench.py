@@ -180,6 +180,24 @@ def iteration_bytes(F, T, M, N):
     return 28 * F * T * M + 56 * F * T * N
 
 
+# ------------------------------------------------------ replicas (N > 1)
+def ranks_max(v: float, device) -> float:
+    """Largest value over the ranks of the default process group (v itself without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return v
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(max_ms: float, world: int, iters: int, steps: int) -> float:
+    """Whole-job MM iterations/s: every rank runs its own mixture for `steps` steps of `iters`
+    iterations; the job takes the slowest rank's time."""
+    return world * iters * steps / (max_ms / 1000.0)
+
+
 # --------------------------------------------------------- CPU oracle arm
 def run_oracle_sample(workload: str, seconds: float, max_iters: int = 1000) -> dict:
     """Time the FP64 oracle (single thread) for about `seconds` of MM iterations."""
@@ -309,12 +327,7 @@ def main():
         return tot
 
     def max_over_ranks(v):
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([v], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            return float(t.item())
-        return v
+        return ranks_max(v, dev)
 
     kb_form = {f: (kernel_bytes(F, T, M, N, Bb, 1, M) if f == "allmic" else kernel_bytes(F, T, M, N, Bb, K, MK))
                for f in forms}
@@ -363,7 +376,7 @@ def main():
         iter_ms = sum(ms for _, ms in kt)
         dom_name, dom_ms = max(kt, key=lambda e: e[1])
         results[form] = dict(
-            value=world * iters * args.steps / (total_ms / 1000.0), ms_per_step=total_ms / args.steps,
+            value=replica_value(total_ms, world, iters, args.steps), ms_per_step=total_ms / args.steps,
             launches_iter=launches_iter, kernels=kt, iter_ms=iter_ms, graph_iter_ms=graph_iter_ms,
             dominant=(dom_name, dom_ms),
             nll=nll_box[-1], clocks=ck)
@@ -440,7 +453,7 @@ def main():
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e2e_ms = float(t.item())
         h2d = xh.numel() * 8 + (W0h.numel() + H0h.numel() + g0h.numel()) * 4 + Q0h.numel() * 16
-        out["e2e"] = {"value": world * iters * args.steps / (e2e_ms / 1000.0), "unit": UNIT,
+        out["e2e"] = {"value": replica_value(e2e_ms, world, iters, args.steps), "unit": UNIT,
                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8 + 16,
                       "ms_per_step": e2e_ms / args.steps}
 
