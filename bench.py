@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--batched", type=int, default=64,
+                    help="also time this many mixtures of mixed length and layout (T in [150, 1250], K in {2, 4, 8} "
+                         "x 4 mics, N in {3, 5, 8}, F = 513) in one graph launch per iteration (0: skip)")
     ap.add_argument("--concurrent", type=int, default=8,
                     help="also time this many independent mixtures run concurrently on separate streams (0: skip)")
     return ap.parse_args()
@@ -256,6 +259,66 @@ def reference_arm(args, rank, world):
         "gpu_launches": 0,
     }
     print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------- batched form
+def batched_measurement(args, D, synth, torch, dev, timed, precision, ip):
+    """args.batched mixtures: T ~ U[150, 1250], K in {2, 4, 8} subarrays of 4 mics, N in {3, 5, 8}, F = 513,
+    B = 16, seeded.  The observations are the first T frames of one generated mixture per (K, N) pair (the
+    generator's cost grows with T; the values do not change the work).  Each context's launch shapes come
+    from dfmnmf_autotune; the batch advances all mixtures with one graph launch per iteration.  Reported:
+    aggregate TF-bin.mic updates/s, against the same contexts iterated one after another."""
+    import numpy as np
+    rng = np.random.default_rng(2026)
+    n = args.batched
+    Ts = rng.integers(150, 1251, size=n)
+    Ks = rng.choice([2, 4, 8], size=n)
+    Ns = rng.choice([3, 5, 8], size=n)
+    F, B, iters = 513, 16, 20
+    base = {}
+    for K, N in sorted(set(zip(Ks.tolist(), Ns.tolist()))):
+        base[(K, N)] = synth.make_problem(F, int(Ts.max()), (4,) * K, N, B, seed=100 + 10 * K + N)
+    ctxs, tune, forms_used = [], {}, {}
+    for T, K, N in zip(Ts.tolist(), Ks.tolist(), Ns.tolist()):
+        p = base[(K, N)]
+        x = np.ascontiguousarray(p.x[:, :T])
+        H0 = np.ascontiguousarray(p.H0[:, :, :T])
+        # tensor-core covariances where the subarrays are underdetermined (N >= 4 sources for 4 microphones);
+        # determined ones keep the float-float covariances (their V reach cond 1e6..1e8)
+        prec = precision if (precision != D.DFMNMF_BF16_TC or N >= 4) else D.DFMNMF_FP32
+        forms_used[prec] = forms_used.get(prec, 0) + 1
+        c = D.dfmnmf_init(F, T, (4,) * K, N, B, x, p.W0, H0, p.g0, None, precision=prec, ip_arith=ip)
+        shape = D.dfmnmf_autotune(c, 3)
+        tune[str(shape)] = tune.get(str(shape), 0) + 1
+        ctxs.append(c)
+    batch = D.dfmnmf_batch_create(ctxs)
+    work = float(sum(F * T * 4 * K for T, K in zip(Ts.tolist(), Ks.tolist()))) * iters  # TF-bin.mic updates per step
+
+    def step_batch(_):
+        D.dfmnmf_batch_iterate(batch, iters)
+
+    def step_loop(_):
+        for c in ctxs:
+            D.dfmnmf_iterate(c, iters)
+
+    for _ in range(2):
+        step_batch(None)
+        step_loop(None)
+    torch.cuda.synchronize()
+    nsteps = max(2, args.steps // 2)
+    tb = timed(step_batch, None, nsteps)
+    tl = timed(step_loop, None, nsteps)
+    res = {"mixtures": n, "iters_per_step": iters, "unit": "TF-bin.mic updates/s",
+           "value": work * nsteps / (tb / 1000.0), "loop_value": work * nsteps / (tl / 1000.0),
+           "speedup_vs_loop": tl / tb, "ms_per_step": tb / nsteps, "loop_ms_per_step": tl / nsteps,
+           "mm_iter_per_s_aggregate": n * iters * nsteps / (tb / 1000.0),
+           "T_range": [int(Ts.min()), int(Ts.max())], "launch_shapes": tune,
+           "forms": {("bf16tc" if k == D.DFMNMF_BF16_TC else "fp32"): v for k, v in forms_used.items()},
+           "note": "per-mixture launch loop = the same contexts' graphs launched one after another on one stream"}
+    del batch
+    for c in ctxs:
+        D.dfmnmf_destroy(c)
+    return res
 
 
 # ---------------------------------------------------------------- our arm
@@ -496,6 +559,10 @@ def main():
                              "frac_of_hbm_peak": ib * val / world / 1e9 / peak}
         for c in cctx:
             D.dfmnmf_destroy(c)
+
+    # many mixtures of uneven length and layout, one graph launch per iteration, launch shapes autotuned
+    if args.batched > 0 and world == 1:
+        out["batched"] = batched_measurement(args, D, synth, torch, dev, timed, precisions[forms[0]], ip)
 
     # variants on the same GPU: native-FP64 and plain-FP32 IP solves (FP32 form)
     if not args.no_variants:

@@ -186,6 +186,39 @@ int dfmnmf_kernel_times(dfmnmf_ctx* ctx, int n_iter, double* avg_ms, const char*
 void dfmnmf_destroy(dfmnmf_ctx* ctx);
 
 /*
+ * Launch shapes picked by measurement (no counterpart in the paper; a GPU
+ * concern): the per-frequency kernels of an iteration run either band-wide
+ * on one graph branch or as two halves of the band on two branches
+ * (*branches = 1 or 2), and the split NMF products of Eqs. (8)-(9) aim for
+ * 2, 4 or 8 CTAs per SM (*nmf_ctas).  Every combination is timed over
+ * iters_per_trial >= 1 replays of the captured iteration (after one warm-up
+ * replay); the fastest is kept for this context.  The trials advance a copy
+ * of the state only: Q, W, H, g and the device flags are restored, so the
+ * call leaves the iterate where it was.  Allocates four temporary device
+ * arrays of the state's size.  branches / nmf_ctas may be NULL.
+ * Synchronises `stream`.  Results are identical under every choice up to
+ * rounding (the split changes the order of the NMF sums).
+ */
+int dfmnmf_autotune(dfmnmf_ctx* ctx, int iters_per_trial, int* branches, int* nmf_ctas, void* stream);
+
+/*
+ * Many mixtures, one CUDA graph launch per iteration (no counterpart in the
+ * paper).  dfmnmf_batch_create captures (if not done yet) each context's
+ * iteration and places them as independent child graphs of one graph; the
+ * contexts may have different sizes and layouts (each keeps its own state,
+ * precision and launch shapes).  dfmnmf_batch_iterate advances every
+ * mixture by n_iter iterations (asynchronous on `stream`), exactly as
+ * dfmnmf_iterate on each context would.  The batch refers to the contexts
+ * without owning them: destroy it before any of them, and create it after
+ * dfmnmf_autotune (it copies the iteration graphs as they are at creation).
+ * All contexts must live on one device.  EINVAL on a NULL or empty list.
+ */
+typedef struct dfmnmf_batch dfmnmf_batch;
+int dfmnmf_batch_create(dfmnmf_batch** out, dfmnmf_ctx* const* ctxs, int count);
+int dfmnmf_batch_iterate(dfmnmf_batch* batch, int n_iter, void* stream);
+void dfmnmf_batch_destroy(dfmnmf_batch* batch);
+
+/*
  * Allocation-free negative log-likelihood.  The paper has no counterpart:
  * this entry point exists for callers that may not allocate device memory
  * when they need the cost -- for example an audio engine's real-time thread,

@@ -1,5 +1,6 @@
 // api.cu -- the C ABI of include/dfmnmf.h: argument checks, device state,
 // the iteration schedule and its CUDA graph.
+#include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -9,6 +10,12 @@
 #include "../../include/dfmnmf.h"
 #include "common.cuh"
 #include "internal.h"
+
+struct dfmnmf_batch {
+  int count, device;
+  cudaGraph_t graph;       // one child graph (a context's iteration) per mixture, no edges
+  cudaGraphExec_t gexec;
+};
 
 namespace {
 
@@ -134,6 +141,7 @@ int enqueue_stage(dfmnmf_ctx* c, int stage, cudaStream_t s) {
 
 // Split point of the band: a multiple of 8 frequencies (whole tensor-core tiles).
 int band_split(const dfmnmf_ctx* c) {
+  if (c->cfg_branches == 1) return 0;
   const int h = ((c->F / 2) + 7) & ~7;
   return (h > 0 && h < c->F) ? h : 0;
 }
@@ -180,6 +188,13 @@ int ensure_graph(dfmnmf_ctx* c) {
   CK(cudaGraphGetNodes(c->graph, nullptr, &nodes));
   c->launches_per_iter = (int)nodes;
   return DFMNMF_OK;
+}
+
+void drop_graph(dfmnmf_ctx* c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  c->gexec = nullptr;
+  c->graph = nullptr;
 }
 
 int refresh_derived(dfmnmf_ctx* c, cudaStream_t s) {
@@ -238,6 +253,9 @@ int dfmnmf_init(dfmnmf_ctx** out, const dfmnmf_desc* d, const void* x, const flo
     delete c;
     return fail(DFMNMF_ECUDA, "no CUDA device");
   }
+  if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) c->num_sms = 152;
+  c->cfg_branches = 2;
+  c->cfg_nmf_ctas = 4;
   int r = 0;
   const int ty = (c->T + 127) / 128;
   c->red_len = (size_t)c->F * ty + (size_t)c->F * c->K;
@@ -395,6 +413,135 @@ int dfmnmf_kernel_times(dfmnmf_ctx* c, int n_iter, double* avg_ms, const char** 
   if (names)
     for (int i = 0; i < n; ++i) names[i] = L[i].name;
   return rc;
+}
+
+int dfmnmf_autotune(dfmnmf_ctx* c, int iters_per_trial, int* branches, int* nmf_ctas, void* stream) {
+  if (!c || iters_per_trial < 1) return fail(DFMNMF_EINVAL, "bad argument");
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = as_stream(stream);
+  // the trials advance the state: keep a copy and put it back after every trial
+  double2* Qb = nullptr;
+  float *Wb = nullptr, *Hb = nullptr, *gb = nullptr;
+  unsigned* fb = nullptr;
+  int r = 0;
+  if ((r = dalloc(&Qb, nQ(c), "Q backup")) || (r = dalloc(&Wb, nW(c), "W backup")) ||
+      (r = dalloc(&Hb, nH(c), "H backup")) || (r = dalloc(&gb, ng(c), "g backup")) ||
+      (r = dalloc(&fb, dfm::FLAG_COUNT, "flags backup"))) {
+    cudaFree(Qb); cudaFree(Wb); cudaFree(Hb); cudaFree(gb); cudaFree(fb);
+    return r;
+  }
+  auto copy_state = [&](bool save) -> cudaError_t {
+    cudaError_t e = cudaSuccess;
+    const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+    if (save) {
+      if (e == cudaSuccess) e = cudaMemcpyAsync(Qb, c->Q64, nQ(c) * sizeof(double2), k, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(Wb, c->W, nW(c) * sizeof(float), k, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(Hb, c->H, nH(c) * sizeof(float), k, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(gb, c->g, ng(c) * sizeof(float), k, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(fb, c->flags, dfm::FLAG_COUNT * sizeof(unsigned), k, s);
+    } else {
+      if (e == cudaSuccess) e = cudaMemcpyAsync(c->Q64, Qb, nQ(c) * sizeof(double2), k, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(c->W, Wb, nW(c) * sizeof(float), k, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(c->H, Hb, nH(c) * sizeof(float), k, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(c->g, gb, ng(c) * sizeof(float), k, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(c->flags, fb, dfm::FLAG_COUNT * sizeof(unsigned), k, s);
+      if (e == cudaSuccess) e = dfm::launch_lambda(c, s);
+      if (e == cudaSuccess) e = dfm::launch_q_convert(c, s);
+    }
+    return e;
+  };
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const int old_br = c->cfg_branches, old_ct = c->cfg_nmf_ctas;
+  int best_br = old_br, best_ct = old_ct;
+  float best = INFINITY;
+  cudaError_t e = copy_state(true);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const int br_opts[2] = {1, 2}, ct_opts[3] = {2, 4, 8};
+  for (int ib = 0; ib < 2 && e == cudaSuccess && !r; ++ib)
+    for (int ic = 0; ic < 3 && e == cudaSuccess && !r; ++ic) {
+      c->cfg_branches = br_opts[ib];
+      c->cfg_nmf_ctas = ct_opts[ic];
+      if (c->cfg_branches == 2 && band_split(c) == 0) continue;  // band too small to split
+      drop_graph(c);
+      if ((r = ensure_graph(c))) break;
+      e = cudaGraphLaunch(c->gexec, s);  // warm-up
+      if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+      for (int i = 0; i < iters_per_trial && e == cudaSuccess; ++i) e = cudaGraphLaunch(c->gexec, s);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && ms < best) {
+        best = ms;
+        best_br = c->cfg_branches;
+        best_ct = c->cfg_nmf_ctas;
+      }
+      if (e == cudaSuccess) e = copy_state(false);
+    }
+  c->cfg_branches = (e == cudaSuccess && !r) ? best_br : old_br;
+  c->cfg_nmf_ctas = (e == cudaSuccess && !r) ? best_ct : old_ct;
+  drop_graph(c);
+  if (e == cudaSuccess) e = copy_state(false);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(Qb); cudaFree(Wb); cudaFree(Hb); cudaFree(gb); cudaFree(fb);
+  if (r) return r;
+  if (e != cudaSuccess) return fail(DFMNMF_ECUDA, "autotune: %s", cudaGetErrorString(e));
+  if (branches) *branches = c->cfg_branches;
+  if (nmf_ctas) *nmf_ctas = c->cfg_nmf_ctas;
+  return DFMNMF_OK;
+}
+
+int dfmnmf_batch_create(dfmnmf_batch** out, dfmnmf_ctx* const* ctxs, int count) {
+  if (!out || !ctxs || count < 1) return fail(DFMNMF_EINVAL, "bad argument");
+  *out = nullptr;
+  for (int i = 0; i < count; ++i) {
+    if (!ctxs[i]) return fail(DFMNMF_EINVAL, "context %d is NULL", i);
+    if (ctxs[i]->device != ctxs[0]->device) return fail(DFMNMF_EINVAL, "contexts on different devices");
+  }
+  CK(cudaSetDevice(ctxs[0]->device));
+  for (int i = 0; i < count; ++i) {
+    const int r = ensure_graph(ctxs[i]);
+    if (r) return r;
+  }
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < count && e == cudaSuccess; ++i) {
+    cudaGraphNode_t node;
+    e = cudaGraphAddChildGraphNode(&node, g, nullptr, 0, ctxs[i]->graph);  // independent branches
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return fail(DFMNMF_ECUDA, "batch graph: %s", cudaGetErrorString(e));
+  }
+  dfmnmf_batch* b = new dfmnmf_batch;
+  b->count = count;
+  b->device = ctxs[0]->device;
+  b->graph = g;
+  b->gexec = ge;
+  *out = b;
+  return DFMNMF_OK;
+}
+
+int dfmnmf_batch_iterate(dfmnmf_batch* b, int n_iter, void* stream) {
+  if (!b) return fail(DFMNMF_EINVAL, "null batch");
+  if (n_iter < 0) return fail(DFMNMF_EINVAL, "n_iter=%d is negative", n_iter);
+  CK(cudaSetDevice(b->device));
+  for (int i = 0; i < n_iter; ++i) CK(cudaGraphLaunch(b->gexec, as_stream(stream)));
+  return DFMNMF_OK;
+}
+
+void dfmnmf_batch_destroy(dfmnmf_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  delete b;
 }
 
 int dfmnmf_loglik(dfmnmf_ctx* c, double* nll_host, void* stream) {

@@ -13,6 +13,11 @@ struct dfmnmf_ctx {
   float eps;            // floor of Sec. IV-A
   float singular_rtol;  // relative pivot / singular-value cut-off of the IP solve
   int device;
+  int num_sms;          // multiprocessors of the device
+  // launch shapes (dfmnmf_autotune): per-frequency kernels on 1 or 2 graph
+  // branches, and the CTAs per SM the split NMF products aim for
+  int cfg_branches;
+  int cfg_nmf_ctas;
   // state and buffers (device)
   float2* x;       // [F][T][M]
   double2* Q64;    // [F][K*MK*MK]   master copy

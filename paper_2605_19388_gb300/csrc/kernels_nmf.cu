@@ -252,10 +252,12 @@ __global__ void __launch_bounds__(256) k_hupd(const float* __restrict__ A, const
   }
 }
 
-// Number of splits of the reduction: enough CTAs for about four per SM, at
-// most NMF_MAX_SPLIT, never more than the number of 64-wide chunks.
-static void split_plan(int tiles, int nch, int* S, int* cps) {
-  int s = (4 * 152 + tiles - 1) / tiles;
+// Number of splits of the reduction: enough CTAs for cfg_nmf_ctas per SM
+// (4 unless tuned), at most NMF_MAX_SPLIT, never more than the number of
+// 64-wide chunks.
+static void split_plan(const dfmnmf_ctx* c, int tiles, int nch, int* S, int* cps) {
+  const int target = (c->cfg_nmf_ctas > 0 ? c->cfg_nmf_ctas : 4) * (c->num_sms > 0 ? c->num_sms : 152);
+  int s = (target + tiles - 1) / tiles;
   s = s < 1 ? 1 : (s > NMF_MAX_SPLIT ? NMF_MAX_SPLIT : s);
   s = s > nch ? nch : s;
   *cps = (nch + s - 1) / s;
@@ -274,7 +276,7 @@ cudaError_t launch_wupd(const dfmnmf_ctx* c, cudaStream_t s) {
   const int nb = (c->B + TILE - 1) / TILE;
   const int tiles = ((c->F + TILE - 1) / TILE) * c->N * nb;
   int S, cps;
-  split_plan(tiles, (c->T + KCH - 1) / KCH, &S, &cps);
+  split_plan(c, tiles, (c->T + KCH - 1) / KCH, &S, &cps);
   dim3 grid((c->F + TILE - 1) / TILE, c->N, nb * S);
   k_wupd<<<grid, 256, 0, s>>>(c->A, c->D, c->H, c->W, c->F, c->T, c->Tp, c->B, c->eps, c->flags, S, cps,
                               c->nmf_part, c->nmf_ticket);
@@ -285,7 +287,7 @@ cudaError_t launch_hupd(const dfmnmf_ctx* c, cudaStream_t s) {
   const int nb = (c->B + TILE - 1) / TILE;
   const int tiles = ((c->T + TILE - 1) / TILE) * c->N * nb;
   int S, cps;
-  split_plan(tiles, (c->F + KCH - 1) / KCH, &S, &cps);
+  split_plan(c, tiles, (c->F + KCH - 1) / KCH, &S, &cps);
   dim3 grid((c->T + TILE - 1) / TILE, c->N, nb * S);
   k_hupd<<<grid, 256, 0, s>>>(c->A, c->D, c->W, c->H, c->F, c->T, c->Tp, c->B, c->eps, c->flags, S, cps,
                               c->nmf_part, c->nmf_ticket);

@@ -28,7 +28,8 @@ DFMNMF_BUF_V, DFMNMF_BUF_P, DFMNMF_BUF_LAMBDA = 1, 2, 3
 EXPORTED = ("dfmnmf_init", "dfmnmf_set_observation", "dfmnmf_iterate", "dfmnmf_run_stage",
             "dfmnmf_loglik", "dfmnmf_separate", "dfmnmf_get_params", "dfmnmf_set_params",
             "dfmnmf_get_buffer", "dfmnmf_launches_per_iteration", "dfmnmf_kernel_times", "dfmnmf_destroy",
-            "dfmnmf_last_error", "dfmnmf_version", "dfmnmf_loglik_noalloc")
+            "dfmnmf_last_error", "dfmnmf_version", "dfmnmf_loglik_noalloc", "dfmnmf_autotune",
+            "dfmnmf_batch_create", "dfmnmf_batch_iterate", "dfmnmf_batch_destroy")
 
 
 class DfmnmfError(RuntimeError):
@@ -73,6 +74,10 @@ def load_library(path: Optional[str] = None):
         "dfmnmf_last_error": (ctypes.c_char_p, []),
         "dfmnmf_version": (ci, []),
         "dfmnmf_loglik_noalloc": (ci, [ctypes.POINTER(dfmnmf_desc), vp, vp, vp, vp, vp, ctypes.POINTER(cd), vp]),
+        "dfmnmf_autotune": (ci, [vp, ci, ctypes.POINTER(ci), ctypes.POINTER(ci), vp]),
+        "dfmnmf_batch_create": (ci, [ctypes.POINTER(vp), ctypes.POINTER(vp), ci]),
+        "dfmnmf_batch_iterate": (ci, [vp, ci, vp]),
+        "dfmnmf_batch_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -219,6 +224,44 @@ def dfmnmf_destroy(ctx: Context):
     if ctx.handle is not None and ctx.handle.value:
         load_library().dfmnmf_destroy(ctx.handle)
         ctx.handle = ctypes.c_void_p()
+
+
+def dfmnmf_autotune(ctx: Context, iters_per_trial: int = 5, stream=None):
+    """Time the launch-shape candidates and keep the fastest; returns (branches, nmf_ctas)."""
+    br, ct = ctypes.c_int(), ctypes.c_int()
+    _check(load_library().dfmnmf_autotune(ctx.handle, int(iters_per_trial), ctypes.byref(br), ctypes.byref(ct),
+                                          _stream(stream)))
+    return br.value, ct.value
+
+
+class Batch:
+    """Owns one dfmnmf_batch*; keeps its contexts alive."""
+
+    def __init__(self, handle, ctxs):
+        self.handle, self.ctxs = handle, list(ctxs)
+
+    def __del__(self):
+        try:
+            dfmnmf_batch_destroy(self)
+        except Exception:  # pragma: no cover
+            pass
+
+
+def dfmnmf_batch_create(ctxs) -> Batch:
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.handle.value for c in ctxs])
+    h = ctypes.c_void_p()
+    _check(load_library().dfmnmf_batch_create(ctypes.byref(h), arr, len(ctxs)))
+    return Batch(h, ctxs)
+
+
+def dfmnmf_batch_iterate(batch: Batch, n_iter: int, stream=None):
+    _check(load_library().dfmnmf_batch_iterate(batch.handle, int(n_iter), _stream(stream)))
+
+
+def dfmnmf_batch_destroy(batch: Batch):
+    if batch.handle is not None and batch.handle.value:
+        load_library().dfmnmf_batch_destroy(batch.handle)
+        batch.handle = ctypes.c_void_p()
 
 
 def dfmnmf_version() -> int:

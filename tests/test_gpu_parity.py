@@ -90,7 +90,7 @@ def test_stage_parity_plain_fp32_ip_well_conditioned():
     stage_parity(p, Q0, D.DFMNMF_IP_F32, tol_ip=1e-4)
 
 
-@pytest.mark.parametrize("mics", [(1, 1, 1), (2, 2), (3, 3), (4,), (4, 4, 4, 4)])
+@pytest.mark.parametrize("mics", [(1, 1, 1), (2, 2), (3, 3), (4,), (4, 4, 4, 4), (4,) * 8])
 def test_stage_parity_block_sizes(mics):
     p = synth.make_problem(19, 71, mics, 3, 6, seed=5)
     Q0 = synth.random_blocks(p.F, p.mics, seed=6)
