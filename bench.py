@@ -361,6 +361,7 @@ def main():
     form_mics = {"bf16tc": p.mics, "fp32": p.mics, "allmic": allmic}
     form_q0 = {"bf16tc": Q0_d, "fp32": Q0_d, "allmic": Q0_all_d}
     ctx_q0 = {}
+    shapes = {}
     forms = [f.strip() for f in args.forms.split(",") if f.strip()]
     nll_box = []
 
@@ -405,6 +406,7 @@ def main():
                           precision=precisions[form])
         ctx_q0[id(c)] = form_q0[form]
         ctxs[form] = c
+        shapes[form] = D.dfmnmf_autotune(c, 5)  # launch shapes measured on this context (state restored)
         for _ in range(args.warmup):
             step(c)
         torch.cuda.synchronize()
@@ -481,6 +483,7 @@ def main():
                               "the per-kernel event times below, band-wide launches in order"},
         "kernels": kernel_table(head["kernels"], head["iter_ms"]),
         "forms": {f: {"value": r["value"], "unit": UNIT, "ms_per_step": r["ms_per_step"],
+                      "launch_shapes": {"branches": shapes[f][0], "nmf_ctas_per_sm": shapes[f][1]},
                       "iter_ms": r["graph_iter_ms"], "kernel_sum_ms": r["iter_ms"],
                       "kernels": kernel_table(r["kernels"], r["iter_ms"], kb_form[f]), "nll_last": r["nll"],
                       "clocks": r["clocks"]} for f, r in results.items()},

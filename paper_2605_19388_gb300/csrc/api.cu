@@ -548,6 +548,7 @@ int dfmnmf_loglik(dfmnmf_ctx* c, double* nll_host, void* stream) {
   if (!c || !nll_host) return fail(DFMNMF_EINVAL, "null argument");
   CK(cudaSetDevice(c->device));
   cudaStream_t s = as_stream(stream);
+  CK(dfm::launch_lambda(c, s));  // lambda = W H of the current state (stages may leave it behind)
   CK(dfm::launch_loglik(c, s));
   unsigned flags[dfm::FLAG_COUNT];
   double v = 0.0;
@@ -566,6 +567,7 @@ int dfmnmf_separate(dfmnmf_ctx* c, void* c_out, void* stream) {
   if (is_host_ptr(c_out)) return fail(DFMNMF_EINVAL, "c_out must be device memory");
   CK(cudaSetDevice(c->device));
   cudaStream_t s = as_stream(stream);
+  CK(dfm::launch_lambda(c, s));
   CK(dfm::launch_qinv(c, s));
   CK(dfm::launch_separate(c, reinterpret_cast<float2*>(c_out), s));
   return DFMNMF_OK;
@@ -609,6 +611,7 @@ int dfmnmf_get_buffer(dfmnmf_ctx* c, int which, void* dst, size_t dst_bytes, voi
   if (dst_bytes < bytes) return fail(DFMNMF_EINVAL, "buffer %d needs %zu bytes, got %zu", which, bytes, dst_bytes);
   CK(cudaSetDevice(c->device));
   cudaStream_t s = as_stream(stream);
+  if (which == DFMNMF_BUF_LAMBDA) CK(dfm::launch_lambda(c, s));  // W H of the current state
   if (which == DFMNMF_BUF_LAMBDA)  // drop the padding of the row stride
     CK(cudaMemcpy2DAsync(dst, (size_t)c->T * sizeof(float), src, (size_t)c->Tp * sizeof(float),
                          (size_t)c->T * sizeof(float), (size_t)c->N * c->F, cudaMemcpyDefault, s));

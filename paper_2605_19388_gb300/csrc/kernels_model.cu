@@ -418,6 +418,110 @@ __global__ void __launch_bounds__(256) k_gupd(const float* __restrict__ lam, con
   }
 }
 
+// Quad variant (M = 4, 8, 16, 32 or 64, N <= 8; 128 threads): thread (slot s,
+// quad q) owns microphones 4q .. 4q+3, so a frame's lambda values serve four
+// microphones per load and P arrives as one 16-byte read; the slots of a warp
+// are added by xor shuffles and the warps through shared memory, in a fixed
+// order.
+template <int NM, int NST>
+__global__ void __launch_bounds__(128) k_gupd4(const float* __restrict__ lam, const float* __restrict__ P,
+                                               float* __restrict__ g, int F, int T, int Tp, int M, int N, float eps,
+                                               unsigned* __restrict__ flags) {
+  extern __shared__ __align__(16) float smq[];
+  const int f = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int Q = M / 4, S = 128 / Q;  // quads per frame, frame slots (128 threads)
+  const int q = tid % Q, s = tid / Q;
+  float* ls = smq;                          // [NST][N][GT]
+  float* ps = ls + NST * NM * GT;           // [NST][GT][M]
+  float* red = ps + NST * GT * M;           // [4 warps][M][2N]
+  const int nchunk = (T + GT - 1) / GT;
+  auto issue = [&](int c) {
+    if (c < nchunk) {
+      const int t0 = c * GT, nt = min(GT, T - t0), buf = c % NST;
+      const int nq = (nt + 3) / 4, qq = tid & 31;
+      if (qq < nq)
+        for (int n = tid >> 5; n < NM; n += 4)
+          cp_async16(ls + (buf * NM + n) * GT + 4 * qq, lam + ((size_t)n * F + f) * Tp + t0 + 4 * qq);
+      const float* src = P + ((size_t)f * T + t0) * M;
+      float* dst = ps + (size_t)buf * GT * M;
+      for (int i = tid; i < nt * M / 4; i += 128) cp_async16(dst + 4 * i, src + 4 * i);
+    }
+    cp_async_commit();
+  };
+  float gr[NM][4], num[NM][4], den[NM][4];
+#pragma unroll
+  for (int n = 0; n < NM; ++n)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      gr[n][j] = g[((size_t)f * NM + n) * M + 4 * q + j];
+      num[n][j] = 0.f;
+      den[n][j] = 0.f;
+    }
+#pragma unroll
+  for (int c = 0; c < NST - 1; ++c) issue(c);
+  for (int c = 0; c < nchunk; ++c) {
+    issue(c + NST - 1);
+    cp_async_wait<NST - 1>();
+    __syncthreads();
+    const int nt = min(GT, T - c * GT), buf = c % NST;
+    const float* lb = ls + buf * NM * GT;
+    const float* pb = ps + (size_t)buf * GT * M;
+    for (int tt = s; tt < nt; tt += S) {
+      float l[NM];
+#pragma unroll
+      for (int n = 0; n < NM; ++n) l[n] = lb[n * GT + tt];
+      const float4 p4 = *reinterpret_cast<const float4*>(pb + tt * M + 4 * q);
+      const float pv[4] = {p4.x, p4.y, p4.z, p4.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        float ys = 0.f;
+#pragma unroll
+        for (int n = 0; n < NM; ++n) ys = fmaf(l[n], gr[n][j], ys);
+        const float w = fast_rcp(fmaxf(ys, eps));
+        const float u = pv[j] * w * w;
+#pragma unroll
+        for (int n = 0; n < NM; ++n) {
+          num[n][j] = fmaf(l[n], u, num[n][j]);
+          den[n][j] = fmaf(l[n], w, den[n][j]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // slots of the warp (lanes differing in the bits above the quad index), then the warps
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1)
+    if (o >= Q)
+#pragma unroll
+      for (int n = 0; n < NM; ++n)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          num[n][j] += __shfl_xor_sync(DFM_FULL_MASK, num[n][j], o);
+          den[n][j] += __shfl_xor_sync(DFM_FULL_MASK, den[n][j], o);
+        }
+  if (lane < Q)
+#pragma unroll
+    for (int n = 0; n < NM; ++n)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        red[(warp * M + 4 * q + j) * 2 * NM + 2 * n] = num[n][j];
+        red[(warp * M + 4 * q + j) * 2 * NM + 2 * n + 1] = den[n][j];
+      }
+  __syncthreads();
+  for (int i = tid; i < NM * M; i += 128) {
+    const int n = i / M, mm = i % M;
+    float a = 0.f, d = 0.f;
+    for (int w = 0; w < 4; ++w) {
+      a += red[(w * M + mm) * 2 * NM + 2 * n];
+      d += red[(w * M + mm) * 2 * NM + 2 * n + 1];
+    }
+    const size_t gi = ((size_t)f * NM + n) * M + mm;
+    const float gnew = g[gi] * sqrtf(a / fmaxf(d, eps));
+    if (!finitef(gnew)) atomicOr(flags + FLAG_NONFINITE, 1u);
+    g[gi] = gnew;
+  }
+}
+
 // ----------------------------------------------------------------- launchers
 
 // Dispatch on the register bound of N (4, 8 or 16) as NM_.
@@ -467,10 +571,36 @@ cudaError_t launch_power_stats(const dfmnmf_ctx* c, cudaStream_t s, int fb, int 
 
 cudaError_t launch_stats(const dfmnmf_ctx* c, cudaStream_t s) { return launch_pstats_impl<false, false>(c, s, 0, c->F); }
 
+
 // Four stages while they fit in 64 KB of shared memory (several CTAs per SM),
 // else two.
+template <int NM>
+static cudaError_t launch_gupd4(const dfmnmf_ctx* c, cudaStream_t s) {
+  const int M = c->M;
+  const size_t stage = (size_t)(NM * GT + GT * M) * sizeof(float);
+  const size_t red = (size_t)4 * M * 2 * NM * sizeof(float);
+  const bool deep = 4 * stage + red <= 64 * 1024;
+  const size_t sm = (deep ? 4 : 2) * stage + red;
+  auto k4 = deep ? k_gupd4<NM, 4> : k_gupd4<NM, 2>;
+  if (sm > 48 * 1024) cudaFuncSetAttribute(k4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k4<<<c->F, 128, sm, s>>>(c->lam, c->P, c->g, c->F, c->T, c->Tp, M, c->N, c->eps, c->flags);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gupd(const dfmnmf_ctx* c, cudaStream_t s) {
   const int M = c->M, N = c->N;
+  if (M >= 4 && M <= 64 && (M & (M - 1)) == 0 && N <= 8) {  // quads per frame a power of two (warp shuffles)
+    switch (N) {
+      case 1: return launch_gupd4<1>(c, s);
+      case 2: return launch_gupd4<2>(c, s);
+      case 3: return launch_gupd4<3>(c, s);
+      case 4: return launch_gupd4<4>(c, s);
+      case 5: return launch_gupd4<5>(c, s);
+      case 6: return launch_gupd4<6>(c, s);
+      case 7: return launch_gupd4<7>(c, s);
+      default: return launch_gupd4<8>(c, s);
+    }
+  }
   const int S = 256 / M;
   const size_t stage = (size_t)(N * GT + GT * M) * sizeof(float);
   const size_t red = (size_t)S * M * 2 * N * sizeof(float);
