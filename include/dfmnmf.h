@@ -186,6 +186,27 @@ int dfmnmf_kernel_times(dfmnmf_ctx* ctx, int n_iter, double* avg_ms, const char*
 void dfmnmf_destroy(dfmnmf_ctx* ctx);
 
 /*
+ * Gradient of the cost of Eq. (12) at the context's current state (no
+ * iteration is taken, nothing of the state changes; the intermediate
+ * buffers V, P and lambda are overwritten).  With y = sum_n lambda g and
+ * G = 1/y - P/y^2 (zero where the floor of Sec. IV-A holds):
+ *   dW[n][f][b] = sum_t H[n][b][t] sum_m g[f][n][m] G[f][t][m]   float32 [N][F][B]
+ *   dH[n][b][t] = sum_f W[n][f][b] sum_m g[f][n][m] G[f][t][m]   float32 [N][B][T]
+ *   dg[f][n][m] = sum_t lambda[n][f][t] G[f][t][m]                float32 [F][N][M]
+ *   dQ          = dL/dRe Q + i dL/dIm Q, block by block,          complex128 like Q:
+ *                 dQ[mu][j] = 2 T ((Q V_mu)[mu][j] - conj(Q^{-1})[j][mu])
+ * (the first three are the differences denominator - numerator of the
+ * multiplicative rules, Eqs. 8-10).  Computed from float-float covariances
+ * and compensated projections whatever the precision of the context; the
+ * inverse and the Q gradient in FP64.  Any output may be NULL; host or
+ * device memory.  *nll_host (may be NULL) receives Eq. (12), and then the
+ * call synchronises `stream` and reports DFMNMF_ENUMERIC as dfmnmf_loglik
+ * does.  The gradient through unrolled iterations is not provided.
+ */
+int dfmnmf_cost_gradient(dfmnmf_ctx* ctx, void* dQ, float* dW, float* dH, float* dg, double* nll_host,
+                         void* stream);
+
+/*
  * Launch shapes picked by measurement (no counterpart in the paper; a GPU
  * concern): the per-frequency kernels of an iteration run either band-wide
  * on one graph branch or as two halves of the band on two branches

@@ -308,6 +308,47 @@ def neg_loglik(x, mics, st: State, eps: float = EPS) -> float:
     return data - T * logdet
 
 
+def cost_gradient(x, mics, st: State, eps: float = EPS):
+    """Gradient of Eq. (12) at the state st (the cost itself, no iteration).
+
+    With y = sum_n lambda g (Eq. 2) and yhat = max(y, eps), the data term
+    sum (P / yhat + ln yhat) has dL/dy = 1/y - P/y^2 =: G where y > eps and 0
+    where the floor holds.  By the chain rule through lambda = W H:
+      dL/dg[f,n,m]   = sum_t lambda[n,f,t] G[f,t,m]
+      dL/dlam[n,f,t] = sum_m g[f,n,m] G[f,t,m]
+      dL/dW[n,f,b]   = sum_t dL/dlam[n,f,t] H[n,b,t]
+      dL/dH[n,b,t]   = sum_f W[n,f,b] dL/dlam[n,f,t]
+    For a block Q_fk with z = Q_fk x_ftk (P = |z|^2) and the log-determinant
+    term -T ln|det Q_fk|^2, the derivative with respect to the real and
+    imaginary parts of each entry, packed as dL/dRe + i dL/dIm (twice the
+    derivative with respect to the conjugate entry), is
+      dQ[mu, j] = 2 sum_t z_mu conj(x_j) / yhat_mu - 2 T conj(Q^{-1})[j, mu].
+    Returns (dQ list of K arrays [F][M_k][M_k] complex128, dW, dH, dg)."""
+    x = np.asarray(x, dtype=np.complex128)
+    F, T, M = x.shape
+    lam = source_psd(st.W, st.H)
+    F_, N, M_ = st.g.shape
+    y = np.zeros((F, T, M))
+    for n in range(N):
+        y += lam[n][:, :, None] * st.g[:, n, None, :]
+    P = projected_power(x, st.Q, mics)
+    G = np.where(y > eps, 1.0 / np.where(y > eps, y, 1.0) - P / np.where(y > eps, y, 1.0) ** 2, 0.0)
+    dg = np.einsum("nft,ftm->fnm", lam, G)
+    dlam = np.einsum("fnm,ftm->nft", st.g, G)
+    dW = np.einsum("nft,nbt->nfb", dlam, st.H)
+    dH = np.einsum("nfb,nft->nbt", st.W, dlam)
+    yhat = np.maximum(y, eps)
+    off = mic_offsets(mics)
+    dQ = []
+    for k, mk in enumerate(mics):
+        xk = x[:, :, off[k]:off[k] + mk]
+        z = np.einsum("fuv,ftv->ftu", st.Q[k], xk)
+        data = 2.0 * np.einsum("ftu,ftj->fuj", z / yhat[:, :, off[k]:off[k] + mk], np.conj(xk))
+        inv = np.linalg.inv(st.Q[k])
+        dQ.append(data - 2.0 * T * np.conj(np.swapaxes(inv, -1, -2)))
+    return dQ, dW, dH, dg
+
+
 def wiener_filter(x, mics, st: State, eps: float = EPS) -> np.ndarray:
     """Source images per subarray: c_n = Q_fk^{-1} diag(lambda_n g_n / yhat) Q_fk x_ftk.
 

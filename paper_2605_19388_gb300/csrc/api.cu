@@ -57,7 +57,7 @@ void free_ctx(dfmnmf_ctx* c) {
   if (c->fork_ev) cudaEventDestroy(c->fork_ev);
   if (c->join_ev) cudaEventDestroy(c->join_ev);
   void* ptrs[] = {c->x, c->Q64, c->Q32, c->Qinv32, c->V, c->Vdd, c->W, c->H, c->g, c->lam,
-                  c->P, c->A, c->D, c->red, c->nll_dev, c->flags, c->nmf_part, c->nmf_ticket, c->Rhi, c->Rlo, c->wy_hi, c->wy_lo};
+                  c->P, c->A, c->D, c->red, c->nll_dev, c->flags, c->nmf_part, c->nmf_ticket, c->Rhi, c->Rlo, c->wy_hi, c->wy_lo, c->gQ, c->gW, c->gH, c->gg};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -413,6 +413,35 @@ int dfmnmf_kernel_times(dfmnmf_ctx* c, int n_iter, double* avg_ms, const char** 
   if (names)
     for (int i = 0; i < n; ++i) names[i] = L[i].name;
   return rc;
+}
+
+int dfmnmf_cost_gradient(dfmnmf_ctx* c, void* dQ, float* dW, float* dH, float* dg, double* nll_host, void* stream) {
+  if (!c) return fail(DFMNMF_EINVAL, "null context");
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = as_stream(stream);
+  int r = 0;
+  if (!c->gQ && ((r = dalloc(&c->gQ, nQ(c), "dQ")) || (r = dalloc(&c->gW, nW(c), "dW")) ||
+                 (r = dalloc(&c->gH, nH(c), "dH")) || (r = dalloc(&c->gg, ng(c), "dg")))) {
+    cudaFree(c->gQ); cudaFree(c->gW); cudaFree(c->gH); cudaFree(c->gg);
+    c->gQ = nullptr; c->gW = c->gH = c->gg = nullptr;
+    return r;
+  }
+  // every statistic from the current state: lambda, float-float V, compensated P with A and D
+  CK(dfm::launch_lambda(c, s));
+  CK(dfm::launch_cov(c, s, 0, c->F));
+  CK(dfm::launch_power_stats_comp(c, s));
+  CK(dfm::launch_wupd(c, s, c->gW));
+  CK(dfm::launch_hupd(c, s, c->gH));
+  CK(dfm::launch_gupd(c, s, c->gg));
+  CK(dfm::launch_qgrad(c, c->gQ, s));
+  bool host = false;
+  if (dQ) { CK(cudaMemcpyAsync(dQ, c->gQ, nQ(c) * sizeof(double2), cudaMemcpyDefault, s)); host |= is_host_ptr(dQ); }
+  if (dW) { CK(cudaMemcpyAsync(dW, c->gW, nW(c) * sizeof(float), cudaMemcpyDefault, s)); host |= is_host_ptr(dW); }
+  if (dH) { CK(copy_H(c, dH, c->gH, false, s)); host |= is_host_ptr(dH); }
+  if (dg) { CK(cudaMemcpyAsync(dg, c->gg, ng(c) * sizeof(float), cudaMemcpyDefault, s)); host |= is_host_ptr(dg); }
+  if (nll_host) return dfmnmf_loglik(c, nll_host, stream);  // synchronises
+  if (host) CK(cudaStreamSynchronize(s));
+  return DFMNMF_OK;
 }
 
 int dfmnmf_autotune(dfmnmf_ctx* c, int iters_per_trial, int* branches, int* nmf_ctas, void* stream) {

@@ -36,6 +36,9 @@ struct dfmnmf_ctx {
   float* nmf_part;       // split-reduction partials of the NMF updates
   unsigned* nmf_ticket;  // per-tile tickets of the split reductions (self-resetting)
   double* nll_dev; // 1 double
+  // gradient of Eq. (12) (dfmnmf_cost_gradient), allocated on first use
+  double2* gQ;
+  float *gW, *gH, *gg;
   unsigned* flags; // dfm::FLAG_COUNT words
   // tensor-core form: x x^H split in two bfloat16 parts, [F * 16 K][Tr] each, and their TMA descriptors
   void* Rhi;
@@ -69,10 +72,15 @@ cudaError_t tc_make_maps(dfmnmf_ctx* c);
 bool tc_supported(int MK, int K);
 cudaError_t launch_ip(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc);
 cudaError_t launch_power_stats(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc);  // P + A/D (current lambda)
-cudaError_t launch_wupd(const dfmnmf_ctx* c, cudaStream_t s);         // Eq. 8
+// The NMF updates take `grad`: NULL updates the factor (Eq. 8, 9 or 10);
+// otherwise the gradient of Eq. (12) with respect to it (den - num of the
+// rule) is written there and the factor is left unchanged.
+cudaError_t launch_wupd(const dfmnmf_ctx* c, cudaStream_t s, float* grad = nullptr);  // Eq. 8
 cudaError_t launch_stats(const dfmnmf_ctx* c, cudaStream_t s);        // A/D from stored P
-cudaError_t launch_hupd(const dfmnmf_ctx* c, cudaStream_t s);         // Eq. 9
-cudaError_t launch_gupd(const dfmnmf_ctx* c, cudaStream_t s);         // Eq. 10
+cudaError_t launch_hupd(const dfmnmf_ctx* c, cudaStream_t s, float* grad = nullptr);  // Eq. 9
+cudaError_t launch_gupd(const dfmnmf_ctx* c, cudaStream_t s, float* grad = nullptr);  // Eq. 10
+cudaError_t launch_power_stats_comp(const dfmnmf_ctx* c, cudaStream_t s);  // P (compensated) + A/D, band-wide
+cudaError_t launch_qgrad(const dfmnmf_ctx* c, double2* dQ, cudaStream_t s);  // d Eq. 12 / d Q from V and Q
 cudaError_t launch_loglik(const dfmnmf_ctx* c, cudaStream_t s);       // Eq. 12 -> c->nll_dev
 cudaError_t launch_qinv(const dfmnmf_ctx* c, cudaStream_t s);
 cudaError_t launch_separate(const dfmnmf_ctx* c, float2* out, cudaStream_t s);

@@ -441,6 +441,85 @@ __global__ void k_qinv(const double2* __restrict__ Q64, float2* __restrict__ Qin
       Qinv[(size_t)blk * MK * MK + r * MK + c] = make_float2((float)ar[r][MK + c], (float)ai[r][MK + c]);
 }
 
+// Gradient of Eq. (12) with respect to one block Q_fk, packed as
+// dL/dRe + i dL/dIm:  dQ[mu][j] = 2 T ((Q V_mu)[mu][j] - conj(Q^{-1})[j][mu]),
+// where (Q V_mu)[mu][:] = (1/T) sum_t z_mu conj(x) / yhat_mu is the data term
+// of the cost (Eq. 13's V) and -T ln|det Q|^2 contributes -conj(Q^{-1})^T.
+// FP64, one thread per block (Gauss-Jordan inverse with partial pivoting).
+template <int MK>
+__global__ void k_qgrad(const double2* __restrict__ Q64, const double2* __restrict__ V, double2* __restrict__ dQ,
+                        int nblocks, int T, unsigned* __restrict__ flags) {
+  const int blk = blockIdx.x * blockDim.x + threadIdx.x;
+  if (blk >= nblocks) return;
+  constexpr int E = MK * MK;
+  double ar[MK][2 * MK], ai[MK][2 * MK];
+  for (int r = 0; r < MK; ++r)
+    for (int c = 0; c < MK; ++c) {
+      const double2 v = Q64[(size_t)blk * E + r * MK + c];
+      ar[r][c] = v.x;
+      ai[r][c] = v.y;
+      ar[r][MK + c] = (r == c) ? 1.0 : 0.0;
+      ai[r][MK + c] = 0.0;
+    }
+  bool ok = true;
+  for (int c = 0; c < MK; ++c) {
+    int p = c;
+    double best = ar[c][c] * ar[c][c] + ai[c][c] * ai[c][c];
+    for (int r = c + 1; r < MK; ++r) {
+      const double m = ar[r][c] * ar[r][c] + ai[r][c] * ai[r][c];
+      if (m > best) { best = m; p = r; }
+    }
+    if (!(best > 0.0)) { ok = false; best = 1.0; }
+    if (p != c)
+      for (int q = 0; q < 2 * MK; ++q) {
+        double t = ar[c][q]; ar[c][q] = ar[p][q]; ar[p][q] = t;
+        t = ai[c][q]; ai[c][q] = ai[p][q]; ai[p][q] = t;
+      }
+    const double ir = ar[c][c] / best, ii = -ai[c][c] / best;
+    for (int q = 0; q < 2 * MK; ++q) {
+      const double xr = ar[c][q], xi = ai[c][q];
+      ar[c][q] = xr * ir - xi * ii;
+      ai[c][q] = xr * ii + xi * ir;
+    }
+    for (int r = 0; r < MK; ++r) {
+      if (r == c) continue;
+      const double mr = ar[r][c], mi = ai[r][c];
+      for (int q = 0; q < 2 * MK; ++q) {
+        ar[r][q] -= mr * ar[c][q] - mi * ai[c][q];
+        ai[r][q] -= mr * ai[c][q] + mi * ar[c][q];
+      }
+    }
+  }
+  if (!ok) atomicOr(flags + FLAG_NONFINITE, 1u);
+  const double t2 = 2.0 * (double)T;
+  for (int mu = 0; mu < MK; ++mu) {
+    const double2* Vm = V + ((size_t)blk * MK + mu) * E;
+    for (int j = 0; j < MK; ++j) {
+      double sr = 0.0, si = 0.0;
+      for (int l = 0; l < MK; ++l) {
+        const double2 q = Q64[(size_t)blk * E + mu * MK + l], v = Vm[l * MK + j];
+        sr += q.x * v.x - q.y * v.y;
+        si += q.x * v.y + q.y * v.x;
+      }
+      // conj(Q^{-1})[j][mu]
+      const double gr = t2 * (sr - ar[j][MK + mu]), gi = t2 * (si + ai[j][MK + mu]);
+      dQ[(size_t)blk * E + mu * MK + j] = make_double2(gr, gi);
+    }
+  }
+}
+
+cudaError_t launch_qgrad(const dfmnmf_ctx* c, double2* dQ, cudaStream_t s) {
+  const int nblocks = c->F * c->K;
+  if (c->MK == 16) {
+    k_qgrad<16><<<(nblocks + 63) / 64, 64, 0, s>>>(c->Q64, c->V, dQ, nblocks, c->T, c->flags);
+    return cudaGetLastError();
+  }
+  DFM_MK_DISPATCH(c->MK, {
+    k_qgrad<MK_><<<(nblocks + 127) / 128, 128, 0, s>>>(c->Q64, c->V, dQ, nblocks, c->T, c->flags);
+  });
+  return cudaGetLastError();
+}
+
 __global__ void k_q32(const double2* __restrict__ Q64, float2* __restrict__ Q32, size_t n) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) Q32[i] = make_float2((float)Q64[i].x, (float)Q64[i].y);

@@ -331,7 +331,7 @@ constexpr int GT = 128;
 template <int NM, int NST>
 __global__ void __launch_bounds__(256) k_gupd(const float* __restrict__ lam, const float* __restrict__ P,
                                               float* __restrict__ g, int F, int T, int Tp, int M, int N, float eps,
-                                              unsigned* __restrict__ flags) {
+                                              unsigned* __restrict__ flags, float* __restrict__ grad) {
   extern __shared__ __align__(16) float smg[];
   const int f = blockIdx.x, tid = threadIdx.x;
   const int S = blockDim.x / M;            // frame slices
@@ -412,6 +412,10 @@ __global__ void __launch_bounds__(256) k_gupd(const float* __restrict__ lam, con
       d += red[(q * M + mm) * 2 * N + 2 * n + 1];
     }
     const size_t gi = ((size_t)f * N + n) * M + mm;
+    if (grad) {  // gradient of Eq. (12): sum_t lambda (1/yhat - P/yhat^2)
+      grad[gi] = d - a;
+      continue;
+    }
     const float gnew = g[gi] * sqrtf(a / fmaxf(d, eps));
     if (!finitef(gnew)) atomicOr(flags + FLAG_NONFINITE, 1u);
     g[gi] = gnew;
@@ -426,7 +430,7 @@ __global__ void __launch_bounds__(256) k_gupd(const float* __restrict__ lam, con
 template <int NM, int NST>
 __global__ void __launch_bounds__(128) k_gupd4(const float* __restrict__ lam, const float* __restrict__ P,
                                                float* __restrict__ g, int F, int T, int Tp, int M, int N, float eps,
-                                               unsigned* __restrict__ flags) {
+                                               unsigned* __restrict__ flags, float* __restrict__ grad) {
   extern __shared__ __align__(16) float smq[];
   const int f = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int Q = M / 4, S = 128 / Q;  // quads per frame, frame slots (128 threads)
@@ -516,6 +520,10 @@ __global__ void __launch_bounds__(128) k_gupd4(const float* __restrict__ lam, co
       d += red[(w * M + mm) * 2 * NM + 2 * n + 1];
     }
     const size_t gi = ((size_t)f * NM + n) * M + mm;
+    if (grad) {  // gradient of Eq. (12)
+      grad[gi] = d - a;
+      continue;
+    }
     const float gnew = g[gi] * sqrtf(a / fmaxf(d, eps));
     if (!finitef(gnew)) atomicOr(flags + FLAG_NONFINITE, 1u);
     g[gi] = gnew;
@@ -569,13 +577,17 @@ cudaError_t launch_power_stats(const dfmnmf_ctx* c, cudaStream_t s, int fb, int 
                                      : launch_pstats_impl<true, false>(c, s, fb, fc);
 }
 
+cudaError_t launch_power_stats_comp(const dfmnmf_ctx* c, cudaStream_t s) {
+  return launch_pstats_impl<true, true>(c, s, 0, c->F);
+}
+
 cudaError_t launch_stats(const dfmnmf_ctx* c, cudaStream_t s) { return launch_pstats_impl<false, false>(c, s, 0, c->F); }
 
 
 // Four stages while they fit in 64 KB of shared memory (several CTAs per SM),
 // else two.
 template <int NM>
-static cudaError_t launch_gupd4(const dfmnmf_ctx* c, cudaStream_t s) {
+static cudaError_t launch_gupd4(const dfmnmf_ctx* c, cudaStream_t s, float* grad) {
   const int M = c->M;
   const size_t stage = (size_t)(NM * GT + GT * M) * sizeof(float);
   const size_t red = (size_t)4 * M * 2 * NM * sizeof(float);
@@ -583,22 +595,22 @@ static cudaError_t launch_gupd4(const dfmnmf_ctx* c, cudaStream_t s) {
   const size_t sm = (deep ? 4 : 2) * stage + red;
   auto k4 = deep ? k_gupd4<NM, 4> : k_gupd4<NM, 2>;
   if (sm > 48 * 1024) cudaFuncSetAttribute(k4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k4<<<c->F, 128, sm, s>>>(c->lam, c->P, c->g, c->F, c->T, c->Tp, M, c->N, c->eps, c->flags);
+  k4<<<c->F, 128, sm, s>>>(c->lam, c->P, c->g, c->F, c->T, c->Tp, M, c->N, c->eps, c->flags, grad);
   return cudaGetLastError();
 }
 
-cudaError_t launch_gupd(const dfmnmf_ctx* c, cudaStream_t s) {
+cudaError_t launch_gupd(const dfmnmf_ctx* c, cudaStream_t s, float* grad) {
   const int M = c->M, N = c->N;
   if (M >= 4 && M <= 64 && (M & (M - 1)) == 0 && N <= 8) {  // quads per frame a power of two (warp shuffles)
     switch (N) {
-      case 1: return launch_gupd4<1>(c, s);
-      case 2: return launch_gupd4<2>(c, s);
-      case 3: return launch_gupd4<3>(c, s);
-      case 4: return launch_gupd4<4>(c, s);
-      case 5: return launch_gupd4<5>(c, s);
-      case 6: return launch_gupd4<6>(c, s);
-      case 7: return launch_gupd4<7>(c, s);
-      default: return launch_gupd4<8>(c, s);
+      case 1: return launch_gupd4<1>(c, s, grad);
+      case 2: return launch_gupd4<2>(c, s, grad);
+      case 3: return launch_gupd4<3>(c, s, grad);
+      case 4: return launch_gupd4<4>(c, s, grad);
+      case 5: return launch_gupd4<5>(c, s, grad);
+      case 6: return launch_gupd4<6>(c, s, grad);
+      case 7: return launch_gupd4<7>(c, s, grad);
+      default: return launch_gupd4<8>(c, s, grad);
     }
   }
   const int S = 256 / M;
@@ -610,7 +622,7 @@ cudaError_t launch_gupd(const dfmnmf_ctx* c, cudaStream_t s) {
   {                                                                                                              \
     if (sm > 48 * 1024)                                                                                          \
       cudaFuncSetAttribute(k_gupd<NMV, NSTV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);             \
-    k_gupd<NMV, NSTV><<<c->F, 256, sm, s>>>(c->lam, c->P, c->g, c->F, c->T, c->Tp, M, N, c->eps, c->flags);      \
+    k_gupd<NMV, NSTV><<<c->F, 256, sm, s>>>(c->lam, c->P, c->g, c->F, c->T, c->Tp, M, N, c->eps, c->flags, grad); \
   }
 #define DFM_GUPD(NMV)           \
   if (deep) DFM_GUPD_K(NMV, 4)  \

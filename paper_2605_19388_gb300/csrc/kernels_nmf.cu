@@ -64,7 +64,8 @@ __global__ void __launch_bounds__(256) k_wupd(const float* __restrict__ A, const
                                               const float* __restrict__ H, float* __restrict__ W,
                                               int F, int T, int Tp, int B, float eps,
                                               unsigned* __restrict__ flags, int S, int cps,
-                                              float* __restrict__ part, unsigned* __restrict__ ticket) {
+                                              float* __restrict__ part, unsigned* __restrict__ ticket,
+                                              float* __restrict__ grad) {
   constexpr int TS = 20;  // padded row of the transposed tiles: conflict-free stores, 16-byte rows
   constexpr int STAGE = 3 * KCH * TS;
   __shared__ __align__(16) float stg[STAGE];
@@ -141,7 +142,9 @@ __global__ void __launch_bounds__(256) k_wupd(const float* __restrict__ A, const
     }
     if (!split_fixup(num, den, S, split, (n * gridDim.x + blockIdx.x) * nb + bt, part, ticket)) return;
     const int f = f0 + fi, b = b0 + bi;
-    if (f < F && b < B) {
+    if (grad) {  // gradient of Eq. (12): sum_t H (D - A)
+      if (f < F && b < B) grad[((size_t)n * F + f) * B + b] = den - num;
+    } else if (f < F && b < B) {
       float* wp = W + ((size_t)n * F + f) * B + b;
       const float wn = *wp * sqrtf(num / fmaxf(den, eps));
       if (!finitef(wn)) atomicOr(flags + FLAG_NONFINITE, 1u);
@@ -159,7 +162,8 @@ __global__ void __launch_bounds__(256) k_hupd(const float* __restrict__ A, const
                                               const float* __restrict__ W, float* __restrict__ H,
                                               int F, int T, int Tp, int B, float eps,
                                               unsigned* __restrict__ flags, int S, int cps,
-                                              float* __restrict__ part, unsigned* __restrict__ ticket) {
+                                              float* __restrict__ part, unsigned* __restrict__ ticket,
+                                              float* __restrict__ grad) {
   constexpr int STAGE = 3 * KCH * TILE;
   __shared__ __align__(16) float stg[2 * STAGE];
   __shared__ float red[NWARP * 32 * RS];
@@ -243,7 +247,9 @@ __global__ void __launch_bounds__(256) k_hupd(const float* __restrict__ A, const
     }
     if (!split_fixup(num, den, S, split, (n * gridDim.x + blockIdx.x) * nb + bt, part, ticket)) return;
     const int b = b0 + bi, t = t0 + ti;
-    if (b < B && t < T) {
+    if (grad) {  // gradient of Eq. (12): sum_f W (D - A)
+      if (b < B && t < T) grad[((size_t)n * B + b) * Tp + t] = den - num;
+    } else if (b < B && t < T) {
       float* hp = H + ((size_t)n * B + b) * Tp + t;
       const float hn = *hp * sqrtf(num / fmaxf(den, eps));
       if (!finitef(hn)) atomicOr(flags + FLAG_NONFINITE, 1u);
@@ -272,25 +278,25 @@ size_t nmf_scratch_floats(const dfmnmf_ctx* c) {
 }
 size_t nmf_ticket_count(const dfmnmf_ctx* c) { return nmf_scratch_floats(c) / (NMF_MAX_SPLIT * 512); }
 
-cudaError_t launch_wupd(const dfmnmf_ctx* c, cudaStream_t s) {
+cudaError_t launch_wupd(const dfmnmf_ctx* c, cudaStream_t s, float* grad) {
   const int nb = (c->B + TILE - 1) / TILE;
   const int tiles = ((c->F + TILE - 1) / TILE) * c->N * nb;
   int S, cps;
   split_plan(c, tiles, (c->T + KCH - 1) / KCH, &S, &cps);
   dim3 grid((c->F + TILE - 1) / TILE, c->N, nb * S);
   k_wupd<<<grid, 256, 0, s>>>(c->A, c->D, c->H, c->W, c->F, c->T, c->Tp, c->B, c->eps, c->flags, S, cps,
-                              c->nmf_part, c->nmf_ticket);
+                              c->nmf_part, c->nmf_ticket, grad);
   return cudaGetLastError();
 }
 
-cudaError_t launch_hupd(const dfmnmf_ctx* c, cudaStream_t s) {
+cudaError_t launch_hupd(const dfmnmf_ctx* c, cudaStream_t s, float* grad) {
   const int nb = (c->B + TILE - 1) / TILE;
   const int tiles = ((c->T + TILE - 1) / TILE) * c->N * nb;
   int S, cps;
   split_plan(c, tiles, (c->F + KCH - 1) / KCH, &S, &cps);
   dim3 grid((c->T + TILE - 1) / TILE, c->N, nb * S);
   k_hupd<<<grid, 256, 0, s>>>(c->A, c->D, c->W, c->H, c->F, c->T, c->Tp, c->B, c->eps, c->flags, S, cps,
-                              c->nmf_part, c->nmf_ticket);
+                              c->nmf_part, c->nmf_ticket, grad);
   return cudaGetLastError();
 }
 

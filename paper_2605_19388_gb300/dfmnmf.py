@@ -29,6 +29,7 @@ EXPORTED = ("dfmnmf_init", "dfmnmf_set_observation", "dfmnmf_iterate", "dfmnmf_r
             "dfmnmf_loglik", "dfmnmf_separate", "dfmnmf_get_params", "dfmnmf_set_params",
             "dfmnmf_get_buffer", "dfmnmf_launches_per_iteration", "dfmnmf_kernel_times", "dfmnmf_destroy",
             "dfmnmf_last_error", "dfmnmf_version", "dfmnmf_loglik_noalloc", "dfmnmf_autotune",
+            "dfmnmf_cost_gradient",
             "dfmnmf_batch_create", "dfmnmf_batch_iterate", "dfmnmf_batch_destroy")
 
 
@@ -75,6 +76,7 @@ def load_library(path: Optional[str] = None):
         "dfmnmf_version": (ci, []),
         "dfmnmf_loglik_noalloc": (ci, [ctypes.POINTER(dfmnmf_desc), vp, vp, vp, vp, vp, ctypes.POINTER(cd), vp]),
         "dfmnmf_autotune": (ci, [vp, ci, ctypes.POINTER(ci), ctypes.POINTER(ci), vp]),
+        "dfmnmf_cost_gradient": (ci, [vp, vp, vp, vp, vp, ctypes.POINTER(cd), vp]),
         "dfmnmf_batch_create": (ci, [ctypes.POINTER(vp), ctypes.POINTER(vp), ci]),
         "dfmnmf_batch_iterate": (ci, [vp, ci, vp]),
         "dfmnmf_batch_destroy": (None, [vp]),
@@ -224,6 +226,16 @@ def dfmnmf_destroy(ctx: Context):
     if ctx.handle is not None and ctx.handle.value:
         load_library().dfmnmf_destroy(ctx.handle)
         ctx.handle = ctypes.c_void_p()
+
+
+def dfmnmf_cost_gradient(ctx: Context, dQ=None, dW=None, dH=None, dg=None, stream=None) -> float:
+    """Gradient of Eq. (12) at the current state into the given arrays (numpy or torch, host or
+    device; None skips one); returns the cost."""
+    v = ctypes.c_double()
+    _check(load_library().dfmnmf_cost_gradient(ctx.handle, _ptr(dQ, _dt("c128")), _ptr(dW, _dt("f32")),
+                                                _ptr(dH, _dt("f32")), _ptr(dg, _dt("f32")), ctypes.byref(v),
+                                                _stream(stream)))
+    return v.value
 
 
 def dfmnmf_autotune(ctx: Context, iters_per_trial: int = 5, stream=None):

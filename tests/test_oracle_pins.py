@@ -348,3 +348,46 @@ def test_block_joint_diagonalisability_theorem():
             bl.append(z @ np.conj(z).T + 0.1 * np.eye(m))
         Rg.append(blkdiag(bl))
     assert commutators(Rg) > 1e-3
+
+
+def test_cost_gradient_matches_central_differences():
+    """The analytic gradient of Eq. (12) against FP64 central differences of the
+    cost itself, entry by entry, on a tiny random state (no floor binding)."""
+    p = synth.make_problem(3, 20, (2, 2), 2, 3, seed=71)
+    x = p.x.astype(np.complex128)
+    st = O.state_from_arrays(synth.random_blocks(p.F, p.mics, seed=72), p.W0, p.H0, p.g0, p.mics)
+    st = O.mm_iteration(x, p.mics, st)  # a generic, non-stationary state
+    dQ, dW, dH, dg = O.cost_gradient(x, p.mics, st)
+    rng = np.random.default_rng(73)
+    h = 1e-6
+
+    def cost(Q, W, H, g):
+        return O.neg_loglik(x, p.mics, O.State(Q=Q, W=W, H=H, g=g))
+
+    def check(arr_name, grad, cplx):
+        base = getattr(st, arr_name)
+        for _ in range(6):
+            idx = tuple(rng.integers(0, s_) for s_ in base.shape)
+            for part in ((1.0,) if not cplx else (1.0, 1j)):
+                plus = base.copy(); minus = base.copy()
+                plus[idx] += h * part * max(abs(base[idx]), 1.0)
+                minus[idx] -= h * part * max(abs(base[idx]), 1.0)
+                args = {"Q": st.Q, "W": st.W, "H": st.H, "g": st.g}
+                fd = (cost(**{**args, arr_name: plus}) - cost(**{**args, arr_name: minus})) / (2 * h * max(abs(base[idx]), 1.0))
+                an = grad[idx].real if part == 1.0 else grad[idx].imag
+                assert abs(fd - an) <= 1e-5 * max(abs(an), 1.0), (arr_name, idx, part, fd, an)
+
+    check("W", dW, False)
+    check("H", dH, False)
+    check("g", dg, False)
+    for k in range(len(p.mics)):
+        base = st.Q[k]
+        for _ in range(6):
+            idx = tuple(rng.integers(0, s_) for s_ in base.shape)
+            for part in (1.0, 1j):
+                Qp = [q.copy() for q in st.Q]; Qm = [q.copy() for q in st.Q]
+                Qp[k][idx] += h * part
+                Qm[k][idx] -= h * part
+                fd = (cost(Qp, st.W, st.H, st.g) - cost(Qm, st.W, st.H, st.g)) / (2 * h)
+                an = dQ[k][idx].real if part == 1.0 else dQ[k][idx].imag
+                assert abs(fd - an) <= 1e-5 * max(abs(an), 1.0), ("Q", k, idx, part, fd, an)
