@@ -82,6 +82,7 @@ cudaError_t launch_gupd(const dfmnmf_ctx* c, cudaStream_t s, float* grad = nullp
 cudaError_t launch_power_stats_comp(const dfmnmf_ctx* c, cudaStream_t s);  // P (compensated) + A/D, band-wide
 cudaError_t launch_qgrad(const dfmnmf_ctx* c, double2* dQ, cudaStream_t s);  // d Eq. 12 / d Q from V and Q
 cudaError_t launch_loglik(const dfmnmf_ctx* c, cudaStream_t s);       // Eq. 12 -> c->nll_dev
+cudaError_t launch_logdet(const dfmnmf_ctx* c, double* out, cudaStream_t s);  // ln|det Q_fk|^2 per block
 cudaError_t launch_qinv(const dfmnmf_ctx* c, cudaStream_t s);
 cudaError_t launch_separate(const dfmnmf_ctx* c, float2* out, cudaStream_t s);
 cudaError_t launch_q_convert(const dfmnmf_ctx* c, cudaStream_t s);    // Q64 -> Q32

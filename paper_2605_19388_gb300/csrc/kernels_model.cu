@@ -532,12 +532,6 @@ __global__ void __launch_bounds__(128) k_gupd4(const float* __restrict__ lam, co
 
 // ----------------------------------------------------------------- launchers
 
-// Dispatch on the register bound of N (4, 8 or 16) as NM_.
-#define DFM_NM_DISPATCH(NV, ...)                                  \
-  if ((NV) <= 4) { constexpr int NM_ = 4; __VA_ARGS__; }          \
-  else if ((NV) <= 8) { constexpr int NM_ = 8; __VA_ARGS__; }     \
-  else { constexpr int NM_ = 16; __VA_ARGS__; }
-
 template <int K, int MK, bool COMPUTE_P, bool COMP>
 static cudaError_t launch_pstats_ft(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
   const int tpc = 128;  // one frame per thread: every load of the CTA is in flight at once

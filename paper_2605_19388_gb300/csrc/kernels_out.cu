@@ -5,8 +5,6 @@
 
 namespace dfm {
 
-cudaError_t launch_logdet(const dfmnmf_ctx* c, double* out, cudaStream_t s);
-
 constexpr int NMAXO = 16;
 
 // Data term of Eq. (12): sum_{t,m} (P/yhat + ln yhat) for one (f, 128-frame

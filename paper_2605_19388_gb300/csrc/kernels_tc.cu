@@ -154,8 +154,8 @@ __global__ void __launch_bounds__(128) k_rprep(const float2* __restrict__ x, __n
 // (Eq. 2 with the floor of Sec. IV-A), split into two bfloat16 parts and
 // stored as rows (f, m) of Tr frames, zero beyond T: the B operand of the
 // contraction, read by TMA in the same 128-byte swizzled tiles as R.  Each
-// thread forms four adjacent frames of one frequency for every microphone
-// (float4 lambda loads, g[f] broadcast from shared memory, 8-byte stores
+// thread forms two adjacent frames of one frequency for every microphone
+// (float2 lambda loads, g[f] broadcast from shared memory, 4-byte stores
 // coalesced along t).  NM is N itself for N <= 8 and 16 (guarded) above.
 template <int NM>
 __global__ void __launch_bounds__(128) k_wprep(const float* __restrict__ lam, const float* __restrict__ g,
@@ -165,39 +165,32 @@ __global__ void __launch_bounds__(128) k_wprep(const float* __restrict__ lam, co
   const int f = fb + blockIdx.y;
   for (int i = threadIdx.x; i < N * M; i += blockDim.x) gw[i] = g[(size_t)f * N * M + i];
   __syncthreads();
-  const int t = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int t = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   if (t >= Tr) return;
-  float4 lv[NM];
+  float2 lv[NM];
 #pragma unroll
   for (int n = 0; n < NM; ++n) {
-    lv[n] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if ((NM <= 8 || n < N) && t < Tp) lv[n] = *reinterpret_cast<const float4*>(lam + ((size_t)n * F + f) * Tp + t);
+    lv[n] = make_float2(0.f, 0.f);
+    if ((NM <= 8 || n < N) && t < Tp) lv[n] = *reinterpret_cast<const float2*>(lam + ((size_t)n * F + f) * Tp + t);
   }
-  const bool v0 = t < T, v1 = t + 1 < T, v2 = t + 2 < T, v3 = t + 3 < T;
+  const bool v0 = t < T, v1 = t + 1 < T;
   for (int m = 0; m < M; ++m) {
-    float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 y = make_float2(0.f, 0.f);
 #pragma unroll
     for (int n = 0; n < NM; ++n)
       if (NM <= 8 || n < N) {
         const float gv = gw[n * M + m];
         y.x = fmaf(lv[n].x, gv, y.x);
         y.y = fmaf(lv[n].y, gv, y.y);
-        y.z = fmaf(lv[n].z, gv, y.z);
-        y.w = fmaf(lv[n].w, gv, y.w);
       }
     const float w0 = v0 ? fast_rcp(fmaxf(y.x, eps)) : 0.f;
     const float w1 = v1 ? fast_rcp(fmaxf(y.y, eps)) : 0.f;
-    const float w2 = v2 ? fast_rcp(fmaxf(y.z, eps)) : 0.f;
-    const float w3 = v3 ? fast_rcp(fmaxf(y.w, eps)) : 0.f;
-    const __nv_bfloat162 h01 = __floats2bfloat162_rn(w0, w1), h23 = __floats2bfloat162_rn(w2, w3);
-    const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
-    const __nv_bfloat162 l01 = __floats2bfloat162_rn(w0 - f01.x, w1 - f01.y);
-    const __nv_bfloat162 l23 = __floats2bfloat162_rn(w2 - f23.x, w3 - f23.y);
+    const __nv_bfloat162 h = __floats2bfloat162_rn(w0, w1);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(w0 - hf.x, w1 - hf.y);
     const size_t o = ((size_t)f * M + m) * Tr + t;
-    *reinterpret_cast<uint2*>(whi + o) =
-        make_uint2(*reinterpret_cast<const unsigned*>(&h01), *reinterpret_cast<const unsigned*>(&h23));
-    *reinterpret_cast<uint2*>(wlo + o) =
-        make_uint2(*reinterpret_cast<const unsigned*>(&l01), *reinterpret_cast<const unsigned*>(&l23));
+    *reinterpret_cast<__nv_bfloat162*>(whi + o) = h;
+    *reinterpret_cast<__nv_bfloat162*>(wlo + o) = l;
   }
 }
 
@@ -401,7 +394,7 @@ cudaError_t launch_rprep(const dfmnmf_ctx* c, cudaStream_t s) {
 }
 
 cudaError_t launch_wprep(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
-  dim3 grid((c->Tr / 4 + 127) / 128, fc);
+  dim3 grid((c->Tr / 2 + 127) / 128, fc);
   const size_t sm = (size_t)c->N * c->M * sizeof(float);
   auto whi = reinterpret_cast<__nv_bfloat16*>(c->wy_hi);
   auto wlo = reinterpret_cast<__nv_bfloat16*>(c->wy_lo);
