@@ -349,6 +349,42 @@ def cost_gradient(x, mics, st: State, eps: float = EPS):
     return dQ, dW, dH, dg
 
 
+def init_from_images(c, mics: Sequence[int]):
+    """Sec. IV-A initialisation, steps 3, 5 and 6, from given source images.
+
+    c: complex [N][F][T][M] initial images (the paper obtains them by soft
+    masking; that step and the IS-NMF of step 4 are not part of this path).
+      step 3: R_fn = sum_t c_nft c_nft^H / T (M x M);
+              h[n, f, t] = c^H R_fn^{-1} c / M;
+      step 5: for every block k, the generalised eigenvectors w of the pair
+              (R_f,N-2^(k), R_f,N-1^(k)) -- the diagonal blocks of the last two
+              sources' covariances -- which diagonalise both; ascending
+              eigenvalues, each w scaled so that w^H R_f,N-1^(k) w = 1;
+              Q_fk has rows w^H (it plays W_i^(init)(l)H);
+      step 6: g[f, n, o_k + mu] = w_mu^H R_fn^(k) w_mu (ddiag of the
+              diagonalised covariance).
+    Needs N >= 2.  Returns (h [N][F][T] real, Q list of K [F][M_k][M_k], g [F][N][M])."""
+    import scipy.linalg
+    c = np.asarray(c, dtype=np.complex128)
+    N, F, T, M = c.shape
+    R = np.einsum("nftm,nftl->nfml", c, np.conj(c)) / T
+    y = np.linalg.solve(R, np.swapaxes(c, 2, 3))                    # [N][F][M][T] = R^{-1} c
+    h = np.real(np.einsum("nftm,nfmt->nft", np.conj(c), y)) / M
+    off = mic_offsets(mics)
+    Q, g = [], np.zeros((F, N, M))
+    for k, mk in enumerate(mics):
+        sl = slice(off[k], off[k] + mk)
+        Qk = np.zeros((F, mk, mk), dtype=np.complex128)
+        for f in range(F):
+            Ra, Rb = R[N - 2, f][sl, sl], R[N - 1, f][sl, sl]
+            lam, Wv = scipy.linalg.eigh(Ra, Rb)                    # ascending; Wv^H Rb Wv = I
+            Qk[f] = np.conj(Wv.T)
+            for n in range(N):
+                g[f, n, sl] = np.real(np.einsum("am,ab,bm->m", np.conj(Wv), R[n, f][sl, sl], Wv))
+        Q.append(Qk)
+    return h, Q, g
+
+
 def wiener_filter(x, mics, st: State, eps: float = EPS) -> np.ndarray:
     """Source images per subarray: c_n = Q_fk^{-1} diag(lambda_n g_n / yhat) Q_fk x_ftk.
 

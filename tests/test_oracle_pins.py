@@ -391,3 +391,50 @@ def test_cost_gradient_matches_central_differences():
                 fd = (cost(Qp, st.W, st.H, st.g) - cost(Qm, st.W, st.H, st.g)) / (2 * h)
                 an = dQ[k][idx].real if part == 1.0 else dQ[k][idx].imag
                 assert abs(fd - an) <= 1e-5 * max(abs(an), 1.0), ("Q", k, idx, part, fd, an)
+
+
+def _images(F=5, T=60, mics=(4, 4), N=3, seed=90):
+    """Soft-masked stand-in images: c_n = (lambda_n / sum lambda) x with the generator's PSDs."""
+    p = synth.make_problem(F, T, mics, N, 4, seed=seed, with_images=True)
+    lam = O.source_psd(p.W0, p.H0) + 1e-3
+    mask = lam / lam.sum(axis=0, keepdims=True)
+    return p, mask[..., None] * p.x.astype(np.complex128)[None]
+
+
+def test_init_gevd_diagonalises_the_last_two_covariances():
+    """Step 5: Q R_{N-1} Q^H = I and Q R_{N-2} Q^H diagonal per block; step 6 then
+    gives g = 1 for the last source and the generalised eigenvalues (ascending)
+    for the one before."""
+    p, c = _images()
+    h, Q, g = O.init_from_images(c, p.mics)
+    N, F, T, M = c.shape
+    R = np.einsum("nftm,nftl->nfml", c, np.conj(c)) / T
+    off = O.mic_offsets(p.mics)
+    for k, mk in enumerate(p.mics):
+        sl = slice(off[k], off[k] + mk)
+        for f in range(F):
+            A = Q[k][f] @ R[N - 2, f][sl, sl] @ np.conj(Q[k][f].T)
+            Bm = Q[k][f] @ R[N - 1, f][sl, sl] @ np.conj(Q[k][f].T)
+            assert np.abs(Bm - np.eye(mk)).max() < 1e-9
+            assert np.abs(A - np.diag(np.diag(A))).max() < 1e-9 * np.abs(A).max()
+            ev = np.real(np.diag(A))
+            assert np.all(np.diff(ev) >= -1e-12)
+            np.testing.assert_allclose(g[f, N - 1, sl], 1.0, rtol=1e-9)
+            np.testing.assert_allclose(g[f, N - 2, sl], ev, rtol=1e-9)
+
+
+def test_init_spectrogram_invariant_to_channel_mixing_and_single_channel_closed_form():
+    """Step 3: h = c^H R^{-1} c / M does not change when every frame is mixed by
+    the same invertible matrix (R -> A R A^H), and for one channel it is
+    |c|^2 / mean_t |c|^2."""
+    p, c = _images(mics=(4, 4))
+    h, _, _ = O.init_from_images(c, p.mics)
+    rng = np.random.default_rng(91)
+    Amix = rng.standard_normal((8, 8)) + 1j * rng.standard_normal((8, 8))
+    h2, _, _ = O.init_from_images(np.einsum("ab,nftb->nfta", Amix, c), p.mics)
+    # R of a masked 3-source, 8-channel mixture has cond ~1e6: FP64 solves agree to ~1e-8
+    np.testing.assert_allclose(h2, h, rtol=1e-6)
+    c1 = c[..., :1]
+    h1, _, _ = O.init_from_images(c1, (1,))
+    ref = np.abs(c1[..., 0]) ** 2 / np.mean(np.abs(c1[..., 0]) ** 2, axis=2, keepdims=True)
+    np.testing.assert_allclose(h1, ref, rtol=1e-10)
