@@ -240,6 +240,32 @@ int dfmnmf_batch_iterate(dfmnmf_batch* batch, int n_iter, void* stream);
 void dfmnmf_batch_destroy(dfmnmf_batch* batch);
 
 /*
+ * Initialisation from given source images, Sec. IV-A steps 3, 5 and 6 (the
+ * soft masks that produce the images, step 2, and the IS-NMF of step 4 are
+ * left to the caller):
+ *   c_img  complex64 [N][F][T][M] device memory, the images c_nft (the
+ *          layout dfmnmf_separate writes);
+ *   h_out  float32 [N][F][T] device memory, or NULL to skip it:
+ *          h[n][f][t] = c_nft^H R_fn^{-1} c_nft / M with
+ *          R_fn = sum_t c_nft c_nft^H / T (step 3);
+ *   the context's Q becomes, block by block, the generalised eigenvectors w
+ *   of the pair (R_f,N-2^(k), R_f,N-1^(k)) of the last two sources'
+ *   diagonal blocks -- ascending eigenvalues, each w scaled so that
+ *   w^H R_f,N-1^(k) w = 1, row mu of Q_fk = w_mu^H (step 5) -- and
+ *   g[f][n][o_k + mu] = w_mu^H R_fn^(k) w_mu (step 6).  W and H are kept.
+ * Each eigenvector is fixed up to a unit phase factor (any choice is a
+ * generalised eigenvector); the cost of Eq. (12) and every update do not
+ * depend on it.  R is summed from exact products in float pairs and
+ * factorised in FP64 (Cholesky of R_f,N-1^(k), cyclic complex Jacobi
+ * rotations); h applies a single-precision L^{-1}.  Needs N >= 2 and
+ * M <= 32 (EINVAL otherwise, and for host pointers).  Allocates stream-
+ * ordered scratch of N F M^2 * 24 bytes; synchronises `stream`; ENUMERIC if
+ * some R_fn (with h) or R_f,N-1^(k) is not positive definite, in which case
+ * the affected values are not meaningful.
+ */
+int dfmnmf_init_from_images(dfmnmf_ctx* ctx, const void* c_img, float* h_out, void* stream);
+
+/*
  * Allocation-free negative log-likelihood.  The paper has no counterpart:
  * this entry point exists for callers that may not allocate device memory
  * when they need the cost -- for example an audio engine's real-time thread,

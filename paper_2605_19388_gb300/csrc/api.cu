@@ -573,6 +573,33 @@ void dfmnmf_batch_destroy(dfmnmf_batch* b) {
   delete b;
 }
 
+int dfmnmf_init_from_images(dfmnmf_ctx* c, const void* c_img, float* h_out, void* stream) {
+  if (!c || !c_img) return fail(DFMNMF_EINVAL, "null argument");
+  if (c->N < 2) return fail(DFMNMF_EINVAL, "the initialisation needs N >= 2 sources (N = %d)", c->N);
+  if (!dfm::init_supported(c->M, c->MK)) return fail(DFMNMF_EINVAL, "the initialisation supports M <= 32 (M = %d)", c->M);
+  if (is_host_ptr(c_img) || (h_out && is_host_ptr(h_out)))
+    return fail(DFMNMF_EINVAL, "c_img and h_out must be device memory");
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = as_stream(stream);
+  const size_t nR = (size_t)c->N * c->F * c->M * c->M;
+  double2* R = nullptr;
+  float2* Linv = nullptr;
+  CK(cudaMallocAsync(reinterpret_cast<void**>(&R), nR * sizeof(double2), s));
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&Linv), nR * sizeof(float2), s);
+  if (e == cudaSuccess)
+    e = dfm::launch_init_from_images(c, reinterpret_cast<const float2*>(c_img), R, Linv, h_out, s);
+  if (e == cudaSuccess) e = dfm::launch_q_convert(c, s);
+  if (Linv) cudaFreeAsync(Linv, s);
+  cudaFreeAsync(R, s);
+  if (e != cudaSuccess) return fail(DFMNMF_ECUDA, "initialisation failed: %s", cudaGetErrorString(e));
+  unsigned flags[dfm::FLAG_COUNT];
+  CK(cudaMemcpyAsync(flags, c->flags, sizeof flags, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (flags[dfm::FLAG_NONFINITE])
+    return fail(DFMNMF_ENUMERIC, "a covariance of the initial images is not positive definite");
+  return DFMNMF_OK;
+}
+
 int dfmnmf_loglik(dfmnmf_ctx* c, double* nll_host, void* stream) {
   if (!c || !nll_host) return fail(DFMNMF_EINVAL, "null argument");
   CK(cudaSetDevice(c->device));

@@ -86,6 +86,11 @@ cudaError_t launch_logdet(const dfmnmf_ctx* c, double* out, cudaStream_t s);  //
 cudaError_t launch_qinv(const dfmnmf_ctx* c, cudaStream_t s);
 cudaError_t launch_separate(const dfmnmf_ctx* c, float2* out, cudaStream_t s);
 cudaError_t launch_q_convert(const dfmnmf_ctx* c, cudaStream_t s);    // Q64 -> Q32
+// initialisation from source images (Sec. IV-A, steps 3, 5, 6): R scratch
+// [N][F][M][M] FP64, Linv scratch [N][F][M][M]; h may be NULL
+bool init_supported(int M, int MK);
+cudaError_t launch_init_from_images(dfmnmf_ctx* c, const float2* cimg, double2* R, float2* Linv, float* h,
+                                    cudaStream_t s);
 
 // Record the message returned by dfmnmf_last_error() on this thread.
 void set_last_error(const char* msg);

@@ -29,7 +29,7 @@ EXPORTED = ("dfmnmf_init", "dfmnmf_set_observation", "dfmnmf_iterate", "dfmnmf_r
             "dfmnmf_loglik", "dfmnmf_separate", "dfmnmf_get_params", "dfmnmf_set_params",
             "dfmnmf_get_buffer", "dfmnmf_launches_per_iteration", "dfmnmf_kernel_times", "dfmnmf_destroy",
             "dfmnmf_last_error", "dfmnmf_version", "dfmnmf_loglik_noalloc", "dfmnmf_autotune",
-            "dfmnmf_cost_gradient",
+            "dfmnmf_cost_gradient", "dfmnmf_init_from_images",
             "dfmnmf_batch_create", "dfmnmf_batch_iterate", "dfmnmf_batch_destroy")
 
 
@@ -77,6 +77,7 @@ def load_library(path: Optional[str] = None):
         "dfmnmf_loglik_noalloc": (ci, [ctypes.POINTER(dfmnmf_desc), vp, vp, vp, vp, vp, ctypes.POINTER(cd), vp]),
         "dfmnmf_autotune": (ci, [vp, ci, ctypes.POINTER(ci), ctypes.POINTER(ci), vp]),
         "dfmnmf_cost_gradient": (ci, [vp, vp, vp, vp, vp, ctypes.POINTER(cd), vp]),
+        "dfmnmf_init_from_images": (ci, [vp, vp, vp, vp]),
         "dfmnmf_batch_create": (ci, [ctypes.POINTER(vp), ctypes.POINTER(vp), ci]),
         "dfmnmf_batch_iterate": (ci, [vp, ci, vp]),
         "dfmnmf_batch_destroy": (None, [vp]),
@@ -236,6 +237,13 @@ def dfmnmf_cost_gradient(ctx: Context, dQ=None, dW=None, dH=None, dg=None, strea
                                                 _ptr(dH, _dt("f32")), _ptr(dg, _dt("f32")), ctypes.byref(v),
                                                 _stream(stream)))
     return v.value
+
+
+def dfmnmf_init_from_images(ctx: Context, c_img, h_out=None, stream=None):
+    """Sec. IV-A steps 3, 5, 6 from source images c_img (complex64 [N][F][T][M], device):
+    sets the context's Q and g; writes h (float32 [N][F][T], device) when h_out is given."""
+    _check(load_library().dfmnmf_init_from_images(ctx.handle, _ptr(c_img, _dt("c64")), _ptr(h_out, _dt("f32")),
+                                                  _stream(stream)))
 
 
 def dfmnmf_autotune(ctx: Context, iters_per_trial: int = 5, stream=None):

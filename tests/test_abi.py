@@ -74,6 +74,7 @@ def test_null_arguments_rejected(lib):
     assert lib.dfmnmf_init(None, None, None, None, None, None, None, None) == D.DFMNMF_EINVAL
     assert b"null" in lib.dfmnmf_last_error()
     assert lib.dfmnmf_autotune(None, 3, None, None, None) == D.DFMNMF_EINVAL
+    assert lib.dfmnmf_init_from_images(None, None, None, None) == D.DFMNMF_EINVAL
     assert lib.dfmnmf_batch_create(None, None, 0) == D.DFMNMF_EINVAL
     out = ctypes.c_void_p()
     assert lib.dfmnmf_batch_create(ctypes.byref(out), None, 2) == D.DFMNMF_EINVAL
