@@ -145,22 +145,24 @@ def kernel_bytes(F, T, M, N, B, K, MK):
 
 
 # DRAM bytes (read + write) of one band-wide launch, from the full-section ncu
-# captures summarised in profiles/kernels_paper_4x4_n5_{bf16tc,fp32}.md (the
-# per-half launches of the two-branch iteration added up).  A figure holds
-# only while the kernel's sources are the ones captured: the digest is the
-# first 16 hex digits of sha256 over csrc/<file>, csrc/common.cuh and
-# csrc/internal.h, and `traffic` is null when it no longer matches.
+# captures summarised in profiles/kernels_paper_4x4_n5_{bf16tc,fp32}.md
+# (band-wide launches: the autotuned launch shapes of that run put the
+# per-frequency kernels on one graph branch).  A figure holds only while the
+# kernel's sources are the ones captured: the digest is the first 16 hex
+# digits of sha256 over csrc/<file>, csrc/common.cuh and csrc/internal.h, and
+# `traffic` is null when it no longer matches.
 NCU_TRAFFIC = {
     "paper_4x4_n5": {
-        "k_pstats": (24.100352e6 + 24.195072e6 + 3840 + 1536, "kernels_model.cu", "6b319bc11fdfb3bd"),
-        "k_stats": (27.179008e6 + 1024, "kernels_model.cu", "6b319bc11fdfb3bd"),
-        "k_gupd": (27.183872e6, "kernels_model.cu", "6b319bc11fdfb3bd"),
-        "k_lambda": (0.388096e6, "kernels_model.cu", "6b319bc11fdfb3bd"),
-        "k_vtc": (52.44672e6 + 52.818688e6 + 154624 + 58880, "kernels_tc.cu", "5927cbffefb4c3ad"),
-        "k_wprep": (3.308288e6 + 3.322112e6, "kernels_tc.cu", "5927cbffefb4c3ad"),
-        "k_ip": (1.385984e6 + 1.391104e6, "kernels_ip.cu", "0d0af64a8e52ca52"),
-        "k_hupd": (13.26976e6, "kernels_nmf.cu", "e6322cff36f663d3"),
-        "k_cov": (23.854592e6 + 23.947776e6, "kernels_cov.cu", "bd8b5880fbb35ec6"),
+        "k_pstats": (48274176 + 1566208, "kernels_model.cu", "a8d43ada86df4c94"),
+        "k_stats": (27177472 + 0, "kernels_model.cu", "a8d43ada86df4c94"),
+        "k_gupd": (27193856 + 0, "kernels_model.cu", "a8d43ada86df4c94"),
+        "k_lambda": (388608 + 0, "kernels_model.cu", "a8d43ada86df4c94"),
+        "k_vtc": (105086208 + 3507712, "kernels_tc.cu", "2e9762d109f23b05"),
+        "k_wprep": (6620416 + 0, "kernels_tc.cu", "2e9762d109f23b05"),
+        "k_ip": (2701824 + 0, "kernels_ip.cu", "26a449bc4878cf7f"),
+        "k_wupd": (13269248 + 0, "kernels_nmf.cu", "6650377c1ec65ff1"),
+        "k_hupd": (13270784 + 0, "kernels_nmf.cu", "6650377c1ec65ff1"),
+        "k_cov": (47757312 + 17920, "kernels_cov.cu", "b3f20ec38d0c0d8f"),
     },
 }
 
