@@ -266,6 +266,42 @@ void dfmnmf_batch_destroy(dfmnmf_batch* batch);
 int dfmnmf_init_from_images(dfmnmf_ctx* ctx, const void* c_img, float* h_out, void* stream);
 
 /*
+ * Gradient through unrolled iterations (no counterpart in the paper; it lets
+ * a learned model upstream of the separator be trained through it).
+ * dfmnmf_adjoint_create prepares, for a context of the FP32 form with
+ * subarrays of 1 to 4 microphones, the workspace of a reverse pass through
+ * n_iter >= 0 iterations that stores the state every `every` >= 1
+ * iterations and recomputes each segment from its checkpoint during the
+ * reverse sweep (ceil(n_iter / every) + every + 1 stored states).
+ * dfmnmf_adjoint_run then takes the context's current state as the initial
+ * state s0 = (Q0, W0, H0, g0), runs n_iter iterations exactly as
+ * dfmnmf_iterate does (the context is left at the final state s_T), and
+ * returns the loss of s_T and its gradient with respect to s0:
+ *   loss DFMNMF_LOSS_NLL          Eq. (12) of s_T (no F T M ln(pi) constant);
+ *   loss DFMNMF_LOSS_WIENER_MSE   mean over (n, f, t, m) of |c_n - c_true_n|^2,
+ *                                 c_n the Wiener filter output of s_T (as
+ *                                 dfmnmf_separate), source n matched to
+ *                                 c_true[n]; c_true complex64 [N][F][T][M]
+ *                                 device memory.
+ * Outputs (each may be NULL; host or device memory): *loss_host,
+ *   dQ0 complex128 [F][sum M_k^2] (dL/dRe Q + i dL/dIm Q, Q's layout),
+ *   dW0 float64 [N][F][B], dH0 float64 [N][B][T], dg0 float64 [F][N][M].
+ * The reverse pass is written out by hand (the transpose of each step's
+ * linearisation, FP64, the floors of Sec. IV-A passing no gradient where
+ * they hold) around the forward values recomputed in FP64 from the stored
+ * FP32-form states.  It needs every IP system to be nonsingular: a system
+ * below the singular threshold returns DFMNMF_ENUMERIC (the gradient is not
+ * defined there).  Synchronises `stream`.  The workspace refers to the
+ * context without owning it: destroy it first.
+ */
+typedef struct dfmnmf_adj dfmnmf_adj;
+enum { DFMNMF_LOSS_NLL = 1, DFMNMF_LOSS_WIENER_MSE = 2 };
+int dfmnmf_adjoint_create(dfmnmf_adj** out, dfmnmf_ctx* ctx, int n_iter, int every);
+int dfmnmf_adjoint_run(dfmnmf_adj* adj, int loss, const void* c_true, double* loss_host, void* dQ0,
+                       double* dW0, double* dH0, double* dg0, void* stream);
+void dfmnmf_adjoint_destroy(dfmnmf_adj* adj);
+
+/*
  * Allocation-free negative log-likelihood.  The paper has no counterpart:
  * this entry point exists for callers that may not allocate device memory
  * when they need the cost -- for example an audio engine's real-time thread,

@@ -1,0 +1,1173 @@
+// adjoint.cu -- reverse-mode gradient of unrolled MM iterations.
+//
+// The loss is a function of the state reached after n_iter iterations of
+// the FP32 form (Sec. III-B schedule): Eq. (12), or the mean squared error
+// of the multichannel Wiener filter output against given source images.
+// The gradient with respect to the initial state (Q0, W0, H0, g0) is the
+// reverse pass of the iteration written out by hand:
+//
+//   forward of one iteration (recomputed in FP64 from the stored state)
+//     lambda0 = W H, y0 = sum_n lambda0 g                      (Eq. 2)
+//     V_k,mu  = (1/T) sum_t x x^H / yhat0_mu                   (Eq. 13)
+//     rows mu of every block: A = Q V_mu, q = A^-1 e_mu,
+//       q <- q / sqrt(max(Re q^H V_mu q, eps)), row mu <- q^H  (Eqs. 14, 15)
+//     P = |Q' x|^2
+//     W' = W sqrt(num/den)  num = A0 H^T, den = D0 H^T        (Eq. 8)
+//     H' = H sqrt(num/den)  num = W'^T A1, den = W'^T D1      (Eq. 9)
+//     g' = g sqrt(num/den)  num = sum_t lambda2 P / yhat2^2,
+//                           den = sum_t lambda2 / yhat2        (Eq. 10)
+//     with A = sum_m g P / yhat^2, D = sum_m g / yhat at the current model;
+//   reverse: the adjoints of (g', H', W', P, Q', V, yhat, lambda) in the
+//   opposite order, each the transpose of the step's linearisation
+//   (conjugate transpose for complex quantities, the floors of Sec. IV-A
+//   passing no gradient where they hold).
+//
+// The forward iterations themselves are the context's own (the captured
+// FP32 iteration graph); the state is stored every `every` iterations and
+// each segment is recomputed from its checkpoint during the reverse sweep.
+// All reverse arithmetic is FP64.  Complex adjoints are dL/dRe + i dL/dIm.
+#include "../../include/dfmnmf.h"
+#include "common.cuh"
+#include "internal.h"
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <utility>
+
+struct dfmnmf_adj {
+  dfmnmf_ctx* c;
+  int n_iter, every, n_ckpt, device;
+  // stored states (context layouts: Q complex128 [F][K][MK][MK], W [N][F][B], H [N][B][Tp], g [F][N][M])
+  double2* ckQ;
+  float *ckW, *ckH, *ckg;
+  double2* sgQ;  // the states of one segment
+  float *sgW, *sgH, *sgg;
+  double2* fnQ;  // the final state
+  float *fnW, *fnH, *fng;
+  // FP64 copies of the state being differentiated and the recomputed forward
+  double *Wd, *Hd, *gd;  // [N][F][B], [N][B][T], [F][N][M]
+  double2* Qd;           // [F][K][MK][MK]
+  double *lam0, *lam1, *lam2, *y0, *y1, *y2, *P, *A0, *D0, *A1, *D1;
+  double *numW, *denW, *W1, *numH, *denH, *H1, *numG, *denG;
+  double2 *V, *Qs;  // V [F][K][MK][MK][MK]; Qs [F][K][MK+1][MK][MK] (rows before each IP row update)
+  // adjoints
+  double2 *Qb, *Qb1;
+  double *Wb, *Wb1, *Hb, *Hb1, *gb, *gb1;
+  double *lamb, *yb, *Pb, *Ab, *Db, *nb, *db;
+  double2* Vb;
+  // Wiener-filter loss
+  double2 *Binv, *ubar, *cvec, *zbar;
+  double* G4;
+  double* red;      // loss accumulator
+  unsigned* flags;  // [0] a system below the singular threshold
+};
+
+namespace dfm {
+namespace {
+
+int afail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  set_last_error(buf);
+  return code;
+}
+
+#define ACK(call)                                                                                     \
+  do {                                                                                                \
+    cudaError_t e_ = (call);                                                                          \
+    if (e_ != cudaSuccess)                                                                            \
+      return afail(DFMNMF_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+#define ACKE(call)                       \
+  do {                                   \
+    cudaError_t e_ = (call);             \
+    if (e_ != cudaSuccess) return e_;    \
+  } while (0)
+
+__device__ __forceinline__ double flo(double y, double eps) { return y > eps ? y : eps; }
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {  // a conj(b)
+  return make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ double2 crecip(double2 a) {  // 1 / a = conj(a) / |a|^2
+  const double d = cabs2(a);
+  return make_double2(a.x / d, -a.y / d);
+}
+__device__ __forceinline__ double2 ld(const float2* p) {
+  const float2 v = __ldg(p);
+  return make_double2((double)v.x, (double)v.y);
+}
+
+// Gauss-Jordan elimination with partial pivoting on A b = rhs (n <= 4, fully
+// unrolled: the pivot row is brought up by compare-and-swap so every index
+// stays static).  The solution replaces rhs; A is destroyed.  Returns the
+// smallest pivot magnitude; *scale receives max |A_ij| of the input.
+template <int n>
+__device__ double gj_solve(double2 (&A)[n][n], double2 (&r)[n], double* scale) {
+  double sc = 0.0;
+#pragma unroll
+  for (int i = 0; i < n; ++i)
+#pragma unroll
+    for (int j = 0; j < n; ++j) sc = fmax(sc, sqrt(cabs2(A[i][j])));
+  *scale = sc;
+  double minpiv = 1e300;
+#pragma unroll
+  for (int c = 0; c < n; ++c) {
+#pragma unroll
+    for (int rr = c + 1; rr < n; ++rr)
+      if (cabs2(A[rr][c]) > cabs2(A[c][c])) {
+#pragma unroll
+        for (int j = 0; j < n; ++j) {
+          const double2 t = A[c][j];
+          A[c][j] = A[rr][j];
+          A[rr][j] = t;
+        }
+        const double2 t = r[c];
+        r[c] = r[rr];
+        r[rr] = t;
+      }
+    const double2 piv = A[c][c];
+    minpiv = fmin(minpiv, sqrt(cabs2(piv)));
+    const double2 inv = cabs2(piv) > 0.0 ? crecip(piv) : make_double2(0.0, 0.0);
+#pragma unroll
+    for (int j = 0; j < n; ++j) A[c][j] = cmul(A[c][j], inv);
+    r[c] = cmul(r[c], inv);
+#pragma unroll
+    for (int rr = 0; rr < n; ++rr) {
+      if (rr == c) continue;
+      const double2 m = A[rr][c];
+#pragma unroll
+      for (int j = 0; j < n; ++j) A[rr][j] = csub(A[rr][j], cmul(m, A[c][j]));
+      r[rr] = csub(r[rr], cmul(m, r[c]));
+    }
+  }
+  return minpiv;
+}
+
+// Inverse by the same elimination (columns of the identity as right-hand sides).
+// Returns ln |det A|^2 (sum of ln |pivot|^2).
+template <int n>
+__device__ double gj_inverse(double2 (&A)[n][n], double2 (&X)[n][n]) {
+#pragma unroll
+  for (int i = 0; i < n; ++i)
+#pragma unroll
+    for (int j = 0; j < n; ++j) X[i][j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  double ld2 = 0.0;
+#pragma unroll
+  for (int c = 0; c < n; ++c) {
+#pragma unroll
+    for (int rr = c + 1; rr < n; ++rr)
+      if (cabs2(A[rr][c]) > cabs2(A[c][c])) {
+#pragma unroll
+        for (int j = 0; j < n; ++j) {
+          double2 t = A[c][j];
+          A[c][j] = A[rr][j];
+          A[rr][j] = t;
+          t = X[c][j];
+          X[c][j] = X[rr][j];
+          X[rr][j] = t;
+        }
+      }
+    const double2 piv = A[c][c];
+    ld2 += log(cabs2(piv));
+    const double2 inv = cabs2(piv) > 0.0 ? crecip(piv) : make_double2(0.0, 0.0);
+#pragma unroll
+    for (int j = 0; j < n; ++j) {
+      A[c][j] = cmul(A[c][j], inv);
+      X[c][j] = cmul(X[c][j], inv);
+    }
+#pragma unroll
+    for (int rr = 0; rr < n; ++rr) {
+      if (rr == c) continue;
+      const double2 m = A[rr][c];
+#pragma unroll
+      for (int j = 0; j < n; ++j) {
+        A[rr][j] = csub(A[rr][j], cmul(m, A[c][j]));
+        X[rr][j] = csub(X[rr][j], cmul(m, X[c][j]));
+      }
+    }
+  }
+  return ld2;
+}
+
+// ---------------------------------------------------------------- conversions and products
+// the state (context layouts, FP32) to FP64 arrays; H loses its row padding
+__global__ void k_a_tod(const float* __restrict__ W, const float* __restrict__ H, const float* __restrict__ g,
+                        double* __restrict__ Wd, double* __restrict__ Hd, double* __restrict__ gd, size_t nW,
+                        size_t nH, size_t ng, int T, int Tp) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nW) {
+    Wd[i] = W[i];
+  } else if (i < nW + nH) {
+    const size_t j = i - nW;
+    Hd[j] = H[(j / T) * Tp + j % T];
+  } else if (i < nW + nH + ng) {
+    const size_t j = i - nW - nH;
+    gd[j] = g[j];
+  }
+}
+
+// out[n][f][t] = sum_b X[n][f][b] Y[n][b][t]
+__global__ void k_a_nmf_b(const double* __restrict__ X, const double* __restrict__ Y, double* __restrict__ out, int N,
+                          int F, int B, int T) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)N * F * T) return;
+  const int t = (int)(i % T), f = (int)((i / T) % F), n = (int)(i / ((size_t)F * T));
+  const double* x = X + ((size_t)n * F + f) * B;
+  const double* y = Y + (size_t)n * B * T + t;
+  double s = 0.0;
+  for (int b = 0; b < B; ++b) s += x[b] * y[(size_t)b * T];
+  out[i] = s;
+}
+
+// out[n][f][b] (+)= sum_t X[n][f][t] Y[n][b][t]; one warp per output, lanes over t
+__global__ void k_a_nmf_t(const double* __restrict__ X, const double* __restrict__ Y, double* __restrict__ out, int N,
+                          int F, int B, int T, int acc) {
+  const size_t w = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= (size_t)N * F * B) return;
+  const int b = (int)(w % B), f = (int)((w / B) % F), n = (int)(w / ((size_t)F * B));
+  const double* x = X + ((size_t)n * F + f) * T;
+  const double* y = Y + ((size_t)n * B + b) * T;
+  double s = 0.0;
+  for (int t = lane; t < T; t += 32) s += x[t] * y[t];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[w] = (acc ? out[w] : 0.0) + s;
+}
+
+// out[n][b][t] (+)= sum_f X[n][f][b] Y[n][f][t]
+__global__ void k_a_nmf_f(const double* __restrict__ X, const double* __restrict__ Y, double* __restrict__ out, int N,
+                          int F, int B, int T, int acc) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)N * B * T) return;
+  const int t = (int)(i % T), b = (int)((i / T) % B), n = (int)(i / ((size_t)B * T));
+  double s = 0.0;
+  for (int f = 0; f < F; ++f) s += X[((size_t)n * F + f) * B + b] * Y[((size_t)n * F + f) * T + t];
+  out[i] = (acc ? out[i] : 0.0) + s;
+}
+
+// y[f][t][m] = sum_n lam[n][f][t] g[f][n][m] (before the floor)
+__global__ void k_a_y(const double* __restrict__ lam, const double* __restrict__ g, double* __restrict__ y, int N,
+                      int F, int T, int M) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)F * T * M) return;
+  const int m = (int)(i % M), t = (int)((i / M) % T), f = (int)(i / ((size_t)T * M));
+  double s = 0.0;
+  for (int n = 0; n < N; ++n) s += lam[((size_t)n * F + f) * T + t] * g[((size_t)f * N + n) * M + m];
+  y[i] = s;
+}
+
+// V[f][k][mu][a][b] = (1/T) sum_t x_a conj(x_b) / yhat0[f][t][o_k + mu]   (Eq. 13)
+__global__ void k_a_V(const float2* __restrict__ x, const double* __restrict__ y0, double2* __restrict__ V, int F,
+                      int T, int K, int MK, double eps) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t per = (size_t)MK * MK * MK;
+  if (i >= (size_t)F * K * per) return;
+  const int b = (int)(i % MK), a = (int)((i / MK) % MK), mu = (int)((i / ((size_t)MK * MK)) % MK);
+  const int k = (int)((i / per) % K), f = (int)(i / (per * K));
+  const int M = K * MK, o = k * MK;
+  double sr = 0.0, si = 0.0;
+  for (int t = 0; t < T; ++t) {
+    const size_t r = ((size_t)f * T + t) * M + o;
+    const double w = 1.0 / flo(y0[((size_t)f * T + t) * M + o + mu], eps);
+    const double2 p = cmulc(ld(x + r + a), ld(x + r + b));
+    sr += w * p.x;
+    si += w * p.y;
+  }
+  V[i] = make_double2(sr / T, si / T);
+}
+
+// P[f][t][o_k + a] = |(Q_fk x_ftk)_a|^2; block (f, k) of Q at Q + (f K + k) * bstride
+__global__ void k_a_P(const float2* __restrict__ x, const double2* __restrict__ Q, size_t bstride,
+                      double* __restrict__ P, int F, int T, int K, int MK) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)F * T * K) return;
+  const int k = (int)(i % K), t = (int)((i / K) % T), f = (int)(i / ((size_t)K * T));
+  const int M = K * MK, o = k * MK;
+  const double2* q = Q + ((size_t)f * K + k) * bstride;
+  const float2* xr = x + ((size_t)f * T + t) * M + o;
+  for (int a = 0; a < MK; ++a) {
+    double2 z = make_double2(0.0, 0.0);
+    for (int c2 = 0; c2 < MK; ++c2) z = cadd(z, cmul(q[a * MK + c2], ld(xr + c2)));
+    P[((size_t)f * T + t) * M + o + a] = cabs2(z);
+  }
+}
+
+// A[n][f][t] = sum_m g P / yhat^2, D[n][f][t] = sum_m g / yhat
+__global__ void k_a_AD(const double* __restrict__ P, const double* __restrict__ y, const double* __restrict__ g,
+                       double* __restrict__ A, double* __restrict__ D, int N, int F, int T, int M, double eps) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)N * F * T) return;
+  const int t = (int)(i % T), f = (int)((i / T) % F), n = (int)(i / ((size_t)F * T));
+  const double* gr = g + ((size_t)f * N + n) * M;
+  const size_t r = ((size_t)f * T + t) * M;
+  double a = 0.0, d = 0.0;
+  for (int m = 0; m < M; ++m) {
+    const double yy = flo(y[r + m], eps);
+    a += gr[m] * P[r + m] / (yy * yy);
+    d += gr[m] / yy;
+  }
+  A[i] = a;
+  D[i] = d;
+}
+
+// out = theta sqrt(num / max(den, eps))   (Eqs. 8-10)
+__global__ void k_a_mu(const double* __restrict__ th, const double* __restrict__ num, const double* __restrict__ den,
+                       double* __restrict__ out, size_t n, double eps) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = th[i] * sqrt(num[i] / flo(den[i], eps));
+}
+
+// num[f][n][m] = sum_t lam P / yhat^2, den = sum_t lam / yhat   (Eq. 10)
+__global__ void k_a_gnum(const double* __restrict__ lam, const double* __restrict__ P, const double* __restrict__ y,
+                         double* __restrict__ num, double* __restrict__ den, int N, int F, int T, int M, double eps) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)F * N * M) return;
+  const int m = (int)(i % M), n = (int)((i / M) % N), f = (int)(i / ((size_t)M * N));
+  const double* l = lam + ((size_t)n * F + f) * T;
+  double a = 0.0, d = 0.0;
+  for (int t = 0; t < T; ++t) {
+    const size_t r = ((size_t)f * T + t) * M + m;
+    const double yy = flo(y[r], eps);
+    a += l[t] * P[r] / (yy * yy);
+    d += l[t] / yy;
+  }
+  num[i] = a;
+  den[i] = d;
+}
+
+// forward IP of every block (Eqs. 14, 15), keeping the rows before each row update
+template <int MK>
+__global__ void k_a_ipfwd(const double2* __restrict__ Q, const double2* __restrict__ V, double2* __restrict__ Qs,
+                          int nb, double eps, double rtol, unsigned* __restrict__ flags) {
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= nb) return;
+  double2 Qc[MK][MK];
+#pragma unroll
+  for (int i = 0; i < MK; ++i)
+#pragma unroll
+    for (int j = 0; j < MK; ++j) Qc[i][j] = Q[(size_t)id * MK * MK + i * MK + j];
+  bool sing = false;
+#pragma unroll
+  for (int mu = 0; mu < MK; ++mu) {
+    double2* qs = Qs + ((size_t)id * (MK + 1) + mu) * MK * MK;
+#pragma unroll
+    for (int i = 0; i < MK; ++i)
+#pragma unroll
+      for (int j = 0; j < MK; ++j) qs[i * MK + j] = Qc[i][j];
+    const double2* Vm = V + ((size_t)id * MK + mu) * MK * MK;
+    double2 A[MK][MK], q[MK];
+#pragma unroll
+    for (int i = 0; i < MK; ++i) {
+#pragma unroll
+      for (int j = 0; j < MK; ++j) {
+        double2 s = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int l = 0; l < MK; ++l) s = cadd(s, cmul(Qc[i][l], Vm[l * MK + j]));
+        A[i][j] = s;
+      }
+      q[i] = make_double2(i == mu ? 1.0 : 0.0, 0.0);
+    }
+    double scale;
+    const double mp = gj_solve<MK>(A, q, &scale);
+    sing |= !(mp > rtol * scale);
+    double s = 0.0;
+#pragma unroll
+    for (int a = 0; a < MK; ++a) {
+      double2 vq = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int b = 0; b < MK; ++b) vq = cadd(vq, cmul(Vm[a * MK + b], q[b]));
+      s += q[a].x * vq.x + q[a].y * vq.y;  // Re(conj(q_a) (V q)_a)
+    }
+    const double inv = 1.0 / sqrt(flo(s, eps));
+#pragma unroll
+    for (int j = 0; j < MK; ++j) Qc[mu][j] = cconj(cscale(q[j], inv));
+  }
+  double2* qs = Qs + ((size_t)id * (MK + 1) + MK) * MK * MK;
+#pragma unroll
+  for (int i = 0; i < MK; ++i)
+#pragma unroll
+    for (int j = 0; j < MK; ++j) qs[i * MK + j] = Qc[i][j];
+  if (sing) atomicOr(flags, 1u);
+}
+
+// ---------------------------------------------------------------- reverse kernels
+// out = theta rho, rho = sqrt(num / max(den, eps)): bar_theta (=/+=) bar_out rho,
+// bar_num = r / max(den, eps), bar_den = -r num / den^2 (0 under the floor),
+// r = bar_out theta / (2 rho)
+__global__ void k_a_mub(const double* __restrict__ th, const double* __restrict__ num, const double* __restrict__ den,
+                        const double* __restrict__ bar_out, double* __restrict__ bar_th, double* __restrict__ numb,
+                        double* __restrict__ denb, size_t n, double eps) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double dn = flo(den[i], eps);
+  const double rho = sqrt(num[i] / dn);
+  bar_th[i] = bar_out[i] * rho;
+  const double r = rho > 0.0 ? bar_out[i] * th[i] / (2.0 * rho) : 0.0;
+  numb[i] = r / dn;
+  denb[i] = den[i] > eps ? -r * num[i] / (dn * dn) : 0.0;
+}
+
+// Reverse of the g update's sums (Eq. 10) and of the model at lambda2, per (f, t):
+//   ybar[m] = sum_n lam2 (-2 numb P / yhat^3 - denb / yhat^2)  (0 under the floor)
+//   Pbar[m] += sum_n numb lam2 / yhat^2
+//   lamb[n] = sum_m (numb P / yhat^2 + denb / yhat + ybar[m] g)
+__global__ void k_a_gstat_b(const double* __restrict__ numb, const double* __restrict__ denb,
+                            const double* __restrict__ lam, const double* __restrict__ P,
+                            const double* __restrict__ y, const double* __restrict__ g, double* __restrict__ lamb,
+                            double* __restrict__ Pb, double* __restrict__ yb, int N, int F, int T, int M, double eps) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)F * T) return;
+  const int t = (int)(i % T), f = (int)(i / T);
+  const size_t r = i * M;
+  for (int m = 0; m < M; ++m) {
+    const double yy = flo(y[r + m], eps);
+    double a = 0.0, pb = 0.0;
+    for (int n = 0; n < N; ++n) {
+      const double l = lam[((size_t)n * F + f) * T + t];
+      const size_t q = ((size_t)f * N + n) * M + m;
+      a += l * (-2.0 * numb[q] * P[r + m] / (yy * yy * yy) - denb[q] / (yy * yy));
+      pb += numb[q] * l / (yy * yy);
+    }
+    yb[r + m] = y[r + m] > eps ? a : 0.0;
+    Pb[r + m] += pb;
+  }
+  for (int n = 0; n < N; ++n) {
+    double s = 0.0;
+    for (int m = 0; m < M; ++m) {
+      const double yy = flo(y[r + m], eps);
+      const size_t q = ((size_t)f * N + n) * M + m;
+      s += numb[q] * P[r + m] / (yy * yy) + denb[q] / yy + yb[r + m] * g[q];
+    }
+    lamb[((size_t)n * F + f) * T + t] = s;
+  }
+}
+
+// Reverse of A = sum_m g P / yhat^2, D = sum_m g / yhat, per (f, t, m):
+//   ybar (=/+=) sum_n (-2 Ab g P / yhat^3 - Db g / yhat^2)  (0 under the floor),
+//   Pbar += sum_n Ab g / yhat^2
+__global__ void k_a_stat_b(const double* __restrict__ Ab, const double* __restrict__ Db,
+                           const double* __restrict__ g, const double* __restrict__ P, const double* __restrict__ y,
+                           double* __restrict__ yb, double* __restrict__ Pb, int N, int F, int T, int M, double eps,
+                           int acc) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)F * T * M) return;
+  const int m = (int)(i % M), t = (int)((i / M) % T), f = (int)(i / ((size_t)T * M));
+  const double yy = flo(y[i], eps);
+  double a = 0.0, pb = 0.0;
+  for (int n = 0; n < N; ++n) {
+    const size_t nf = ((size_t)n * F + f) * T + t;
+    const double gg = g[((size_t)f * N + n) * M + m];
+    a += -2.0 * Ab[nf] * gg * P[i] / (yy * yy * yy) - Db[nf] * gg / (yy * yy);
+    pb += Ab[nf] * gg / (yy * yy);
+  }
+  const double v = y[i] > eps ? a : 0.0;
+  yb[i] = (acc ? yb[i] : 0.0) + v;
+  Pb[i] += pb;
+}
+
+// lamb[n][f][t] (=/+=) sum_m ybar[f][t][m] g[f][n][m]   (reverse of y = sum_n lambda g)
+__global__ void k_a_y_b(const double* __restrict__ yb, const double* __restrict__ g, double* __restrict__ lamb,
+                        int N, int F, int T, int M, int acc) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)N * F * T) return;
+  const int t = (int)(i % T), f = (int)((i / T) % F), n = (int)(i / ((size_t)F * T));
+  const double* gr = g + ((size_t)f * N + n) * M;
+  const double* yr = yb + ((size_t)f * T + t) * M;
+  double s = 0.0;
+  for (int m = 0; m < M; ++m) s += yr[m] * gr[m];
+  lamb[i] = (acc ? lamb[i] : 0.0) + s;
+}
+
+// gbar[f][n][m] += sum_t (Ab P / yhat^2 + Db / yhat + ybar lam); NULL terms are skipped
+__global__ void k_a_gbar(const double* __restrict__ Ab, const double* __restrict__ Db, const double* __restrict__ yb,
+                         const double* __restrict__ lam, const double* __restrict__ P, const double* __restrict__ y,
+                         double* __restrict__ gb, int N, int F, int T, int M, double eps) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)F * N * M) return;
+  const int m = (int)(i % M), n = (int)((i / M) % N), f = (int)(i / ((size_t)M * N));
+  const size_t nf = ((size_t)n * F + f) * T;
+  double s = 0.0;
+  for (int t = 0; t < T; ++t) {
+    const size_t r = ((size_t)f * T + t) * M + m;
+    const double yy = flo(y[r], eps);
+    if (Ab) s += Ab[nf + t] * P[r] / (yy * yy);
+    if (Db) s += Db[nf + t] / yy;
+    if (yb) s += yb[r] * lam[nf + t];
+  }
+  gb[i] += s;
+}
+
+// gbar[f][n][m] += sum_t G4[n][f][t][m]
+__global__ void k_a_red_t4(const double* __restrict__ G4, double* __restrict__ gb, int N, int F, int T, int M) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)F * N * M) return;
+  const int m = (int)(i % M), n = (int)((i / M) % N), f = (int)(i / ((size_t)M * N));
+  double s = 0.0;
+  for (int t = 0; t < T; ++t) s += G4[(((size_t)n * F + f) * T + t) * M + m];
+  gb[i] += s;
+}
+
+// Reverse of P = |Q x|^2: Qbar[f][k][a][b] += sum_t 2 Pbar_a z_a conj(x_b)
+__global__ void k_a_Pb(const float2* __restrict__ x, const double2* __restrict__ Q, size_t bstride,
+                       const double* __restrict__ Pb, double2* __restrict__ Qb, int F, int T, int K, int MK) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)F * K * MK * MK) return;
+  const int b = (int)(i % MK), a = (int)((i / MK) % MK), k = (int)((i / ((size_t)MK * MK)) % K);
+  const int f = (int)(i / ((size_t)MK * MK * K));
+  const int M = K * MK, o = k * MK;
+  const double2* q = Q + ((size_t)f * K + k) * bstride + a * MK;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int t = 0; t < T; ++t) {
+    const size_t r = ((size_t)f * T + t) * M + o;
+    double2 z = make_double2(0.0, 0.0);
+    for (int c2 = 0; c2 < MK; ++c2) z = cadd(z, cmul(q[c2], ld(x + r + c2)));
+    acc = cadd(acc, cscale(cmulc(z, ld(x + r + b)), 2.0 * Pb[((size_t)f * T + t) * M + o + a]));
+  }
+  Qb[i] = cadd(Qb[i], acc);
+}
+
+// Reverse of the IP rows of one block, mu = MK-1 .. 0.  For row mu with
+// A = Qc V_mu, q = A^-1 e_mu, s = Re q^H V_mu q, sigma = sqrt(max(s, eps)):
+//   qbar_n = conj(row mu of Qbar); Qbar row mu <- 0
+//   qbar = qbar_n / sigma;  if s > eps: sbar = -Re(qbar_n^H q) / (2 sigma^3),
+//   qbar += 2 sbar V q
+//   y = A^-H qbar;  Qbar += -y (q^H V_mu);  Vbar_mu = (sbar q - Qc^H y) q^H
+template <int MK>
+__global__ void k_a_ipb(const double2* __restrict__ Qs, const double2* __restrict__ V,
+                        const double2* __restrict__ Qbin, double2* __restrict__ Qbout, double2* __restrict__ Vb,
+                        int nb, double eps) {
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= nb) return;
+  double2 Qb[MK][MK];
+#pragma unroll
+  for (int i = 0; i < MK; ++i)
+#pragma unroll
+    for (int j = 0; j < MK; ++j) Qb[i][j] = Qbin[(size_t)id * MK * MK + i * MK + j];
+#pragma unroll
+  for (int mu = MK - 1; mu >= 0; --mu) {
+    const double2* Qc = Qs + ((size_t)id * (MK + 1) + mu) * MK * MK;
+    const double2* Vm = V + ((size_t)id * MK + mu) * MK * MK;
+    double2 A[MK][MK], q[MK];
+#pragma unroll
+    for (int i = 0; i < MK; ++i) {
+#pragma unroll
+      for (int j = 0; j < MK; ++j) {
+        double2 s = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int l = 0; l < MK; ++l) s = cadd(s, cmul(Qc[i * MK + l], Vm[l * MK + j]));
+        A[i][j] = s;
+      }
+      q[i] = make_double2(i == mu ? 1.0 : 0.0, 0.0);
+    }
+    double2 AH[MK][MK];  // A^H for the adjoint solve
+#pragma unroll
+    for (int i = 0; i < MK; ++i)
+#pragma unroll
+      for (int j = 0; j < MK; ++j) AH[i][j] = cconj(A[j][i]);
+    double scale;
+    gj_solve<MK>(A, q, &scale);
+    double2 vq[MK];
+    double s = 0.0;
+#pragma unroll
+    for (int a = 0; a < MK; ++a) {
+      double2 v = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int b = 0; b < MK; ++b) v = cadd(v, cmul(Vm[a * MK + b], q[b]));
+      vq[a] = v;
+      s += q[a].x * v.x + q[a].y * v.y;
+    }
+    const double sig = sqrt(flo(s, eps));
+    double2 qb[MK];
+    double dotr = 0.0;  // Re(qbar_n^H q)
+#pragma unroll
+    for (int j = 0; j < MK; ++j) {
+      const double2 qn = cconj(Qb[mu][j]);
+      dotr += qn.x * q[j].x + qn.y * q[j].y;
+      qb[j] = cscale(qn, 1.0 / sig);
+      Qb[mu][j] = make_double2(0.0, 0.0);
+    }
+    double sb = 0.0;
+    if (s > eps) {
+      sb = -dotr / (2.0 * sig * sig * sig);
+#pragma unroll
+      for (int j = 0; j < MK; ++j) qb[j] = cadd(qb[j], cscale(vq[j], 2.0 * sb));
+    }
+    gj_solve<MK>(AH, qb, &scale);  // qb <- A^-H qbar
+    double2 w[MK];                   // q^H V_mu
+#pragma unroll
+    for (int j = 0; j < MK; ++j) {
+      double2 v = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int l = 0; l < MK; ++l) v = cadd(v, cmul(cconj(q[l]), Vm[l * MK + j]));
+      w[j] = v;
+    }
+#pragma unroll
+    for (int i = 0; i < MK; ++i)
+#pragma unroll
+      for (int j = 0; j < MK; ++j) Qb[i][j] = csub(Qb[i][j], cmul(qb[i], w[j]));
+    double2* vb = Vb + ((size_t)id * MK + mu) * MK * MK;
+#pragma unroll
+    for (int i = 0; i < MK; ++i) {
+      double2 u = cscale(q[i], sb);  // sbar q - Qc^H y
+#pragma unroll
+      for (int l = 0; l < MK; ++l) u = csub(u, cmul(cconj(Qc[l * MK + i]), qb[l]));
+#pragma unroll
+      for (int j = 0; j < MK; ++j) vb[i * MK + j] = cmulc(u, q[j]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < MK; ++i)
+#pragma unroll
+    for (int j = 0; j < MK; ++j) Qbout[(size_t)id * MK * MK + i * MK + j] = Qb[i][j];
+}
+
+// Reverse of Eq. 13 and of 1/yhat0: ybar0[f][t][o_k+mu] += -Re(x^H Vbar_mu x) / (T yhat0^2)
+__global__ void k_a_Vb(const float2* __restrict__ x, const double2* __restrict__ Vb, const double* __restrict__ y0,
+                       double* __restrict__ yb, int F, int T, int K, int MK, double eps) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int M = K * MK;
+  if (i >= (size_t)F * T * M) return;
+  const int m = (int)(i % M), t = (int)((i / M) % T), f = (int)(i / ((size_t)T * M));
+  const int k = m / MK, mu = m % MK, o = k * MK;
+  if (!(y0[i] > eps)) return;
+  const double2* vb = Vb + (((size_t)f * K + k) * MK + mu) * MK * MK;
+  const float2* xr = x + ((size_t)f * T + t) * M + o;
+  double s = 0.0;
+  for (int a = 0; a < MK; ++a) {
+    double2 v = make_double2(0.0, 0.0);
+    for (int b = 0; b < MK; ++b) v = cadd(v, cmul(vb[a * MK + b], ld(xr + b)));
+    const double2 xa = ld(xr + a);
+    s += xa.x * v.x + xa.y * v.y;  // Re(conj(x_a) (Vbar x)_a)
+  }
+  yb[i] += -s / ((double)T * y0[i] * y0[i]);
+}
+
+// ---------------------------------------------------------------- losses
+__device__ void block_add(double v, double* red) {
+  __shared__ double sm[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) atomicAdd(red, v);
+  }
+}
+
+// data term of Eq. 12 and its adjoints: Pbar = 1/yhat, ybar = 1/yhat - P/yhat^2 (0 under the floor)
+__global__ void k_a_nll_data(const double* __restrict__ P, const double* __restrict__ y, double* __restrict__ Pb,
+                             double* __restrict__ yb, double* __restrict__ red, size_t n, double eps) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double v = 0.0;
+  if (i < n) {
+    const double yy = flo(y[i], eps);
+    v = P[i] / yy + log(yy);
+    Pb[i] = 1.0 / yy;
+    yb[i] = y[i] > eps ? 1.0 / yy - P[i] / (yy * yy) : 0.0;
+  }
+  block_add(v, red);
+}
+
+// -T ln|det Q_fk|^2 and its adjoint -2 T Q^-H, added to Qbar
+template <int MK>
+__global__ void k_a_logdet_b(const double2* __restrict__ Q, double2* __restrict__ Qb, double* __restrict__ red, int nb,
+                             int T) {
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  double v = 0.0;
+  if (id < nb) {
+    double2 A[MK][MK], X[MK][MK];
+#pragma unroll
+    for (int i = 0; i < MK; ++i)
+#pragma unroll
+      for (int j = 0; j < MK; ++j) A[i][j] = Q[(size_t)id * MK * MK + i * MK + j];
+    v = -(double)T * gj_inverse<MK>(A, X);
+#pragma unroll
+    for (int i = 0; i < MK; ++i)
+#pragma unroll
+      for (int j = 0; j < MK; ++j) {
+        double2* p = Qb + (size_t)id * MK * MK + i * MK + j;
+        *p = csub(*p, cscale(cconj(X[j][i]), 2.0 * T));
+      }
+  }
+  block_add(v, red);
+}
+
+template <int MK>
+__global__ void k_a_inv(const double2* __restrict__ Q, double2* __restrict__ Binv, int nb) {
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= nb) return;
+  double2 A[MK][MK], X[MK][MK];
+#pragma unroll
+  for (int i = 0; i < MK; ++i)
+#pragma unroll
+    for (int j = 0; j < MK; ++j) A[i][j] = Q[(size_t)id * MK * MK + i * MK + j];
+  gj_inverse<MK>(A, X);
+#pragma unroll
+  for (int i = 0; i < MK; ++i)
+#pragma unroll
+    for (int j = 0; j < MK; ++j) Binv[(size_t)id * MK * MK + i * MK + j] = X[i][j];
+}
+
+// Wiener filter MSE, per (f, t): for each block and source, z = Q x, gamma = lam g / yhat,
+// u = gamma z, c = B u (B = Q^-1), d = c - c_true, loss += |d|^2 / S, cbar = 2 d / S,
+// ubar = B^H cbar, gammabar = Re(conj(ubar) z), zbar += gamma ubar;
+// lamb[n] = sum_m gammabar g / yhat, ybar[m] = -sum_n gammabar lam g / yhat^2 (0 under the floor),
+// G4[n][f][t][m] = gammabar lam / yhat (summed over t into gbar); ubar, c and zbar are kept
+// for the Q adjoint
+template <int MK>
+__global__ void k_a_wiener_ft(const float2* __restrict__ x, const double2* __restrict__ Q,
+                              const double2* __restrict__ Binv, const float2* __restrict__ ct,
+                              const double* __restrict__ lam, const double* __restrict__ g,
+                              const double* __restrict__ y, double* __restrict__ lamb, double* __restrict__ yb,
+                              double* __restrict__ G4, double2* __restrict__ ubar, double2* __restrict__ cvec,
+                              double2* __restrict__ zbar, double* __restrict__ red, int N, int F, int T, int K,
+                              double eps, double invS) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int M = K * MK;
+  double loss = 0.0;
+  if (i < (size_t)F * T) {
+    const int t = (int)(i % T), f = (int)(i / T);
+    for (int n = 0; n < N; ++n) lamb[((size_t)n * F + f) * T + t] = 0.0;
+    for (int k = 0; k < K; ++k) {
+      const int o = k * MK;
+      const double2* q = Q + ((size_t)f * K + k) * MK * MK;
+      const double2* B = Binv + ((size_t)f * K + k) * MK * MK;
+      const size_t r = ((size_t)f * T + t) * M + o;
+      double2 z[MK], zb[MK];
+      double yh[MK], ybm[MK];
+#pragma unroll
+      for (int a = 0; a < MK; ++a) {
+        double2 s = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int c2 = 0; c2 < MK; ++c2) s = cadd(s, cmul(q[a * MK + c2], ld(x + r + c2)));
+        z[a] = s;
+        zb[a] = make_double2(0.0, 0.0);
+        yh[a] = flo(y[r + a], eps);
+        ybm[a] = 0.0;
+      }
+      for (int n = 0; n < N; ++n) {
+        const double l = lam[((size_t)n * F + f) * T + t];
+        const double* gr = g + ((size_t)f * N + n) * M + o;
+        const size_t rn = (((size_t)n * F + f) * T + t) * M + o;
+        double2 u[MK], cb[MK];
+        double gam[MK];
+#pragma unroll
+        for (int a = 0; a < MK; ++a) {
+          gam[a] = l * gr[a] / yh[a];
+          u[a] = cscale(z[a], gam[a]);
+        }
+#pragma unroll
+        for (int a = 0; a < MK; ++a) {
+          double2 c = make_double2(0.0, 0.0);
+#pragma unroll
+          for (int b = 0; b < MK; ++b) c = cadd(c, cmul(B[a * MK + b], u[b]));
+          cvec[rn + a] = c;
+          const double2 d = csub(c, ld(ct + rn + a));
+          loss += cabs2(d) * invS;
+          cb[a] = cscale(d, 2.0 * invS);
+        }
+        double lb = 0.0;
+#pragma unroll
+        for (int a = 0; a < MK; ++a) {
+          double2 ub = make_double2(0.0, 0.0);  // (B^H cbar)_a
+#pragma unroll
+          for (int j = 0; j < MK; ++j) ub = cadd(ub, cmul(cconj(B[j * MK + a]), cb[j]));
+          ubar[rn + a] = ub;
+          const double gb = ub.x * z[a].x + ub.y * z[a].y;  // Re(conj(ubar) z)
+          zb[a] = cadd(zb[a], cscale(ub, gam[a]));
+          lb += gb * gr[a] / yh[a];
+          ybm[a] += -gb * l * gr[a] / (yh[a] * yh[a]);
+          G4[rn + a] = gb * l / yh[a];
+        }
+        lamb[((size_t)n * F + f) * T + t] += lb;
+      }
+#pragma unroll
+      for (int a = 0; a < MK; ++a) {
+        zbar[r + a] = zb[a];
+        yb[r + a] = y[r + a] > eps ? ybm[a] : 0.0;
+      }
+    }
+  }
+  block_add(loss, red);
+}
+
+// Qbar[f][k][a][b] = sum_t (zbar_a conj(x_b) - sum_n ubar_n,a conj(c_n,b))
+// (the second sum is -B^H (sum cbar u^H) B^H, the adjoint through B = Q^-1)
+__global__ void k_a_wiener_q(const float2* __restrict__ x, const double2* __restrict__ zbar,
+                             const double2* __restrict__ ubar, const double2* __restrict__ cvec,
+                             double2* __restrict__ Qb, int N, int F, int T, int K, int MK) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)F * K * MK * MK) return;
+  const int b = (int)(i % MK), a = (int)((i / MK) % MK), k = (int)((i / ((size_t)MK * MK)) % K);
+  const int f = (int)(i / ((size_t)MK * MK * K));
+  const int M = K * MK, o = k * MK;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int t = 0; t < T; ++t) {
+    const size_t r = ((size_t)f * T + t) * M + o;
+    acc = cadd(acc, cmulc(zbar[r + a], ld(x + r + b)));
+    for (int n = 0; n < N; ++n) {
+      const size_t rn = (((size_t)n * F + f) * T + t) * M + o;
+      acc = csub(acc, cmulc(ubar[rn + a], cvec[rn + b]));
+    }
+  }
+  Qb[i] = acc;
+}
+
+inline unsigned nblk(size_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+#define AL(...)                                   \
+  do {                                            \
+    __VA_ARGS__;                                  \
+    cudaError_t e_ = cudaGetLastError();          \
+    if (e_ != cudaSuccess) return e_;             \
+  } while (0)
+
+#define MK_DISPATCH(MK, KERNEL, GRID, BLOCK, SMEM, STREAM, ...)                        \
+  switch (MK) {                                                                        \
+    case 1: KERNEL<1><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__); break;              \
+    case 2: KERNEL<2><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__); break;              \
+    case 3: KERNEL<3><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__); break;              \
+    case 4: KERNEL<4><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__); break;              \
+    default: return cudaErrorInvalidValue;                                             \
+  }
+
+struct Dims {
+  int N, F, T, B, K, MK, M, Tp;
+  size_t nft, ftm, nfb, nbt, fnm, nq, nv, nqs, nftm;
+  double eps;
+};
+
+Dims dims_of(const dfmnmf_ctx* c) {
+  Dims d;
+  d.N = c->N; d.F = c->F; d.T = c->T; d.B = c->B; d.K = c->K; d.MK = c->MK; d.M = c->M; d.Tp = c->Tp;
+  d.nft = (size_t)d.N * d.F * d.T;
+  d.ftm = (size_t)d.F * d.T * d.M;
+  d.nfb = (size_t)d.N * d.F * d.B;
+  d.nbt = (size_t)d.N * d.B * d.T;
+  d.fnm = (size_t)d.F * d.N * d.M;
+  d.nq = (size_t)d.F * d.K * d.MK * d.MK;
+  d.nv = d.nq * d.MK;
+  d.nqs = d.nq * (d.MK + 1);
+  d.nftm = d.nft * d.M;
+  d.eps = (double)c->eps;
+  return d;
+}
+
+// FP64 copy of a stored state (context layouts) into Wd, Hd, gd, Qd
+cudaError_t load_state(dfmnmf_adj* a, const Dims& d, const double2* Q, const float* W, const float* H,
+                       const float* g, cudaStream_t s) {
+  AL(k_a_tod<<<nblk(d.nfb + d.nbt + d.fnm), 256, 0, s>>>(W, H, g, a->Wd, a->Hd, a->gd, d.nfb, d.nbt, d.fnm, d.T,
+                                                          d.Tp));
+  return cudaMemcpyAsync(a->Qd, Q, d.nq * sizeof(double2), cudaMemcpyDeviceToDevice, s);
+}
+
+// lam = W H and yraw = sum_n lam g
+cudaError_t model(const Dims& d, const double* W, const double* H, const double* g, double* lam, double* y,
+                  cudaStream_t s) {
+  AL(k_a_nmf_b<<<nblk(d.nft), 256, 0, s>>>(W, H, lam, d.N, d.F, d.B, d.T));
+  AL(k_a_y<<<nblk(d.ftm), 256, 0, s>>>(lam, g, y, d.N, d.F, d.T, d.M));
+  return cudaSuccess;
+}
+
+cudaError_t nmf_t(const Dims& d, const double* X, const double* Y, double* out, int acc, cudaStream_t s) {
+  AL(k_a_nmf_t<<<nblk(d.nfb * 32), 256, 0, s>>>(X, Y, out, d.N, d.F, d.B, d.T, acc));
+  return cudaSuccess;
+}
+cudaError_t nmf_f(const Dims& d, const double* X, const double* Y, double* out, int acc, cudaStream_t s) {
+  AL(k_a_nmf_f<<<nblk(d.nbt), 256, 0, s>>>(X, Y, out, d.N, d.F, d.B, d.T, acc));
+  return cudaSuccess;
+}
+
+// Reverse of one iteration whose input state is in Wd, Hd, gd, Qd; the adjoint of its
+// output state is in (Qb1, Wb1, Hb1, gb1) (consumed); the adjoint of its input state is
+// written to (Qb, Wb, Hb, gb).
+cudaError_t reverse_iteration(dfmnmf_adj* a, const Dims& d, cudaStream_t s) {
+  const dfmnmf_ctx* c = a->c;
+  const double eps = d.eps;
+  const int nb = d.F * d.K;
+  // forward, recomputed in FP64
+  cudaError_t e = model(d, a->Wd, a->Hd, a->gd, a->lam0, a->y0, s);
+  if (e != cudaSuccess) return e;
+  AL(k_a_V<<<nblk(d.nv), 256, 0, s>>>(c->x, a->y0, a->V, d.F, d.T, d.K, d.MK, eps));
+  MK_DISPATCH(d.MK, k_a_ipfwd, nblk(nb, 64), 64, 0, s, a->Qd, a->V, a->Qs, nb, eps, (double)c->singular_rtol, a->flags);
+  AL((void)0);
+  const double2* Qn = a->Qs + (size_t)d.MK * d.MK * d.MK;  // rows after the last update, stride (MK+1) MK^2
+  const size_t qstr = (size_t)(d.MK + 1) * d.MK * d.MK;
+  AL(k_a_P<<<nblk((size_t)d.F * d.T * d.K), 256, 0, s>>>(c->x, Qn, qstr, a->P, d.F, d.T, d.K, d.MK));
+  AL(k_a_AD<<<nblk(d.nft), 256, 0, s>>>(a->P, a->y0, a->gd, a->A0, a->D0, d.N, d.F, d.T, d.M, eps));
+  if ((e = nmf_t(d, a->A0, a->Hd, a->numW, 0, s)) || (e = nmf_t(d, a->D0, a->Hd, a->denW, 0, s))) return e;
+  AL(k_a_mu<<<nblk(d.nfb), 256, 0, s>>>(a->Wd, a->numW, a->denW, a->W1, d.nfb, eps));
+  if ((e = model(d, a->W1, a->Hd, a->gd, a->lam1, a->y1, s))) return e;
+  AL(k_a_AD<<<nblk(d.nft), 256, 0, s>>>(a->P, a->y1, a->gd, a->A1, a->D1, d.N, d.F, d.T, d.M, eps));
+  if ((e = nmf_f(d, a->W1, a->A1, a->numH, 0, s)) || (e = nmf_f(d, a->W1, a->D1, a->denH, 0, s))) return e;
+  AL(k_a_mu<<<nblk(d.nbt), 256, 0, s>>>(a->Hd, a->numH, a->denH, a->H1, d.nbt, eps));
+  if ((e = model(d, a->W1, a->H1, a->gd, a->lam2, a->y2, s))) return e;
+  AL(k_a_gnum<<<nblk(d.fnm), 256, 0, s>>>(a->lam2, a->P, a->y2, a->numG, a->denG, d.N, d.F, d.T, d.M, eps));
+
+  // reverse of the g update (Eq. 10)
+  AL(k_a_mub<<<nblk(d.fnm), 256, 0, s>>>(a->gd, a->numG, a->denG, a->gb1, a->gb, a->nb, a->db, d.fnm, eps));
+  ACKE(cudaMemsetAsync(a->Pb, 0, d.ftm * sizeof(double), s));
+  AL(k_a_gstat_b<<<nblk((size_t)d.F * d.T), 256, 0, s>>>(a->nb, a->db, a->lam2, a->P, a->y2, a->gd, a->lamb, a->Pb,
+                                                          a->yb, d.N, d.F, d.T, d.M, eps));
+  AL(k_a_gbar<<<nblk(d.fnm), 256, 0, s>>>(nullptr, nullptr, a->yb, a->lam2, a->P, a->y2, a->gb, d.N, d.F, d.T, d.M,
+                                           eps));
+  if ((e = nmf_t(d, a->lamb, a->H1, a->Wb1, 1, s)) || (e = nmf_f(d, a->W1, a->lamb, a->Hb1, 1, s))) return e;
+  // reverse of the H update (Eq. 9)
+  AL(k_a_mub<<<nblk(d.nbt), 256, 0, s>>>(a->Hd, a->numH, a->denH, a->Hb1, a->Hb, a->nb, a->db, d.nbt, eps));
+  if ((e = nmf_t(d, a->A1, a->nb, a->Wb1, 1, s)) || (e = nmf_t(d, a->D1, a->db, a->Wb1, 1, s))) return e;
+  AL(k_a_nmf_b<<<nblk(d.nft), 256, 0, s>>>(a->W1, a->nb, a->Ab, d.N, d.F, d.B, d.T));
+  AL(k_a_nmf_b<<<nblk(d.nft), 256, 0, s>>>(a->W1, a->db, a->Db, d.N, d.F, d.B, d.T));
+  AL(k_a_stat_b<<<nblk(d.ftm), 256, 0, s>>>(a->Ab, a->Db, a->gd, a->P, a->y1, a->yb, a->Pb, d.N, d.F, d.T, d.M, eps,
+                                             0));
+  AL(k_a_gbar<<<nblk(d.fnm), 256, 0, s>>>(a->Ab, a->Db, a->yb, a->lam1, a->P, a->y1, a->gb, d.N, d.F, d.T, d.M,
+                                           eps));
+  AL(k_a_y_b<<<nblk(d.nft), 256, 0, s>>>(a->yb, a->gd, a->lamb, d.N, d.F, d.T, d.M, 0));
+  if ((e = nmf_t(d, a->lamb, a->Hd, a->Wb1, 1, s)) || (e = nmf_f(d, a->W1, a->lamb, a->Hb, 1, s))) return e;
+  // reverse of the W update (Eq. 8)
+  AL(k_a_mub<<<nblk(d.nfb), 256, 0, s>>>(a->Wd, a->numW, a->denW, a->Wb1, a->Wb, a->nb, a->db, d.nfb, eps));
+  if ((e = nmf_f(d, a->nb, a->A0, a->Hb, 1, s)) || (e = nmf_f(d, a->db, a->D0, a->Hb, 1, s))) return e;
+  AL(k_a_nmf_b<<<nblk(d.nft), 256, 0, s>>>(a->nb, a->Hd, a->Ab, d.N, d.F, d.B, d.T));
+  AL(k_a_nmf_b<<<nblk(d.nft), 256, 0, s>>>(a->db, a->Hd, a->Db, d.N, d.F, d.B, d.T));
+  AL(k_a_stat_b<<<nblk(d.ftm), 256, 0, s>>>(a->Ab, a->Db, a->gd, a->P, a->y0, a->yb, a->Pb, d.N, d.F, d.T, d.M, eps,
+                                             0));
+  // reverse of the projections and of the IP rows (Eqs. 13-15)
+  AL(k_a_Pb<<<nblk(d.nq), 256, 0, s>>>(c->x, Qn, qstr, a->Pb, a->Qb1, d.F, d.T, d.K, d.MK));
+  MK_DISPATCH(d.MK, k_a_ipb, nblk(nb, 64), 64, 0, s, a->Qs, a->V, a->Qb1, a->Qb, a->Vb, nb, eps);
+  AL((void)0);
+  AL(k_a_Vb<<<nblk(d.ftm), 256, 0, s>>>(c->x, a->Vb, a->y0, a->yb, d.F, d.T, d.K, d.MK, eps));
+  // reverse of the model at the input state
+  AL(k_a_gbar<<<nblk(d.fnm), 256, 0, s>>>(a->Ab, a->Db, a->yb, a->lam0, a->P, a->y0, a->gb, d.N, d.F, d.T, d.M,
+                                           eps));
+  AL(k_a_y_b<<<nblk(d.nft), 256, 0, s>>>(a->yb, a->gd, a->lamb, d.N, d.F, d.T, d.M, 0));
+  if ((e = nmf_t(d, a->lamb, a->Hd, a->Wb, 1, s)) || (e = nmf_f(d, a->Wd, a->lamb, a->Hb, 1, s))) return e;
+  return cudaSuccess;
+}
+
+// Loss of the state in (Wd, Hd, gd, Qd) into red and its adjoint into (Qb, Wb, Hb, gb).
+cudaError_t loss_and_adjoint(dfmnmf_adj* a, const Dims& d, int loss, const float2* ct, cudaStream_t s) {
+  const dfmnmf_ctx* c = a->c;
+  const double eps = d.eps;
+  const int nb = d.F * d.K;
+  cudaError_t e = model(d, a->Wd, a->Hd, a->gd, a->lam0, a->y0, s);
+  if (e != cudaSuccess) return e;
+  ACKE(cudaMemsetAsync(a->red, 0, sizeof(double), s));
+  ACKE(cudaMemsetAsync(a->gb, 0, d.fnm * sizeof(double), s));
+  const size_t qstr = (size_t)d.MK * d.MK;
+  if (loss == DFMNMF_LOSS_NLL) {
+    AL(k_a_P<<<nblk((size_t)d.F * d.T * d.K), 256, 0, s>>>(c->x, a->Qd, qstr, a->P, d.F, d.T, d.K, d.MK));
+    AL(k_a_nll_data<<<nblk(d.ftm), 256, 0, s>>>(a->P, a->y0, a->Pb, a->yb, a->red, d.ftm, eps));
+    ACKE(cudaMemsetAsync(a->Qb, 0, d.nq * sizeof(double2), s));
+    AL(k_a_Pb<<<nblk(d.nq), 256, 0, s>>>(c->x, a->Qd, qstr, a->Pb, a->Qb, d.F, d.T, d.K, d.MK));
+    MK_DISPATCH(d.MK, k_a_logdet_b, nblk(nb, 64), 64, 0, s, a->Qd, a->Qb, a->red, nb, d.T);
+    AL((void)0);
+    AL(k_a_y_b<<<nblk(d.nft), 256, 0, s>>>(a->yb, a->gd, a->lamb, d.N, d.F, d.T, d.M, 0));
+  } else {
+    MK_DISPATCH(d.MK, k_a_inv, nblk(nb, 64), 64, 0, s, a->Qd, a->Binv, nb);
+    AL((void)0);
+    const double invS = 1.0 / (double)d.nftm;
+    MK_DISPATCH(d.MK, k_a_wiener_ft, nblk((size_t)d.F * d.T), 256, 0, s, c->x, a->Qd, a->Binv, ct, a->lam0, a->gd,
+                a->y0, a->lamb, a->yb, a->G4, a->ubar, a->cvec, a->zbar, a->red, d.N, d.F, d.T, d.K, eps, invS);
+    AL((void)0);
+    AL(k_a_wiener_q<<<nblk(d.nq), 256, 0, s>>>(c->x, a->zbar, a->ubar, a->cvec, a->Qb, d.N, d.F, d.T, d.K, d.MK));
+    AL(k_a_red_t4<<<nblk(d.fnm), 256, 0, s>>>(a->G4, a->gb, d.N, d.F, d.T, d.M));
+    AL(k_a_y_b<<<nblk(d.nft), 256, 0, s>>>(a->yb, a->gd, a->lamb, d.N, d.F, d.T, d.M, 1));
+  }
+  AL(k_a_gbar<<<nblk(d.fnm), 256, 0, s>>>(nullptr, nullptr, a->yb, a->lam0, a->P, a->y0, a->gb, d.N, d.F, d.T, d.M,
+                                           eps));
+  if ((e = nmf_t(d, a->lamb, a->Hd, a->Wb, 0, s)) || (e = nmf_f(d, a->Wd, a->lamb, a->Hb, 0, s))) return e;
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace dfm
+
+using dfm::afail;
+
+namespace {
+
+size_t q_n(const dfmnmf_ctx* c) { return (size_t)c->F * c->K * c->MK * c->MK; }
+size_t w_n(const dfmnmf_ctx* c) { return (size_t)c->N * c->F * c->B; }
+size_t h_n(const dfmnmf_ctx* c) { return (size_t)c->N * c->B * c->Tp; }
+size_t g_n(const dfmnmf_ctx* c) { return (size_t)c->F * c->N * c->M; }
+
+cudaError_t save_state(const dfmnmf_ctx* c, double2* Q, float* W, float* H, float* g, cudaStream_t s) {
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(Q, c->Q64, q_n(c) * sizeof(double2), cudaMemcpyDeviceToDevice, s))) return e;
+  if ((e = cudaMemcpyAsync(W, c->W, w_n(c) * sizeof(float), cudaMemcpyDeviceToDevice, s))) return e;
+  if ((e = cudaMemcpyAsync(H, c->H, h_n(c) * sizeof(float), cudaMemcpyDeviceToDevice, s))) return e;
+  return cudaMemcpyAsync(g, c->g, g_n(c) * sizeof(float), cudaMemcpyDeviceToDevice, s);
+}
+
+cudaError_t restore_state(dfmnmf_ctx* c, const double2* Q, const float* W, const float* H, const float* g,
+                          cudaStream_t s) {
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(c->Q64, Q, q_n(c) * sizeof(double2), cudaMemcpyDeviceToDevice, s))) return e;
+  if ((e = cudaMemcpyAsync(c->W, W, w_n(c) * sizeof(float), cudaMemcpyDeviceToDevice, s))) return e;
+  if ((e = cudaMemcpyAsync(c->H, H, h_n(c) * sizeof(float), cudaMemcpyDeviceToDevice, s))) return e;
+  if ((e = cudaMemcpyAsync(c->g, g, g_n(c) * sizeof(float), cudaMemcpyDeviceToDevice, s))) return e;
+  if ((e = dfm::launch_lambda(c, s))) return e;
+  return dfm::launch_q_convert(c, s);
+}
+
+void free_adj(dfmnmf_adj* a) {
+  if (!a) return;
+  void* p[] = {a->ckQ, a->ckW, a->ckH, a->ckg, a->sgQ, a->sgW, a->sgH, a->sgg, a->fnQ, a->fnW, a->fnH, a->fng,
+               a->Wd, a->Hd, a->gd, a->Qd, a->lam0, a->lam1, a->lam2, a->y0, a->y1, a->y2, a->P, a->A0, a->D0,
+               a->A1, a->D1, a->numW, a->denW, a->W1, a->numH, a->denH, a->H1, a->numG, a->denG, a->V, a->Qs,
+               a->Qb, a->Qb1, a->Wb, a->Wb1, a->Hb, a->Hb1, a->gb, a->gb1, a->lamb, a->yb, a->Pb, a->Ab, a->Db,
+               a->nb, a->db, a->Vb, a->Binv, a->ubar, a->cvec, a->zbar, a->G4, a->red, a->flags};
+  for (void* q : p)
+    if (q) cudaFree(q);
+  delete a;
+}
+
+template <class T>
+bool aalloc(T** p, size_t n) {
+  if (cudaMalloc(reinterpret_cast<void**>(p), (n ? n : 1) * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dfmnmf_adjoint_create(dfmnmf_adj** out, dfmnmf_ctx* c, int n_iter, int every) {
+  if (!out || !c) return afail(DFMNMF_EINVAL, "null argument");
+  *out = nullptr;
+  if (n_iter < 0 || every < 1) return afail(DFMNMF_EINVAL, "n_iter >= 0 and every >= 1 required");
+  if (c->precision != DFMNMF_FP32) return afail(DFMNMF_EINVAL, "the adjoint differentiates the FP32 form");
+  if (c->MK < 1 || c->MK > 4) return afail(DFMNMF_EINVAL, "the adjoint supports subarrays of 1 to 4 microphones");
+  if (cudaSetDevice(c->device) != cudaSuccess) return afail(DFMNMF_ECUDA, "cudaSetDevice failed");
+  dfmnmf_adj* a = new dfmnmf_adj();
+  a->c = c;
+  a->n_iter = n_iter;
+  a->every = every;
+  a->device = c->device;
+  a->n_ckpt = n_iter > 0 ? (n_iter + every - 1) / every : 0;
+  const dfm::Dims d = dfm::dims_of(c);
+  const size_t nck = (size_t)(a->n_ckpt > 0 ? a->n_ckpt : 1), nsg = (size_t)every;
+  const size_t nmax = std::max(std::max(d.nfb, d.nbt), d.fnm);
+  const bool wien = true;
+  bool ok = aalloc(&a->ckQ, nck * q_n(c)) && aalloc(&a->ckW, nck * w_n(c)) && aalloc(&a->ckH, nck * h_n(c)) &&
+            aalloc(&a->ckg, nck * g_n(c)) && aalloc(&a->sgQ, nsg * q_n(c)) && aalloc(&a->sgW, nsg * w_n(c)) &&
+            aalloc(&a->sgH, nsg * h_n(c)) && aalloc(&a->sgg, nsg * g_n(c)) && aalloc(&a->fnQ, q_n(c)) &&
+            aalloc(&a->fnW, w_n(c)) && aalloc(&a->fnH, h_n(c)) && aalloc(&a->fng, g_n(c)) &&
+            aalloc(&a->Wd, d.nfb) && aalloc(&a->Hd, d.nbt) && aalloc(&a->gd, d.fnm) && aalloc(&a->Qd, d.nq) &&
+            aalloc(&a->lam0, d.nft) && aalloc(&a->lam1, d.nft) && aalloc(&a->lam2, d.nft) &&
+            aalloc(&a->y0, d.ftm) && aalloc(&a->y1, d.ftm) && aalloc(&a->y2, d.ftm) && aalloc(&a->P, d.ftm) &&
+            aalloc(&a->A0, d.nft) && aalloc(&a->D0, d.nft) && aalloc(&a->A1, d.nft) && aalloc(&a->D1, d.nft) &&
+            aalloc(&a->numW, d.nfb) && aalloc(&a->denW, d.nfb) && aalloc(&a->W1, d.nfb) &&
+            aalloc(&a->numH, d.nbt) && aalloc(&a->denH, d.nbt) && aalloc(&a->H1, d.nbt) &&
+            aalloc(&a->numG, d.fnm) && aalloc(&a->denG, d.fnm) && aalloc(&a->V, d.nv) && aalloc(&a->Qs, d.nqs) &&
+            aalloc(&a->Qb, d.nq) && aalloc(&a->Qb1, d.nq) && aalloc(&a->Wb, d.nfb) && aalloc(&a->Wb1, d.nfb) &&
+            aalloc(&a->Hb, d.nbt) && aalloc(&a->Hb1, d.nbt) && aalloc(&a->gb, d.fnm) && aalloc(&a->gb1, d.fnm) &&
+            aalloc(&a->lamb, d.nft) && aalloc(&a->yb, d.ftm) && aalloc(&a->Pb, d.ftm) && aalloc(&a->Ab, d.nft) &&
+            aalloc(&a->Db, d.nft) && aalloc(&a->nb, nmax) && aalloc(&a->db, nmax) && aalloc(&a->Vb, d.nv) &&
+            aalloc(&a->Binv, d.nq) && (!wien || (aalloc(&a->ubar, d.nftm) && aalloc(&a->cvec, d.nftm) &&
+                                                 aalloc(&a->zbar, d.ftm) && aalloc(&a->G4, d.nftm))) &&
+            aalloc(&a->red, 1) && aalloc(&a->flags, 4);
+  if (!ok) {
+    free_adj(a);
+    return afail(DFMNMF_ENOMEM, "device allocation of the adjoint workspace failed");
+  }
+  *out = a;
+  return DFMNMF_OK;
+}
+
+int dfmnmf_adjoint_run(dfmnmf_adj* a, int loss, const void* c_true, double* loss_host, void* dQ0, double* dW0,
+                       double* dH0, double* dg0, void* stream) {
+  if (!a) return afail(DFMNMF_EINVAL, "null adjoint");
+  if (loss != DFMNMF_LOSS_NLL && loss != DFMNMF_LOSS_WIENER_MSE) return afail(DFMNMF_EINVAL, "unknown loss %d", loss);
+  if (loss == DFMNMF_LOSS_WIENER_MSE && !c_true) return afail(DFMNMF_EINVAL, "the Wiener loss needs c_true");
+  dfmnmf_ctx* c = a->c;
+  ACK(cudaSetDevice(a->device));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const dfm::Dims d = dfm::dims_of(c);
+  ACK(cudaMemsetAsync(a->flags, 0, 4 * sizeof(unsigned), s));
+  // forward: the context's own iterations, the state stored every `every` iterations
+  for (int i = 0; i < a->n_iter; ++i) {
+    if (i % a->every == 0) {
+      const size_t j = (size_t)(i / a->every);
+      ACK(save_state(c, a->ckQ + j * q_n(c), a->ckW + j * w_n(c), a->ckH + j * h_n(c), a->ckg + j * g_n(c), s));
+    }
+    int r = dfmnmf_iterate(c, 1, stream);
+    if (r) return r;
+  }
+  ACK(save_state(c, a->fnQ, a->fnW, a->fnH, a->fng, s));
+  // loss of the final state and its adjoint
+  ACK(dfm::load_state(a, d, a->fnQ, a->fnW, a->fnH, a->fng, s));
+  ACK(dfm::loss_and_adjoint(a, d, loss, reinterpret_cast<const float2*>(c_true), s));
+  // reverse sweep, one segment per checkpoint, recomputing the segment's states
+  for (int j = a->n_ckpt - 1; j >= 0; --j) {
+    const int i0 = j * a->every, len = std::min(a->every, a->n_iter - i0);
+    ACK(cudaMemcpyAsync(a->sgQ, a->ckQ + (size_t)j * q_n(c), q_n(c) * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    ACK(cudaMemcpyAsync(a->sgW, a->ckW + (size_t)j * w_n(c), w_n(c) * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    ACK(cudaMemcpyAsync(a->sgH, a->ckH + (size_t)j * h_n(c), h_n(c) * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    ACK(cudaMemcpyAsync(a->sgg, a->ckg + (size_t)j * g_n(c), g_n(c) * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    if (len > 1) {
+      ACK(restore_state(c, a->sgQ, a->sgW, a->sgH, a->sgg, s));
+      for (int i = 1; i < len; ++i) {
+        int r = dfmnmf_iterate(c, 1, stream);
+        if (r) return r;
+        ACK(save_state(c, a->sgQ + (size_t)i * q_n(c), a->sgW + (size_t)i * w_n(c), a->sgH + (size_t)i * h_n(c),
+                       a->sgg + (size_t)i * g_n(c), s));
+      }
+    }
+    for (int i = len - 1; i >= 0; --i) {
+      std::swap(a->Qb, a->Qb1);
+      std::swap(a->Wb, a->Wb1);
+      std::swap(a->Hb, a->Hb1);
+      std::swap(a->gb, a->gb1);
+      ACK(dfm::load_state(a, d, a->sgQ + (size_t)i * q_n(c), a->sgW + (size_t)i * w_n(c),
+                          a->sgH + (size_t)i * h_n(c), a->sgg + (size_t)i * g_n(c), s));
+      ACK(dfm::reverse_iteration(a, d, s));
+    }
+  }
+  // the context ends at the final state, as after dfmnmf_iterate(n_iter)
+  ACK(restore_state(c, a->fnQ, a->fnW, a->fnH, a->fng, s));
+  if (dQ0) ACK(cudaMemcpyAsync(dQ0, a->Qb, d.nq * sizeof(double2), cudaMemcpyDefault, s));
+  if (dW0) ACK(cudaMemcpyAsync(dW0, a->Wb, d.nfb * sizeof(double), cudaMemcpyDefault, s));
+  if (dH0) ACK(cudaMemcpyAsync(dH0, a->Hb, d.nbt * sizeof(double), cudaMemcpyDefault, s));
+  if (dg0) ACK(cudaMemcpyAsync(dg0, a->gb, d.fnm * sizeof(double), cudaMemcpyDefault, s));
+  double L = 0.0;
+  unsigned fl[4], cf[dfm::FLAG_COUNT];
+  ACK(cudaMemcpyAsync(&L, a->red, sizeof(double), cudaMemcpyDeviceToHost, s));
+  ACK(cudaMemcpyAsync(fl, a->flags, sizeof fl, cudaMemcpyDeviceToHost, s));
+  ACK(cudaMemcpyAsync(cf, c->flags, sizeof cf, cudaMemcpyDeviceToHost, s));
+  ACK(cudaStreamSynchronize(s));
+  if (loss_host) *loss_host = L;
+  if (fl[0]) return afail(DFMNMF_ENUMERIC, "a system of the IP update was singular: the gradient is not defined");
+  if (cf[dfm::FLAG_NONFINITE] || !(L == L) || L > 1e308 || L < -1e308)
+    return afail(DFMNMF_ENUMERIC, "a non-finite value was produced");
+  return DFMNMF_OK;
+}
+
+void dfmnmf_adjoint_destroy(dfmnmf_adj* a) {
+  if (!a) return;
+  cudaSetDevice(a->device);
+  cudaDeviceSynchronize();
+  free_adj(a);
+}
+
+}  // extern "C"

@@ -23,6 +23,7 @@ DFMNMF_FP32, DFMNMF_BF16_TC, DFMNMF_TF32_TC = 0, 1, 2
 DFMNMF_IP_F64, DFMNMF_IP_F32X2, DFMNMF_IP_F32 = 0, 1, 2
 DFMNMF_STAGE_COV, DFMNMF_STAGE_IP, DFMNMF_STAGE_W, DFMNMF_STAGE_H, DFMNMF_STAGE_G = 1, 2, 3, 4, 5
 DFMNMF_BUF_V, DFMNMF_BUF_P, DFMNMF_BUF_LAMBDA = 1, 2, 3
+DFMNMF_LOSS_NLL, DFMNMF_LOSS_WIENER_MSE = 1, 2
 
 # Every symbol include/dfmnmf.h declares.
 EXPORTED = ("dfmnmf_init", "dfmnmf_set_observation", "dfmnmf_iterate", "dfmnmf_run_stage",
@@ -30,7 +31,8 @@ EXPORTED = ("dfmnmf_init", "dfmnmf_set_observation", "dfmnmf_iterate", "dfmnmf_r
             "dfmnmf_get_buffer", "dfmnmf_launches_per_iteration", "dfmnmf_kernel_times", "dfmnmf_destroy",
             "dfmnmf_last_error", "dfmnmf_version", "dfmnmf_loglik_noalloc", "dfmnmf_autotune",
             "dfmnmf_cost_gradient", "dfmnmf_init_from_images",
-            "dfmnmf_batch_create", "dfmnmf_batch_iterate", "dfmnmf_batch_destroy")
+            "dfmnmf_batch_create", "dfmnmf_batch_iterate", "dfmnmf_batch_destroy",
+            "dfmnmf_adjoint_create", "dfmnmf_adjoint_run", "dfmnmf_adjoint_destroy")
 
 
 class DfmnmfError(RuntimeError):
@@ -81,6 +83,9 @@ def load_library(path: Optional[str] = None):
         "dfmnmf_batch_create": (ci, [ctypes.POINTER(vp), ctypes.POINTER(vp), ci]),
         "dfmnmf_batch_iterate": (ci, [vp, ci, vp]),
         "dfmnmf_batch_destroy": (None, [vp]),
+        "dfmnmf_adjoint_create": (ci, [ctypes.POINTER(vp), vp, ci, ci]),
+        "dfmnmf_adjoint_run": (ci, [vp, ci, vp, ctypes.POINTER(cd), vp, vp, vp, vp, vp]),
+        "dfmnmf_adjoint_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -282,6 +287,44 @@ def dfmnmf_batch_destroy(batch: Batch):
     if batch.handle is not None and batch.handle.value:
         load_library().dfmnmf_batch_destroy(batch.handle)
         batch.handle = ctypes.c_void_p()
+
+
+class Adjoint:
+    """Owns one dfmnmf_adj* (reverse pass through unrolled iterations); keeps its context alive."""
+
+    def __init__(self, handle, ctx, n_iter, every):
+        self.handle, self.ctx, self.n_iter, self.every = handle, ctx, n_iter, every
+
+    def __del__(self):
+        try:
+            dfmnmf_adjoint_destroy(self)
+        except Exception:  # pragma: no cover
+            pass
+
+
+def dfmnmf_adjoint_create(ctx: Context, n_iter: int, every: int = 5) -> Adjoint:
+    h = ctypes.c_void_p()
+    _check(load_library().dfmnmf_adjoint_create(ctypes.byref(h), ctx.handle, int(n_iter), int(every)))
+    return Adjoint(h, ctx, int(n_iter), int(every))
+
+
+def dfmnmf_adjoint_run(adj: Adjoint, loss: int = DFMNMF_LOSS_NLL, c_true=None, dQ0=None, dW0=None, dH0=None,
+                       dg0=None, stream=None) -> float:
+    """Runs adj.n_iter iterations from the context's state and writes the gradient of the loss of the
+    final state with respect to the initial one (float64 arrays, complex128 for Q); returns the loss."""
+    import torch
+    f64 = (torch.float64, np.float64)
+    v = ctypes.c_double()
+    _check(load_library().dfmnmf_adjoint_run(adj.handle, int(loss), _ptr(c_true, _dt("c64")), ctypes.byref(v),
+                                             _ptr(dQ0, _dt("c128")), _ptr(dW0, f64), _ptr(dH0, f64),
+                                             _ptr(dg0, f64), _stream(stream)))
+    return v.value
+
+
+def dfmnmf_adjoint_destroy(adj: Adjoint):
+    if adj.handle is not None and adj.handle.value:
+        load_library().dfmnmf_adjoint_destroy(adj.handle)
+        adj.handle = ctypes.c_void_p()
 
 
 def dfmnmf_version() -> int:
