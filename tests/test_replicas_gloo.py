@@ -30,7 +30,7 @@ def _worker(rank, world, port, out):
 
 def test_ranks_take_the_slowest_rank_and_count_every_replica():
     world, port = 2, 29517
-    with mp.Manager() as man:
+    with mp.get_context("spawn").Manager() as man:
         out = man.dict()
         mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
