@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip the gradient through 20 unrolled iterations (4 x 4 mics, N = 5, F = 257, T = 313)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--batched", type=int, default=64,
                     help="also time this many mixtures of mixed length and layout (T in [150, 1250], K in {2, 4, 8} "
@@ -261,6 +263,48 @@ def reference_arm(args, rank, world):
         "gpu_launches": 0,
     }
     print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------- gradient through unrolled iterations
+def adjoint_measurement(D, synth, torch, timed):
+    """Reverse pass through 20 iterations of the FP32 form, checkpoints every 5, on 4 x 4 mics, N = 5,
+    B = 16, F = 257, T = 313 (seeded), for Eq. 12 and for the Wiener-filter MSE against the seeded images.
+    Each timed gradient runs the 20 forward iterations, the loss, the reverse sweep with its
+    recomputation, and copies the gradients to device arrays; the forward alone (the state reset and
+    20 iterations) is timed beside it."""
+    import numpy as np
+    p = synth.make_problem(257, 313, (4, 4, 4, 4), 5, 16, seed=27, with_images=True)
+    dev = torch.device("cuda")
+    x, W0, H0, g0 = (torch.from_numpy(a).to(dev) for a in (p.x, p.W0, p.H0, p.g0))
+    Q0 = torch.from_numpy(p.Q0).to(dev)
+    ct = torch.from_numpy(p.c).to(dev)
+    ctx = D.dfmnmf_init(p.F, p.T, p.mics, p.N, p.B, x, W0, H0, g0, Q0)
+    adj = D.dfmnmf_adjoint_create(ctx, 20, 5)
+    dQ = torch.empty_like(Q0)
+    dW, dH, dg = (torch.empty(a.shape, dtype=torch.float64, device=dev) for a in (W0, H0, g0))
+    out = {"workload": "diff_4x4_n5_f257_t313", "n_iter": 20, "every": 5, "form": "fp32",
+           "note": "ms_per_gradient: forward iterations + loss + reverse sweep with segment recomputation; "
+                   "forward_ms: state reset + the same 20 iterations"}
+
+    def fwd(_):
+        D.dfmnmf_set_params(ctx, Q0, W0, H0, g0)
+        D.dfmnmf_iterate(ctx, 20)
+
+    for name, code in (("nll", D.DFMNMF_LOSS_NLL), ("wiener_mse", D.DFMNMF_LOSS_WIENER_MSE)):
+        def grad(_):
+            D.dfmnmf_set_params(ctx, Q0, W0, H0, g0)
+            D.dfmnmf_adjoint_run(adj, code, ct if code == D.DFMNMF_LOSS_WIENER_MSE else None, dQ, dW, dH, dg)
+
+        for _ in range(2):
+            grad(None)
+        out[name] = {"ms_per_gradient": timed(grad, None, 5) / 5}
+    for _ in range(2):
+        fwd(None)
+    out["forward_ms"] = timed(fwd, None, 5) / 5
+    out["nll"]["ratio_to_forward"] = out["nll"]["ms_per_gradient"] / out["forward_ms"]
+    D.dfmnmf_adjoint_destroy(adj)
+    D.dfmnmf_destroy(ctx)
+    return out
 
 
 # ----------------------------------------------------------- batched form
@@ -568,6 +612,9 @@ def main():
     # many mixtures of uneven length and layout, one graph launch per iteration, launch shapes autotuned
     if args.batched > 0 and world == 1:
         out["batched"] = batched_measurement(args, D, synth, torch, dev, timed, precisions[forms[0]], ip)
+
+    if not args.no_adjoint and world == 1:
+        out["adjoint"] = adjoint_measurement(D, synth, torch, timed)
 
     # variants on the same GPU: native-FP64 and plain-FP32 IP solves (FP32 form)
     if not args.no_variants:

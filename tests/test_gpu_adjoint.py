@@ -119,8 +119,9 @@ def test_block_sizes(mics):
 
 
 def test_checkpoint_interval_does_not_change_the_result():
-    """Recomputed segments replay the same deterministic iterations: bit-identical gradients,
-    and the context ends where dfmnmf_iterate would leave it."""
+    """Recomputed segments replay the same deterministic iterations: bit-identical gradients
+    (the loss value itself is summed across blocks with atomics, so only its last bits may
+    move), and the context ends where dfmnmf_iterate would leave it."""
     p, Q0, ctx, st = setup(9, 40, (4, 4), 5, 4, seed=23)
     ref = None
     for every in (1, 3, 7, 10):
@@ -134,7 +135,7 @@ def test_checkpoint_interval_does_not_change_the_result():
             for a, b in zip(state, D.params_numpy(ctx2)):
                 np.testing.assert_array_equal(a, b)
             continue
-        assert got[0] == ref[0]
+        assert abs(got[0] - ref[0]) <= 1e-14 * abs(ref[0])  # the loss sums blocks with atomics
         for a, b in zip(got[1] + list(got[2:]), ref[1] + list(ref[2:])):
             np.testing.assert_array_equal(a, b)
 
