@@ -80,6 +80,9 @@ cudaError_t launch_stats(const dfmnmf_ctx* c, cudaStream_t s);        // A/D fro
 cudaError_t launch_hupd(const dfmnmf_ctx* c, cudaStream_t s, float* grad = nullptr);  // Eq. 9
 cudaError_t launch_gupd(const dfmnmf_ctx* c, cudaStream_t s, float* grad = nullptr);  // Eq. 10
 cudaError_t launch_power_stats_comp(const dfmnmf_ctx* c, cudaStream_t s);  // P (compensated) + A/D, band-wide
+// P + A/D with TMA tiles (4 subarrays of 4 microphones, N <= 16); comp: compensated projections
+bool pstats_tma_supported(int K, int MK, int N);
+cudaError_t launch_pstats_tma(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc, bool comp);
 cudaError_t launch_qgrad(const dfmnmf_ctx* c, double2* dQ, cudaStream_t s);  // d Eq. 12 / d Q from V and Q
 cudaError_t launch_loglik(const dfmnmf_ctx* c, cudaStream_t s);       // Eq. 12 -> c->nll_dev
 cudaError_t launch_logdet(const dfmnmf_ctx* c, double* out, cudaStream_t s);  // ln|det Q_fk|^2 per block

@@ -289,10 +289,24 @@ __global__ void __launch_bounds__(128) k_pstats_ft(const float2* __restrict__ x,
         for (int m = 0; m < M; ++m) pv[m] = Pt[m];
       }
     }
+    // the lambda of up to LAM_R sources are requested together (one memory
+    // latency instead of one per source); more sources follow in a loop
+    constexpr int LAM_R = 8;
+    float lv[LAM_R];
+#pragma unroll
+    for (int n = 0; n < LAM_R; ++n) lv[n] = n < N ? __ldg(lt + (size_t)n * F * Tp + t) : 0.f;
     float ys[M];
 #pragma unroll
     for (int m = 0; m < M; ++m) ys[m] = 0.f;
-    for (int n = 0; n < N; ++n) {
+#pragma unroll
+    for (int n = 0; n < LAM_R; ++n) {
+      if (n < N) {
+        const float* gr = gs + n * M;
+#pragma unroll
+        for (int m = 0; m < M; ++m) ys[m] = fmaf(lv[n], gr[m], ys[m]);
+      }
+    }
+    for (int n = LAM_R; n < N; ++n) {
       const float l = __ldg(lt + (size_t)n * F * Tp + t);
       const float* gr = gs + n * M;
 #pragma unroll
@@ -545,6 +559,7 @@ static cudaError_t launch_pstats_ft(const dfmnmf_ctx* c, cudaStream_t s, int fb,
 
 template <bool COMPUTE_P, bool COMP>
 static cudaError_t launch_pstats_impl(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
+  if (COMPUTE_P && pstats_tma_supported(c->K, c->MK, c->N)) return launch_pstats_tma(c, s, fb, fc, COMP);
   if (c->MK == 4 && c->K == 4) return launch_pstats_ft<4, 4, COMPUTE_P, COMP>(c, s, fb, fc);
   if (c->MK == 4 && c->K == 2) return launch_pstats_ft<2, 4, COMPUTE_P, COMP>(c, s, fb, fc);
   if (c->MK == 4 && c->K == 1) return launch_pstats_ft<1, 4, COMPUTE_P, COMP>(c, s, fb, fc);

@@ -341,6 +341,146 @@ __global__ void __launch_bounds__(128, 2) k_vtc(const __grid_constant__ CUtensor
   }
 }
 
+// ------------------------------------------------- projections and MU statistics through TMA
+// P = |Q x|^2 and the MU statistics A = sum_m g P / yhat^2, D = sum_m g / yhat
+// for 4 subarrays of 4 microphones, one CTA per (frequency, 128 frames).
+// Thread 0 brings the x tile (128 frames x 16 complex, 16 KB, 128-byte
+// swizzle) and the lambda rows of every source (N x 512 B) into shared memory
+// with two tensor copies on one mbarrier; every thread reads its frame's row
+// with the swizzle undone (16-byte chunk c of row i sits at chunk c ^ (i % 8),
+// so the eight rows of a quarter-warp hit eight different bank groups); P is
+// staged in shared memory with a 64-byte swizzle (chunk c of row i at
+// c ^ ((i / 2) % 4)) and written back by one tensor store, which clips the
+// frames past T; A and D are stored directly (consecutive frames per warp).
+constexpr int PT_ROWS = 128;
+constexpr int PT_X_BYTES = PT_ROWS * 128;  // 16 complex64 per frame
+constexpr int PT_P_BYTES = PT_ROWS * 64;   // 16 float per frame
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, int c0, int c1, int c2, const void* src) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                   reinterpret_cast<unsigned long long>(map)),
+               "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(src))
+               : "memory");
+}
+
+template <bool COMP>
+__global__ void __launch_bounds__(128) k_pstats_tma(const __grid_constant__ CUtensorMap map_x,
+                                                    const __grid_constant__ CUtensorMap map_l,
+                                                    const __grid_constant__ CUtensorMap map_p,
+                                                    const double2* __restrict__ Q64, const float* __restrict__ g,
+                                                    float* __restrict__ A, float* __restrict__ D, int F, int T,
+                                                    int Tp, int N, float eps, int fb, unsigned* __restrict__ flags) {
+  constexpr int K = 4, MK = 4, M = 16;
+  extern __shared__ __align__(16) unsigned char pt_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(pt_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* xs = base;                                    // [128][128 B], 128-byte swizzle
+  unsigned char* ps = base + PT_X_BYTES;                       // [128][64 B], 64-byte swizzle
+  float* ls = reinterpret_cast<float*>(ps + PT_P_BYTES);       // [N][128]
+  float* gs = ls + N * PT_ROWS;                                // [N][M]
+  float2* Qh = reinterpret_cast<float2*>(gs + ((N * M + 3) & ~3));  // [K][MK][MK]
+  float2* Ql = Qh + K * MK * MK;
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(Ql + K * MK * MK);
+  const int f = fb + blockIdx.x, tid = threadIdx.x, t0 = blockIdx.y * PT_ROWS;
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_arrive_expect_tx(bar, (unsigned)(PT_X_BYTES + N * PT_ROWS * 4));
+    tma_load_3d(xs, &map_x, 0, t0, f, bar);
+    tma_load_3d(ls, &map_l, t0, f, 0, bar);
+  }
+  for (int i = tid; i < N * M; i += blockDim.x) gs[i] = g[(size_t)f * N * M + i];
+  for (int i = tid; i < K * MK * MK; i += blockDim.x) split_c(Q64[(size_t)f * K * MK * MK + i], Qh[i], Ql[i]);
+  __syncthreads();
+  if (!mbar_wait(bar, 0)) {  // the copies did not arrive within the budget: report, skip the tile
+    if (tid == 0) atomicOr(flags + FLAG_TIMEOUT, 1u);
+    return;
+  }
+  const int i = tid, t = t0 + i;
+  float pv[M];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    float2 xv[MK];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int c = 2 * k + h;
+      const float4 q = *reinterpret_cast<const float4*>(xs + i * 128 + ((c ^ (i & 7)) << 4));
+      xv[2 * h] = make_float2(q.x, q.y);
+      xv[2 * h + 1] = make_float2(q.z, q.w);
+    }
+#pragma unroll
+    for (int mu = 0; mu < MK; ++mu) {
+      const float2* qh = Qh + (k * MK + mu) * MK;
+      float2 y;
+      if (COMP) {
+        y = cdot2<MK>(qh, Ql + (k * MK + mu) * MK, xv);
+      } else {
+        float yr = 0.f, yi = 0.f;
+#pragma unroll
+        for (int nu = 0; nu < MK; ++nu) {
+          yr = fmaf(qh[nu].x, xv[nu].x, fmaf(-qh[nu].y, xv[nu].y, yr));
+          yi = fmaf(qh[nu].x, xv[nu].y, fmaf(qh[nu].y, xv[nu].x, yi));
+        }
+        y = make_float2(yr, yi);
+      }
+      pv[k * MK + mu] = fmaf(y.x, y.x, y.y * y.y);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+    *reinterpret_cast<float4*>(ps + i * 64 + ((c ^ ((i >> 1) & 3)) << 4)) =
+        make_float4(pv[4 * c], pv[4 * c + 1], pv[4 * c + 2], pv[4 * c + 3]);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  if (tid == 0) {
+    tma_store_3d(&map_p, 0, t0, f, ps);
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+  }
+  float ys[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) ys[m] = 0.f;
+  for (int n = 0; n < N; ++n) {
+    const float l = ls[n * PT_ROWS + i];
+    const float* gr = gs + n * M;
+#pragma unroll
+    for (int m = 0; m < M; ++m) ys[m] = fmaf(l, gr[m], ys[m]);
+  }
+  float w[M], u[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    w[m] = fast_rcp(fmaxf(ys[m], eps));
+    u[m] = pv[m] * w[m] * w[m];
+  }
+  if (t < T)
+    for (int n = 0; n < N; ++n) {
+      const float* gr = gs + n * M;
+      float a = 0.f, d = 0.f;
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        a = fmaf(gr[m], u[m], a);
+        d = fmaf(gr[m], w[m], d);
+      }
+      const size_t o = ((size_t)n * F + f) * Tp + t;
+      A[o] = a;
+      D[o] = d;
+    }
+  if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // ps is read before the CTA exits
+}
+
+bool pstats_tma_supported(int K, int MK, int N) { return K == 4 && MK == 4 && N >= 1 && N <= 16; }
+
+static size_t pstats_tma_smem(int N) {
+  return 1024 + PT_X_BYTES + PT_P_BYTES + (size_t)N * PT_ROWS * 4 + (size_t)((N * 16 + 3) & ~3) * 4 +
+         2 * 4 * 16 * sizeof(float2) + 16;
+}
+
 // ------------------------------------------------------------- host side
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -412,6 +552,51 @@ cudaError_t launch_wprep(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
     default: DFM_WPREP(16); break;
   }
 #undef DFM_WPREP
+  return cudaGetLastError();
+}
+
+// x as floats [F][T][2M] (boxes of 128 frames x 32 floats, 128-byte swizzle),
+// lambda [N][F][Tp] (boxes of 128 frames x 1 frequency x N sources), P
+// [F][T][M] (boxes of 128 frames x 16 floats, 64-byte swizzle).  Frames past
+// T (or Tp) read as zeros and are not written.  The maps are encoded at
+// launch and passed by value, so a captured graph keeps them.
+cudaError_t launch_pstats_tma(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc, bool comp) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || !pstats_tma_supported(c->K, c->MK, c->N)) return cudaErrorNotSupported;
+  CUtensorMap mx, ml, mp;
+  const cuuint32_t e3[3] = {1, 1, 1};
+  {
+    const cuuint64_t dims[3] = {32, (cuuint64_t)c->T, (cuuint64_t)c->F};
+    const cuuint64_t str[2] = {128, (cuuint64_t)c->T * 128};
+    const cuuint32_t box[3] = {32, PT_ROWS, 1};
+    if (fn(&mx, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->x, dims, str, box, e3, CU_TENSOR_MAP_INTERLEAVE_NONE,
+           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  {
+    const cuuint64_t dims[3] = {(cuuint64_t)c->Tp, (cuuint64_t)c->F, (cuuint64_t)c->N};
+    const cuuint64_t str[2] = {(cuuint64_t)c->Tp * 4, (cuuint64_t)c->F * c->Tp * 4};
+    const cuuint32_t box[3] = {PT_ROWS, 1, (cuuint32_t)c->N};
+    if (fn(&ml, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->lam, dims, str, box, e3, CU_TENSOR_MAP_INTERLEAVE_NONE,
+           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  {
+    const cuuint64_t dims[3] = {16, (cuuint64_t)c->T, (cuuint64_t)c->F};
+    const cuuint64_t str[2] = {64, (cuuint64_t)c->T * 64};
+    const cuuint32_t box[3] = {16, PT_ROWS, 1};
+    if (fn(&mp, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->P, dims, str, box, e3, CU_TENSOR_MAP_INTERLEAVE_NONE,
+           CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  const size_t sm = pstats_tma_smem(c->N);
+  auto kern = comp ? k_pstats_tma<true> : k_pstats_tma<false>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  dim3 grid(fc, (c->T + PT_ROWS - 1) / PT_ROWS);
+  kern<<<grid, 128, sm, s>>>(mx, ml, mp, c->Q64, c->g, c->A, c->D, c->F, c->T, c->Tp, c->N, c->eps, fb, c->flags);
   return cudaGetLastError();
 }
 
