@@ -18,6 +18,8 @@
 //
 // The arithmetic type R is a template parameter: IEEE double, float-float
 // pairs (dfm::dd) or float.
+#include <type_traits>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -110,6 +112,7 @@ __global__ void __launch_bounds__(128) k_ip(const double2* __restrict__ V, const
                                             float2* __restrict__ Q32, int nblocks, float eps, float rtol,
                                             unsigned* __restrict__ flags) {
   using O = RealOps<R>;
+  constexpr bool MIXED = std::is_same<R, dd>::value && (MK == 2 || MK == 4);
   constexpr int E = MK * MK;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int seg = lane >> 4, e = lane & 15, sb = seg << 4;
@@ -142,6 +145,84 @@ __global__ void __launch_bounds__(128) k_ip(const double2* __restrict__ V, const
     float maxabs = act ? sqrtf(cabs2_f(a)) : 0.f;
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1) maxabs = fmaxf(maxabs, __shfl_xor_sync(DFM_FULL_MASK, maxabs, o));
+    cx<R> qi;
+    bool solved = false;
+    if constexpr (MIXED) {
+      // 2a. Mixed precision: Gauss-Jordan in single precision on [A | I] gives an
+      // approximate inverse X (lane (i, j) ends with X_ij); three refinement
+      // steps q <- q + X (e_mu - A q), the residual formed in float pairs from
+      // the float-pair A, converge to the float-pair solution when cond(A) u is
+      // small.  Taken only when every block of the warp has its smallest single
+      // precision pivot above 1e-5 max|A_ij| (far from the singular threshold,
+      // so the pseudo-inverse decision cannot differ) and its last correction
+      // below 1e-9 |q|; otherwise the warp redoes the solve in float pairs.
+      cx<float> af = cmake(O::to_f(a.re), O::to_f(a.im));
+      cx<float> xf = cmake((act && i == j) ? 1.f : 0.f, 0.f);
+      float mpf = INFINITY;
+#pragma unroll
+      for (int c = 0; c < MK; ++c) {
+        float key = (act && j == c && i >= c) ? cabs2_f(af) : -1.f;
+        int prow = i;
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+          const float ok = __shfl_xor_sync(DFM_FULL_MASK, key, o);
+          const int orow = __shfl_xor_sync(DFM_FULL_MASK, prow, o);
+          if (ok > key || (ok == key && orow < prow)) {
+            key = ok;
+            prow = orow;
+          }
+        }
+        int src = lane;
+        if (act && i == c) src = L(prow, j);
+        else if (act && i == prow) src = L(c, j);
+        af = cshfl(af, src);
+        xf = cshfl(xf, src);
+        const cx<float> piv = cshfl(af, L(c, c));
+        mpf = fminf(mpf, sqrtf(cabs2_f(piv)));
+        const cx<float> inv = crecip(piv);
+        const cx<float> rowc = cmul(cshfl(af, L(c, j)), inv);
+        const cx<float> xc = cmul(cshfl(xf, L(c, j)), inv);
+        const cx<float> m = cshfl(af, L(i, c));
+        if (i == c) {
+          af = rowc;
+          xf = xc;
+        } else {
+          af = csub(af, cmul(m, rowc));
+          xf = csub(xf, cmul(m, xc));
+        }
+      }
+      if (__all_sync(DFM_FULL_MASK, mpf > 1e-5f * maxabs)) {
+        const cx<float> x0 = cshfl(xf, L(i, mu));
+        cx<R> q = cmake(O::from_f(x0.re), O::from_f(x0.im));
+        float dlast = 0.f;
+#pragma unroll
+        for (int it = 0; it < 3; ++it) {
+          const cx<R> qj = cshfl(q, L(j, 0));
+          cx<R> t = cmul(a, qj);
+#pragma unroll
+          for (int o = 1; o < MK; o <<= 1) t = cadd(t, cmake(O::shfl_xor(t.re, o), O::shfl_xor(t.im, o)));
+          const cx<R> r = csub((i == mu) ? cmake(O::one(), O::zero()) : czero<R>(), t);
+          const cx<float> rj = cshfl(cmake(O::to_f(r.re), O::to_f(r.im)), L(j, 0));
+          cx<float> d = cmul(xf, rj);
+#pragma unroll
+          for (int o = 1; o < MK; o <<= 1)
+            d = cadd(d, cmake(__shfl_xor_sync(DFM_FULL_MASK, d.re, o), __shfl_xor_sync(DFM_FULL_MASK, d.im, o)));
+          q = cadd(q, cmake(O::from_f(d.re), O::from_f(d.im)));
+          dlast = act ? sqrtf(cabs2_f(d)) : 0.f;
+        }
+        float qmax = act ? sqrtf(cabs2_f(q)) : 0.f;
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+          dlast = fmaxf(dlast, __shfl_xor_sync(DFM_FULL_MASK, dlast, o));
+          qmax = fmaxf(qmax, __shfl_xor_sync(DFM_FULL_MASK, qmax, o));
+        }
+        if (__all_sync(DFM_FULL_MASK, dlast <= 1e-9f * qmax)) {
+          qi = q;
+          solved = true;
+        }
+      }
+    }
+    if (!solved) {
     cx<R> b = (act && i == mu) ? cmake(O::one(), O::zero()) : czero<R>();
     float minpiv = INFINITY;
     // 2. Gauss-Jordan with partial pivoting
@@ -178,7 +259,7 @@ __global__ void __launch_bounds__(128) k_ip(const double2* __restrict__ V, const
       }
     }
     const bool singular = !(minpiv > rtol * maxabs);
-    cx<R> qi = b;
+    qi = b;
     if (singular) {
       if (e == 0 && valid) {
         cx<double> U[MK][MK], q[MK];
@@ -200,6 +281,7 @@ __global__ void __launch_bounds__(128) k_ip(const double2* __restrict__ V, const
       }
       __syncwarp(segmask);
       qi = cfrom_d2<R>(make_double2(qfb[warp][seg][i].re, qfb[warp][seg][i].im));
+    }
     }
     // 3. normalisation (Eq. 15) and row update
     const cx<R> qj = cshfl(qi, L(j, 0));
