@@ -147,7 +147,8 @@ def kernel_bytes(F, T, M, N, B, K, MK):
 
 
 # DRAM bytes (read + write) of one band-wide launch, from the full-section ncu
-# captures summarised in profiles/kernels_paper_4x4_n5_{bf16tc,fp32}.md
+# captures summarised in profiles/kernels_paper_4x4_n5_{bf16tc,fp32}.md and
+# profiles/k_pstats_tma_paper_4x4_n5.md
 # (band-wide launches: the autotuned launch shapes of that run put the
 # per-frequency kernels on one graph branch).  A figure holds only while the
 # kernel's sources are the ones captured: the digest is the first 16 hex
@@ -155,18 +156,55 @@ def kernel_bytes(F, T, M, N, B, K, MK):
 # `traffic` is null when it no longer matches.
 NCU_TRAFFIC = {
     "paper_4x4_n5": {
-        "k_pstats": (48274176 + 1566208, "kernels_model.cu", "a8d43ada86df4c94"),
-        "k_stats": (27177472 + 0, "kernels_model.cu", "a8d43ada86df4c94"),
-        "k_gupd": (27193856 + 0, "kernels_model.cu", "a8d43ada86df4c94"),
-        "k_lambda": (388608 + 0, "kernels_model.cu", "a8d43ada86df4c94"),
-        "k_vtc": (105086208 + 3507712, "kernels_tc.cu", "2e9762d109f23b05"),
-        "k_wprep": (6620416 + 0, "kernels_tc.cu", "2e9762d109f23b05"),
-        "k_ip": (2701824 + 0, "kernels_ip.cu", "26a449bc4878cf7f"),
-        "k_wupd": (13269248 + 0, "kernels_nmf.cu", "6650377c1ec65ff1"),
-        "k_hupd": (13270784 + 0, "kernels_nmf.cu", "6650377c1ec65ff1"),
-        "k_cov": (47757312 + 17920, "kernels_cov.cu", "b3f20ec38d0c0d8f"),
+        "k_pstats": (48278016 + 2411264, "kernels_tc.cu", "377d4027f74bd128"),  # k_pstats_tma
+        "k_stats": (27180800 + 512, "kernels_model.cu", "055798c598a0a212"),
+        "k_gupd": (27193600 + 0, "kernels_model.cu", "055798c598a0a212"),
+        "k_lambda": (388352 + 0, "kernels_model.cu", "055798c598a0a212"),
+        "k_vtc": (105085952 + 2994176, "kernels_tc.cu", "377d4027f74bd128"),
+        "k_wprep": (6620416 + 0, "kernels_tc.cu", "377d4027f74bd128"),
+        "k_ip": (2703104 + 0, "kernels_ip.cu", "662ea8729857afc2"),
+        "k_wupd": (13268480 + 0, "kernels_nmf.cu", "115f2802f9bdee8b"),
+        "k_hupd": (13270016 + 0, "kernels_nmf.cu", "115f2802f9bdee8b"),
+        "k_cov": (47757312 + 24320, "kernels_cov.cu", "dad4d0b2f3648048"),
     },
 }
+
+
+# Kernels bound by instruction issue (float-pair arithmetic chains), not by
+# HBM: their roofline is the issue rate, 4 warp-instructions per clock per SM
+# (one per scheduler) at the maximum SM clock.  Executed warp instructions of
+# one band-wide launch (smsp__inst_executed.sum of the same captures, with the
+# same digest rule as NCU_TRAFFIC).
+ALU_KERNELS = ("k_ip", "k_cov")
+NCU_INST = {
+    "paper_4x4_n5": {
+        "k_ip": (9149494, "kernels_ip.cu", "662ea8729857afc2"),
+        "k_cov": (56279691, "kernels_cov.cu", "dad4d0b2f3648048"),
+    },
+}
+
+
+def ncu_inst(workload, kernel):
+    import hashlib
+    ent = NCU_INST.get(workload, {}).get(kernel)
+    if ent is None:
+        return None
+    n, src, digest = ent
+    h = hashlib.sha256()
+    for name in (src, "common.cuh", "internal.h"):
+        with open(os.path.join(ROOT, "paper_2605_19388_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return n if h.hexdigest()[:16] == digest else None
+
+
+def issue_peak_ginst(sm_count):
+    """Warp instructions per second, in G: SMs x 4 schedulers x 1 per clock x the maximum SM clock."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            mhz = float(json.load(fh)["sm_max_mhz"])
+    except Exception:
+        mhz = 2070.0
+    return sm_count * 4 * mhz * 1e6 / 1e9, mhz
 
 
 def ncu_traffic(workload, kernel, form):
@@ -496,10 +534,27 @@ def main():
     head = results[forms[0]]
     dom_name, dom_ms = head["dominant"]
     base = lambda n: n.split("#")[0]
-    ach = kb[base(dom_name)] / (dom_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": dom_name, "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "traffic": ncu_traffic(args.workload, base(dom_name), forms[0]), "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
-                "alg_bytes_per_launch": kb[base(dom_name)]}
+
+    def hbm_roofline(name, ms):
+        ach = kb[base(name)] / (ms * 1e-3) / 1e9
+        return {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": ncu_traffic(args.workload, base(name), forms[0]),
+                "peak_kind": f"{peak_kind} hbm_gbs (burst copy)", "alg_bytes_per_launch": kb[base(name)]}
+
+    if base(dom_name) in ALU_KERNELS:
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        ipeak, mhz = issue_peak_ginst(sms)
+        inst = ncu_inst(args.workload, base(dom_name))
+        ach = inst / (dom_ms * 1e-3) / 1e9 if inst else None
+        roofline = {"bound": "alu", "kernel": dom_name, "achieved": ach, "peak": ipeak,
+                    "unit": "G warp-instructions/s", "frac": (ach / ipeak) if ach else None,
+                    "traffic": ncu_traffic(args.workload, base(dom_name), forms[0]),
+                    "peak_kind": f"derived: {sms} SMs x 4 schedulers x 1 warp-instruction/clock x {mhz:.0f} MHz",
+                    "instructions_per_launch": inst}
+    else:
+        roofline = hbm_roofline(dom_name, dom_ms)
+    hbm_kernels = [(n, ms) for n, ms in head["kernels"] if base(n) not in ALU_KERNELS]
+    roofline_hbm = hbm_roofline(*max(hbm_kernels, key=lambda e: e[1]))
 
     def kernel_table(kt, iter_ms, kbf=None):
         kbf = kb if kbf is None else kbf
@@ -521,6 +576,7 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "tf_bin_mic_updates_per_s": F * T * M * head["value"],
         "roofline": roofline,
+        "roofline_hbm": roofline_hbm,
         "iteration": {"ms": head["graph_iter_ms"], "alg_bytes": ib,
                       "GBps": ib / (head["graph_iter_ms"] * 1e-3) / 1e9,
                       "frac_of_hbm_peak": ib / (head["graph_iter_ms"] * 1e-3) / 1e9 / peak,
