@@ -160,9 +160,9 @@ NCU_TRAFFIC = {
         "k_stats": (27180800 + 512, "kernels_model.cu", "055798c598a0a212"),
         "k_gupd": (27193600 + 0, "kernels_model.cu", "055798c598a0a212"),
         "k_lambda": (388352 + 0, "kernels_model.cu", "055798c598a0a212"),
-        "k_vtc": (105085952 + 2994176, "kernels_tc.cu", "377d4027f74bd128"),
+        "k_vtc": (105301248 + 2824960, "kernels_tc.cu", "57539cc9bcff2e66"),
         "k_wprep": (6620416 + 0, "kernels_tc.cu", "377d4027f74bd128"),
-        "k_ip": (2703104 + 0, "kernels_ip.cu", "662ea8729857afc2"),
+        "k_ip": (2702080 + 0, "kernels_ip.cu", "77060888d10b3a1c"),
         "k_wupd": (13268480 + 0, "kernels_nmf.cu", "115f2802f9bdee8b"),
         "k_hupd": (13270016 + 0, "kernels_nmf.cu", "115f2802f9bdee8b"),
         "k_cov": (47757312 + 24320, "kernels_cov.cu", "dad4d0b2f3648048"),
@@ -176,17 +176,17 @@ NCU_TRAFFIC = {
 # one band-wide launch (smsp__inst_executed.sum of the same captures, with the
 # same digest rule as NCU_TRAFFIC).
 ALU_KERNELS = ("k_ip", "k_cov")
-NCU_INST = {
+NCU_INST = {  # keyed by (kernel, form): k_ip refines three times in the FP32 form, once in the tensor-core form
     "paper_4x4_n5": {
-        "k_ip": (9149494, "kernels_ip.cu", "662ea8729857afc2"),
-        "k_cov": (56279691, "kernels_cov.cu", "dad4d0b2f3648048"),
+        ("k_ip", "bf16tc"): (6995412, "kernels_ip.cu", "77060888d10b3a1c"),
+        ("k_cov", "fp32"): (56279691, "kernels_cov.cu", "dad4d0b2f3648048"),
     },
 }
 
 
-def ncu_inst(workload, kernel):
+def ncu_inst(workload, kernel, form):
     import hashlib
-    ent = NCU_INST.get(workload, {}).get(kernel)
+    ent = NCU_INST.get(workload, {}).get((kernel, form))
     if ent is None:
         return None
     n, src, digest = ent
@@ -544,7 +544,7 @@ def main():
     if base(dom_name) in ALU_KERNELS:
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         ipeak, mhz = issue_peak_ginst(sms)
-        inst = ncu_inst(args.workload, base(dom_name))
+        inst = ncu_inst(args.workload, base(dom_name), forms[0])
         ach = inst / (dom_ms * 1e-3) / 1e9 if inst else None
         roofline = {"bound": "alu", "kernel": dom_name, "achieved": ach, "peak": ipeak,
                     "unit": "G warp-instructions/s", "frac": (ach / ipeak) if ach else None,

@@ -49,6 +49,7 @@ struct dfmnmf_adj {
   double *Wd, *Hd, *gd;  // [N][F][B], [N][B][T], [F][N][M]
   double2* Qd;           // [F][K][MK][MK]
   double *lam0, *lam1, *lam2, *y0, *y1, *y2, *P, *A0, *D0, *A1, *D1;
+  double *r0, *r1, *r2;  // 1 / max(y, eps) of y0, y1, y2: every division by the model becomes a product
   double *numW, *denW, *W1, *numH, *denH, *H1, *numG, *denG;
   double2 *V, *Qs;  // V [F][K][MK][MK][MK]; Qs [F][K][MK+1][MK][MK] (rows before each IP row update)
   // adjoints
@@ -108,6 +109,12 @@ __device__ __forceinline__ double2 crecip(double2 a) {  // 1 / a = conj(a) / |a|
 __device__ __forceinline__ double2 ld(const float2* p) {
   const float2 v = __ldg(p);
   return make_double2((double)v.x, (double)v.y);
+}
+// Sum over the 32 lanes of a warp in a fixed butterfly order (deterministic).
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
 }
 
 // Gauss-Jordan elimination with partial pivoting on A b = rhs (n <= 4, fully
@@ -259,35 +266,56 @@ __global__ void k_a_nmf_f(const double* __restrict__ X, const double* __restrict
   out[i] = (acc ? out[i] : 0.0) + s;
 }
 
-// y[f][t][m] = sum_n lam[n][f][t] g[f][n][m] (before the floor)
-__global__ void k_a_y(const double* __restrict__ lam, const double* __restrict__ g, double* __restrict__ y, int N,
-                      int F, int T, int M) {
+// y[f][t][m] = sum_n lam[n][f][t] g[f][n][m] (before the floor) and ry = 1 / max(y, eps).
+// GB300 issues FP64 at a small fraction of its FP32 rate and a division costs
+// about ten FP64 instructions, so the reverse kernels multiply by ry instead
+// of dividing by the model.
+__global__ void k_a_y(const double* __restrict__ lam, const double* __restrict__ g, double* __restrict__ y,
+                      double* __restrict__ ry, int N, int F, int T, int M, double eps) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (size_t)F * T * M) return;
   const int m = (int)(i % M), t = (int)((i / M) % T), f = (int)(i / ((size_t)T * M));
   double s = 0.0;
   for (int n = 0; n < N; ++n) s += lam[((size_t)n * F + f) * T + t] * g[((size_t)f * N + n) * M + m];
   y[i] = s;
+  ry[i] = 1.0 / flo(s, eps);
 }
 
 // V[f][k][mu][a][b] = (1/T) sum_t x_a conj(x_b) / yhat0[f][t][o_k + mu]   (Eq. 13)
-__global__ void k_a_V(const float2* __restrict__ x, const double* __restrict__ y0, double2* __restrict__ V, int F,
-                      int T, int K, int MK, double eps) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const size_t per = (size_t)MK * MK * MK;
-  if (i >= (size_t)F * K * per) return;
-  const int b = (int)(i % MK), a = (int)((i / MK) % MK), mu = (int)((i / ((size_t)MK * MK)) % MK);
-  const int k = (int)((i / per) % K), f = (int)(i / (per * K));
+// One warp per (f, k, a, b), lanes over t: the product x_a conj(x_b) is formed
+// once per frame and weighted by the reciprocals r0 of all MK microphones.
+template <int MK>
+__global__ void k_a_V(const float2* __restrict__ x, const double* __restrict__ r0, double2* __restrict__ V, int F,
+                      int T, int K) {
+  const size_t w = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= (size_t)F * K * MK * MK) return;
+  const int b = (int)(w % MK), a = (int)((w / MK) % MK), k = (int)((w / (MK * MK)) % K);
+  const int f = (int)(w / ((size_t)MK * MK * K));
   const int M = K * MK, o = k * MK;
-  double sr = 0.0, si = 0.0;
-  for (int t = 0; t < T; ++t) {
+  double sr[MK], si[MK];
+#pragma unroll
+  for (int mu = 0; mu < MK; ++mu) sr[mu] = si[mu] = 0.0;
+  for (int t = lane; t < T; t += 32) {
     const size_t r = ((size_t)f * T + t) * M + o;
-    const double w = 1.0 / flo(y0[((size_t)f * T + t) * M + o + mu], eps);
     const double2 p = cmulc(ld(x + r + a), ld(x + r + b));
-    sr += w * p.x;
-    si += w * p.y;
+#pragma unroll
+    for (int mu = 0; mu < MK; ++mu) {
+      const double wv = r0[r + mu];
+      sr[mu] += wv * p.x;
+      si[mu] += wv * p.y;
+    }
   }
-  V[i] = make_double2(sr / T, si / T);
+#pragma unroll
+  for (int mu = 0; mu < MK; ++mu) {
+    sr[mu] = warp_sum(sr[mu]);
+    si[mu] = warp_sum(si[mu]);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int mu = 0; mu < MK; ++mu)
+      V[(((size_t)f * K + k) * MK + mu) * MK * MK + a * MK + b] = make_double2(sr[mu] / T, si[mu] / T);
+  }
 }
 
 // P[f][t][o_k + a] = |(Q_fk x_ftk)_a|^2; block (f, k) of Q at Q + (f K + k) * bstride
@@ -307,8 +335,8 @@ __global__ void k_a_P(const float2* __restrict__ x, const double2* __restrict__ 
 }
 
 // A[n][f][t] = sum_m g P / yhat^2, D[n][f][t] = sum_m g / yhat
-__global__ void k_a_AD(const double* __restrict__ P, const double* __restrict__ y, const double* __restrict__ g,
-                       double* __restrict__ A, double* __restrict__ D, int N, int F, int T, int M, double eps) {
+__global__ void k_a_AD(const double* __restrict__ P, const double* __restrict__ ry, const double* __restrict__ g,
+                       double* __restrict__ A, double* __restrict__ D, int N, int F, int T, int M) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (size_t)N * F * T) return;
   const int t = (int)(i % T), f = (int)((i / T) % F), n = (int)(i / ((size_t)F * T));
@@ -316,9 +344,9 @@ __global__ void k_a_AD(const double* __restrict__ P, const double* __restrict__ 
   const size_t r = ((size_t)f * T + t) * M;
   double a = 0.0, d = 0.0;
   for (int m = 0; m < M; ++m) {
-    const double yy = flo(y[r + m], eps);
-    a += gr[m] * P[r + m] / (yy * yy);
-    d += gr[m] / yy;
+    const double rv = ry[r + m];
+    a += gr[m] * P[r + m] * (rv * rv);
+    d += gr[m] * rv;
   }
   A[i] = a;
   D[i] = d;
@@ -331,22 +359,28 @@ __global__ void k_a_mu(const double* __restrict__ th, const double* __restrict__
   if (i < n) out[i] = th[i] * sqrt(num[i] / flo(den[i], eps));
 }
 
-// num[f][n][m] = sum_t lam P / yhat^2, den = sum_t lam / yhat   (Eq. 10)
-__global__ void k_a_gnum(const double* __restrict__ lam, const double* __restrict__ P, const double* __restrict__ y,
-                         double* __restrict__ num, double* __restrict__ den, int N, int F, int T, int M, double eps) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+// num[f][n][m] = sum_t lam P / yhat^2, den = sum_t lam / yhat   (Eq. 10); one warp per
+// output, lanes over t
+__global__ void k_a_gnum(const double* __restrict__ lam, const double* __restrict__ P, const double* __restrict__ ry,
+                         double* __restrict__ num, double* __restrict__ den, int N, int F, int T, int M) {
+  const size_t i = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (i >= (size_t)F * N * M) return;
   const int m = (int)(i % M), n = (int)((i / M) % N), f = (int)(i / ((size_t)M * N));
   const double* l = lam + ((size_t)n * F + f) * T;
   double a = 0.0, d = 0.0;
-  for (int t = 0; t < T; ++t) {
+  for (int t = lane; t < T; t += 32) {
     const size_t r = ((size_t)f * T + t) * M + m;
-    const double yy = flo(y[r], eps);
-    a += l[t] * P[r] / (yy * yy);
-    d += l[t] / yy;
+    const double rv = ry[r];
+    a += l[t] * P[r] * (rv * rv);
+    d += l[t] * rv;
   }
-  num[i] = a;
-  den[i] = d;
+  a = warp_sum(a);
+  d = warp_sum(d);
+  if (lane == 0) {
+    num[i] = a;
+    den[i] = d;
+  }
 }
 
 // forward IP of every block (Eqs. 14, 15), keeping the rows before each row update
@@ -427,20 +461,21 @@ __global__ void k_a_mub(const double* __restrict__ th, const double* __restrict_
 //   lamb[n] = sum_m (numb P / yhat^2 + denb / yhat + ybar[m] g)
 __global__ void k_a_gstat_b(const double* __restrict__ numb, const double* __restrict__ denb,
                             const double* __restrict__ lam, const double* __restrict__ P,
-                            const double* __restrict__ y, const double* __restrict__ g, double* __restrict__ lamb,
-                            double* __restrict__ Pb, double* __restrict__ yb, int N, int F, int T, int M, double eps) {
+                            const double* __restrict__ y, const double* __restrict__ ry, const double* __restrict__ g,
+                            double* __restrict__ lamb, double* __restrict__ Pb, double* __restrict__ yb, int N, int F,
+                            int T, int M, double eps) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (size_t)F * T) return;
   const int t = (int)(i % T), f = (int)(i / T);
   const size_t r = i * M;
   for (int m = 0; m < M; ++m) {
-    const double yy = flo(y[r + m], eps);
+    const double rv = ry[r + m], r2 = rv * rv, r3 = r2 * rv, pm = P[r + m];
     double a = 0.0, pb = 0.0;
     for (int n = 0; n < N; ++n) {
       const double l = lam[((size_t)n * F + f) * T + t];
       const size_t q = ((size_t)f * N + n) * M + m;
-      a += l * (-2.0 * numb[q] * P[r + m] / (yy * yy * yy) - denb[q] / (yy * yy));
-      pb += numb[q] * l / (yy * yy);
+      a += l * (-2.0 * numb[q] * pm * r3 - denb[q] * r2);
+      pb += numb[q] * l * r2;
     }
     yb[r + m] = y[r + m] > eps ? a : 0.0;
     Pb[r + m] += pb;
@@ -448,9 +483,9 @@ __global__ void k_a_gstat_b(const double* __restrict__ numb, const double* __res
   for (int n = 0; n < N; ++n) {
     double s = 0.0;
     for (int m = 0; m < M; ++m) {
-      const double yy = flo(y[r + m], eps);
+      const double rv = ry[r + m];
       const size_t q = ((size_t)f * N + n) * M + m;
-      s += numb[q] * P[r + m] / (yy * yy) + denb[q] / yy + yb[r + m] * g[q];
+      s += numb[q] * P[r + m] * (rv * rv) + denb[q] * rv + yb[r + m] * g[q];
     }
     lamb[((size_t)n * F + f) * T + t] = s;
   }
@@ -461,18 +496,18 @@ __global__ void k_a_gstat_b(const double* __restrict__ numb, const double* __res
 //   Pbar += sum_n Ab g / yhat^2
 __global__ void k_a_stat_b(const double* __restrict__ Ab, const double* __restrict__ Db,
                            const double* __restrict__ g, const double* __restrict__ P, const double* __restrict__ y,
-                           double* __restrict__ yb, double* __restrict__ Pb, int N, int F, int T, int M, double eps,
-                           int acc) {
+                           const double* __restrict__ ry, double* __restrict__ yb, double* __restrict__ Pb, int N,
+                           int F, int T, int M, double eps, int acc) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (size_t)F * T * M) return;
   const int m = (int)(i % M), t = (int)((i / M) % T), f = (int)(i / ((size_t)T * M));
-  const double yy = flo(y[i], eps);
+  const double rv = ry[i], r2 = rv * rv, r3 = r2 * rv, pi = P[i];
   double a = 0.0, pb = 0.0;
   for (int n = 0; n < N; ++n) {
     const size_t nf = ((size_t)n * F + f) * T + t;
     const double gg = g[((size_t)f * N + n) * M + m];
-    a += -2.0 * Ab[nf] * gg * P[i] / (yy * yy * yy) - Db[nf] * gg / (yy * yy);
-    pb += Ab[nf] * gg / (yy * yy);
+    a += -2.0 * Ab[nf] * gg * pi * r3 - Db[nf] * gg * r2;
+    pb += Ab[nf] * gg * r2;
   }
   const double v = y[i] > eps ? a : 0.0;
   yb[i] = (acc ? yb[i] : 0.0) + v;
@@ -492,52 +527,79 @@ __global__ void k_a_y_b(const double* __restrict__ yb, const double* __restrict_
   lamb[i] = (acc ? lamb[i] : 0.0) + s;
 }
 
-// gbar[f][n][m] += sum_t (Ab P / yhat^2 + Db / yhat + ybar lam); NULL terms are skipped
+// gbar[f][n][m] += sum_t (Ab P / yhat^2 + Db / yhat + ybar lam); NULL terms are skipped.
+// One warp per output, lanes over t.
 __global__ void k_a_gbar(const double* __restrict__ Ab, const double* __restrict__ Db, const double* __restrict__ yb,
-                         const double* __restrict__ lam, const double* __restrict__ P, const double* __restrict__ y,
-                         double* __restrict__ gb, int N, int F, int T, int M, double eps) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+                         const double* __restrict__ lam, const double* __restrict__ P, const double* __restrict__ ry,
+                         double* __restrict__ gb, int N, int F, int T, int M) {
+  const size_t i = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (i >= (size_t)F * N * M) return;
   const int m = (int)(i % M), n = (int)((i / M) % N), f = (int)(i / ((size_t)M * N));
   const size_t nf = ((size_t)n * F + f) * T;
   double s = 0.0;
-  for (int t = 0; t < T; ++t) {
+  for (int t = lane; t < T; t += 32) {
     const size_t r = ((size_t)f * T + t) * M + m;
-    const double yy = flo(y[r], eps);
-    if (Ab) s += Ab[nf + t] * P[r] / (yy * yy);
-    if (Db) s += Db[nf + t] / yy;
+    const double rv = ry[r];
+    if (Ab) s += Ab[nf + t] * P[r] * (rv * rv);
+    if (Db) s += Db[nf + t] * rv;
     if (yb) s += yb[r] * lam[nf + t];
   }
-  gb[i] += s;
+  s = warp_sum(s);
+  if (lane == 0) gb[i] += s;
 }
 
-// gbar[f][n][m] += sum_t G4[n][f][t][m]
+// gbar[f][n][m] += sum_t G4[n][f][t][m]; one warp per output, lanes over t
 __global__ void k_a_red_t4(const double* __restrict__ G4, double* __restrict__ gb, int N, int F, int T, int M) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t i = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (i >= (size_t)F * N * M) return;
   const int m = (int)(i % M), n = (int)((i / M) % N), f = (int)(i / ((size_t)M * N));
   double s = 0.0;
-  for (int t = 0; t < T; ++t) s += G4[(((size_t)n * F + f) * T + t) * M + m];
-  gb[i] += s;
+  for (int t = lane; t < T; t += 32) s += G4[(((size_t)n * F + f) * T + t) * M + m];
+  s = warp_sum(s);
+  if (lane == 0) gb[i] += s;
 }
 
-// Reverse of P = |Q x|^2: Qbar[f][k][a][b] += sum_t 2 Pbar_a z_a conj(x_b)
+// Reverse of P = |Q x|^2: Qbar[f][k][a][b] += sum_t 2 Pbar_a z_a conj(x_b), z = Q_fk x_ftk.
+// One warp per (f, k, a), lanes over t: z_a is formed once per frame for all b.
+template <int MK>
 __global__ void k_a_Pb(const float2* __restrict__ x, const double2* __restrict__ Q, size_t bstride,
-                       const double* __restrict__ Pb, double2* __restrict__ Qb, int F, int T, int K, int MK) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (size_t)F * K * MK * MK) return;
-  const int b = (int)(i % MK), a = (int)((i / MK) % MK), k = (int)((i / ((size_t)MK * MK)) % K);
-  const int f = (int)(i / ((size_t)MK * MK * K));
+                       const double* __restrict__ Pb, double2* __restrict__ Qb, int F, int T, int K) {
+  const size_t w = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= (size_t)F * K * MK) return;
+  const int a = (int)(w % MK), k = (int)((w / MK) % K), f = (int)(w / ((size_t)MK * K));
   const int M = K * MK, o = k * MK;
   const double2* q = Q + ((size_t)f * K + k) * bstride + a * MK;
-  double2 acc = make_double2(0.0, 0.0);
-  for (int t = 0; t < T; ++t) {
-    const size_t r = ((size_t)f * T + t) * M + o;
-    double2 z = make_double2(0.0, 0.0);
-    for (int c2 = 0; c2 < MK; ++c2) z = cadd(z, cmul(q[c2], ld(x + r + c2)));
-    acc = cadd(acc, cscale(cmulc(z, ld(x + r + b)), 2.0 * Pb[((size_t)f * T + t) * M + o + a]));
+  double2 qa[MK], acc[MK];
+#pragma unroll
+  for (int c2 = 0; c2 < MK; ++c2) {
+    qa[c2] = q[c2];
+    acc[c2] = make_double2(0.0, 0.0);
   }
-  Qb[i] = cadd(Qb[i], acc);
+  for (int t = lane; t < T; t += 32) {
+    const size_t r = ((size_t)f * T + t) * M + o;
+    double2 xv[MK];
+    double2 z = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int c2 = 0; c2 < MK; ++c2) {
+      xv[c2] = ld(x + r + c2);
+      z = cadd(z, cmul(qa[c2], xv[c2]));
+    }
+    const double s2 = 2.0 * Pb[r + a];
+#pragma unroll
+    for (int b = 0; b < MK; ++b) acc[b] = cadd(acc[b], cscale(cmulc(z, xv[b]), s2));
+  }
+#pragma unroll
+  for (int b = 0; b < MK; ++b) acc[b] = make_double2(warp_sum(acc[b].x), warp_sum(acc[b].y));
+  if (lane == 0) {
+#pragma unroll
+    for (int b = 0; b < MK; ++b) {
+      double2* p = Qb + (((size_t)f * K + k) * MK + a) * MK + b;
+      *p = cadd(*p, acc[b]);
+    }
+  }
 }
 
 // Reverse of the IP rows of one block, mu = MK-1 .. 0.  For row mu with
@@ -637,7 +699,8 @@ __global__ void k_a_ipb(const double2* __restrict__ Qs, const double2* __restric
 
 // Reverse of Eq. 13 and of 1/yhat0: ybar0[f][t][o_k+mu] += -Re(x^H Vbar_mu x) / (T yhat0^2)
 __global__ void k_a_Vb(const float2* __restrict__ x, const double2* __restrict__ Vb, const double* __restrict__ y0,
-                       double* __restrict__ yb, int F, int T, int K, int MK, double eps) {
+                       const double* __restrict__ r0, double* __restrict__ yb, int F, int T, int K, int MK,
+                       double eps) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int M = K * MK;
   if (i >= (size_t)F * T * M) return;
@@ -653,7 +716,7 @@ __global__ void k_a_Vb(const float2* __restrict__ x, const double2* __restrict__
     const double2 xa = ld(xr + a);
     s += xa.x * v.x + xa.y * v.y;  // Re(conj(x_a) (Vbar x)_a)
   }
-  yb[i] += -s / ((double)T * y0[i] * y0[i]);
+  yb[i] += -s * (r0[i] * r0[i]) / (double)T;
 }
 
 // ---------------------------------------------------------------- losses
@@ -672,15 +735,16 @@ __device__ void block_add(double v, double* red) {
 }
 
 // data term of Eq. 12 and its adjoints: Pbar = 1/yhat, ybar = 1/yhat - P/yhat^2 (0 under the floor)
-__global__ void k_a_nll_data(const double* __restrict__ P, const double* __restrict__ y, double* __restrict__ Pb,
-                             double* __restrict__ yb, double* __restrict__ red, size_t n, double eps) {
+__global__ void k_a_nll_data(const double* __restrict__ P, const double* __restrict__ y,
+                             const double* __restrict__ ry, double* __restrict__ Pb, double* __restrict__ yb,
+                             double* __restrict__ red, size_t n, double eps) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   double v = 0.0;
   if (i < n) {
-    const double yy = flo(y[i], eps);
-    v = P[i] / yy + log(yy);
-    Pb[i] = 1.0 / yy;
-    yb[i] = y[i] > eps ? 1.0 / yy - P[i] / (yy * yy) : 0.0;
+    const double yy = flo(y[i], eps), rv = ry[i];
+    v = P[i] * rv + log(yy);
+    Pb[i] = rv;
+    yb[i] = y[i] > eps ? rv - P[i] * (rv * rv) : 0.0;
   }
   block_add(v, red);
 }
@@ -878,11 +942,11 @@ cudaError_t load_state(dfmnmf_adj* a, const Dims& d, const double2* Q, const flo
   return cudaMemcpyAsync(a->Qd, Q, d.nq * sizeof(double2), cudaMemcpyDeviceToDevice, s);
 }
 
-// lam = W H and yraw = sum_n lam g
+// lam = W H, yraw = sum_n lam g and ry = 1 / max(yraw, eps)
 cudaError_t model(const Dims& d, const double* W, const double* H, const double* g, double* lam, double* y,
-                  cudaStream_t s) {
+                  double* ry, cudaStream_t s) {
   AL(k_a_nmf_b<<<nblk(d.nft), 256, 0, s>>>(W, H, lam, d.N, d.F, d.B, d.T));
-  AL(k_a_y<<<nblk(d.ftm), 256, 0, s>>>(lam, g, y, d.N, d.F, d.T, d.M));
+  AL(k_a_y<<<nblk(d.ftm), 256, 0, s>>>(lam, g, y, ry, d.N, d.F, d.T, d.M, d.eps));
   return cudaSuccess;
 }
 
@@ -903,41 +967,42 @@ cudaError_t reverse_iteration(dfmnmf_adj* a, const Dims& d, cudaStream_t s) {
   const double eps = d.eps;
   const int nb = d.F * d.K;
   // forward, recomputed in FP64
-  cudaError_t e = model(d, a->Wd, a->Hd, a->gd, a->lam0, a->y0, s);
+  cudaError_t e = model(d, a->Wd, a->Hd, a->gd, a->lam0, a->y0, a->r0, s);
   if (e != cudaSuccess) return e;
-  AL(k_a_V<<<nblk(d.nv), 256, 0, s>>>(c->x, a->y0, a->V, d.F, d.T, d.K, d.MK, eps));
+  MK_DISPATCH(d.MK, k_a_V, nblk(d.nq * 32), 256, 0, s, c->x, a->r0, a->V, d.F, d.T, d.K);
+  AL((void)0);
   MK_DISPATCH(d.MK, k_a_ipfwd, nblk(nb, 64), 64, 0, s, a->Qd, a->V, a->Qs, nb, eps, (double)c->singular_rtol, a->flags);
   AL((void)0);
   const double2* Qn = a->Qs + (size_t)d.MK * d.MK * d.MK;  // rows after the last update, stride (MK+1) MK^2
   const size_t qstr = (size_t)(d.MK + 1) * d.MK * d.MK;
   AL(k_a_P<<<nblk((size_t)d.F * d.T * d.K), 256, 0, s>>>(c->x, Qn, qstr, a->P, d.F, d.T, d.K, d.MK));
-  AL(k_a_AD<<<nblk(d.nft), 256, 0, s>>>(a->P, a->y0, a->gd, a->A0, a->D0, d.N, d.F, d.T, d.M, eps));
+  AL(k_a_AD<<<nblk(d.nft), 256, 0, s>>>(a->P, a->r0, a->gd, a->A0, a->D0, d.N, d.F, d.T, d.M));
   if ((e = nmf_t(d, a->A0, a->Hd, a->numW, 0, s)) || (e = nmf_t(d, a->D0, a->Hd, a->denW, 0, s))) return e;
   AL(k_a_mu<<<nblk(d.nfb), 256, 0, s>>>(a->Wd, a->numW, a->denW, a->W1, d.nfb, eps));
-  if ((e = model(d, a->W1, a->Hd, a->gd, a->lam1, a->y1, s))) return e;
-  AL(k_a_AD<<<nblk(d.nft), 256, 0, s>>>(a->P, a->y1, a->gd, a->A1, a->D1, d.N, d.F, d.T, d.M, eps));
+  if ((e = model(d, a->W1, a->Hd, a->gd, a->lam1, a->y1, a->r1, s))) return e;
+  AL(k_a_AD<<<nblk(d.nft), 256, 0, s>>>(a->P, a->r1, a->gd, a->A1, a->D1, d.N, d.F, d.T, d.M));
   if ((e = nmf_f(d, a->W1, a->A1, a->numH, 0, s)) || (e = nmf_f(d, a->W1, a->D1, a->denH, 0, s))) return e;
   AL(k_a_mu<<<nblk(d.nbt), 256, 0, s>>>(a->Hd, a->numH, a->denH, a->H1, d.nbt, eps));
-  if ((e = model(d, a->W1, a->H1, a->gd, a->lam2, a->y2, s))) return e;
-  AL(k_a_gnum<<<nblk(d.fnm), 256, 0, s>>>(a->lam2, a->P, a->y2, a->numG, a->denG, d.N, d.F, d.T, d.M, eps));
+  if ((e = model(d, a->W1, a->H1, a->gd, a->lam2, a->y2, a->r2, s))) return e;
+  AL(k_a_gnum<<<nblk(d.fnm * 32), 256, 0, s>>>(a->lam2, a->P, a->r2, a->numG, a->denG, d.N, d.F, d.T, d.M));
 
   // reverse of the g update (Eq. 10)
   AL(k_a_mub<<<nblk(d.fnm), 256, 0, s>>>(a->gd, a->numG, a->denG, a->gb1, a->gb, a->nb, a->db, d.fnm, eps));
   ACKE(cudaMemsetAsync(a->Pb, 0, d.ftm * sizeof(double), s));
-  AL(k_a_gstat_b<<<nblk((size_t)d.F * d.T), 256, 0, s>>>(a->nb, a->db, a->lam2, a->P, a->y2, a->gd, a->lamb, a->Pb,
-                                                          a->yb, d.N, d.F, d.T, d.M, eps));
-  AL(k_a_gbar<<<nblk(d.fnm), 256, 0, s>>>(nullptr, nullptr, a->yb, a->lam2, a->P, a->y2, a->gb, d.N, d.F, d.T, d.M,
-                                           eps));
+  AL(k_a_gstat_b<<<nblk((size_t)d.F * d.T), 256, 0, s>>>(a->nb, a->db, a->lam2, a->P, a->y2, a->r2, a->gd, a->lamb,
+                                                          a->Pb, a->yb, d.N, d.F, d.T, d.M, eps));
+  AL(k_a_gbar<<<nblk(d.fnm * 32), 256, 0, s>>>(nullptr, nullptr, a->yb, a->lam2, a->P, a->r2, a->gb, d.N, d.F, d.T,
+                                                d.M));
   if ((e = nmf_t(d, a->lamb, a->H1, a->Wb1, 1, s)) || (e = nmf_f(d, a->W1, a->lamb, a->Hb1, 1, s))) return e;
   // reverse of the H update (Eq. 9)
   AL(k_a_mub<<<nblk(d.nbt), 256, 0, s>>>(a->Hd, a->numH, a->denH, a->Hb1, a->Hb, a->nb, a->db, d.nbt, eps));
   if ((e = nmf_t(d, a->A1, a->nb, a->Wb1, 1, s)) || (e = nmf_t(d, a->D1, a->db, a->Wb1, 1, s))) return e;
   AL(k_a_nmf_b<<<nblk(d.nft), 256, 0, s>>>(a->W1, a->nb, a->Ab, d.N, d.F, d.B, d.T));
   AL(k_a_nmf_b<<<nblk(d.nft), 256, 0, s>>>(a->W1, a->db, a->Db, d.N, d.F, d.B, d.T));
-  AL(k_a_stat_b<<<nblk(d.ftm), 256, 0, s>>>(a->Ab, a->Db, a->gd, a->P, a->y1, a->yb, a->Pb, d.N, d.F, d.T, d.M, eps,
-                                             0));
-  AL(k_a_gbar<<<nblk(d.fnm), 256, 0, s>>>(a->Ab, a->Db, a->yb, a->lam1, a->P, a->y1, a->gb, d.N, d.F, d.T, d.M,
-                                           eps));
+  AL(k_a_stat_b<<<nblk(d.ftm), 256, 0, s>>>(a->Ab, a->Db, a->gd, a->P, a->y1, a->r1, a->yb, a->Pb, d.N, d.F, d.T,
+                                             d.M, eps, 0));
+  AL(k_a_gbar<<<nblk(d.fnm * 32), 256, 0, s>>>(a->Ab, a->Db, a->yb, a->lam1, a->P, a->r1, a->gb, d.N, d.F, d.T,
+                                                d.M));
   AL(k_a_y_b<<<nblk(d.nft), 256, 0, s>>>(a->yb, a->gd, a->lamb, d.N, d.F, d.T, d.M, 0));
   if ((e = nmf_t(d, a->lamb, a->Hd, a->Wb1, 1, s)) || (e = nmf_f(d, a->W1, a->lamb, a->Hb, 1, s))) return e;
   // reverse of the W update (Eq. 8)
@@ -945,16 +1010,18 @@ cudaError_t reverse_iteration(dfmnmf_adj* a, const Dims& d, cudaStream_t s) {
   if ((e = nmf_f(d, a->nb, a->A0, a->Hb, 1, s)) || (e = nmf_f(d, a->db, a->D0, a->Hb, 1, s))) return e;
   AL(k_a_nmf_b<<<nblk(d.nft), 256, 0, s>>>(a->nb, a->Hd, a->Ab, d.N, d.F, d.B, d.T));
   AL(k_a_nmf_b<<<nblk(d.nft), 256, 0, s>>>(a->db, a->Hd, a->Db, d.N, d.F, d.B, d.T));
-  AL(k_a_stat_b<<<nblk(d.ftm), 256, 0, s>>>(a->Ab, a->Db, a->gd, a->P, a->y0, a->yb, a->Pb, d.N, d.F, d.T, d.M, eps,
-                                             0));
+  AL(k_a_stat_b<<<nblk(d.ftm), 256, 0, s>>>(a->Ab, a->Db, a->gd, a->P, a->y0, a->r0, a->yb, a->Pb, d.N, d.F, d.T,
+                                             d.M, eps, 0));
   // reverse of the projections and of the IP rows (Eqs. 13-15)
-  AL(k_a_Pb<<<nblk(d.nq), 256, 0, s>>>(c->x, Qn, qstr, a->Pb, a->Qb1, d.F, d.T, d.K, d.MK));
+  MK_DISPATCH(d.MK, k_a_Pb, nblk((size_t)d.F * d.K * d.MK * 32), 256, 0, s, c->x, Qn, qstr, a->Pb, a->Qb1, d.F, d.T,
+              d.K);
+  AL((void)0);
   MK_DISPATCH(d.MK, k_a_ipb, nblk(nb, 64), 64, 0, s, a->Qs, a->V, a->Qb1, a->Qb, a->Vb, nb, eps);
   AL((void)0);
-  AL(k_a_Vb<<<nblk(d.ftm), 256, 0, s>>>(c->x, a->Vb, a->y0, a->yb, d.F, d.T, d.K, d.MK, eps));
+  AL(k_a_Vb<<<nblk(d.ftm), 256, 0, s>>>(c->x, a->Vb, a->y0, a->r0, a->yb, d.F, d.T, d.K, d.MK, eps));
   // reverse of the model at the input state
-  AL(k_a_gbar<<<nblk(d.fnm), 256, 0, s>>>(a->Ab, a->Db, a->yb, a->lam0, a->P, a->y0, a->gb, d.N, d.F, d.T, d.M,
-                                           eps));
+  AL(k_a_gbar<<<nblk(d.fnm * 32), 256, 0, s>>>(a->Ab, a->Db, a->yb, a->lam0, a->P, a->r0, a->gb, d.N, d.F, d.T,
+                                                d.M));
   AL(k_a_y_b<<<nblk(d.nft), 256, 0, s>>>(a->yb, a->gd, a->lamb, d.N, d.F, d.T, d.M, 0));
   if ((e = nmf_t(d, a->lamb, a->Hd, a->Wb, 1, s)) || (e = nmf_f(d, a->Wd, a->lamb, a->Hb, 1, s))) return e;
   return cudaSuccess;
@@ -965,16 +1032,18 @@ cudaError_t loss_and_adjoint(dfmnmf_adj* a, const Dims& d, int loss, const float
   const dfmnmf_ctx* c = a->c;
   const double eps = d.eps;
   const int nb = d.F * d.K;
-  cudaError_t e = model(d, a->Wd, a->Hd, a->gd, a->lam0, a->y0, s);
+  cudaError_t e = model(d, a->Wd, a->Hd, a->gd, a->lam0, a->y0, a->r0, s);
   if (e != cudaSuccess) return e;
   ACKE(cudaMemsetAsync(a->red, 0, sizeof(double), s));
   ACKE(cudaMemsetAsync(a->gb, 0, d.fnm * sizeof(double), s));
   const size_t qstr = (size_t)d.MK * d.MK;
   if (loss == DFMNMF_LOSS_NLL) {
     AL(k_a_P<<<nblk((size_t)d.F * d.T * d.K), 256, 0, s>>>(c->x, a->Qd, qstr, a->P, d.F, d.T, d.K, d.MK));
-    AL(k_a_nll_data<<<nblk(d.ftm), 256, 0, s>>>(a->P, a->y0, a->Pb, a->yb, a->red, d.ftm, eps));
+    AL(k_a_nll_data<<<nblk(d.ftm), 256, 0, s>>>(a->P, a->y0, a->r0, a->Pb, a->yb, a->red, d.ftm, eps));
     ACKE(cudaMemsetAsync(a->Qb, 0, d.nq * sizeof(double2), s));
-    AL(k_a_Pb<<<nblk(d.nq), 256, 0, s>>>(c->x, a->Qd, qstr, a->Pb, a->Qb, d.F, d.T, d.K, d.MK));
+    MK_DISPATCH(d.MK, k_a_Pb, nblk((size_t)d.F * d.K * d.MK * 32), 256, 0, s, c->x, a->Qd, qstr, a->Pb, a->Qb, d.F,
+                d.T, d.K);
+    AL((void)0);
     MK_DISPATCH(d.MK, k_a_logdet_b, nblk(nb, 64), 64, 0, s, a->Qd, a->Qb, a->red, nb, d.T);
     AL((void)0);
     AL(k_a_y_b<<<nblk(d.nft), 256, 0, s>>>(a->yb, a->gd, a->lamb, d.N, d.F, d.T, d.M, 0));
@@ -986,11 +1055,11 @@ cudaError_t loss_and_adjoint(dfmnmf_adj* a, const Dims& d, int loss, const float
                 a->y0, a->lamb, a->yb, a->G4, a->ubar, a->cvec, a->zbar, a->red, d.N, d.F, d.T, d.K, eps, invS);
     AL((void)0);
     AL(k_a_wiener_q<<<nblk(d.nq), 256, 0, s>>>(c->x, a->zbar, a->ubar, a->cvec, a->Qb, d.N, d.F, d.T, d.K, d.MK));
-    AL(k_a_red_t4<<<nblk(d.fnm), 256, 0, s>>>(a->G4, a->gb, d.N, d.F, d.T, d.M));
+    AL(k_a_red_t4<<<nblk(d.fnm * 32), 256, 0, s>>>(a->G4, a->gb, d.N, d.F, d.T, d.M));
     AL(k_a_y_b<<<nblk(d.nft), 256, 0, s>>>(a->yb, a->gd, a->lamb, d.N, d.F, d.T, d.M, 1));
   }
-  AL(k_a_gbar<<<nblk(d.fnm), 256, 0, s>>>(nullptr, nullptr, a->yb, a->lam0, a->P, a->y0, a->gb, d.N, d.F, d.T, d.M,
-                                           eps));
+  AL(k_a_gbar<<<nblk(d.fnm * 32), 256, 0, s>>>(nullptr, nullptr, a->yb, a->lam0, a->P, a->r0, a->gb, d.N, d.F, d.T,
+                                                d.M));
   if ((e = nmf_t(d, a->lamb, a->Hd, a->Wb, 0, s)) || (e = nmf_f(d, a->Wd, a->lamb, a->Hb, 0, s))) return e;
   return cudaSuccess;
 }
@@ -1029,7 +1098,8 @@ cudaError_t restore_state(dfmnmf_ctx* c, const double2* Q, const float* W, const
 void free_adj(dfmnmf_adj* a) {
   if (!a) return;
   void* p[] = {a->ckQ, a->ckW, a->ckH, a->ckg, a->sgQ, a->sgW, a->sgH, a->sgg, a->fnQ, a->fnW, a->fnH, a->fng,
-               a->Wd, a->Hd, a->gd, a->Qd, a->lam0, a->lam1, a->lam2, a->y0, a->y1, a->y2, a->P, a->A0, a->D0,
+               a->Wd, a->Hd, a->gd, a->Qd, a->lam0, a->lam1, a->lam2, a->y0, a->y1, a->y2, a->r0, a->r1, a->r2,
+               a->P, a->A0, a->D0,
                a->A1, a->D1, a->numW, a->denW, a->W1, a->numH, a->denH, a->H1, a->numG, a->denG, a->V, a->Qs,
                a->Qb, a->Qb1, a->Wb, a->Wb1, a->Hb, a->Hb1, a->gb, a->gb1, a->lamb, a->yb, a->Pb, a->Ab, a->Db,
                a->nb, a->db, a->Vb, a->Binv, a->ubar, a->cvec, a->zbar, a->G4, a->red, a->flags};
@@ -1076,6 +1146,7 @@ int dfmnmf_adjoint_create(dfmnmf_adj** out, dfmnmf_ctx* c, int n_iter, int every
             aalloc(&a->Wd, d.nfb) && aalloc(&a->Hd, d.nbt) && aalloc(&a->gd, d.fnm) && aalloc(&a->Qd, d.nq) &&
             aalloc(&a->lam0, d.nft) && aalloc(&a->lam1, d.nft) && aalloc(&a->lam2, d.nft) &&
             aalloc(&a->y0, d.ftm) && aalloc(&a->y1, d.ftm) && aalloc(&a->y2, d.ftm) && aalloc(&a->P, d.ftm) &&
+            aalloc(&a->r0, d.ftm) && aalloc(&a->r1, d.ftm) && aalloc(&a->r2, d.ftm) &&
             aalloc(&a->A0, d.nft) && aalloc(&a->D0, d.nft) && aalloc(&a->A1, d.nft) && aalloc(&a->D1, d.nft) &&
             aalloc(&a->numW, d.nfb) && aalloc(&a->denW, d.nfb) && aalloc(&a->W1, d.nfb) &&
             aalloc(&a->numH, d.nbt) && aalloc(&a->denH, d.nbt) && aalloc(&a->H1, d.nbt) &&

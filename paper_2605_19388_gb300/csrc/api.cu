@@ -273,7 +273,8 @@ int dfmnmf_init(dfmnmf_ctx** out, const dfmnmf_desc* d, const void* x, const flo
     return r;
   }
   if (c->precision == DFMNMF_BF16_TC) {
-    const size_t nr = (size_t)c->F * 16 * c->K * c->Tr, nw = (size_t)c->F * c->M * c->Tr;
+    size_t nr = 0, nw = 0;
+    dfm::tc_operand_elems(c, &nr, &nw);
     unsigned short *rh = nullptr, *rl = nullptr, *wh = nullptr, *wl = nullptr;
     r = dalloc(&rh, nr, "R hi");
     if (!r) r = dalloc(&rl, nr, "R lo");
@@ -283,6 +284,10 @@ int dfmnmf_init(dfmnmf_ctx** out, const dfmnmf_desc* d, const void* x, const flo
     c->Rlo = rl;
     c->wy_hi = wh;
     c->wy_lo = wl;
+    // the padding rows of a partial last tile are never written: zero them once
+    if (!r && (cudaMemset(rh, 0, nr * 2) != cudaSuccess || cudaMemset(rl, 0, nr * 2) != cudaSuccess ||
+               cudaMemset(wh, 0, nw * 2) != cudaSuccess || cudaMemset(wl, 0, nw * 2) != cudaSuccess))
+      r = fail(DFMNMF_ECUDA, "clearing the tensor-core operands failed");
     if (r) {
       free_ctx(c);
       return r;

@@ -40,10 +40,11 @@ struct dfmnmf_ctx {
   double2* gQ;
   float *gW, *gH, *gg;
   unsigned* flags; // dfm::FLAG_COUNT words
-  // tensor-core form: x x^H split in two bfloat16 parts, [F * 16 K][Tr] each, and their TMA descriptors
+  // tensor-core form: x x^H split in two bfloat16 parts and their TMA descriptors; R and w are stored
+  // as contiguous (tile of 8 / K frequencies, 64-frame chunk) blocks, [tiles][Tr / 64][rows][64]
   void* Rhi;
   void* Rlo;
-  void* wy_hi;  // 1/yhat split in two bfloat16 parts, [F * M][Tr] each (k_wprep)
+  void* wy_hi;  // 1/yhat split in two bfloat16 parts, 32 rows (f, m) per tile (k_wprep)
   void* wy_lo;
   alignas(64) unsigned char tmap_hi[128];
   alignas(64) unsigned char tmap_lo[128];
@@ -69,6 +70,7 @@ cudaError_t launch_vtc(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc);  //
 cudaError_t launch_rprep(const dfmnmf_ctx* c, cudaStream_t s);   // split-bfloat16 x x^H for the TC form
 cudaError_t launch_wprep(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc);  // split-bfloat16 1/yhat for the TC form
 cudaError_t tc_make_maps(dfmnmf_ctx* c);
+void tc_operand_elems(const dfmnmf_ctx* c, size_t* nr, size_t* nw);  // elements of R (each part) and of w (each part)
 bool tc_supported(int MK, int K);
 cudaError_t launch_ip(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc);
 cudaError_t launch_power_stats(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc);  // P + A/D (current lambda)

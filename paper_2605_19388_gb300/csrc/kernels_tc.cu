@@ -11,11 +11,18 @@
 // it moves the IP update by 6e-2 relative, the split form by 1.5e-4.
 //
 // R depends only on the observation, so it is formed once (k_rprep) into
-// two bfloat16 arrays [F * 16K][Tr] (Tr = T rounded up to 64, zero tail).
-// The weights change every iteration: k_wprep forms w_hi / w_lo [F * M][Tr]
-// from lambda and g in one streaming pass.  k_vtc then only moves and
+// two bfloat16 arrays; the weights change every iteration: k_wprep forms
+// w_hi / w_lo from lambda and g in one streaming pass.  Both are stored in
+// the order k_vtc reads them: a tile of FPC = 8 / K frequencies (128 rows of
+// R, 32 rows of w) is cut into chunks of 64 frames, and each (tile, chunk)
+// block of 128 x 64 (R) or 32 x 64 (w) values is contiguous in memory
+// ([tiles][Tr / 64][rows][64], Tr = T rounded up to 64, zero tail), so every
+// tensor copy reads one contiguous 16 KB or 4 KB block instead of 128-byte
+// pieces of rows 2 Tr bytes apart.  k_vtc then only moves and
 // multiplies: one thread streams the four operand tiles of each 64-frame
-// chunk with TMA (128-byte swizzled, 128 rows of R and 32 rows of w) into a
+// chunk with TMA (128-byte swizzled; R with an evict-first L2 policy, since
+// it is read once per iteration and would otherwise push the streaming
+// kernels' operands out of L2) into a
 // 2-stage shared-memory ring (two CTAs per SM), one thread issues
 // tcgen05.mma (M = 128 rows = 128 / (16 K) frequencies, N = 32 weights,
 // K = 16 frames per instruction, FP32 accumulators in tensor memory) and the
@@ -82,6 +89,26 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
       : "memory");
 }
+// The same copy with an L2 cache policy (createpolicy).
+__device__ __forceinline__ void tma_load_2d_hint(void* dst, const CUtensorMap* map, int c0, int c1,
+                                                 unsigned long long* bar, unsigned long long policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%2, "
+      "%3}], [%4], %5;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar)), "l"(policy)
+      : "memory");
+}
+__device__ __forceinline__ unsigned long long l2_evict_first_policy() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+// Position of element (row, t) of a tensor-core operand in the tiled layout:
+// rows of tile `tile` (rows_per_tile of them), chunk t / 64 of nch, frame t % 64.
+__host__ __device__ __forceinline__ size_t tc_index(int tile, int row, int t, int nch, int rows_per_tile) {
+  return (((size_t)tile * nch + (t >> 6)) * rows_per_tile + row) * TC_KC + (t & (TC_KC - 1));
+}
 
 // Shared-memory matrix descriptor: K-major operand tile with 128-byte
 // swizzle, 8-row groups 1024 bytes apart (stride byte offset), descriptor
@@ -113,13 +140,16 @@ __device__ __forceinline__ void umma_commit(unsigned long long* bar) {
 }
 
 // ------------------------------------------------------------- R prepare
-// Rhi/Rlo[(f * K + k) * 16 + r][t] for t < Tr (zero beyond T).
+// Packed entry r of block k of frequency f at frame t, for t < Tr (zero beyond
+// T), in the tiled layout: row (f % FPC) * 16K + 16 k + r of tile f / FPC.
 __global__ void __launch_bounds__(128) k_rprep(const float2* __restrict__ x, __nv_bfloat16* __restrict__ Rhi,
                                                __nv_bfloat16* __restrict__ Rlo, int F, int T, int Tr, int K) {
   const int f = blockIdx.y;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= Tr) return;
   const int M = K * 4;
+  const int FPC = TC_ROWS / (16 * K), nch = Tr / TC_KC;
+  const int tile = f / FPC, frow = (f % FPC) * 16 * K;
   for (int k = 0; k < K; ++k) {
     float R[16];
     if (t < T) {
@@ -142,7 +172,7 @@ __global__ void __launch_bounds__(128) k_rprep(const float2* __restrict__ x, __n
     for (int r = 0; r < 16; ++r) {
       const __nv_bfloat16 h = __float2bfloat16_rn(R[r]);
       const __nv_bfloat16 l = __float2bfloat16_rn(R[r] - __bfloat162float(h));
-      const size_t o = ((size_t)(f * K + k) * 16 + r) * Tr + t;
+      const size_t o = tc_index(tile, frow + k * 16 + r, t, nch, TC_ROWS);
       Rhi[o] = h;
       Rlo[o] = l;
     }
@@ -152,8 +182,9 @@ __global__ void __launch_bounds__(128) k_rprep(const float2* __restrict__ x, __n
 // ------------------------------------------------------------- weights
 // w = 1 / max(yhat, eps), yhat[f][t][m] = sum_n lambda[n][f][t] g[f][n][m]
 // (Eq. 2 with the floor of Sec. IV-A), split into two bfloat16 parts and
-// stored as rows (f, m) of Tr frames, zero beyond T: the B operand of the
-// contraction, read by TMA in the same 128-byte swizzled tiles as R.  Each
+// stored as rows (f % FPC) * M + m of tile f / FPC, Tr frames, zero beyond T:
+// the B operand of the contraction, read by TMA in the same 128-byte swizzled
+// tiles as R.  Each
 // thread forms two adjacent frames of one frequency for every microphone
 // (float2 lambda loads, g[f] broadcast from shared memory, 4-byte stores
 // coalesced along t).  NM is N itself for N <= 8 and 16 (guarded) above.
@@ -167,6 +198,8 @@ __global__ void __launch_bounds__(128) k_wprep(const float* __restrict__ lam, co
   __syncthreads();
   const int t = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   if (t >= Tr) return;
+  const int FPC = TC_COLS / M, nch = Tr / TC_KC;
+  const int tile = f / FPC, frow = (f % FPC) * M;
   float2 lv[NM];
 #pragma unroll
   for (int n = 0; n < NM; ++n) {
@@ -188,7 +221,7 @@ __global__ void __launch_bounds__(128) k_wprep(const float* __restrict__ lam, co
     const __nv_bfloat162 h = __floats2bfloat162_rn(w0, w1);
     const float2 hf = __bfloat1622float2(h);
     const __nv_bfloat162 l = __floats2bfloat162_rn(w0 - hf.x, w1 - hf.y);
-    const size_t o = ((size_t)f * M + m) * Tr + t;
+    const size_t o = tc_index(tile, frow + m, t, nch, TC_COLS);
     *reinterpret_cast<__nv_bfloat162*>(whi + o) = h;
     *reinterpret_cast<__nv_bfloat162*>(wlo + o) = l;
   }
@@ -244,7 +277,9 @@ __global__ void __launch_bounds__(128, 2) k_vtc(const __grid_constant__ CUtensor
   const unsigned tmem = ctl->tmem_base;
 
   if (warp == 0 && lane == 0) {
-    // ---- TMA producer: rows f0 * 16K .. of R, rows f0 * M .. of w, frames chunk * 64 ..
+    // ---- TMA producer: block (tile, chunk) of R and of w, one contiguous copy each
+    const unsigned long long evict_first = l2_evict_first_policy();
+    const int tile = f0 / FPC;
     for (int c = 0; c < nch; ++c) {
       const int s = c % TC_STAGES;
       if (c >= TC_STAGES && !mbar_wait(&ctl->empty[s], ((c / TC_STAGES) + 1) & 1)) {
@@ -254,10 +289,11 @@ __global__ void __launch_bounds__(128, 2) k_vtc(const __grid_constant__ CUtensor
       if (ctl->abort) break;
       unsigned char* st = ring + s * TC_STAGE_BYTES;
       mbar_arrive_expect_tx(&ctl->full[s], TC_STAGE_BYTES);
-      tma_load_2d(st, &map_rhi, c * TC_KC, f0 * 16 * K, &ctl->full[s]);
-      tma_load_2d(st + TC_A_BYTES, &map_rlo, c * TC_KC, f0 * 16 * K, &ctl->full[s]);
-      tma_load_2d(st + 2 * TC_A_BYTES, &map_whi, c * TC_KC, f0 * M, &ctl->full[s]);
-      tma_load_2d(st + 2 * TC_A_BYTES + TC_B_BYTES, &map_wlo, c * TC_KC, f0 * M, &ctl->full[s]);
+      const int blk = tile * nch + c;
+      tma_load_2d_hint(st, &map_rhi, 0, blk * TC_ROWS, &ctl->full[s], evict_first);
+      tma_load_2d_hint(st + TC_A_BYTES, &map_rlo, 0, blk * TC_ROWS, &ctl->full[s], evict_first);
+      tma_load_2d_hint(st + 2 * TC_A_BYTES, &map_whi, 0, blk * TC_COLS, &ctl->full[s], evict_first);
+      tma_load_2d_hint(st + 2 * TC_A_BYTES + TC_B_BYTES, &map_wlo, 0, blk * TC_COLS, &ctl->full[s], evict_first);
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer
@@ -502,21 +538,33 @@ bool tc_supported(int MK, int K) { return MK == 4 && (K == 1 || K == 2 || K == 4
 
 size_t tc_smem_bytes(const dfmnmf_ctx*) { return 1024 + tc_ring_bytes() + sizeof(TcSmem); }
 
-// Four 2-D bfloat16 maps with 128-byte swizzle: R_hi / R_lo ([F * 16K][Tr],
-// boxes of 128 rows x 64 frames) and w_hi / w_lo ([F * M][Tr], boxes of 32
-// rows x 64 frames).  Rows past the end read as zeros.
+// Tiles of FPC = 8 / K frequencies of the tiled operand layout (the last one
+// padded with zero rows), and the elements of R (each part) and w (each part).
+int tc_tiles(const dfmnmf_ctx* c) {
+  const int FPC = TC_ROWS / (16 * c->K);
+  return (c->F + FPC - 1) / FPC;
+}
+void tc_operand_elems(const dfmnmf_ctx* c, size_t* nr, size_t* nw) {
+  *nr = (size_t)tc_tiles(c) * TC_ROWS * c->Tr;
+  *nw = (size_t)tc_tiles(c) * TC_COLS * c->Tr;
+}
+
+// Four 2-D bfloat16 maps with 128-byte swizzle over the tiled layout viewed as
+// rows of 64 frames: R_hi / R_lo (boxes of 128 rows, one (tile, chunk) block)
+// and w_hi / w_lo (boxes of 32 rows).  The x coordinate of every copy is 0.
 cudaError_t tc_make_maps(dfmnmf_ctx* c) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
-  const cuuint64_t strides[1] = {(cuuint64_t)c->Tr * 2};
+  const cuuint64_t strides[1] = {(cuuint64_t)TC_KC * 2};
   const cuuint32_t estr[2] = {1, 1};
+  const cuuint64_t blocks = (cuuint64_t)tc_tiles(c) * (c->Tr / TC_KC);
   struct { unsigned char* map; void* base; cuuint64_t rows; cuuint32_t box_rows; } m[4] = {
-      {c->tmap_hi, c->Rhi, (cuuint64_t)c->F * 16 * c->K, TC_ROWS},
-      {c->tmap_lo, c->Rlo, (cuuint64_t)c->F * 16 * c->K, TC_ROWS},
-      {c->tmap_whi, c->wy_hi, (cuuint64_t)c->F * c->M, TC_COLS},
-      {c->tmap_wlo, c->wy_lo, (cuuint64_t)c->F * c->M, TC_COLS}};
+      {c->tmap_hi, c->Rhi, blocks * TC_ROWS, TC_ROWS},
+      {c->tmap_lo, c->Rlo, blocks * TC_ROWS, TC_ROWS},
+      {c->tmap_whi, c->wy_hi, blocks * TC_COLS, TC_COLS},
+      {c->tmap_wlo, c->wy_lo, blocks * TC_COLS, TC_COLS}};
   for (int i = 0; i < 4; ++i) {
-    const cuuint64_t dims[2] = {(cuuint64_t)c->Tr, m[i].rows};
+    const cuuint64_t dims[2] = {(cuuint64_t)TC_KC, m[i].rows};
     const cuuint32_t box[2] = {TC_KC, m[i].box_rows};
     const CUresult r = fn(reinterpret_cast<CUtensorMap*>(m[i].map), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, m[i].base,
                           dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
