@@ -146,26 +146,24 @@ def kernel_bytes(F, T, M, N, B, K, MK):
     }
 
 
-# DRAM bytes (read + write) of one band-wide launch, from the full-section ncu
-# captures summarised in profiles/kernels_paper_4x4_n5_{bf16tc,fp32}.md and
-# profiles/k_pstats_tma_paper_4x4_n5.md
-# (band-wide launches: the autotuned launch shapes of that run put the
-# per-frequency kernels on one graph branch).  A figure holds only while the
+# DRAM bytes (read + write) of one band-wide launch of the tensor-core form,
+# from the full-section ncu captures summarised in
+# profiles/kernels_paper_4x4_n5_bf16tc.md (band-wide launches: the autotuned
+# launch shapes of that run put the per-frequency kernels on one graph branch).  A figure holds only while the
 # kernel's sources are the ones captured: the digest is the first 16 hex
 # digits of sha256 over csrc/<file>, csrc/common.cuh and csrc/internal.h, and
 # `traffic` is null when it no longer matches.
 NCU_TRAFFIC = {
     "paper_4x4_n5": {
-        "k_pstats": (48278016 + 2411264, "kernels_tc.cu", "377d4027f74bd128"),  # k_pstats_tma
-        "k_stats": (27180800 + 512, "kernels_model.cu", "055798c598a0a212"),
-        "k_gupd": (27193600 + 0, "kernels_model.cu", "055798c598a0a212"),
-        "k_lambda": (388352 + 0, "kernels_model.cu", "055798c598a0a212"),
+        "k_pstats": (48276992 + 2136320, "kernels_tc.cu", "57539cc9bcff2e66"),  # k_pstats_tma<0>
+        "k_stats": (27180800 + 0, "kernels_model.cu", "709a9daa60865e43"),
+        "k_gupd": (27193856 + 0, "kernels_model.cu", "709a9daa60865e43"),
+        "k_lambda": (388608 + 0, "kernels_model.cu", "709a9daa60865e43"),
         "k_vtc": (105301248 + 2824960, "kernels_tc.cu", "57539cc9bcff2e66"),
-        "k_wprep": (6620416 + 0, "kernels_tc.cu", "377d4027f74bd128"),
+        "k_wprep": (6621440 + 0, "kernels_tc.cu", "57539cc9bcff2e66"),
         "k_ip": (2702080 + 0, "kernels_ip.cu", "77060888d10b3a1c"),
-        "k_wupd": (13268480 + 0, "kernels_nmf.cu", "115f2802f9bdee8b"),
-        "k_hupd": (13270016 + 0, "kernels_nmf.cu", "115f2802f9bdee8b"),
-        "k_cov": (47757312 + 24320, "kernels_cov.cu", "dad4d0b2f3648048"),
+        "k_wupd": (13268480 + 0, "kernels_nmf.cu", "fb942ef849bd9bf5"),
+        "k_hupd": (13270528 + 0, "kernels_nmf.cu", "fb942ef849bd9bf5"),
     },
 }
 

@@ -57,6 +57,7 @@ struct dfmnmf_adj {
   double *Wb, *Wb1, *Hb, *Hb1, *gb, *gb1;
   double *lamb, *yb, *Pb, *Ab, *Db, *nb, *db;
   double2* Vb;
+  double* Vh;  // packed Hermitian parts of Vb (k_a_Vh)
   // Wiener-filter loss
   double2 *Binv, *ubar, *cvec, *zbar;
   double* G4;
@@ -255,15 +256,31 @@ __global__ void k_a_nmf_t(const double* __restrict__ X, const double* __restrict
   if (lane == 0) out[w] = (acc ? out[w] : 0.0) + s;
 }
 
-// out[n][b][t] (+)= sum_f X[n][f][b] Y[n][f][t]
-__global__ void k_a_nmf_f(const double* __restrict__ X, const double* __restrict__ Y, double* __restrict__ out, int N,
-                          int F, int B, int T, int acc) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (size_t)N * B * T) return;
-  const int t = (int)(i % T), b = (int)((i / T) % B), n = (int)(i / ((size_t)B * T));
+// out[n][b][t] (+)= sum_f X[n][f][b] Y[n][f][t].  CTA = (32 frames, one (n, b)); its 8 warps
+// take every 8th frequency and their partial sums are added in warp order through shared
+// memory (a fixed order: the result does not depend on scheduling).
+constexpr int NMF_F_WARPS = 8;
+__global__ void __launch_bounds__(32 * NMF_F_WARPS) k_a_nmf_f(const double* __restrict__ X,
+                                                             const double* __restrict__ Y,
+                                                             double* __restrict__ out, int N, int F, int B, int T,
+                                                             int acc) {
+  __shared__ double part[NMF_F_WARPS][32];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int t = blockIdx.x * 32 + lane;
+  const int b = (int)(blockIdx.y % B), n = (int)(blockIdx.y / B);
   double s = 0.0;
-  for (int f = 0; f < F; ++f) s += X[((size_t)n * F + f) * B + b] * Y[((size_t)n * F + f) * T + t];
-  out[i] = (acc ? out[i] : 0.0) + s;
+  if (t < T)
+    for (int f = wp; f < F; f += NMF_F_WARPS)
+      s += X[((size_t)n * F + f) * B + b] * Y[((size_t)n * F + f) * T + t];
+  part[wp][lane] = s;
+  __syncthreads();
+  if (wp == 0 && t < T) {
+    double v = 0.0;
+#pragma unroll
+    for (int w = 0; w < NMF_F_WARPS; ++w) v += part[w][lane];
+    const size_t i = ((size_t)n * B + b) * T + t;
+    out[i] = (acc ? out[i] : 0.0) + v;
+  }
 }
 
 // y[f][t][m] = sum_n lam[n][f][t] g[f][n][m] (before the floor) and ry = 1 / max(y, eps).
@@ -282,16 +299,23 @@ __global__ void k_a_y(const double* __restrict__ lam, const double* __restrict__
 }
 
 // V[f][k][mu][a][b] = (1/T) sum_t x_a conj(x_b) / yhat0[f][t][o_k + mu]   (Eq. 13)
-// One warp per (f, k, a, b), lanes over t: the product x_a conj(x_b) is formed
-// once per frame and weighted by the reciprocals r0 of all MK microphones.
+// One warp per (f, k) and pair a <= b (V[b][a] = conj V[a][b]), lanes over t: the product
+// x_a conj(x_b) is formed once per frame and weighted by the reciprocals r0 of all MK
+// microphones.
 template <int MK>
 __global__ void k_a_V(const float2* __restrict__ x, const double* __restrict__ r0, double2* __restrict__ V, int F,
                       int T, int K) {
+  constexpr int NP = MK * (MK + 1) / 2;
   const size_t w = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (w >= (size_t)F * K * MK * MK) return;
-  const int b = (int)(w % MK), a = (int)((w / MK) % MK), k = (int)((w / (MK * MK)) % K);
-  const int f = (int)(w / ((size_t)MK * MK * K));
+  if (w >= (size_t)F * K * NP) return;
+  int pidx = (int)(w % NP), a = 0;
+  while (pidx >= MK - a) {  // pair index -> (a, b), a <= b, row by row
+    pidx -= MK - a;
+    ++a;
+  }
+  const int b = a + pidx;
+  const int k = (int)((w / NP) % K), f = (int)(w / ((size_t)NP * K));
   const int M = K * MK, o = k * MK;
   double sr[MK], si[MK];
 #pragma unroll
@@ -313,8 +337,12 @@ __global__ void k_a_V(const float2* __restrict__ x, const double* __restrict__ r
   }
   if (lane == 0) {
 #pragma unroll
-    for (int mu = 0; mu < MK; ++mu)
-      V[(((size_t)f * K + k) * MK + mu) * MK * MK + a * MK + b] = make_double2(sr[mu] / T, si[mu] / T);
+    for (int mu = 0; mu < MK; ++mu) {
+      double2* Vm = V + (((size_t)f * K + k) * MK + mu) * MK * MK;
+      const double vr = sr[mu] / T, vi = si[mu] / T;
+      Vm[a * MK + b] = make_double2(vr, vi);
+      if (a != b) Vm[b * MK + a] = make_double2(vr, -vi);
+    }
   }
 }
 
@@ -334,22 +362,33 @@ __global__ void k_a_P(const float2* __restrict__ x, const double2* __restrict__ 
   }
 }
 
-// A[n][f][t] = sum_m g P / yhat^2, D[n][f][t] = sum_m g / yhat
+// A[n][f][t] = sum_m g P / yhat^2, D[n][f][t] = sum_m g / yhat; one thread per (f, t) for all
+// sources, P / yhat^2 and 1 / yhat formed once per microphone
 __global__ void k_a_AD(const double* __restrict__ P, const double* __restrict__ ry, const double* __restrict__ g,
                        double* __restrict__ A, double* __restrict__ D, int N, int F, int T, int M) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (size_t)N * F * T) return;
-  const int t = (int)(i % T), f = (int)((i / T) % F), n = (int)(i / ((size_t)F * T));
-  const double* gr = g + ((size_t)f * N + n) * M;
-  const size_t r = ((size_t)f * T + t) * M;
-  double a = 0.0, d = 0.0;
+  if (i >= (size_t)F * T) return;
+  const int t = (int)(i % T), f = (int)(i / T);
+  const size_t r = i * M;
+  double a[16], d[16];
+#pragma unroll
+  for (int n = 0; n < 16; ++n) a[n] = d[n] = 0.0;
   for (int m = 0; m < M; ++m) {
-    const double rv = ry[r + m];
-    a += gr[m] * P[r + m] * (rv * rv);
-    d += gr[m] * rv;
+    const double rv = ry[r + m], u = P[r + m] * (rv * rv);
+#pragma unroll
+    for (int n = 0; n < 16; ++n)
+      if (n < N) {
+        const double gg = g[((size_t)f * N + n) * M + m];
+        a[n] += gg * u;
+        d[n] += gg * rv;
+      }
   }
-  A[i] = a;
-  D[i] = d;
+#pragma unroll
+  for (int n = 0; n < 16; ++n)
+    if (n < N) {
+      A[((size_t)n * F + f) * T + t] = a[n];
+      D[((size_t)n * F + f) * T + t] = d[n];
+    }
 }
 
 // out = theta sqrt(num / max(den, eps))   (Eqs. 8-10)
@@ -469,16 +508,18 @@ __global__ void k_a_gstat_b(const double* __restrict__ numb, const double* __res
   const int t = (int)(i % T), f = (int)(i / T);
   const size_t r = i * M;
   for (int m = 0; m < M; ++m) {
-    const double rv = ry[r + m], r2 = rv * rv, r3 = r2 * rv, pm = P[r + m];
-    double a = 0.0, pb = 0.0;
+    // sum_n lam numb and sum_n lam denb first, then the per-microphone factors
+    const double rv = ry[r + m], r2 = rv * rv, pm = P[r + m];
+    double u = 0.0, v = 0.0;
     for (int n = 0; n < N; ++n) {
       const double l = lam[((size_t)n * F + f) * T + t];
       const size_t q = ((size_t)f * N + n) * M + m;
-      a += l * (-2.0 * numb[q] * pm * r3 - denb[q] * r2);
-      pb += numb[q] * l * r2;
+      u += l * numb[q];
+      v += l * denb[q];
     }
+    const double a = -2.0 * pm * (r2 * rv) * u - r2 * v;
     yb[r + m] = y[r + m] > eps ? a : 0.0;
-    Pb[r + m] += pb;
+    Pb[r + m] += r2 * u;
   }
   for (int n = 0; n < N; ++n) {
     double s = 0.0;
@@ -501,14 +542,17 @@ __global__ void k_a_stat_b(const double* __restrict__ Ab, const double* __restri
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (size_t)F * T * M) return;
   const int m = (int)(i % M), t = (int)((i / M) % T), f = (int)(i / ((size_t)T * M));
-  const double rv = ry[i], r2 = rv * rv, r3 = r2 * rv, pi = P[i];
-  double a = 0.0, pb = 0.0;
+  // the source sums first: sum_n Ab g and sum_n Db g, then the per-microphone factors
+  const double rv = ry[i], r2 = rv * rv, pi = P[i];
+  double sa = 0.0, sd = 0.0;
   for (int n = 0; n < N; ++n) {
     const size_t nf = ((size_t)n * F + f) * T + t;
     const double gg = g[((size_t)f * N + n) * M + m];
-    a += -2.0 * Ab[nf] * gg * pi * r3 - Db[nf] * gg * r2;
-    pb += Ab[nf] * gg * r2;
+    sa += Ab[nf] * gg;
+    sd += Db[nf] * gg;
   }
+  const double a = -2.0 * pi * (r2 * rv) * sa - r2 * sd;
+  const double pb = r2 * sa;
   const double v = y[i] > eps ? a : 0.0;
   yb[i] = (acc ? yb[i] : 0.0) + v;
   Pb[i] += pb;
@@ -697,26 +741,64 @@ __global__ void k_a_ipb(const double2* __restrict__ Qs, const double2* __restric
     for (int j = 0; j < MK; ++j) Qbout[(size_t)id * MK * MK + i * MK + j] = Qb[i][j];
 }
 
-// Reverse of Eq. 13 and of 1/yhat0: ybar0[f][t][o_k+mu] += -Re(x^H Vbar_mu x) / (T yhat0^2)
-__global__ void k_a_Vb(const float2* __restrict__ x, const double2* __restrict__ Vb, const double* __restrict__ y0,
-                       const double* __restrict__ r0, double* __restrict__ yb, int F, int T, int K, int MK,
-                       double eps) {
+// Reverse of Eq. 13 and of 1/yhat0: ybar0[f][t][o_k+mu] += -Re(x^H Vbar_mu x) / (T yhat0^2).
+// Re(x^H Vb x) = sum_a Re Vb_aa |x_a|^2 + sum_{a<b} [(Re Vb_ab + Re Vb_ba) Re p_ab
+// - (Im Vb_ab - Im Vb_ba) Im p_ab] with p_ab = conj(x_a) x_b: k_a_Vh packs these MK^2 reals per
+// (f, k, mu) (diagonal at [a][a], the sums at [a][b], the differences at [b][a] for a < b), and
+// k_a_Vb forms the products p_ab of one (f, t, k) once for all mu.
+template <int MK>
+__global__ void k_a_Vh(const double2* __restrict__ Vb, double* __restrict__ Vh, size_t n) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int M = K * MK;
-  if (i >= (size_t)F * T * M) return;
-  const int m = (int)(i % M), t = (int)((i / M) % T), f = (int)(i / ((size_t)T * M));
-  const int k = m / MK, mu = m % MK, o = k * MK;
-  if (!(y0[i] > eps)) return;
-  const double2* vb = Vb + (((size_t)f * K + k) * MK + mu) * MK * MK;
-  const float2* xr = x + ((size_t)f * T + t) * M + o;
-  double s = 0.0;
+  if (i >= n) return;  // i = (f K + k) MK + mu
+  const double2* v = Vb + i * MK * MK;
+  double* h = Vh + i * MK * MK;
+#pragma unroll
   for (int a = 0; a < MK; ++a) {
-    double2 v = make_double2(0.0, 0.0);
-    for (int b = 0; b < MK; ++b) v = cadd(v, cmul(vb[a * MK + b], ld(xr + b)));
-    const double2 xa = ld(xr + a);
-    s += xa.x * v.x + xa.y * v.y;  // Re(conj(x_a) (Vbar x)_a)
+    h[a * MK + a] = v[a * MK + a].x;
+#pragma unroll
+    for (int b = a + 1; b < MK; ++b) {
+      h[a * MK + b] = v[a * MK + b].x + v[b * MK + a].x;
+      h[b * MK + a] = v[a * MK + b].y - v[b * MK + a].y;
+    }
   }
-  yb[i] += -s * (r0[i] * r0[i]) / (double)T;
+}
+
+template <int MK>
+__global__ void k_a_Vb(const float2* __restrict__ x, const double* __restrict__ Vh, const double* __restrict__ y0,
+                       const double* __restrict__ r0, double* __restrict__ yb, int F, int T, int K, double eps) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)F * T * K) return;
+  const int k = (int)(i % K), t = (int)((i / K) % T), f = (int)(i / ((size_t)K * T));
+  const int M = K * MK, o = k * MK;
+  const float2* xr = x + ((size_t)f * T + t) * M + o;
+  double2 xv[MK];
+#pragma unroll
+  for (int a = 0; a < MK; ++a) xv[a] = ld(xr + a);
+  double pr[MK][MK], pi[MK][MK];  // pr[a][a] = |x_a|^2; pr/pi[a][b] = Re/Im conj(x_a) x_b for a < b
+#pragma unroll
+  for (int a = 0; a < MK; ++a) {
+    pr[a][a] = xv[a].x * xv[a].x + xv[a].y * xv[a].y;
+#pragma unroll
+    for (int b = a + 1; b < MK; ++b) {
+      pr[a][b] = xv[a].x * xv[b].x + xv[a].y * xv[b].y;
+      pi[a][b] = xv[a].x * xv[b].y - xv[a].y * xv[b].x;
+    }
+  }
+  const double invT = 1.0 / (double)T;
+#pragma unroll
+  for (int mu = 0; mu < MK; ++mu) {
+    const size_t e = ((size_t)f * T + t) * M + o + mu;
+    if (!(y0[e] > eps)) continue;
+    const double* h = Vh + (((size_t)f * K + k) * MK + mu) * MK * MK;
+    double s = 0.0;
+#pragma unroll
+    for (int a = 0; a < MK; ++a) {
+      s += h[a * MK + a] * pr[a][a];
+#pragma unroll
+      for (int b = a + 1; b < MK; ++b) s += h[a * MK + b] * pr[a][b] - h[b * MK + a] * pi[a][b];
+    }
+    yb[e] += -s * (r0[e] * r0[e]) * invT;
+  }
 }
 
 // ---------------------------------------------------------------- losses
@@ -955,7 +1037,8 @@ cudaError_t nmf_t(const Dims& d, const double* X, const double* Y, double* out, 
   return cudaSuccess;
 }
 cudaError_t nmf_f(const Dims& d, const double* X, const double* Y, double* out, int acc, cudaStream_t s) {
-  AL(k_a_nmf_f<<<nblk(d.nbt), 256, 0, s>>>(X, Y, out, d.N, d.F, d.B, d.T, acc));
+  AL(k_a_nmf_f<<<dim3((unsigned)((d.T + 31) / 32), (unsigned)(d.N * d.B)), 32 * NMF_F_WARPS, 0, s>>>(
+      X, Y, out, d.N, d.F, d.B, d.T, acc));
   return cudaSuccess;
 }
 
@@ -969,18 +1052,19 @@ cudaError_t reverse_iteration(dfmnmf_adj* a, const Dims& d, cudaStream_t s) {
   // forward, recomputed in FP64
   cudaError_t e = model(d, a->Wd, a->Hd, a->gd, a->lam0, a->y0, a->r0, s);
   if (e != cudaSuccess) return e;
-  MK_DISPATCH(d.MK, k_a_V, nblk(d.nq * 32), 256, 0, s, c->x, a->r0, a->V, d.F, d.T, d.K);
+  MK_DISPATCH(d.MK, k_a_V, nblk((size_t)d.F * d.K * (d.MK * (d.MK + 1) / 2) * 32), 256, 0, s, c->x, a->r0, a->V,
+              d.F, d.T, d.K);
   AL((void)0);
   MK_DISPATCH(d.MK, k_a_ipfwd, nblk(nb, 64), 64, 0, s, a->Qd, a->V, a->Qs, nb, eps, (double)c->singular_rtol, a->flags);
   AL((void)0);
   const double2* Qn = a->Qs + (size_t)d.MK * d.MK * d.MK;  // rows after the last update, stride (MK+1) MK^2
   const size_t qstr = (size_t)(d.MK + 1) * d.MK * d.MK;
   AL(k_a_P<<<nblk((size_t)d.F * d.T * d.K), 256, 0, s>>>(c->x, Qn, qstr, a->P, d.F, d.T, d.K, d.MK));
-  AL(k_a_AD<<<nblk(d.nft), 256, 0, s>>>(a->P, a->r0, a->gd, a->A0, a->D0, d.N, d.F, d.T, d.M));
+  AL(k_a_AD<<<nblk((size_t)d.F * d.T), 256, 0, s>>>(a->P, a->r0, a->gd, a->A0, a->D0, d.N, d.F, d.T, d.M));
   if ((e = nmf_t(d, a->A0, a->Hd, a->numW, 0, s)) || (e = nmf_t(d, a->D0, a->Hd, a->denW, 0, s))) return e;
   AL(k_a_mu<<<nblk(d.nfb), 256, 0, s>>>(a->Wd, a->numW, a->denW, a->W1, d.nfb, eps));
   if ((e = model(d, a->W1, a->Hd, a->gd, a->lam1, a->y1, a->r1, s))) return e;
-  AL(k_a_AD<<<nblk(d.nft), 256, 0, s>>>(a->P, a->r1, a->gd, a->A1, a->D1, d.N, d.F, d.T, d.M));
+  AL(k_a_AD<<<nblk((size_t)d.F * d.T), 256, 0, s>>>(a->P, a->r1, a->gd, a->A1, a->D1, d.N, d.F, d.T, d.M));
   if ((e = nmf_f(d, a->W1, a->A1, a->numH, 0, s)) || (e = nmf_f(d, a->W1, a->D1, a->denH, 0, s))) return e;
   AL(k_a_mu<<<nblk(d.nbt), 256, 0, s>>>(a->Hd, a->numH, a->denH, a->H1, d.nbt, eps));
   if ((e = model(d, a->W1, a->H1, a->gd, a->lam2, a->y2, a->r2, s))) return e;
@@ -1018,7 +1102,11 @@ cudaError_t reverse_iteration(dfmnmf_adj* a, const Dims& d, cudaStream_t s) {
   AL((void)0);
   MK_DISPATCH(d.MK, k_a_ipb, nblk(nb, 64), 64, 0, s, a->Qs, a->V, a->Qb1, a->Qb, a->Vb, nb, eps);
   AL((void)0);
-  AL(k_a_Vb<<<nblk(d.ftm), 256, 0, s>>>(c->x, a->Vb, a->y0, a->r0, a->yb, d.F, d.T, d.K, d.MK, eps));
+  MK_DISPATCH(d.MK, k_a_Vh, nblk(d.nq / d.MK), 256, 0, s, a->Vb, a->Vh, d.nq / d.MK);  // one thread per (f, k, mu)
+  AL((void)0);
+  MK_DISPATCH(d.MK, k_a_Vb, nblk((size_t)d.F * d.T * d.K), 256, 0, s, c->x, a->Vh, a->y0, a->r0, a->yb, d.F, d.T,
+              d.K, eps);
+  AL((void)0);
   // reverse of the model at the input state
   AL(k_a_gbar<<<nblk(d.fnm * 32), 256, 0, s>>>(a->Ab, a->Db, a->yb, a->lam0, a->P, a->r0, a->gb, d.N, d.F, d.T,
                                                 d.M));
@@ -1102,7 +1190,7 @@ void free_adj(dfmnmf_adj* a) {
                a->P, a->A0, a->D0,
                a->A1, a->D1, a->numW, a->denW, a->W1, a->numH, a->denH, a->H1, a->numG, a->denG, a->V, a->Qs,
                a->Qb, a->Qb1, a->Wb, a->Wb1, a->Hb, a->Hb1, a->gb, a->gb1, a->lamb, a->yb, a->Pb, a->Ab, a->Db,
-               a->nb, a->db, a->Vb, a->Binv, a->ubar, a->cvec, a->zbar, a->G4, a->red, a->flags};
+               a->nb, a->db, a->Vb, a->Vh, a->Binv, a->ubar, a->cvec, a->zbar, a->G4, a->red, a->flags};
   for (void* q : p)
     if (q) cudaFree(q);
   delete a;
@@ -1154,7 +1242,7 @@ int dfmnmf_adjoint_create(dfmnmf_adj** out, dfmnmf_ctx* c, int n_iter, int every
             aalloc(&a->Qb, d.nq) && aalloc(&a->Qb1, d.nq) && aalloc(&a->Wb, d.nfb) && aalloc(&a->Wb1, d.nfb) &&
             aalloc(&a->Hb, d.nbt) && aalloc(&a->Hb1, d.nbt) && aalloc(&a->gb, d.fnm) && aalloc(&a->gb1, d.fnm) &&
             aalloc(&a->lamb, d.nft) && aalloc(&a->yb, d.ftm) && aalloc(&a->Pb, d.ftm) && aalloc(&a->Ab, d.nft) &&
-            aalloc(&a->Db, d.nft) && aalloc(&a->nb, nmax) && aalloc(&a->db, nmax) && aalloc(&a->Vb, d.nv) &&
+            aalloc(&a->Db, d.nft) && aalloc(&a->nb, nmax) && aalloc(&a->db, nmax) && aalloc(&a->Vb, d.nv) && aalloc(&a->Vh, d.nv) &&
             aalloc(&a->Binv, d.nq) && (!wien || (aalloc(&a->ubar, d.nftm) && aalloc(&a->cvec, d.nftm) &&
                                                  aalloc(&a->zbar, d.ftm) && aalloc(&a->G4, d.nftm))) &&
             aalloc(&a->red, 1) && aalloc(&a->flags, 4);
