@@ -155,15 +155,15 @@ def kernel_bytes(F, T, M, N, B, K, MK):
 # `traffic` is null when it no longer matches.
 NCU_TRAFFIC = {
     "paper_4x4_n5": {
-        "k_pstats": (48276992 + 2136320, "kernels_tc.cu", "57539cc9bcff2e66"),  # k_pstats_tma<0>
-        "k_stats": (27180800 + 0, "kernels_model.cu", "709a9daa60865e43"),
-        "k_gupd": (27193856 + 0, "kernels_model.cu", "709a9daa60865e43"),
-        "k_lambda": (388608 + 0, "kernels_model.cu", "709a9daa60865e43"),
-        "k_vtc": (105301248 + 2824960, "kernels_tc.cu", "57539cc9bcff2e66"),
-        "k_wprep": (6621440 + 0, "kernels_tc.cu", "57539cc9bcff2e66"),
-        "k_ip": (2702080 + 0, "kernels_ip.cu", "77060888d10b3a1c"),
-        "k_wupd": (13268480 + 0, "kernels_nmf.cu", "fb942ef849bd9bf5"),
-        "k_hupd": (13270528 + 0, "kernels_nmf.cu", "fb942ef849bd9bf5"),
+        "k_pstats": (48269824 + 2129152, "kernels_tc.cu", "8477a9db91e4a1db"),  # k_pstats_tma<0>
+        "k_stats": (27179264 + 0, "kernels_model.cu", "d019e79f136de230"),
+        "k_gupd": (27192832 + 0, "kernels_model.cu", "d019e79f136de230"),
+        "k_lambda": (388608 + 0, "kernels_model.cu", "d019e79f136de230"),
+        "k_vtc": (105289728 + 2770688, "kernels_tc.cu", "8477a9db91e4a1db"),
+        "k_wprep": (6619648 + 0, "kernels_tc.cu", "8477a9db91e4a1db"),
+        "k_ip": (2701824 + 0, "kernels_ip.cu", "8f14118b76b1c4d8"),
+        "k_wupd": (13268736 + 0, "kernels_nmf.cu", "36821db759ba7376"),
+        "k_hupd": (13270272 + 0, "kernels_nmf.cu", "36821db759ba7376"),
     },
 }
 
@@ -176,7 +176,7 @@ NCU_TRAFFIC = {
 ALU_KERNELS = ("k_ip", "k_cov")
 NCU_INST = {  # keyed by (kernel, form): k_ip refines three times in the FP32 form, once in the tensor-core form
     "paper_4x4_n5": {
-        ("k_ip", "bf16tc"): (6995412, "kernels_ip.cu", "77060888d10b3a1c"),
+        ("k_ip", "bf16tc"): (6995412, "kernels_ip.cu", "8f14118b76b1c4d8"),
         ("k_cov", "fp32"): (56279691, "kernels_cov.cu", "dad4d0b2f3648048"),
     },
 }

@@ -92,7 +92,8 @@ typedef struct dfmnmf_desc {
   int N, B;           /* sources, NMF bases per source                          */
   int precision;      /* dfmnmf_precision                                      */
   int ip_arith;       /* dfmnmf_ip_arith                                       */
-  double floor_eps;   /* floor of yhat, MU denominators, IP normaliser (Sec. IV-A: 1e-6); <= 0 means 1e-6 */
+  double floor_eps;   /* floor of yhat, MU denominators, IP normaliser (Sec. IV-A: 1e-6); <= 0 means 1e-6;
+                         below the smallest normal float (about 1.2e-38) it is raised to that value */
 } dfmnmf_desc;
 
 /*

@@ -7,6 +7,8 @@
 
 #include <string>
 
+#include <float.h>
+
 #include "../../include/dfmnmf.h"
 #include "common.cuh"
 #include "internal.h"
@@ -247,6 +249,7 @@ int dfmnmf_init(dfmnmf_ctx** out, const dfmnmf_desc* d, const void* x, const flo
   c->precision = d->precision;
   c->ip_arith = d->ip_arith;
   c->eps = (float)(d->floor_eps > 0 ? d->floor_eps : 1e-6);
+  if (c->eps < FLT_MIN) c->eps = FLT_MIN;  // the floored quantities stay normal floats
   c->singular_rtol = (d->ip_arith == DFMNMF_IP_F32) ? 1e-6f : 1e-12f;
   if (cudaGetDevice(&c->device) != cudaSuccess) {
     cudaGetLastError();

@@ -215,11 +215,15 @@ __device__ __forceinline__ void warp_reduce_scatter(float (&v)[C], int lane) {
 
 __device__ __forceinline__ bool finitef(float v) { return isfinite(v); }
 
-// Hardware reciprocal (rcp.approx.f32, relative error <= 2^-23): the weights
-// 1/yhat only ever enter as relative perturbations of positive terms.
+// Hardware reciprocal (rcp.approx.ftz.f32, relative error <= 2^-23): the
+// weights 1/yhat only ever enter as relative perturbations of positive terms.
+// Every argument is max(yhat, eps) with eps at least the smallest normal float
+// (dfmnmf_init raises a smaller floor to it), so flushing subnormal inputs
+// changes nothing; the flush variant needs no subnormal handling around the
+// hardware instruction.
 __device__ __forceinline__ float fast_rcp(float a) {
   float r;
-  asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(a));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
   return r;
 }
 

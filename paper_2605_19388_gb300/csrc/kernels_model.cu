@@ -94,11 +94,17 @@ cudaError_t launch_lambda(const dfmnmf_ctx* c, cudaStream_t s) {
 // from shared memory), so nothing is padded to a maximum source count.  The
 // K shares of a frame sit in adjacent lanes and are added by xor shuffles
 // (K a power of two) or through shared memory.
+// Row of MK floats from shared memory, 16 bytes per load when MK is a
+// multiple of 4 (callers pass rows that start at multiples of MK floats of a
+// 16-byte aligned array).
 template <int MK>
-__device__ __forceinline__ void load_row(const float* p, float (&v)[MK]) {
-  if constexpr (MK == 4) {
-    const float4 q = *reinterpret_cast<const float4*>(p);
-    v[0] = q.x; v[1] = q.y; v[2 % MK] = q.z; v[3 % MK] = q.w;
+__device__ __forceinline__ void load_row(const float* __restrict__ p, float (&v)[MK]) {
+  if constexpr (MK % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < MK; i += 4) {
+      const float4 q = *reinterpret_cast<const float4*>(p + i);
+      v[i] = q.x; v[i + 1] = q.y; v[i + 2] = q.z; v[i + 3] = q.w;
+    }
   } else {
 #pragma unroll
     for (int i = 0; i < MK; ++i) v[i] = p[i];
@@ -301,14 +307,16 @@ __global__ void __launch_bounds__(128) k_pstats_ft(const float2* __restrict__ x,
 #pragma unroll
     for (int n = 0; n < LAM_R; ++n) {
       if (n < N) {
-        const float* gr = gs + n * M;
+        float gr[M];
+        load_row<M>(gs + n * M, gr);
 #pragma unroll
         for (int m = 0; m < M; ++m) ys[m] = fmaf(lv[n], gr[m], ys[m]);
       }
     }
     for (int n = LAM_R; n < N; ++n) {
       const float l = __ldg(lt + (size_t)n * F * Tp + t);
-      const float* gr = gs + n * M;
+      float gr[M];
+      load_row<M>(gs + n * M, gr);
 #pragma unroll
       for (int m = 0; m < M; ++m) ys[m] = fmaf(l, gr[m], ys[m]);
     }
@@ -319,7 +327,8 @@ __global__ void __launch_bounds__(128) k_pstats_ft(const float2* __restrict__ x,
       u[m] = pv[m] * w[m] * w[m];
     }
     for (int n = 0; n < N; ++n) {
-      const float* gr = gs + n * M;
+      float gr[M];
+      load_row<M>(gs + n * M, gr);
       float a = 0.f, d = 0.f;
 #pragma unroll
       for (int m = 0; m < M; ++m) {

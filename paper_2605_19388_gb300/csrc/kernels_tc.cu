@@ -184,22 +184,24 @@ __global__ void __launch_bounds__(128) k_rprep(const float2* __restrict__ x, __n
 // (Eq. 2 with the floor of Sec. IV-A), split into two bfloat16 parts and
 // stored as rows (f % FPC) * M + m of tile f / FPC, Tr frames, zero beyond T:
 // the B operand of the contraction, read by TMA in the same 128-byte swizzled
-// tiles as R.  Each
-// thread forms two adjacent frames of one frequency for every microphone
-// (float2 lambda loads, g[f] broadcast from shared memory, 4-byte stores
-// coalesced along t).  NM is N itself for N <= 8 and 16 (guarded) above.
-template <int NM>
+// tiles as R.  Each thread forms two adjacent frames of one frequency for
+// every microphone (float2 lambda loads, g[f] from shared memory four
+// microphones per load, 4-byte stores coalesced along t; row m + 1 of a tile
+// block sits 64 frames after row m).  NM is N itself for N <= 8 and 16
+// (guarded) above; MV is M (4, 8, 16 or 32).
+template <int NM, int MV>
 __global__ void __launch_bounds__(128) k_wprep(const float* __restrict__ lam, const float* __restrict__ g,
                                                __nv_bfloat16* __restrict__ whi, __nv_bfloat16* __restrict__ wlo,
-                                               int F, int T, int Tp, int Tr, int M, int N, float eps, int fb) {
-  extern __shared__ float gw[];  // [N][M]
+                                               int F, int T, int Tp, int Tr, int N, float eps, int fb) {
+  extern __shared__ __align__(16) float gw[];  // [N][MV]
   const int f = fb + blockIdx.y;
-  for (int i = threadIdx.x; i < N * M; i += blockDim.x) gw[i] = g[(size_t)f * N * M + i];
+  for (int i = threadIdx.x; i < N * MV; i += blockDim.x) gw[i] = g[(size_t)f * N * MV + i];
   __syncthreads();
   const int t = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   if (t >= Tr) return;
-  const int FPC = TC_COLS / M, nch = Tr / TC_KC;
-  const int tile = f / FPC, frow = (f % FPC) * M;
+  constexpr int FPC = TC_COLS / MV;
+  const int nch = Tr / TC_KC;
+  const int tile = f / FPC, frow = (f % FPC) * MV;
   float2 lv[NM];
 #pragma unroll
   for (int n = 0; n < NM; ++n) {
@@ -207,23 +209,35 @@ __global__ void __launch_bounds__(128) k_wprep(const float* __restrict__ lam, co
     if ((NM <= 8 || n < N) && t < Tp) lv[n] = *reinterpret_cast<const float2*>(lam + ((size_t)n * F + f) * Tp + t);
   }
   const bool v0 = t < T, v1 = t + 1 < T;
-  for (int m = 0; m < M; ++m) {
-    float2 y = make_float2(0.f, 0.f);
+  const size_t o0 = tc_index(tile, frow, t, nch, TC_COLS);
+  __nv_bfloat162* ph = reinterpret_cast<__nv_bfloat162*>(whi + o0);
+  __nv_bfloat162* pl = reinterpret_cast<__nv_bfloat162*>(wlo + o0);
+#pragma unroll
+  for (int m4 = 0; m4 < MV; m4 += 4) {
+    float2 y[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) y[j] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int n = 0; n < NM; ++n)
       if (NM <= 8 || n < N) {
-        const float gv = gw[n * M + m];
-        y.x = fmaf(lv[n].x, gv, y.x);
-        y.y = fmaf(lv[n].y, gv, y.y);
+        const float4 gv4 = *reinterpret_cast<const float4*>(gw + n * MV + m4);
+        const float gv[4] = {gv4.x, gv4.y, gv4.z, gv4.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          y[j].x = fmaf(lv[n].x, gv[j], y[j].x);
+          y[j].y = fmaf(lv[n].y, gv[j], y[j].y);
+        }
       }
-    const float w0 = v0 ? fast_rcp(fmaxf(y.x, eps)) : 0.f;
-    const float w1 = v1 ? fast_rcp(fmaxf(y.y, eps)) : 0.f;
-    const __nv_bfloat162 h = __floats2bfloat162_rn(w0, w1);
-    const float2 hf = __bfloat1622float2(h);
-    const __nv_bfloat162 l = __floats2bfloat162_rn(w0 - hf.x, w1 - hf.y);
-    const size_t o = tc_index(tile, frow + m, t, nch, TC_COLS);
-    *reinterpret_cast<__nv_bfloat162*>(whi + o) = h;
-    *reinterpret_cast<__nv_bfloat162*>(wlo + o) = l;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float w0 = v0 ? fast_rcp(fmaxf(y[j].x, eps)) : 0.f;
+      const float w1 = v1 ? fast_rcp(fmaxf(y[j].y, eps)) : 0.f;
+      const __nv_bfloat162 h = __floats2bfloat162_rn(w0, w1);
+      const float2 hf = __bfloat1622float2(h);
+      const __nv_bfloat162 l = __floats2bfloat162_rn(w0 - hf.x, w1 - hf.y);
+      ph[(m4 + j) * (TC_KC / 2)] = h;
+      pl[(m4 + j) * (TC_KC / 2)] = l;
+    }
   }
 }
 
@@ -458,11 +472,15 @@ __global__ void __launch_bounds__(128) k_pstats_tma(const __grid_constant__ CUte
       if (COMP) {
         y = cdot2<MK>(qh, Ql + (k * MK + mu) * MK, xv);
       } else {
+        // the row of Q as two 16-byte shared-memory loads (rows are 32 bytes, 16-byte aligned)
+        const float4 q01 = reinterpret_cast<const float4*>(qh)[0], q23 = reinterpret_cast<const float4*>(qh)[1];
+        const float2 qv[4] = {make_float2(q01.x, q01.y), make_float2(q01.z, q01.w), make_float2(q23.x, q23.y),
+                              make_float2(q23.z, q23.w)};
         float yr = 0.f, yi = 0.f;
 #pragma unroll
         for (int nu = 0; nu < MK; ++nu) {
-          yr = fmaf(qh[nu].x, xv[nu].x, fmaf(-qh[nu].y, xv[nu].y, yr));
-          yi = fmaf(qh[nu].x, xv[nu].y, fmaf(qh[nu].y, xv[nu].x, yi));
+          yr = fmaf(qv[nu].x, xv[nu].x, fmaf(-qv[nu].y, xv[nu].y, yr));
+          yi = fmaf(qv[nu].x, xv[nu].y, fmaf(qv[nu].y, xv[nu].x, yi));
         }
         y = make_float2(yr, yi);
       }
@@ -484,9 +502,15 @@ __global__ void __launch_bounds__(128) k_pstats_tma(const __grid_constant__ CUte
   for (int m = 0; m < M; ++m) ys[m] = 0.f;
   for (int n = 0; n < N; ++n) {
     const float l = ls[n * PT_ROWS + i];
-    const float* gr = gs + n * M;
+    const float4* gr4 = reinterpret_cast<const float4*>(gs + n * M);  // 16-byte aligned: M = 16
 #pragma unroll
-    for (int m = 0; m < M; ++m) ys[m] = fmaf(l, gr[m], ys[m]);
+    for (int m4 = 0; m4 < M / 4; ++m4) {
+      const float4 gv = gr4[m4];
+      ys[4 * m4] = fmaf(l, gv.x, ys[4 * m4]);
+      ys[4 * m4 + 1] = fmaf(l, gv.y, ys[4 * m4 + 1]);
+      ys[4 * m4 + 2] = fmaf(l, gv.z, ys[4 * m4 + 2]);
+      ys[4 * m4 + 3] = fmaf(l, gv.w, ys[4 * m4 + 3]);
+    }
   }
   float w[M], u[M];
 #pragma unroll
@@ -496,12 +520,17 @@ __global__ void __launch_bounds__(128) k_pstats_tma(const __grid_constant__ CUte
   }
   if (t < T)
     for (int n = 0; n < N; ++n) {
-      const float* gr = gs + n * M;
+      const float4* gr4 = reinterpret_cast<const float4*>(gs + n * M);
       float a = 0.f, d = 0.f;
 #pragma unroll
-      for (int m = 0; m < M; ++m) {
-        a = fmaf(gr[m], u[m], a);
-        d = fmaf(gr[m], w[m], d);
+      for (int m4 = 0; m4 < M / 4; ++m4) {
+        const float4 gv4 = gr4[m4];
+        const float gv[4] = {gv4.x, gv4.y, gv4.z, gv4.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          a = fmaf(gv[j], u[4 * m4 + j], a);
+          d = fmaf(gv[j], w[4 * m4 + j], d);
+        }
       }
       const size_t o = ((size_t)n * F + f) * Tp + t;
       A[o] = a;
@@ -586,19 +615,28 @@ cudaError_t launch_wprep(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
   const size_t sm = (size_t)c->N * c->M * sizeof(float);
   auto whi = reinterpret_cast<__nv_bfloat16*>(c->wy_hi);
   auto wlo = reinterpret_cast<__nv_bfloat16*>(c->wy_lo);
-#define DFM_WPREP(NMV) \
-  k_wprep<NMV><<<grid, 128, sm, s>>>(c->lam, c->g, whi, wlo, c->F, c->T, c->Tp, c->Tr, c->M, c->N, c->eps, fb)
-  switch (c->N) {
-    case 1: DFM_WPREP(1); break;
-    case 2: DFM_WPREP(2); break;
-    case 3: DFM_WPREP(3); break;
-    case 4: DFM_WPREP(4); break;
-    case 5: DFM_WPREP(5); break;
-    case 6: DFM_WPREP(6); break;
-    case 7: DFM_WPREP(7); break;
-    case 8: DFM_WPREP(8); break;
-    default: DFM_WPREP(16); break;
+#define DFM_WPREP(NMV, MV) \
+  k_wprep<NMV, MV><<<grid, 128, sm, s>>>(c->lam, c->g, whi, wlo, c->F, c->T, c->Tp, c->Tr, c->N, c->eps, fb)
+#define DFM_WPREP_N(MV)               \
+  switch (c->N) {                     \
+    case 1: DFM_WPREP(1, MV); break;  \
+    case 2: DFM_WPREP(2, MV); break;  \
+    case 3: DFM_WPREP(3, MV); break;  \
+    case 4: DFM_WPREP(4, MV); break;  \
+    case 5: DFM_WPREP(5, MV); break;  \
+    case 6: DFM_WPREP(6, MV); break;  \
+    case 7: DFM_WPREP(7, MV); break;  \
+    case 8: DFM_WPREP(8, MV); break;  \
+    default: DFM_WPREP(16, MV); break; \
   }
+  switch (c->M) {
+    case 4: DFM_WPREP_N(4); break;
+    case 8: DFM_WPREP_N(8); break;
+    case 16: DFM_WPREP_N(16); break;
+    case 32: DFM_WPREP_N(32); break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef DFM_WPREP_N
 #undef DFM_WPREP
   return cudaGetLastError();
 }

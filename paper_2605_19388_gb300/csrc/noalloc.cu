@@ -20,6 +20,7 @@
 // the one array: every entry a call reads is written earlier by the same
 // call, so nothing has to be cleared, but two calls whose work overlaps on
 // the GPU (different streams, no ordering between them) race on it.
+#include <float.h>
 #include <math.h>
 #include <mutex>
 
@@ -214,7 +215,7 @@ extern "C" int dfmnmf_loglik_noalloc(const dfmnmf_desc* d, const void* x_dev, co
   int r = scratch_address(&scratch);
   if (r) return r;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const float eps = (float)(d->floor_eps > 0 ? d->floor_eps : 1e-6);
+  const float eps = fmaxf((float)(d->floor_eps > 0 ? d->floor_eps : 1e-6), FLT_MIN);  // as dfmnmf_init
   const int F = d->F, T = d->T, K = d->K, N = d->N, B = d->B, M = K * MK;
   double* part = scratch;
   double* logdet = scratch + (size_t)F * ty;
