@@ -422,59 +422,127 @@ __global__ void k_a_gnum(const double* __restrict__ lam, const double* __restric
   }
 }
 
-// forward IP of every block (Eqs. 14, 15), keeping the rows before each row update
+// ---------------------------------------------------------------- lane-parallel block algebra
+// One MK x MK block (MK <= 4) per 16-lane half warp: lane sb + e holds entry (i, j) = (e / MK,
+// e % MK) of a matrix for e < MK^2 (the other lanes carry don't-care values and contribute zeros
+// to sums); a vector v is held in "row layout" (lane (i, j) holds v_i) or "column layout" (lane
+// (i, j) holds v_j).  GB300 issues an FP64 warp instruction at a small fraction of the FP32
+// rate, so a block per thread leaves each thread a long serial FP64 chain; a block per half warp
+// divides the chain by the block size.
+__device__ __forceinline__ double2 shfl2(double2 v, int src) {
+  return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+// sum over the 16 lanes of a half warp (xor butterfly, fixed order)
+__device__ __forceinline__ double half_sum(double v) {
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double half_max(double v) {
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+// sum_l v(l, j) (to every lane of column j) and sum_l v(i, l) (to every lane of row i)
 template <int MK>
-__global__ void k_a_ipfwd(const double2* __restrict__ Q, const double2* __restrict__ V, double2* __restrict__ Qs,
-                          int nb, double eps, double rtol, unsigned* __restrict__ flags) {
-  const int id = blockIdx.x * blockDim.x + threadIdx.x;
-  if (id >= nb) return;
-  double2 Qc[MK][MK];
+__device__ __forceinline__ double2 col_sum(double2 v, int j, int sb) {
+  double2 s = make_double2(0.0, 0.0);
 #pragma unroll
-  for (int i = 0; i < MK; ++i)
+  for (int l = 0; l < MK; ++l) s = cadd(s, shfl2(v, sb + l * MK + j));
+  return s;
+}
+template <int MK>
+__device__ __forceinline__ double2 row_sum(double2 v, int i, int sb) {
+  double2 s = make_double2(0.0, 0.0);
 #pragma unroll
-    for (int j = 0; j < MK; ++j) Qc[i][j] = Q[(size_t)id * MK * MK + i * MK + j];
+  for (int l = 0; l < MK; ++l) s = cadd(s, shfl2(v, sb + i * MK + l));
+  return s;
+}
+
+// Gauss-Jordan elimination with partial pivoting on A q = b, lane-parallel: lane (i, j) holds
+// A_ij and b_i (row layout); the pivot of column c is the largest |A_rc| for r >= c, the lowest
+// row on ties.  b ends as the solution (row layout); A is destroyed.  Returns the smallest
+// |pivot| (the same in every lane of the block).
+template <int MK>
+__device__ double gj_lanes(double2& a, double2& b, int i, int j, bool act, int sb) {
+  double minpiv = 1e300;
+#pragma unroll
+  for (int c = 0; c < MK; ++c) {
+    double key = (act && j == c && i >= c) ? cabs2(a) : -1.0;
+    int prow = i;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+      const double ok = __shfl_xor_sync(0xffffffffu, key, o);
+      const int orow = __shfl_xor_sync(0xffffffffu, prow, o);
+      if (ok > key || (ok == key && orow < prow)) {
+        key = ok;
+        prow = orow;
+      }
+    }
+    int src = threadIdx.x & 31;
+    if (act && i == c) src = sb + prow * MK + j;
+    else if (act && i == prow) src = sb + c * MK + j;
+    a = shfl2(a, src);
+    b = shfl2(b, src);
+    const double2 piv = shfl2(a, sb + c * MK + c);
+    minpiv = fmin(minpiv, sqrt(cabs2(piv)));
+    const double2 inv = cabs2(piv) > 0.0 ? crecip(piv) : make_double2(0.0, 0.0);
+    const double2 rowc = cmul(shfl2(a, sb + c * MK + j), inv);
+    const double2 bc = cmul(shfl2(b, sb + c * MK), inv);
+    const double2 m = shfl2(a, sb + i * MK + c);
+    if (i == c) {
+      a = rowc;
+      b = bc;
+    } else {
+      a = csub(a, cmul(m, rowc));
+      b = csub(b, cmul(m, bc));
+    }
+  }
+  return minpiv;
+}
+
+// Forward IP of every block (Eqs. 14, 15), keeping the rows before each row update: one block
+// per half warp (lane layout above), four warps per CTA.
+template <int MK>
+__global__ void __launch_bounds__(128) k_a_ipfwd(const double2* __restrict__ Q, const double2* __restrict__ V,
+                                                 double2* __restrict__ Qs, int nb, double eps, double rtol,
+                                                 unsigned* __restrict__ flags) {
+  constexpr int E = MK * MK;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int seg = lane >> 4, e = lane & 15, sb = seg << 4;
+  const bool act = e < E;
+  const int i = act ? e / MK : 0, j = act ? e % MK : 0;
+  const int blk = (blockIdx.x * (blockDim.x >> 5) + warp) * 2 + seg;
+  const bool valid = blk < nb;
+  const size_t id = valid ? (size_t)blk : 0;  // a spare half warp repeats block 0 and writes nothing
+  double2 qc = act ? Q[id * E + e] : make_double2(0.0, 0.0);
   bool sing = false;
 #pragma unroll
   for (int mu = 0; mu < MK; ++mu) {
-    double2* qs = Qs + ((size_t)id * (MK + 1) + mu) * MK * MK;
+    if (act && valid) Qs[(id * (MK + 1) + mu) * E + e] = qc;
+    const double2* Vm = V + (id * MK + mu) * E;
+    double2 a = make_double2(0.0, 0.0);  // A = Qc V_mu
 #pragma unroll
-    for (int i = 0; i < MK; ++i)
-#pragma unroll
-      for (int j = 0; j < MK; ++j) qs[i * MK + j] = Qc[i][j];
-    const double2* Vm = V + ((size_t)id * MK + mu) * MK * MK;
-    double2 A[MK][MK], q[MK];
-#pragma unroll
-    for (int i = 0; i < MK; ++i) {
-#pragma unroll
-      for (int j = 0; j < MK; ++j) {
-        double2 s = make_double2(0.0, 0.0);
-#pragma unroll
-        for (int l = 0; l < MK; ++l) s = cadd(s, cmul(Qc[i][l], Vm[l * MK + j]));
-        A[i][j] = s;
-      }
-      q[i] = make_double2(i == mu ? 1.0 : 0.0, 0.0);
+    for (int l = 0; l < MK; ++l) {
+      const double2 ql = shfl2(qc, sb + i * MK + l);
+      if (act) a = cadd(a, cmul(ql, Vm[l * MK + j]));
     }
-    double scale;
-    const double mp = gj_solve<MK>(A, q, &scale);
+    const double scale = half_max(act ? sqrt(cabs2(a)) : 0.0);
+    double2 b = make_double2((act && i == mu) ? 1.0 : 0.0, 0.0);
+    const double mp = gj_lanes<MK>(a, b, i, j, act, sb);
     sing |= !(mp > rtol * scale);
-    double s = 0.0;
-#pragma unroll
-    for (int a = 0; a < MK; ++a) {
-      double2 vq = make_double2(0.0, 0.0);
-#pragma unroll
-      for (int b = 0; b < MK; ++b) vq = cadd(vq, cmul(Vm[a * MK + b], q[b]));
-      s += q[a].x * vq.x + q[a].y * vq.y;  // Re(conj(q_a) (V q)_a)
+    const double2 qj = shfl2(b, sb + j * MK);
+    double term = 0.0;  // Re(conj(q_i) V_ij q_j)
+    if (act) {
+      const double2 vq = cmul(Vm[i * MK + j], qj);
+      term = b.x * vq.x + b.y * vq.y;
     }
+    const double s = half_sum(term);
     const double inv = 1.0 / sqrt(flo(s, eps));
-#pragma unroll
-    for (int j = 0; j < MK; ++j) Qc[mu][j] = cconj(cscale(q[j], inv));
+    if (i == mu) qc = cconj(cscale(qj, inv));
   }
-  double2* qs = Qs + ((size_t)id * (MK + 1) + MK) * MK * MK;
-#pragma unroll
-  for (int i = 0; i < MK; ++i)
-#pragma unroll
-    for (int j = 0; j < MK; ++j) qs[i * MK + j] = Qc[i][j];
-  if (sing) atomicOr(flags, 1u);
+  if (act && valid) Qs[(id * (MK + 1) + MK) * E + e] = qc;
+  if (sing && valid && e == 0) atomicOr(flags, 1u);
 }
 
 // ---------------------------------------------------------------- reverse kernels
@@ -652,93 +720,55 @@ __global__ void k_a_Pb(const float2* __restrict__ x, const double2* __restrict__
 //   qbar = qbar_n / sigma;  if s > eps: sbar = -Re(qbar_n^H q) / (2 sigma^3),
 //   qbar += 2 sbar V q
 //   y = A^-H qbar;  Qbar += -y (q^H V_mu);  Vbar_mu = (sbar q - Qc^H y) q^H
+// One block per half warp (lane layout above), four warps per CTA.
 template <int MK>
-__global__ void k_a_ipb(const double2* __restrict__ Qs, const double2* __restrict__ V,
-                        const double2* __restrict__ Qbin, double2* __restrict__ Qbout, double2* __restrict__ Vb,
-                        int nb, double eps) {
-  const int id = blockIdx.x * blockDim.x + threadIdx.x;
-  if (id >= nb) return;
-  double2 Qb[MK][MK];
-#pragma unroll
-  for (int i = 0; i < MK; ++i)
-#pragma unroll
-    for (int j = 0; j < MK; ++j) Qb[i][j] = Qbin[(size_t)id * MK * MK + i * MK + j];
+__global__ void __launch_bounds__(128) k_a_ipb(const double2* __restrict__ Qs, const double2* __restrict__ V,
+                                               const double2* __restrict__ Qbin, double2* __restrict__ Qbout,
+                                               double2* __restrict__ Vb, int nb, double eps) {
+  constexpr int E = MK * MK;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int seg = lane >> 4, e = lane & 15, sb = seg << 4;
+  const bool act = e < E;
+  const int i = act ? e / MK : 0, j = act ? e % MK : 0;
+  const int blk = (blockIdx.x * (blockDim.x >> 5) + warp) * 2 + seg;
+  const bool valid = blk < nb;
+  const size_t id = valid ? (size_t)blk : 0;  // a spare half warp repeats block 0 and writes nothing
+  const double2 z = make_double2(0.0, 0.0);
+  double2 qbe = act ? Qbin[id * E + e] : z;  // Qbar_ij
 #pragma unroll
   for (int mu = MK - 1; mu >= 0; --mu) {
-    const double2* Qc = Qs + ((size_t)id * (MK + 1) + mu) * MK * MK;
-    const double2* Vm = V + ((size_t)id * MK + mu) * MK * MK;
-    double2 A[MK][MK], q[MK];
+    const double2* Qc = Qs + (id * (MK + 1) + mu) * E;
+    const double2* Vm = V + (id * MK + mu) * E;
+    double2 a = z;  // A = Qc V_mu
+    if (act)
 #pragma unroll
-    for (int i = 0; i < MK; ++i) {
-#pragma unroll
-      for (int j = 0; j < MK; ++j) {
-        double2 s = make_double2(0.0, 0.0);
-#pragma unroll
-        for (int l = 0; l < MK; ++l) s = cadd(s, cmul(Qc[i * MK + l], Vm[l * MK + j]));
-        A[i][j] = s;
-      }
-      q[i] = make_double2(i == mu ? 1.0 : 0.0, 0.0);
-    }
-    double2 AH[MK][MK];  // A^H for the adjoint solve
-#pragma unroll
-    for (int i = 0; i < MK; ++i)
-#pragma unroll
-      for (int j = 0; j < MK; ++j) AH[i][j] = cconj(A[j][i]);
-    double scale;
-    gj_solve<MK>(A, q, &scale);
-    double2 vq[MK];
-    double s = 0.0;
-#pragma unroll
-    for (int a = 0; a < MK; ++a) {
-      double2 v = make_double2(0.0, 0.0);
-#pragma unroll
-      for (int b = 0; b < MK; ++b) v = cadd(v, cmul(Vm[a * MK + b], q[b]));
-      vq[a] = v;
-      s += q[a].x * v.x + q[a].y * v.y;
-    }
+      for (int l = 0; l < MK; ++l) a = cadd(a, cmul(Qc[i * MK + l], Vm[l * MK + j]));
+    double2 ah = cconj(shfl2(a, sb + j * MK + i));  // (A^H)_ij for the adjoint solve
+    double2 q = make_double2((act && i == mu) ? 1.0 : 0.0, 0.0);
+    gj_lanes<MK>(a, q, i, j, act, sb);  // q = A^-1 e_mu (row layout)
+    const double2 qj = shfl2(q, sb + j * MK);
+    const double2 vij = act ? Vm[i * MK + j] : z;
+    const double2 vq = row_sum<MK>(cmul(vij, qj), i, sb);  // (V q)_i, row layout
+    const double s = half_sum((act && j == 0) ? q.x * vq.x + q.y * vq.y : 0.0);
     const double sig = sqrt(flo(s, eps));
-    double2 qb[MK];
-    double dotr = 0.0;  // Re(qbar_n^H q)
-#pragma unroll
-    for (int j = 0; j < MK; ++j) {
-      const double2 qn = cconj(Qb[mu][j]);
-      dotr += qn.x * q[j].x + qn.y * q[j].y;
-      qb[j] = cscale(qn, 1.0 / sig);
-      Qb[mu][j] = make_double2(0.0, 0.0);
-    }
-    double sb = 0.0;
+    const double2 qn = cconj(shfl2(qbe, sb + mu * MK + i));  // conj(Qbar_mu,i), row layout
+    const double dotr = half_sum((act && j == 0) ? qn.x * q.x + qn.y * q.y : 0.0);
+    double2 y = cscale(qn, 1.0 / sig);
+    if (i == mu) qbe = z;
+    double sbar = 0.0;
     if (s > eps) {
-      sb = -dotr / (2.0 * sig * sig * sig);
-#pragma unroll
-      for (int j = 0; j < MK; ++j) qb[j] = cadd(qb[j], cscale(vq[j], 2.0 * sb));
+      sbar = -dotr / (2.0 * sig * sig * sig);
+      y = cadd(y, cscale(vq, 2.0 * sbar));
     }
-    gj_solve<MK>(AH, qb, &scale);  // qb <- A^-H qbar
-    double2 w[MK];                   // q^H V_mu
-#pragma unroll
-    for (int j = 0; j < MK; ++j) {
-      double2 v = make_double2(0.0, 0.0);
-#pragma unroll
-      for (int l = 0; l < MK; ++l) v = cadd(v, cmul(cconj(q[l]), Vm[l * MK + j]));
-      w[j] = v;
-    }
-#pragma unroll
-    for (int i = 0; i < MK; ++i)
-#pragma unroll
-      for (int j = 0; j < MK; ++j) Qb[i][j] = csub(Qb[i][j], cmul(qb[i], w[j]));
-    double2* vb = Vb + ((size_t)id * MK + mu) * MK * MK;
-#pragma unroll
-    for (int i = 0; i < MK; ++i) {
-      double2 u = cscale(q[i], sb);  // sbar q - Qc^H y
-#pragma unroll
-      for (int l = 0; l < MK; ++l) u = csub(u, cmul(cconj(Qc[l * MK + i]), qb[l]));
-#pragma unroll
-      for (int j = 0; j < MK; ++j) vb[i * MK + j] = cmulc(u, q[j]);
-    }
+    gj_lanes<MK>(ah, y, i, j, act, sb);  // y = A^-H qbar (row layout)
+    const double2 w = col_sum<MK>(cmul(cconj(q), vij), j, sb);  // (q^H V_mu)_j, column layout
+    qbe = csub(qbe, cmul(y, w));
+    // u_i = sbar q_i - sum_l conj(Qc_li) y_l: column sums of conj(Qc_ij) y_i, taken from column i
+    const double2 cs = col_sum<MK>(act ? cmul(cconj(Qc[i * MK + j]), y) : z, j, sb);
+    const double2 u = csub(cscale(q, sbar), shfl2(cs, sb + i));
+    if (act && valid) Vb[(id * MK + mu) * E + e] = cmulc(u, qj);  // Vbar_ij = u_i conj(q_j)
   }
-#pragma unroll
-  for (int i = 0; i < MK; ++i)
-#pragma unroll
-    for (int j = 0; j < MK; ++j) Qbout[(size_t)id * MK * MK + i * MK + j] = Qb[i][j];
+  if (act && valid) Qbout[id * E + e] = qbe;
 }
 
 // Reverse of Eq. 13 and of 1/yhat0: ybar0[f][t][o_k+mu] += -Re(x^H Vbar_mu x) / (T yhat0^2).
@@ -1055,7 +1085,7 @@ cudaError_t reverse_iteration(dfmnmf_adj* a, const Dims& d, cudaStream_t s) {
   MK_DISPATCH(d.MK, k_a_V, nblk((size_t)d.F * d.K * (d.MK * (d.MK + 1) / 2) * 32), 256, 0, s, c->x, a->r0, a->V,
               d.F, d.T, d.K);
   AL((void)0);
-  MK_DISPATCH(d.MK, k_a_ipfwd, nblk(nb, 64), 64, 0, s, a->Qd, a->V, a->Qs, nb, eps, (double)c->singular_rtol, a->flags);
+  MK_DISPATCH(d.MK, k_a_ipfwd, nblk(nb, 8), 128, 0, s, a->Qd, a->V, a->Qs, nb, eps, (double)c->singular_rtol, a->flags);
   AL((void)0);
   const double2* Qn = a->Qs + (size_t)d.MK * d.MK * d.MK;  // rows after the last update, stride (MK+1) MK^2
   const size_t qstr = (size_t)(d.MK + 1) * d.MK * d.MK;
@@ -1100,7 +1130,7 @@ cudaError_t reverse_iteration(dfmnmf_adj* a, const Dims& d, cudaStream_t s) {
   MK_DISPATCH(d.MK, k_a_Pb, nblk((size_t)d.F * d.K * d.MK * 32), 256, 0, s, c->x, Qn, qstr, a->Pb, a->Qb1, d.F, d.T,
               d.K);
   AL((void)0);
-  MK_DISPATCH(d.MK, k_a_ipb, nblk(nb, 64), 64, 0, s, a->Qs, a->V, a->Qb1, a->Qb, a->Vb, nb, eps);
+  MK_DISPATCH(d.MK, k_a_ipb, nblk(nb, 8), 128, 0, s, a->Qs, a->V, a->Qb1, a->Qb, a->Vb, nb, eps);
   AL((void)0);
   MK_DISPATCH(d.MK, k_a_Vh, nblk(d.nq / d.MK), 256, 0, s, a->Vb, a->Vh, d.nq / d.MK);  // one thread per (f, k, mu)
   AL((void)0);

@@ -425,7 +425,8 @@ template <bool COMP>
 __global__ void __launch_bounds__(128) k_pstats_tma(const __grid_constant__ CUtensorMap map_x,
                                                     const __grid_constant__ CUtensorMap map_l,
                                                     const __grid_constant__ CUtensorMap map_p,
-                                                    const double2* __restrict__ Q64, const float* __restrict__ g,
+                                                    const double2* __restrict__ Q64,
+                                                    const float2* __restrict__ Q32, const float* __restrict__ g,
                                                     float* __restrict__ A, float* __restrict__ D, int F, int T,
                                                     int Tp, int N, float eps, int fb, unsigned* __restrict__ flags) {
   constexpr int K = 4, MK = 4, M = 16;
@@ -447,7 +448,12 @@ __global__ void __launch_bounds__(128) k_pstats_tma(const __grid_constant__ CUte
     tma_load_3d(ls, &map_l, t0, f, 0, bar);
   }
   for (int i = tid; i < N * M; i += blockDim.x) gs[i] = g[(size_t)f * N * M + i];
-  for (int i = tid; i < K * MK * MK; i += blockDim.x) split_c(Q64[(size_t)f * K * MK * MK + i], Qh[i], Ql[i]);
+  // plain projections take the single-precision copy of Q (the rounded FP64
+  // master, written beside it), compensated ones split the master in two floats
+  for (int i = tid; i < K * MK * MK; i += blockDim.x) {
+    if (COMP) split_c(Q64[(size_t)f * K * MK * MK + i], Qh[i], Ql[i]);
+    else Qh[i] = Q32[(size_t)f * K * MK * MK + i];
+  }
   __syncthreads();
   if (!mbar_wait(bar, 0)) {  // the copies did not arrive within the budget: report, skip the tile
     if (tid == 0) atomicOr(flags + FLAG_TIMEOUT, 1u);
@@ -682,7 +688,8 @@ cudaError_t launch_pstats_tma(const dfmnmf_ctx* c, cudaStream_t s, int fb, int f
   auto kern = comp ? k_pstats_tma<true> : k_pstats_tma<false>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   dim3 grid(fc, (c->T + PT_ROWS - 1) / PT_ROWS);
-  kern<<<grid, 128, sm, s>>>(mx, ml, mp, c->Q64, c->g, c->A, c->D, c->F, c->T, c->Tp, c->N, c->eps, fb, c->flags);
+  kern<<<grid, 128, sm, s>>>(mx, ml, mp, c->Q64, c->Q32, c->g, c->A, c->D, c->F, c->T, c->Tp, c->N, c->eps, fb,
+                             c->flags);
   return cudaGetLastError();
 }
 
