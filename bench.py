@@ -146,24 +146,26 @@ def kernel_bytes(F, T, M, N, B, K, MK):
     }
 
 
-# DRAM bytes (read + write) of one band-wide launch of the tensor-core form,
-# from the full-section ncu captures summarised in
-# profiles/kernels_paper_4x4_n5_bf16tc.md (band-wide launches: the autotuned
-# launch shapes of that run put the per-frequency kernels on one graph branch).  A figure holds only while the
+# DRAM bytes (read + write) of one band-wide launch, from the full-section ncu
+# captures summarised in profiles/kernels_paper_4x4_n5_bf16tc.md and
+# profiles/kernels_paper_4x4_n5_fp32.md (`k_cov`) (band-wide launches: the
+# autotuned launch shapes of those runs put the per-frequency kernels on one
+# graph branch).  A figure holds only while the
 # kernel's sources are the ones captured: the digest is the first 16 hex
 # digits of sha256 over csrc/<file>, csrc/common.cuh and csrc/internal.h, and
 # `traffic` is null when it no longer matches.
 NCU_TRAFFIC = {
     "paper_4x4_n5": {
-        "k_pstats": (48269824 + 2129152, "kernels_tc.cu", "8477a9db91e4a1db"),  # k_pstats_tma<0>
-        "k_stats": (27179264 + 0, "kernels_model.cu", "d019e79f136de230"),
-        "k_gupd": (27192832 + 0, "kernels_model.cu", "d019e79f136de230"),
-        "k_lambda": (388608 + 0, "kernels_model.cu", "d019e79f136de230"),
-        "k_vtc": (105289728 + 2770688, "kernels_tc.cu", "8477a9db91e4a1db"),
-        "k_wprep": (6619648 + 0, "kernels_tc.cu", "8477a9db91e4a1db"),
+        "k_pstats": (48004352 + 2192128, "kernels_tc.cu", "94eea8ca4bb862b7"),  # k_pstats_tma<0>
+        "k_stats": (27179776 + 1024, "kernels_model.cu", "d019e79f136de230"),
+        "k_gupd": (27193344 + 0, "kernels_model.cu", "d019e79f136de230"),
+        "k_lambda": (388352 + 0, "kernels_model.cu", "d019e79f136de230"),
+        "k_vtc": (105289984 + 2793216, "kernels_tc.cu", "94eea8ca4bb862b7"),
+        "k_wprep": (6619648 + 0, "kernels_tc.cu", "94eea8ca4bb862b7"),
         "k_ip": (2701824 + 0, "kernels_ip.cu", "8f14118b76b1c4d8"),
         "k_wupd": (13268736 + 0, "kernels_nmf.cu", "36821db759ba7376"),
-        "k_hupd": (13270272 + 0, "kernels_nmf.cu", "36821db759ba7376"),
+        "k_hupd": (13270016 + 0, "kernels_nmf.cu", "36821db759ba7376"),
+        "k_cov": (47757056 + 43776, "kernels_cov.cu", "b9e9240ac9819186"),  # FP32 form
     },
 }
 
@@ -177,7 +179,8 @@ ALU_KERNELS = ("k_ip", "k_cov")
 NCU_INST = {  # keyed by (kernel, form): k_ip refines three times in the FP32 form, once in the tensor-core form
     "paper_4x4_n5": {
         ("k_ip", "bf16tc"): (6995412, "kernels_ip.cu", "8f14118b76b1c4d8"),
-        ("k_cov", "fp32"): (56279691, "kernels_cov.cu", "dad4d0b2f3648048"),
+        ("k_ip", "fp32"): (9148758, "kernels_ip.cu", "8f14118b76b1c4d8"),
+        ("k_cov", "fp32"): (54227691, "kernels_cov.cu", "b9e9240ac9819186"),
     },
 }
 
