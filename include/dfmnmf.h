@@ -72,11 +72,16 @@ typedef enum dfmnmf_status {
   DFMNMF_ETIMEOUT = 5  /* a bounded device wait gave up (reserved) */
 } dfmnmf_status;
 
-/* Arithmetic of the weighted-covariance contraction and the NMF products. */
+/* Arithmetic of the weighted-covariance contraction (Eq. 13). */
 typedef enum dfmnmf_precision {
-  DFMNMF_FP32 = 0,    /* CUDA-core FP32 everywhere except the IP solves   */
-  DFMNMF_BF16_TC = 1, /* tensor-core BF16 operands, FP32 accumulation     */
-  DFMNMF_TF32_TC = 2  /* tensor-core TF32 operands, FP32 accumulation     */
+  DFMNMF_FP32 = 0,    /* CUDA cores: x x^H and the weights as exact float pairs
+                         (float-float sums), for ill-conditioned covariances     */
+  DFMNMF_BF16_TC = 1, /* tensor cores (tcgen05): x x^H and 1/yhat each split in
+                         two bfloat16 parts, three products, FP32 accumulation;
+                         M_k = 4 with K in {1, 2, 4, 8}.  The NMF products stay
+                         FP32 on the CUDA cores in both forms                    */
+  DFMNMF_TF32_TC = 2  /* reserved: returns DFMNMF_EINVAL (TF32 operands miss the
+                         accuracy of the split bfloat16 form)                   */
 } dfmnmf_precision;
 
 /* Arithmetic of the M_k x M_k iterative-projection solves (Eqs. 14-15). */

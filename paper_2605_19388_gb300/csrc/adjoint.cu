@@ -118,54 +118,9 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Gauss-Jordan elimination with partial pivoting on A b = rhs (n <= 4, fully
-// unrolled: the pivot row is brought up by compare-and-swap so every index
-// stays static).  The solution replaces rhs; A is destroyed.  Returns the
-// smallest pivot magnitude; *scale receives max |A_ij| of the input.
-template <int n>
-__device__ double gj_solve(double2 (&A)[n][n], double2 (&r)[n], double* scale) {
-  double sc = 0.0;
-#pragma unroll
-  for (int i = 0; i < n; ++i)
-#pragma unroll
-    for (int j = 0; j < n; ++j) sc = fmax(sc, sqrt(cabs2(A[i][j])));
-  *scale = sc;
-  double minpiv = 1e300;
-#pragma unroll
-  for (int c = 0; c < n; ++c) {
-#pragma unroll
-    for (int rr = c + 1; rr < n; ++rr)
-      if (cabs2(A[rr][c]) > cabs2(A[c][c])) {
-#pragma unroll
-        for (int j = 0; j < n; ++j) {
-          const double2 t = A[c][j];
-          A[c][j] = A[rr][j];
-          A[rr][j] = t;
-        }
-        const double2 t = r[c];
-        r[c] = r[rr];
-        r[rr] = t;
-      }
-    const double2 piv = A[c][c];
-    minpiv = fmin(minpiv, sqrt(cabs2(piv)));
-    const double2 inv = cabs2(piv) > 0.0 ? crecip(piv) : make_double2(0.0, 0.0);
-#pragma unroll
-    for (int j = 0; j < n; ++j) A[c][j] = cmul(A[c][j], inv);
-    r[c] = cmul(r[c], inv);
-#pragma unroll
-    for (int rr = 0; rr < n; ++rr) {
-      if (rr == c) continue;
-      const double2 m = A[rr][c];
-#pragma unroll
-      for (int j = 0; j < n; ++j) A[rr][j] = csub(A[rr][j], cmul(m, A[c][j]));
-      r[rr] = csub(r[rr], cmul(m, r[c]));
-    }
-  }
-  return minpiv;
-}
-
-// Inverse by the same elimination (columns of the identity as right-hand sides).
-// Returns ln |det A|^2 (sum of ln |pivot|^2).
+// Inverse by Gauss-Jordan elimination with partial pivoting (n <= 4, fully unrolled: the
+// pivot row is brought up by compare-and-swap so every index stays static; the columns of the
+// identity are the right-hand sides).  Returns ln |det A|^2 (sum of ln |pivot|^2).
 template <int n>
 __device__ double gj_inverse(double2 (&A)[n][n], double2 (&X)[n][n]) {
 #pragma unroll
