@@ -101,6 +101,28 @@ def test_tc_trajectory_50_iterations_paper_workload():
     assert np.max(np.abs(np.sort(s_gpu) - np.sort(s_ref))) <= 0.2, (s_gpu, s_ref)
 
 
+@pytest.mark.parametrize("autotune", [False, True])
+def test_tc_paper_workload_one_iteration_full_size(autotune):
+    """The 4 x 4-mic, N = 5, F = 513, T = 626 workload: one captured iteration
+    from identical state, every output within the 3e-3 bar.  Without the
+    autotuner the per-frequency kernels run on two graph branches (one per
+    half of the band); with it, in the launch shapes the benchmark uses."""
+    p = synth.make_workload("paper_4x4_n5", seed=0)
+    x = p.x.astype(np.complex128)
+    ctx = ctx_for(p, D.DFMNMF_BF16_TC)
+    if autotune:
+        D.dfmnmf_autotune(ctx, 2)  # restores the initial state
+    D.dfmnmf_iterate(ctx, 1)
+    got = state(ctx)
+    rec = {}
+    ref = O.mm_iteration(x, p.mics, oracle_state(p), record=rec)
+    errs = {"Q": max(rel_err(got.Q[k], ref.Q[k]) for k in range(p.K)), "W": rel_err(got.W, ref.W),
+            "H": rel_err(got.H, ref.H), "g": rel_err(got.g, ref.g),
+            "P": rel_err(D.buffer_numpy(ctx, D.DFMNMF_BUF_P), rec["P"])}
+    print("tensor-core form, one full-size iteration, autotune", autotune, errs)
+    assert max(errs.values()) < TOL_TC, errs
+
+
 def test_tc_form_rejects_unsupported_layouts():
     p = synth.make_problem(5, 20, (2, 2), 2, 3, seed=1)
     with pytest.raises(D.DfmnmfError) as ei:
