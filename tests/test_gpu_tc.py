@@ -53,9 +53,8 @@ def test_tc_covariances_match_oracle(shape):
     assert err < 1e-4, err
 
 
-def test_tc_stage_parity_paper_shaped():
-    """Every update of one iteration within 3e-3 (oracle fed the GPU's inputs)."""
-    p = synth.make_problem(41, 120, (4, 4, 4, 4), 5, 16, seed=32)
+def tc_stage_errors(p):
+    """Every update of one iteration against the oracle fed the GPU's inputs."""
     x = p.x.astype(np.complex128)
     ctx = ctx_for(p, D.DFMNMF_BF16_TC)
     st = state(ctx)
@@ -79,7 +78,24 @@ def test_tc_stage_parity_paper_shaped():
     D.dfmnmf_run_stage(ctx, D.DFMNMF_STAGE_G)
     st5 = state(ctx)
     errs["g"] = rel_err(st5.g, O.update_g(st4.W, st4.H, st4.g, P))
+    return errs
+
+
+def test_tc_stage_parity_paper_shaped():
+    """Every update of one iteration within 3e-3 (oracle fed the GPU's inputs)."""
+    errs = tc_stage_errors(synth.make_problem(41, 120, (4, 4, 4, 4), 5, 16, seed=32))
     assert max(errs.values()) < TOL_TC, errs
+
+
+@pytest.mark.parametrize("shape", [
+    dict(F=1, T=65, mics=(4, 4, 4, 4), N=5, B=1),       # one bin (partial operand tile), one frame in the last chunk
+    dict(F=9, T=100, mics=(4, 4, 4, 4), N=16, B=64),    # the largest source and basis counts
+    dict(F=3, T=64, mics=(4,) * 8, N=12, B=2),          # eight subarrays, exactly one 64-frame chunk
+])
+def test_tc_stage_parity_edge_sizes(shape):
+    p = synth.make_problem(shape["F"], shape["T"], shape["mics"], shape["N"], shape["B"], seed=33)
+    errs = tc_stage_errors(p)
+    assert max(errs.values()) < TOL_TC, (shape, errs)
 
 
 def test_tc_trajectory_50_iterations_paper_workload():
