@@ -146,11 +146,10 @@ def kernel_bytes(F, T, M, N, B, K, MK):
     }
 
 
-# DRAM bytes (read + write) of one band-wide launch, from the full-section ncu
-# captures summarised in profiles/kernels_paper_4x4_n5_bf16tc.md and
-# profiles/kernels_paper_4x4_n5_fp32.md (`k_cov`) (band-wide launches: the
-# autotuned launch shapes of those runs put the per-frequency kernels on one
-# graph branch).  A figure holds only while the
+# DRAM bytes (read + write) of one band-wide launch, from full-section ncu
+# captures of one iteration of each form (`k_cov` from the FP32 form, the
+# rest from the tensor-core form; band-wide launches: the autotuned launch
+# shapes of those runs put the per-frequency kernels on one graph branch).  A figure holds only while the
 # kernel's sources are the ones captured: the digest is the first 16 hex
 # digits of sha256 over csrc/<file>, csrc/common.cuh and csrc/internal.h, and
 # `traffic` is null when it no longer matches.
