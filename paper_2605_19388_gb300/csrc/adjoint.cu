@@ -25,15 +25,32 @@
 // The forward iterations themselves are the context's own (the captured
 // FP32 iteration graph); the state is stored every `every` iterations and
 // each segment is recomputed from its checkpoint during the reverse sweep.
-// All reverse arithmetic is FP64.  Complex adjoints are dL/dRe + i dL/dIm.
+// The loss and its adjoint are FP64.  Inside the unrolled iterations the IP
+// side (V, the IP rows, P = |Q x|^2 and their adjoints) is FP64 and the NMF
+// side (model, statistics, multiplicative updates and their adjoints) is
+// single precision, as in the forward iterations it differentiates: GB300
+// issues FP64 at about 1/64 of its FP32 rate.  Complex adjoints are
+// dL/dRe + i dL/dIm.
 #include "../../include/dfmnmf.h"
 #include "common.cuh"
 #include "internal.h"
 
 #include <algorithm>
+#include <type_traits>
 #include <cstdarg>
 #include <cstdio>
 #include <utility>
+
+// The NMF side of the reverse pass (the recomputed model, statistics and multiplicative
+// updates, and their adjoints) in one real type: single precision through the unrolled
+// iterations, double precision for the loss and its adjoint.
+template <class R>
+struct AdjSide {
+  R *Wd, *Hd, *gd;  // the state being differentiated: [N][F][B], [N][B][T], [F][N][M]
+  R *lam0, *lam1, *lam2, *y0, *y1, *y2, *r0, *r1, *r2, *P, *A0, *D0, *A1, *D1;
+  R *numW, *denW, *W1, *numH, *denH, *H1, *numG, *denG;
+  R *Wb, *Wb1, *Hb, *Hb1, *gb, *gb1, *lamb, *yb, *Pb, *Ab, *Db, *nb, *db;
+};
 
 struct dfmnmf_adj {
   dfmnmf_ctx* c;
@@ -63,6 +80,9 @@ struct dfmnmf_adj {
   double* G4;
   double* red;      // loss accumulator
   unsigned* flags;  // [0] a system below the singular threshold
+  AdjSide<float> sf;  // single-precision NMF side of the unrolled iterations
+  double2* x64;       // the observation in FP64 [F][T][M]
+  double* r0d;        // FP64 copy of sf.r0 for the covariances of Eq. 13
 };
 
 namespace dfm {
@@ -91,7 +111,7 @@ int afail(int code, const char* fmt, ...) {
     if (e_ != cudaSuccess) return e_;    \
   } while (0)
 
-__device__ __forceinline__ double flo(double y, double eps) { return y > eps ? y : eps; }
+template <class R> __device__ __forceinline__ R flo(R y, R eps) { return y > eps ? y : eps; }
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
@@ -111,8 +131,10 @@ __device__ __forceinline__ double2 ld(const float2* p) {
   const float2 v = __ldg(p);
   return make_double2((double)v.x, (double)v.y);
 }
+// the observation converted once to FP64 (conversions run on the FP64 pipe too)
+__device__ __forceinline__ double2 ld(const double2* p) { return __ldg(p); }
 // Sum over the 32 lanes of a warp in a fixed butterfly order (deterministic).
-__device__ __forceinline__ double warp_sum(double v) {
+template <class R> __device__ __forceinline__ R warp_sum(R v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -166,75 +188,79 @@ __device__ double gj_inverse(double2 (&A)[n][n], double2 (&X)[n][n]) {
 }
 
 // ---------------------------------------------------------------- conversions and products
-// the state (context layouts, FP32) to FP64 arrays; H loses its row padding
+// the state (context layouts, FP32) to arrays of type R; H loses its row padding
+template <class R>
 __global__ void k_a_tod(const float* __restrict__ W, const float* __restrict__ H, const float* __restrict__ g,
-                        double* __restrict__ Wd, double* __restrict__ Hd, double* __restrict__ gd, size_t nW,
+                        R* __restrict__ Wd, R* __restrict__ Hd, R* __restrict__ gd, size_t nW,
                         size_t nH, size_t ng, int T, int Tp) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < nW) {
-    Wd[i] = W[i];
+    Wd[i] = (R)W[i];
   } else if (i < nW + nH) {
     const size_t j = i - nW;
-    Hd[j] = H[(j / T) * Tp + j % T];
+    Hd[j] = (R)H[(j / T) * Tp + j % T];
   } else if (i < nW + nH + ng) {
     const size_t j = i - nW - nH;
-    gd[j] = g[j];
+    gd[j] = (R)g[j];
   }
 }
 
 // out[n][f][t] = sum_b X[n][f][b] Y[n][b][t]
-__global__ void k_a_nmf_b(const double* __restrict__ X, const double* __restrict__ Y, double* __restrict__ out, int N,
+template <class R>
+__global__ void k_a_nmf_b(const R* __restrict__ X, const R* __restrict__ Y, R* __restrict__ out, int N,
                           int F, int B, int T) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (size_t)N * F * T) return;
   const int t = (int)(i % T), f = (int)((i / T) % F), n = (int)(i / ((size_t)F * T));
-  const double* x = X + ((size_t)n * F + f) * B;
-  const double* y = Y + (size_t)n * B * T + t;
-  double s = 0.0;
+  const R* x = X + ((size_t)n * F + f) * B;
+  const R* y = Y + (size_t)n * B * T + t;
+  R s = R(0);
   for (int b = 0; b < B; ++b) s += x[b] * y[(size_t)b * T];
   out[i] = s;
 }
 
 // out[n][f][b] (+)= sum_t X[n][f][t] Y[n][b][t]; one warp per output, lanes over t
-__global__ void k_a_nmf_t(const double* __restrict__ X, const double* __restrict__ Y, double* __restrict__ out, int N,
+template <class R>
+__global__ void k_a_nmf_t(const R* __restrict__ X, const R* __restrict__ Y, R* __restrict__ out, int N,
                           int F, int B, int T, int acc) {
   const size_t w = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= (size_t)N * F * B) return;
   const int b = (int)(w % B), f = (int)((w / B) % F), n = (int)(w / ((size_t)F * B));
-  const double* x = X + ((size_t)n * F + f) * T;
-  const double* y = Y + ((size_t)n * B + b) * T;
-  double s = 0.0;
+  const R* x = X + ((size_t)n * F + f) * T;
+  const R* y = Y + ((size_t)n * B + b) * T;
+  R s = R(0);
   for (int t = lane; t < T; t += 32) s += x[t] * y[t];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) out[w] = (acc ? out[w] : 0.0) + s;
+  if (lane == 0) out[w] = (acc ? out[w] : R(0)) + s;
 }
 
 // out[n][b][t] (+)= sum_f X[n][f][b] Y[n][f][t].  CTA = (32 frames, one (n, b)); its 8 warps
 // take every 8th frequency and their partial sums are added in warp order through shared
 // memory (a fixed order: the result does not depend on scheduling).
 constexpr int NMF_F_WARPS = 8;
-__global__ void __launch_bounds__(32 * NMF_F_WARPS) k_a_nmf_f(const double* __restrict__ X,
-                                                             const double* __restrict__ Y,
-                                                             double* __restrict__ out, int N, int F, int B, int T,
+template <class R>
+__global__ void __launch_bounds__(32 * NMF_F_WARPS) k_a_nmf_f(const R* __restrict__ X,
+                                                             const R* __restrict__ Y,
+                                                             R* __restrict__ out, int N, int F, int B, int T,
                                                              int acc) {
-  __shared__ double part[NMF_F_WARPS][32];
+  __shared__ R part[NMF_F_WARPS][32];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int t = blockIdx.x * 32 + lane;
   const int b = (int)(blockIdx.y % B), n = (int)(blockIdx.y / B);
-  double s = 0.0;
+  R s = R(0);
   if (t < T)
     for (int f = wp; f < F; f += NMF_F_WARPS)
       s += X[((size_t)n * F + f) * B + b] * Y[((size_t)n * F + f) * T + t];
   part[wp][lane] = s;
   __syncthreads();
   if (wp == 0 && t < T) {
-    double v = 0.0;
+    R v = R(0);
 #pragma unroll
     for (int w = 0; w < NMF_F_WARPS; ++w) v += part[w][lane];
     const size_t i = ((size_t)n * B + b) * T + t;
-    out[i] = (acc ? out[i] : 0.0) + v;
+    out[i] = (acc ? out[i] : R(0)) + v;
   }
 }
 
@@ -242,15 +268,16 @@ __global__ void __launch_bounds__(32 * NMF_F_WARPS) k_a_nmf_f(const double* __re
 // GB300 issues FP64 at a small fraction of its FP32 rate and a division costs
 // about ten FP64 instructions, so the reverse kernels multiply by ry instead
 // of dividing by the model.
-__global__ void k_a_y(const double* __restrict__ lam, const double* __restrict__ g, double* __restrict__ y,
-                      double* __restrict__ ry, int N, int F, int T, int M, double eps) {
+template <class R>
+__global__ void k_a_y(const R* __restrict__ lam, const R* __restrict__ g, R* __restrict__ y,
+                      R* __restrict__ ry, int N, int F, int T, int M, R eps) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (size_t)F * T * M) return;
   const int m = (int)(i % M), t = (int)((i / M) % T), f = (int)(i / ((size_t)T * M));
-  double s = 0.0;
+  R s = R(0);
   for (int n = 0; n < N; ++n) s += lam[((size_t)n * F + f) * T + t] * g[((size_t)f * N + n) * M + m];
   y[i] = s;
-  ry[i] = 1.0 / flo(s, eps);
+  ry[i] = R(1) / flo(s, eps);
 }
 
 // V[f][k][mu][a][b] = (1/T) sum_t x_a conj(x_b) / yhat0[f][t][o_k + mu]   (Eq. 13)
@@ -258,7 +285,7 @@ __global__ void k_a_y(const double* __restrict__ lam, const double* __restrict__
 // x_a conj(x_b) is formed once per frame and weighted by the reciprocals r0 of all MK
 // microphones.
 template <int MK>
-__global__ void k_a_V(const float2* __restrict__ x, const double* __restrict__ r0, double2* __restrict__ V, int F,
+__global__ void k_a_V(const double2* __restrict__ x, const double* __restrict__ r0, double2* __restrict__ V, int F,
                       int T, int K) {
   constexpr int NP = MK * (MK + 1) / 2;
   const size_t w = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -301,39 +328,42 @@ __global__ void k_a_V(const float2* __restrict__ x, const double* __restrict__ r
   }
 }
 
-// P[f][t][o_k + a] = |(Q_fk x_ftk)_a|^2; block (f, k) of Q at Q + (f K + k) * bstride
-__global__ void k_a_P(const float2* __restrict__ x, const double2* __restrict__ Q, size_t bstride,
-                      double* __restrict__ P, int F, int T, int K, int MK) {
+// P[f][t][o_k + a] = |(Q_fk x_ftk)_a|^2 (formed in FP64, stored as RR); block (f, k) of Q at
+// Q + (f K + k) * bstride
+template <class RR>
+__global__ void k_a_P(const double2* __restrict__ x, const double2* __restrict__ Q, size_t bstride,
+                      RR* __restrict__ P, int F, int T, int K, int MK) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (size_t)F * T * K) return;
   const int k = (int)(i % K), t = (int)((i / K) % T), f = (int)(i / ((size_t)K * T));
   const int M = K * MK, o = k * MK;
   const double2* q = Q + ((size_t)f * K + k) * bstride;
-  const float2* xr = x + ((size_t)f * T + t) * M + o;
+  const double2* xr = x + ((size_t)f * T + t) * M + o;
   for (int a = 0; a < MK; ++a) {
     double2 z = make_double2(0.0, 0.0);
     for (int c2 = 0; c2 < MK; ++c2) z = cadd(z, cmul(q[a * MK + c2], ld(xr + c2)));
-    P[((size_t)f * T + t) * M + o + a] = cabs2(z);
+    P[((size_t)f * T + t) * M + o + a] = (RR)cabs2(z);
   }
 }
 
 // A[n][f][t] = sum_m g P / yhat^2, D[n][f][t] = sum_m g / yhat; one thread per (f, t) for all
 // sources, P / yhat^2 and 1 / yhat formed once per microphone
-__global__ void k_a_AD(const double* __restrict__ P, const double* __restrict__ ry, const double* __restrict__ g,
-                       double* __restrict__ A, double* __restrict__ D, int N, int F, int T, int M) {
+template <class R>
+__global__ void k_a_AD(const R* __restrict__ P, const R* __restrict__ ry, const R* __restrict__ g,
+                       R* __restrict__ A, R* __restrict__ D, int N, int F, int T, int M) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (size_t)F * T) return;
   const int t = (int)(i % T), f = (int)(i / T);
   const size_t r = i * M;
-  double a[16], d[16];
+  R a[16], d[16];
 #pragma unroll
-  for (int n = 0; n < 16; ++n) a[n] = d[n] = 0.0;
+  for (int n = 0; n < 16; ++n) a[n] = d[n] = R(0);
   for (int m = 0; m < M; ++m) {
-    const double rv = ry[r + m], u = P[r + m] * (rv * rv);
+    const R rv = ry[r + m], u = P[r + m] * (rv * rv);
 #pragma unroll
     for (int n = 0; n < 16; ++n)
       if (n < N) {
-        const double gg = g[((size_t)f * N + n) * M + m];
+        const R gg = g[((size_t)f * N + n) * M + m];
         a[n] += gg * u;
         d[n] += gg * rv;
       }
@@ -347,25 +377,27 @@ __global__ void k_a_AD(const double* __restrict__ P, const double* __restrict__ 
 }
 
 // out = theta sqrt(num / max(den, eps))   (Eqs. 8-10)
-__global__ void k_a_mu(const double* __restrict__ th, const double* __restrict__ num, const double* __restrict__ den,
-                       double* __restrict__ out, size_t n, double eps) {
+template <class R>
+__global__ void k_a_mu(const R* __restrict__ th, const R* __restrict__ num, const R* __restrict__ den,
+                       R* __restrict__ out, size_t n, R eps) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = th[i] * sqrt(num[i] / flo(den[i], eps));
 }
 
 // num[f][n][m] = sum_t lam P / yhat^2, den = sum_t lam / yhat   (Eq. 10); one warp per
 // output, lanes over t
-__global__ void k_a_gnum(const double* __restrict__ lam, const double* __restrict__ P, const double* __restrict__ ry,
-                         double* __restrict__ num, double* __restrict__ den, int N, int F, int T, int M) {
+template <class R>
+__global__ void k_a_gnum(const R* __restrict__ lam, const R* __restrict__ P, const R* __restrict__ ry,
+                         R* __restrict__ num, R* __restrict__ den, int N, int F, int T, int M) {
   const size_t i = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= (size_t)F * N * M) return;
   const int m = (int)(i % M), n = (int)((i / M) % N), f = (int)(i / ((size_t)M * N));
-  const double* l = lam + ((size_t)n * F + f) * T;
-  double a = 0.0, d = 0.0;
+  const R* l = lam + ((size_t)n * F + f) * T;
+  R a = R(0), d = R(0);
   for (int t = lane; t < T; t += 32) {
     const size_t r = ((size_t)f * T + t) * M + m;
-    const double rv = ry[r];
+    const R rv = ry[r];
     a += l[t] * P[r] * (rv * rv);
     d += l[t] * rv;
   }
@@ -504,50 +536,52 @@ __global__ void __launch_bounds__(128) k_a_ipfwd(const double2* __restrict__ Q, 
 // out = theta rho, rho = sqrt(num / max(den, eps)): bar_theta (=/+=) bar_out rho,
 // bar_num = r / max(den, eps), bar_den = -r num / den^2 (0 under the floor),
 // r = bar_out theta / (2 rho)
-__global__ void k_a_mub(const double* __restrict__ th, const double* __restrict__ num, const double* __restrict__ den,
-                        const double* __restrict__ bar_out, double* __restrict__ bar_th, double* __restrict__ numb,
-                        double* __restrict__ denb, size_t n, double eps) {
+template <class R>
+__global__ void k_a_mub(const R* __restrict__ th, const R* __restrict__ num, const R* __restrict__ den,
+                        const R* __restrict__ bar_out, R* __restrict__ bar_th, R* __restrict__ numb,
+                        R* __restrict__ denb, size_t n, R eps) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const double dn = flo(den[i], eps);
-  const double rho = sqrt(num[i] / dn);
+  const R dn = flo(den[i], eps);
+  const R rho = sqrt(num[i] / dn);
   bar_th[i] = bar_out[i] * rho;
-  const double r = rho > 0.0 ? bar_out[i] * th[i] / (2.0 * rho) : 0.0;
+  const R r = rho > R(0) ? bar_out[i] * th[i] / (R(2) * rho) : R(0);
   numb[i] = r / dn;
-  denb[i] = den[i] > eps ? -r * num[i] / (dn * dn) : 0.0;
+  denb[i] = den[i] > eps ? -r * num[i] / (dn * dn) : R(0);
 }
 
 // Reverse of the g update's sums (Eq. 10) and of the model at lambda2, per (f, t):
 //   ybar[m] = sum_n lam2 (-2 numb P / yhat^3 - denb / yhat^2)  (0 under the floor)
 //   Pbar[m] += sum_n numb lam2 / yhat^2
 //   lamb[n] = sum_m (numb P / yhat^2 + denb / yhat + ybar[m] g)
-__global__ void k_a_gstat_b(const double* __restrict__ numb, const double* __restrict__ denb,
-                            const double* __restrict__ lam, const double* __restrict__ P,
-                            const double* __restrict__ y, const double* __restrict__ ry, const double* __restrict__ g,
-                            double* __restrict__ lamb, double* __restrict__ Pb, double* __restrict__ yb, int N, int F,
-                            int T, int M, double eps) {
+template <class R>
+__global__ void k_a_gstat_b(const R* __restrict__ numb, const R* __restrict__ denb,
+                            const R* __restrict__ lam, const R* __restrict__ P,
+                            const R* __restrict__ y, const R* __restrict__ ry, const R* __restrict__ g,
+                            R* __restrict__ lamb, R* __restrict__ Pb, R* __restrict__ yb, int N, int F,
+                            int T, int M, R eps) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (size_t)F * T) return;
   const int t = (int)(i % T), f = (int)(i / T);
   const size_t r = i * M;
   for (int m = 0; m < M; ++m) {
     // sum_n lam numb and sum_n lam denb first, then the per-microphone factors
-    const double rv = ry[r + m], r2 = rv * rv, pm = P[r + m];
-    double u = 0.0, v = 0.0;
+    const R rv = ry[r + m], r2 = rv * rv, pm = P[r + m];
+    R u = R(0), v = R(0);
     for (int n = 0; n < N; ++n) {
-      const double l = lam[((size_t)n * F + f) * T + t];
+      const R l = lam[((size_t)n * F + f) * T + t];
       const size_t q = ((size_t)f * N + n) * M + m;
       u += l * numb[q];
       v += l * denb[q];
     }
-    const double a = -2.0 * pm * (r2 * rv) * u - r2 * v;
-    yb[r + m] = y[r + m] > eps ? a : 0.0;
+    const R a = R(-2) * pm * (r2 * rv) * u - r2 * v;
+    yb[r + m] = y[r + m] > eps ? a : R(0);
     Pb[r + m] += r2 * u;
   }
   for (int n = 0; n < N; ++n) {
-    double s = 0.0;
+    R s = R(0);
     for (int m = 0; m < M; ++m) {
-      const double rv = ry[r + m];
+      const R rv = ry[r + m];
       const size_t q = ((size_t)f * N + n) * M + m;
       s += numb[q] * P[r + m] * (rv * rv) + denb[q] * rv + yb[r + m] * g[q];
     }
@@ -558,56 +592,59 @@ __global__ void k_a_gstat_b(const double* __restrict__ numb, const double* __res
 // Reverse of A = sum_m g P / yhat^2, D = sum_m g / yhat, per (f, t, m):
 //   ybar (=/+=) sum_n (-2 Ab g P / yhat^3 - Db g / yhat^2)  (0 under the floor),
 //   Pbar += sum_n Ab g / yhat^2
-__global__ void k_a_stat_b(const double* __restrict__ Ab, const double* __restrict__ Db,
-                           const double* __restrict__ g, const double* __restrict__ P, const double* __restrict__ y,
-                           const double* __restrict__ ry, double* __restrict__ yb, double* __restrict__ Pb, int N,
-                           int F, int T, int M, double eps, int acc) {
+template <class R>
+__global__ void k_a_stat_b(const R* __restrict__ Ab, const R* __restrict__ Db,
+                           const R* __restrict__ g, const R* __restrict__ P, const R* __restrict__ y,
+                           const R* __restrict__ ry, R* __restrict__ yb, R* __restrict__ Pb, int N,
+                           int F, int T, int M, R eps, int acc) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (size_t)F * T * M) return;
   const int m = (int)(i % M), t = (int)((i / M) % T), f = (int)(i / ((size_t)T * M));
   // the source sums first: sum_n Ab g and sum_n Db g, then the per-microphone factors
-  const double rv = ry[i], r2 = rv * rv, pi = P[i];
-  double sa = 0.0, sd = 0.0;
+  const R rv = ry[i], r2 = rv * rv, pi = P[i];
+  R sa = R(0), sd = R(0);
   for (int n = 0; n < N; ++n) {
     const size_t nf = ((size_t)n * F + f) * T + t;
-    const double gg = g[((size_t)f * N + n) * M + m];
+    const R gg = g[((size_t)f * N + n) * M + m];
     sa += Ab[nf] * gg;
     sd += Db[nf] * gg;
   }
-  const double a = -2.0 * pi * (r2 * rv) * sa - r2 * sd;
-  const double pb = r2 * sa;
-  const double v = y[i] > eps ? a : 0.0;
-  yb[i] = (acc ? yb[i] : 0.0) + v;
+  const R a = R(-2) * pi * (r2 * rv) * sa - r2 * sd;
+  const R pb = r2 * sa;
+  const R v = y[i] > eps ? a : R(0);
+  yb[i] = (acc ? yb[i] : R(0)) + v;
   Pb[i] += pb;
 }
 
 // lamb[n][f][t] (=/+=) sum_m ybar[f][t][m] g[f][n][m]   (reverse of y = sum_n lambda g)
-__global__ void k_a_y_b(const double* __restrict__ yb, const double* __restrict__ g, double* __restrict__ lamb,
+template <class R>
+__global__ void k_a_y_b(const R* __restrict__ yb, const R* __restrict__ g, R* __restrict__ lamb,
                         int N, int F, int T, int M, int acc) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (size_t)N * F * T) return;
   const int t = (int)(i % T), f = (int)((i / T) % F), n = (int)(i / ((size_t)F * T));
-  const double* gr = g + ((size_t)f * N + n) * M;
-  const double* yr = yb + ((size_t)f * T + t) * M;
-  double s = 0.0;
+  const R* gr = g + ((size_t)f * N + n) * M;
+  const R* yr = yb + ((size_t)f * T + t) * M;
+  R s = R(0);
   for (int m = 0; m < M; ++m) s += yr[m] * gr[m];
-  lamb[i] = (acc ? lamb[i] : 0.0) + s;
+  lamb[i] = (acc ? lamb[i] : R(0)) + s;
 }
 
 // gbar[f][n][m] += sum_t (Ab P / yhat^2 + Db / yhat + ybar lam); NULL terms are skipped.
 // One warp per output, lanes over t.
-__global__ void k_a_gbar(const double* __restrict__ Ab, const double* __restrict__ Db, const double* __restrict__ yb,
-                         const double* __restrict__ lam, const double* __restrict__ P, const double* __restrict__ ry,
-                         double* __restrict__ gb, int N, int F, int T, int M) {
+template <class R>
+__global__ void k_a_gbar(const R* __restrict__ Ab, const R* __restrict__ Db, const R* __restrict__ yb,
+                         const R* __restrict__ lam, const R* __restrict__ P, const R* __restrict__ ry,
+                         R* __restrict__ gb, int N, int F, int T, int M) {
   const size_t i = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= (size_t)F * N * M) return;
   const int m = (int)(i % M), n = (int)((i / M) % N), f = (int)(i / ((size_t)M * N));
   const size_t nf = ((size_t)n * F + f) * T;
-  double s = 0.0;
+  R s = R(0);
   for (int t = lane; t < T; t += 32) {
     const size_t r = ((size_t)f * T + t) * M + m;
-    const double rv = ry[r];
+    const R rv = ry[r];
     if (Ab) s += Ab[nf + t] * P[r] * (rv * rv);
     if (Db) s += Db[nf + t] * rv;
     if (yb) s += yb[r] * lam[nf + t];
@@ -630,9 +667,9 @@ __global__ void k_a_red_t4(const double* __restrict__ G4, double* __restrict__ g
 
 // Reverse of P = |Q x|^2: Qbar[f][k][a][b] += sum_t 2 Pbar_a z_a conj(x_b), z = Q_fk x_ftk.
 // One warp per (f, k, a), lanes over t: z_a is formed once per frame for all b.
-template <int MK>
-__global__ void k_a_Pb(const float2* __restrict__ x, const double2* __restrict__ Q, size_t bstride,
-                       const double* __restrict__ Pb, double2* __restrict__ Qb, int F, int T, int K) {
+template <int MK, class RR>
+__global__ void k_a_Pb(const double2* __restrict__ x, const double2* __restrict__ Q, size_t bstride,
+                       const RR* __restrict__ Pb, double2* __restrict__ Qb, int F, int T, int K) {
   const size_t w = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= (size_t)F * K * MK) return;
@@ -654,7 +691,7 @@ __global__ void k_a_Pb(const float2* __restrict__ x, const double2* __restrict__
       xv[c2] = ld(x + r + c2);
       z = cadd(z, cmul(qa[c2], xv[c2]));
     }
-    const double s2 = 2.0 * Pb[r + a];
+    const double s2 = 2.0 * (double)Pb[r + a];
 #pragma unroll
     for (int b = 0; b < MK; ++b) acc[b] = cadd(acc[b], cscale(cmulc(z, xv[b]), s2));
   }
@@ -748,14 +785,14 @@ __global__ void k_a_Vh(const double2* __restrict__ Vb, double* __restrict__ Vh, 
   }
 }
 
-template <int MK>
-__global__ void k_a_Vb(const float2* __restrict__ x, const double* __restrict__ Vh, const double* __restrict__ y0,
-                       const double* __restrict__ r0, double* __restrict__ yb, int F, int T, int K, double eps) {
+template <int MK, class RR>
+__global__ void k_a_Vb(const double2* __restrict__ x, const double* __restrict__ Vh, const RR* __restrict__ y0,
+                       const RR* __restrict__ r0, RR* __restrict__ yb, int F, int T, int K, double eps) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (size_t)F * T * K) return;
   const int k = (int)(i % K), t = (int)((i / K) % T), f = (int)(i / ((size_t)K * T));
   const int M = K * MK, o = k * MK;
-  const float2* xr = x + ((size_t)f * T + t) * M + o;
+  const double2* xr = x + ((size_t)f * T + t) * M + o;
   double2 xv[MK];
 #pragma unroll
   for (int a = 0; a < MK; ++a) xv[a] = ld(xr + a);
@@ -773,7 +810,7 @@ __global__ void k_a_Vb(const float2* __restrict__ x, const double* __restrict__ 
 #pragma unroll
   for (int mu = 0; mu < MK; ++mu) {
     const size_t e = ((size_t)f * T + t) * M + o + mu;
-    if (!(y0[e] > eps)) continue;
+    if (!((double)y0[e] > eps)) continue;
     const double* h = Vh + (((size_t)f * K + k) * MK + mu) * MK * MK;
     double s = 0.0;
 #pragma unroll
@@ -782,7 +819,8 @@ __global__ void k_a_Vb(const float2* __restrict__ x, const double* __restrict__ 
 #pragma unroll
       for (int b = a + 1; b < MK; ++b) s += h[a * MK + b] * pr[a][b] - h[b * MK + a] * pi[a][b];
     }
-    yb[e] += -s * (r0[e] * r0[e]) * invT;
+    const double r = (double)r0[e];
+    yb[e] += (RR)(-s * (r * r) * invT);
   }
 }
 
@@ -979,6 +1017,15 @@ inline unsigned nblk(size_t n, int t = 256) { return (unsigned)((n + t - 1) / t)
     default: return cudaErrorInvalidValue;                                             \
   }
 
+#define MK_DISPATCH2(MK, KERNEL, RT, GRID, BLOCK, SMEM, STREAM, ...)                \
+  switch (MK) {                                                                        \
+    case 1: KERNEL<1, RT><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__); break;          \
+    case 2: KERNEL<2, RT><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__); break;          \
+    case 3: KERNEL<3, RT><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__); break;          \
+    case 4: KERNEL<4, RT><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__); break;          \
+    default: return cudaErrorInvalidValue;                                             \
+  }
+
 struct Dims {
   int N, F, T, B, K, MK, M, Tp;
   size_t nft, ftm, nfb, nbt, fnm, nq, nv, nqs, nftm;
@@ -1001,102 +1048,137 @@ Dims dims_of(const dfmnmf_ctx* c) {
   return d;
 }
 
-// FP64 copy of a stored state (context layouts) into Wd, Hd, gd, Qd
-cudaError_t load_state(dfmnmf_adj* a, const Dims& d, const double2* Q, const float* W, const float* H,
-                       const float* g, cudaStream_t s) {
-  AL(k_a_tod<<<nblk(d.nfb + d.nbt + d.fnm), 256, 0, s>>>(W, H, g, a->Wd, a->Hd, a->gd, d.nfb, d.nbt, d.fnm, d.T,
-                                                          d.Tp));
+// The double-precision NMF side: the FP64 arrays of the workspace.
+AdjSide<double> dside(dfmnmf_adj* a) {
+  AdjSide<double> v;
+  v.Wd = a->Wd; v.Hd = a->Hd; v.gd = a->gd;
+  v.lam0 = a->lam0; v.lam1 = a->lam1; v.lam2 = a->lam2; v.y0 = a->y0; v.y1 = a->y1; v.y2 = a->y2;
+  v.r0 = a->r0; v.r1 = a->r1; v.r2 = a->r2; v.P = a->P; v.A0 = a->A0; v.D0 = a->D0; v.A1 = a->A1; v.D1 = a->D1;
+  v.numW = a->numW; v.denW = a->denW; v.W1 = a->W1; v.numH = a->numH; v.denH = a->denH; v.H1 = a->H1;
+  v.numG = a->numG; v.denG = a->denG;
+  v.Wb = a->Wb; v.Wb1 = a->Wb1; v.Hb = a->Hb; v.Hb1 = a->Hb1; v.gb = a->gb; v.gb1 = a->gb1;
+  v.lamb = a->lamb; v.yb = a->yb; v.Pb = a->Pb; v.Ab = a->Ab; v.Db = a->Db; v.nb = a->nb; v.db = a->db;
+  return v;
+}
+
+template <class S, class D>
+__global__ void k_a_cvt(const S* __restrict__ in, D* __restrict__ out, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (D)in[i];
+}
+template <class S, class D>
+cudaError_t convert(const S* in, D* out, size_t n, cudaStream_t s) {
+  AL(k_a_cvt<S, D><<<nblk(n), 256, 0, s>>>(in, out, n));
+  return cudaSuccess;
+}
+
+// A stored state (context layouts) into the side's Wd, Hd, gd (type R) and Qd (FP64)
+template <class R>
+cudaError_t load_state(dfmnmf_adj* a, const AdjSide<R>& v, const Dims& d, const double2* Q, const float* W,
+                       const float* H, const float* g, cudaStream_t s) {
+  AL(k_a_tod<R><<<nblk(d.nfb + d.nbt + d.fnm), 256, 0, s>>>(W, H, g, v.Wd, v.Hd, v.gd, d.nfb, d.nbt, d.fnm, d.T,
+                                                             d.Tp));
   return cudaMemcpyAsync(a->Qd, Q, d.nq * sizeof(double2), cudaMemcpyDeviceToDevice, s);
 }
 
 // lam = W H, yraw = sum_n lam g and ry = 1 / max(yraw, eps)
-cudaError_t model(const Dims& d, const double* W, const double* H, const double* g, double* lam, double* y,
-                  double* ry, cudaStream_t s) {
-  AL(k_a_nmf_b<<<nblk(d.nft), 256, 0, s>>>(W, H, lam, d.N, d.F, d.B, d.T));
-  AL(k_a_y<<<nblk(d.ftm), 256, 0, s>>>(lam, g, y, ry, d.N, d.F, d.T, d.M, d.eps));
+template <class R>
+cudaError_t model(const Dims& d, const R* W, const R* H, const R* g, R* lam, R* y, R* ry, cudaStream_t s) {
+  AL(k_a_nmf_b<R><<<nblk(d.nft), 256, 0, s>>>(W, H, lam, d.N, d.F, d.B, d.T));
+  AL(k_a_y<R><<<nblk(d.ftm), 256, 0, s>>>(lam, g, y, ry, d.N, d.F, d.T, d.M, (R)d.eps));
   return cudaSuccess;
 }
 
-cudaError_t nmf_t(const Dims& d, const double* X, const double* Y, double* out, int acc, cudaStream_t s) {
-  AL(k_a_nmf_t<<<nblk(d.nfb * 32), 256, 0, s>>>(X, Y, out, d.N, d.F, d.B, d.T, acc));
+template <class R>
+cudaError_t nmf_t(const Dims& d, const R* X, const R* Y, R* out, int acc, cudaStream_t s) {
+  AL(k_a_nmf_t<R><<<nblk(d.nfb * 32), 256, 0, s>>>(X, Y, out, d.N, d.F, d.B, d.T, acc));
   return cudaSuccess;
 }
-cudaError_t nmf_f(const Dims& d, const double* X, const double* Y, double* out, int acc, cudaStream_t s) {
-  AL(k_a_nmf_f<<<dim3((unsigned)((d.T + 31) / 32), (unsigned)(d.N * d.B)), 32 * NMF_F_WARPS, 0, s>>>(
+template <class R>
+cudaError_t nmf_f(const Dims& d, const R* X, const R* Y, R* out, int acc, cudaStream_t s) {
+  AL(k_a_nmf_f<R><<<dim3((unsigned)((d.T + 31) / 32), (unsigned)(d.N * d.B)), 32 * NMF_F_WARPS, 0, s>>>(
       X, Y, out, d.N, d.F, d.B, d.T, acc));
   return cudaSuccess;
 }
 
-// Reverse of one iteration whose input state is in Wd, Hd, gd, Qd; the adjoint of its
-// output state is in (Qb1, Wb1, Hb1, gb1) (consumed); the adjoint of its input state is
-// written to (Qb, Wb, Hb, gb).
-cudaError_t reverse_iteration(dfmnmf_adj* a, const Dims& d, cudaStream_t s) {
+// Reverse of one iteration whose input state is in (v.Wd, v.Hd, v.gd, Qd); the adjoint of its
+// output state is in (Qb1, v.Wb1, v.Hb1, v.gb1) (consumed); the adjoint of its input state is
+// written to (Qb, v.Wb, v.Hb, v.gb).  The IP side (V, the IP rows, P = |Q x|^2 and their
+// adjoints) is FP64; the NMF side runs in R.
+template <class R>
+cudaError_t reverse_iteration(dfmnmf_adj* a, const AdjSide<R>& v, const Dims& d, cudaStream_t s) {
   const dfmnmf_ctx* c = a->c;
   const double eps = d.eps;
+  const R epsr = (R)d.eps;
   const int nb = d.F * d.K;
-  // forward, recomputed in FP64
-  cudaError_t e = model(d, a->Wd, a->Hd, a->gd, a->lam0, a->y0, a->r0, s);
+  // forward, recomputed
+  cudaError_t e = model<R>(d, v.Wd, v.Hd, v.gd, v.lam0, v.y0, v.r0, s);
   if (e != cudaSuccess) return e;
-  MK_DISPATCH(d.MK, k_a_V, nblk((size_t)d.F * d.K * (d.MK * (d.MK + 1) / 2) * 32), 256, 0, s, c->x, a->r0, a->V,
+  const double* r0d = reinterpret_cast<const double*>(v.r0);
+  if constexpr (!std::is_same<R, double>::value) {  // the weights of Eq. 13 in FP64, converted once
+    if ((e = convert(v.r0, a->r0d, d.ftm, s))) return e;
+    r0d = a->r0d;
+  }
+  MK_DISPATCH(d.MK, k_a_V, nblk((size_t)d.F * d.K * (d.MK * (d.MK + 1) / 2) * 32), 256, 0, s, a->x64, r0d, a->V,
               d.F, d.T, d.K);
   AL((void)0);
   MK_DISPATCH(d.MK, k_a_ipfwd, nblk(nb, 8), 128, 0, s, a->Qd, a->V, a->Qs, nb, eps, (double)c->singular_rtol, a->flags);
   AL((void)0);
   const double2* Qn = a->Qs + (size_t)d.MK * d.MK * d.MK;  // rows after the last update, stride (MK+1) MK^2
   const size_t qstr = (size_t)(d.MK + 1) * d.MK * d.MK;
-  AL(k_a_P<<<nblk((size_t)d.F * d.T * d.K), 256, 0, s>>>(c->x, Qn, qstr, a->P, d.F, d.T, d.K, d.MK));
-  AL(k_a_AD<<<nblk((size_t)d.F * d.T), 256, 0, s>>>(a->P, a->r0, a->gd, a->A0, a->D0, d.N, d.F, d.T, d.M));
-  if ((e = nmf_t(d, a->A0, a->Hd, a->numW, 0, s)) || (e = nmf_t(d, a->D0, a->Hd, a->denW, 0, s))) return e;
-  AL(k_a_mu<<<nblk(d.nfb), 256, 0, s>>>(a->Wd, a->numW, a->denW, a->W1, d.nfb, eps));
-  if ((e = model(d, a->W1, a->Hd, a->gd, a->lam1, a->y1, a->r1, s))) return e;
-  AL(k_a_AD<<<nblk((size_t)d.F * d.T), 256, 0, s>>>(a->P, a->r1, a->gd, a->A1, a->D1, d.N, d.F, d.T, d.M));
-  if ((e = nmf_f(d, a->W1, a->A1, a->numH, 0, s)) || (e = nmf_f(d, a->W1, a->D1, a->denH, 0, s))) return e;
-  AL(k_a_mu<<<nblk(d.nbt), 256, 0, s>>>(a->Hd, a->numH, a->denH, a->H1, d.nbt, eps));
-  if ((e = model(d, a->W1, a->H1, a->gd, a->lam2, a->y2, a->r2, s))) return e;
-  AL(k_a_gnum<<<nblk(d.fnm * 32), 256, 0, s>>>(a->lam2, a->P, a->r2, a->numG, a->denG, d.N, d.F, d.T, d.M));
+  AL(k_a_P<R><<<nblk((size_t)d.F * d.T * d.K), 256, 0, s>>>(a->x64, Qn, qstr, v.P, d.F, d.T, d.K, d.MK));
+  AL(k_a_AD<R><<<nblk((size_t)d.F * d.T), 256, 0, s>>>(v.P, v.r0, v.gd, v.A0, v.D0, d.N, d.F, d.T, d.M));
+  if ((e = nmf_t<R>(d, v.A0, v.Hd, v.numW, 0, s)) || (e = nmf_t<R>(d, v.D0, v.Hd, v.denW, 0, s))) return e;
+  AL(k_a_mu<R><<<nblk(d.nfb), 256, 0, s>>>(v.Wd, v.numW, v.denW, v.W1, d.nfb, epsr));
+  if ((e = model<R>(d, v.W1, v.Hd, v.gd, v.lam1, v.y1, v.r1, s))) return e;
+  AL(k_a_AD<R><<<nblk((size_t)d.F * d.T), 256, 0, s>>>(v.P, v.r1, v.gd, v.A1, v.D1, d.N, d.F, d.T, d.M));
+  if ((e = nmf_f<R>(d, v.W1, v.A1, v.numH, 0, s)) || (e = nmf_f<R>(d, v.W1, v.D1, v.denH, 0, s))) return e;
+  AL(k_a_mu<R><<<nblk(d.nbt), 256, 0, s>>>(v.Hd, v.numH, v.denH, v.H1, d.nbt, epsr));
+  if ((e = model<R>(d, v.W1, v.H1, v.gd, v.lam2, v.y2, v.r2, s))) return e;
+  AL(k_a_gnum<R><<<nblk(d.fnm * 32), 256, 0, s>>>(v.lam2, v.P, v.r2, v.numG, v.denG, d.N, d.F, d.T, d.M));
 
   // reverse of the g update (Eq. 10)
-  AL(k_a_mub<<<nblk(d.fnm), 256, 0, s>>>(a->gd, a->numG, a->denG, a->gb1, a->gb, a->nb, a->db, d.fnm, eps));
-  ACKE(cudaMemsetAsync(a->Pb, 0, d.ftm * sizeof(double), s));
-  AL(k_a_gstat_b<<<nblk((size_t)d.F * d.T), 256, 0, s>>>(a->nb, a->db, a->lam2, a->P, a->y2, a->r2, a->gd, a->lamb,
-                                                          a->Pb, a->yb, d.N, d.F, d.T, d.M, eps));
-  AL(k_a_gbar<<<nblk(d.fnm * 32), 256, 0, s>>>(nullptr, nullptr, a->yb, a->lam2, a->P, a->r2, a->gb, d.N, d.F, d.T,
+  AL(k_a_mub<R><<<nblk(d.fnm), 256, 0, s>>>(v.gd, v.numG, v.denG, v.gb1, v.gb, v.nb, v.db, d.fnm, epsr));
+  ACKE(cudaMemsetAsync(v.Pb, 0, d.ftm * sizeof(R), s));
+  AL(k_a_gstat_b<R><<<nblk((size_t)d.F * d.T), 256, 0, s>>>(v.nb, v.db, v.lam2, v.P, v.y2, v.r2, v.gd, v.lamb,
+                                                          v.Pb, v.yb, d.N, d.F, d.T, d.M, epsr));
+  AL(k_a_gbar<R><<<nblk(d.fnm * 32), 256, 0, s>>>(nullptr, nullptr, v.yb, v.lam2, v.P, v.r2, v.gb, d.N, d.F, d.T,
                                                 d.M));
-  if ((e = nmf_t(d, a->lamb, a->H1, a->Wb1, 1, s)) || (e = nmf_f(d, a->W1, a->lamb, a->Hb1, 1, s))) return e;
+  if ((e = nmf_t<R>(d, v.lamb, v.H1, v.Wb1, 1, s)) || (e = nmf_f<R>(d, v.W1, v.lamb, v.Hb1, 1, s))) return e;
   // reverse of the H update (Eq. 9)
-  AL(k_a_mub<<<nblk(d.nbt), 256, 0, s>>>(a->Hd, a->numH, a->denH, a->Hb1, a->Hb, a->nb, a->db, d.nbt, eps));
-  if ((e = nmf_t(d, a->A1, a->nb, a->Wb1, 1, s)) || (e = nmf_t(d, a->D1, a->db, a->Wb1, 1, s))) return e;
-  AL(k_a_nmf_b<<<nblk(d.nft), 256, 0, s>>>(a->W1, a->nb, a->Ab, d.N, d.F, d.B, d.T));
-  AL(k_a_nmf_b<<<nblk(d.nft), 256, 0, s>>>(a->W1, a->db, a->Db, d.N, d.F, d.B, d.T));
-  AL(k_a_stat_b<<<nblk(d.ftm), 256, 0, s>>>(a->Ab, a->Db, a->gd, a->P, a->y1, a->r1, a->yb, a->Pb, d.N, d.F, d.T,
-                                             d.M, eps, 0));
-  AL(k_a_gbar<<<nblk(d.fnm * 32), 256, 0, s>>>(a->Ab, a->Db, a->yb, a->lam1, a->P, a->r1, a->gb, d.N, d.F, d.T,
+  AL(k_a_mub<R><<<nblk(d.nbt), 256, 0, s>>>(v.Hd, v.numH, v.denH, v.Hb1, v.Hb, v.nb, v.db, d.nbt, epsr));
+  if ((e = nmf_t<R>(d, v.A1, v.nb, v.Wb1, 1, s)) || (e = nmf_t<R>(d, v.D1, v.db, v.Wb1, 1, s))) return e;
+  AL(k_a_nmf_b<R><<<nblk(d.nft), 256, 0, s>>>(v.W1, v.nb, v.Ab, d.N, d.F, d.B, d.T));
+  AL(k_a_nmf_b<R><<<nblk(d.nft), 256, 0, s>>>(v.W1, v.db, v.Db, d.N, d.F, d.B, d.T));
+  AL(k_a_stat_b<R><<<nblk(d.ftm), 256, 0, s>>>(v.Ab, v.Db, v.gd, v.P, v.y1, v.r1, v.yb, v.Pb, d.N, d.F, d.T,
+                                             d.M, epsr, 0));
+  AL(k_a_gbar<R><<<nblk(d.fnm * 32), 256, 0, s>>>(v.Ab, v.Db, v.yb, v.lam1, v.P, v.r1, v.gb, d.N, d.F, d.T,
                                                 d.M));
-  AL(k_a_y_b<<<nblk(d.nft), 256, 0, s>>>(a->yb, a->gd, a->lamb, d.N, d.F, d.T, d.M, 0));
-  if ((e = nmf_t(d, a->lamb, a->Hd, a->Wb1, 1, s)) || (e = nmf_f(d, a->W1, a->lamb, a->Hb, 1, s))) return e;
+  AL(k_a_y_b<R><<<nblk(d.nft), 256, 0, s>>>(v.yb, v.gd, v.lamb, d.N, d.F, d.T, d.M, 0));
+  if ((e = nmf_t<R>(d, v.lamb, v.Hd, v.Wb1, 1, s)) || (e = nmf_f<R>(d, v.W1, v.lamb, v.Hb, 1, s))) return e;
   // reverse of the W update (Eq. 8)
-  AL(k_a_mub<<<nblk(d.nfb), 256, 0, s>>>(a->Wd, a->numW, a->denW, a->Wb1, a->Wb, a->nb, a->db, d.nfb, eps));
-  if ((e = nmf_f(d, a->nb, a->A0, a->Hb, 1, s)) || (e = nmf_f(d, a->db, a->D0, a->Hb, 1, s))) return e;
-  AL(k_a_nmf_b<<<nblk(d.nft), 256, 0, s>>>(a->nb, a->Hd, a->Ab, d.N, d.F, d.B, d.T));
-  AL(k_a_nmf_b<<<nblk(d.nft), 256, 0, s>>>(a->db, a->Hd, a->Db, d.N, d.F, d.B, d.T));
-  AL(k_a_stat_b<<<nblk(d.ftm), 256, 0, s>>>(a->Ab, a->Db, a->gd, a->P, a->y0, a->r0, a->yb, a->Pb, d.N, d.F, d.T,
-                                             d.M, eps, 0));
+  AL(k_a_mub<R><<<nblk(d.nfb), 256, 0, s>>>(v.Wd, v.numW, v.denW, v.Wb1, v.Wb, v.nb, v.db, d.nfb, epsr));
+  if ((e = nmf_f<R>(d, v.nb, v.A0, v.Hb, 1, s)) || (e = nmf_f<R>(d, v.db, v.D0, v.Hb, 1, s))) return e;
+  AL(k_a_nmf_b<R><<<nblk(d.nft), 256, 0, s>>>(v.nb, v.Hd, v.Ab, d.N, d.F, d.B, d.T));
+  AL(k_a_nmf_b<R><<<nblk(d.nft), 256, 0, s>>>(v.db, v.Hd, v.Db, d.N, d.F, d.B, d.T));
+  AL(k_a_stat_b<R><<<nblk(d.ftm), 256, 0, s>>>(v.Ab, v.Db, v.gd, v.P, v.y0, v.r0, v.yb, v.Pb, d.N, d.F, d.T,
+                                             d.M, epsr, 0));
   // reverse of the projections and of the IP rows (Eqs. 13-15)
-  MK_DISPATCH(d.MK, k_a_Pb, nblk((size_t)d.F * d.K * d.MK * 32), 256, 0, s, c->x, Qn, qstr, a->Pb, a->Qb1, d.F, d.T,
-              d.K);
+  MK_DISPATCH2(d.MK, k_a_Pb, R, nblk((size_t)d.F * d.K * d.MK * 32), 256, 0, s, a->x64, Qn, qstr, v.Pb, a->Qb1, d.F,
+               d.T, d.K);
   AL((void)0);
   MK_DISPATCH(d.MK, k_a_ipb, nblk(nb, 8), 128, 0, s, a->Qs, a->V, a->Qb1, a->Qb, a->Vb, nb, eps);
   AL((void)0);
   MK_DISPATCH(d.MK, k_a_Vh, nblk(d.nq / d.MK), 256, 0, s, a->Vb, a->Vh, d.nq / d.MK);  // one thread per (f, k, mu)
   AL((void)0);
-  MK_DISPATCH(d.MK, k_a_Vb, nblk((size_t)d.F * d.T * d.K), 256, 0, s, c->x, a->Vh, a->y0, a->r0, a->yb, d.F, d.T,
-              d.K, eps);
+  MK_DISPATCH2(d.MK, k_a_Vb, R, nblk((size_t)d.F * d.T * d.K), 256, 0, s, a->x64, a->Vh, v.y0, v.r0, v.yb, d.F,
+               d.T, d.K, eps);
   AL((void)0);
   // reverse of the model at the input state
-  AL(k_a_gbar<<<nblk(d.fnm * 32), 256, 0, s>>>(a->Ab, a->Db, a->yb, a->lam0, a->P, a->r0, a->gb, d.N, d.F, d.T,
+  AL(k_a_gbar<R><<<nblk(d.fnm * 32), 256, 0, s>>>(v.Ab, v.Db, v.yb, v.lam0, v.P, v.r0, v.gb, d.N, d.F, d.T,
                                                 d.M));
-  AL(k_a_y_b<<<nblk(d.nft), 256, 0, s>>>(a->yb, a->gd, a->lamb, d.N, d.F, d.T, d.M, 0));
-  if ((e = nmf_t(d, a->lamb, a->Hd, a->Wb, 1, s)) || (e = nmf_f(d, a->Wd, a->lamb, a->Hb, 1, s))) return e;
+  AL(k_a_y_b<R><<<nblk(d.nft), 256, 0, s>>>(v.yb, v.gd, v.lamb, d.N, d.F, d.T, d.M, 0));
+  if ((e = nmf_t<R>(d, v.lamb, v.Hd, v.Wb, 1, s)) || (e = nmf_f<R>(d, v.Wd, v.lamb, v.Hb, 1, s))) return e;
   return cudaSuccess;
 }
 
@@ -1105,21 +1187,21 @@ cudaError_t loss_and_adjoint(dfmnmf_adj* a, const Dims& d, int loss, const float
   const dfmnmf_ctx* c = a->c;
   const double eps = d.eps;
   const int nb = d.F * d.K;
-  cudaError_t e = model(d, a->Wd, a->Hd, a->gd, a->lam0, a->y0, a->r0, s);
+  cudaError_t e = model<double>(d, a->Wd, a->Hd, a->gd, a->lam0, a->y0, a->r0, s);
   if (e != cudaSuccess) return e;
   ACKE(cudaMemsetAsync(a->red, 0, sizeof(double), s));
   ACKE(cudaMemsetAsync(a->gb, 0, d.fnm * sizeof(double), s));
   const size_t qstr = (size_t)d.MK * d.MK;
   if (loss == DFMNMF_LOSS_NLL) {
-    AL(k_a_P<<<nblk((size_t)d.F * d.T * d.K), 256, 0, s>>>(c->x, a->Qd, qstr, a->P, d.F, d.T, d.K, d.MK));
+    AL(k_a_P<double><<<nblk((size_t)d.F * d.T * d.K), 256, 0, s>>>(a->x64, a->Qd, qstr, a->P, d.F, d.T, d.K, d.MK));
     AL(k_a_nll_data<<<nblk(d.ftm), 256, 0, s>>>(a->P, a->y0, a->r0, a->Pb, a->yb, a->red, d.ftm, eps));
     ACKE(cudaMemsetAsync(a->Qb, 0, d.nq * sizeof(double2), s));
-    MK_DISPATCH(d.MK, k_a_Pb, nblk((size_t)d.F * d.K * d.MK * 32), 256, 0, s, c->x, a->Qd, qstr, a->Pb, a->Qb, d.F,
+    MK_DISPATCH2(d.MK, k_a_Pb, double, nblk((size_t)d.F * d.K * d.MK * 32), 256, 0, s, a->x64, a->Qd, qstr, a->Pb, a->Qb, d.F,
                 d.T, d.K);
     AL((void)0);
     MK_DISPATCH(d.MK, k_a_logdet_b, nblk(nb, 64), 64, 0, s, a->Qd, a->Qb, a->red, nb, d.T);
     AL((void)0);
-    AL(k_a_y_b<<<nblk(d.nft), 256, 0, s>>>(a->yb, a->gd, a->lamb, d.N, d.F, d.T, d.M, 0));
+    AL(k_a_y_b<double><<<nblk(d.nft), 256, 0, s>>>(a->yb, a->gd, a->lamb, d.N, d.F, d.T, d.M, 0));
   } else {
     MK_DISPATCH(d.MK, k_a_inv, nblk(nb, 64), 64, 0, s, a->Qd, a->Binv, nb);
     AL((void)0);
@@ -1129,11 +1211,11 @@ cudaError_t loss_and_adjoint(dfmnmf_adj* a, const Dims& d, int loss, const float
     AL((void)0);
     AL(k_a_wiener_q<<<nblk(d.nq), 256, 0, s>>>(c->x, a->zbar, a->ubar, a->cvec, a->Qb, d.N, d.F, d.T, d.K, d.MK));
     AL(k_a_red_t4<<<nblk(d.fnm * 32), 256, 0, s>>>(a->G4, a->gb, d.N, d.F, d.T, d.M));
-    AL(k_a_y_b<<<nblk(d.nft), 256, 0, s>>>(a->yb, a->gd, a->lamb, d.N, d.F, d.T, d.M, 1));
+    AL(k_a_y_b<double><<<nblk(d.nft), 256, 0, s>>>(a->yb, a->gd, a->lamb, d.N, d.F, d.T, d.M, 1));
   }
-  AL(k_a_gbar<<<nblk(d.fnm * 32), 256, 0, s>>>(nullptr, nullptr, a->yb, a->lam0, a->P, a->r0, a->gb, d.N, d.F, d.T,
+  AL(k_a_gbar<double><<<nblk(d.fnm * 32), 256, 0, s>>>(nullptr, nullptr, a->yb, a->lam0, a->P, a->r0, a->gb, d.N, d.F, d.T,
                                                 d.M));
-  if ((e = nmf_t(d, a->lamb, a->Hd, a->Wb, 0, s)) || (e = nmf_f(d, a->Wd, a->lamb, a->Hb, 0, s))) return e;
+  if ((e = nmf_t<double>(d, a->lamb, a->Hd, a->Wb, 0, s)) || (e = nmf_f<double>(d, a->Wd, a->lamb, a->Hb, 0, s))) return e;
   return cudaSuccess;
 }
 
@@ -1178,6 +1260,14 @@ void free_adj(dfmnmf_adj* a) {
                a->nb, a->db, a->Vb, a->Vh, a->Binv, a->ubar, a->cvec, a->zbar, a->G4, a->red, a->flags};
   for (void* q : p)
     if (q) cudaFree(q);
+  const AdjSide<float>& f = a->sf;
+  void* ps[] = {f.Wd, f.Hd, f.gd, f.lam0, f.lam1, f.lam2, f.y0, f.y1, f.y2, f.r0, f.r1, f.r2, f.P, f.A0, f.D0,
+                f.A1, f.D1, f.numW, f.denW, f.W1, f.numH, f.denH, f.H1, f.numG, f.denG, f.Wb, f.Wb1, f.Hb, f.Hb1,
+                f.gb, f.gb1, f.lamb, f.yb, f.Pb, f.Ab, f.Db, f.nb, f.db};
+  for (void* q : ps)
+    if (q) cudaFree(q);
+  if (a->x64) cudaFree(a->x64);
+  if (a->r0d) cudaFree(a->r0d);
   delete a;
 }
 
@@ -1231,6 +1321,17 @@ int dfmnmf_adjoint_create(dfmnmf_adj** out, dfmnmf_ctx* c, int n_iter, int every
             aalloc(&a->Binv, d.nq) && (!wien || (aalloc(&a->ubar, d.nftm) && aalloc(&a->cvec, d.nftm) &&
                                                  aalloc(&a->zbar, d.ftm) && aalloc(&a->G4, d.nftm))) &&
             aalloc(&a->red, 1) && aalloc(&a->flags, 4);
+  AdjSide<float>& f = a->sf;
+  ok = ok && aalloc(&f.Wd, d.nfb) && aalloc(&f.Hd, d.nbt) && aalloc(&f.gd, d.fnm) && aalloc(&f.lam0, d.nft) &&
+       aalloc(&f.lam1, d.nft) && aalloc(&f.lam2, d.nft) && aalloc(&f.y0, d.ftm) && aalloc(&f.y1, d.ftm) &&
+       aalloc(&f.y2, d.ftm) && aalloc(&f.r0, d.ftm) && aalloc(&f.r1, d.ftm) && aalloc(&f.r2, d.ftm) &&
+       aalloc(&f.P, d.ftm) && aalloc(&f.A0, d.nft) && aalloc(&f.D0, d.nft) && aalloc(&f.A1, d.nft) &&
+       aalloc(&f.D1, d.nft) && aalloc(&f.numW, d.nfb) && aalloc(&f.denW, d.nfb) && aalloc(&f.W1, d.nfb) &&
+       aalloc(&f.numH, d.nbt) && aalloc(&f.denH, d.nbt) && aalloc(&f.H1, d.nbt) && aalloc(&f.numG, d.fnm) &&
+       aalloc(&f.denG, d.fnm) && aalloc(&f.Wb, d.nfb) && aalloc(&f.Wb1, d.nfb) && aalloc(&f.Hb, d.nbt) &&
+       aalloc(&f.Hb1, d.nbt) && aalloc(&f.gb, d.fnm) && aalloc(&f.gb1, d.fnm) && aalloc(&f.lamb, d.nft) &&
+       aalloc(&f.yb, d.ftm) && aalloc(&f.Pb, d.ftm) && aalloc(&f.Ab, d.nft) && aalloc(&f.Db, d.nft) &&
+       aalloc(&f.nb, nmax) && aalloc(&f.db, nmax) && aalloc(&a->x64, d.ftm) && aalloc(&a->r0d, d.ftm);
   if (!ok) {
     free_adj(a);
     return afail(DFMNMF_ENOMEM, "device allocation of the adjoint workspace failed");
@@ -1249,6 +1350,7 @@ int dfmnmf_adjoint_run(dfmnmf_adj* a, int loss, const void* c_true, double* loss
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const dfm::Dims d = dfm::dims_of(c);
   ACK(cudaMemsetAsync(a->flags, 0, 4 * sizeof(unsigned), s));
+  ACK(dfm::convert(reinterpret_cast<const float*>(c->x), reinterpret_cast<double*>(a->x64), 2 * d.ftm, s));
   // forward: the context's own iterations, the state stored every `every` iterations
   for (int i = 0; i < a->n_iter; ++i) {
     if (i % a->every == 0) {
@@ -1260,8 +1362,16 @@ int dfmnmf_adjoint_run(dfmnmf_adj* a, int loss, const void* c_true, double* loss
   }
   ACK(save_state(c, a->fnQ, a->fnW, a->fnH, a->fng, s));
   // loss of the final state and its adjoint
-  ACK(dfm::load_state(a, d, a->fnQ, a->fnW, a->fnH, a->fng, s));
+  ACK(dfm::load_state<double>(a, dfm::dside(a), d, a->fnQ, a->fnW, a->fnH, a->fng, s));
   ACK(dfm::loss_and_adjoint(a, d, loss, reinterpret_cast<const float2*>(c_true), s));
+  // the unrolled iterations are reversed with the NMF side in single precision (the forward
+  // iterations they differentiate run it in single precision too); the loss and its adjoint
+  // above, and the IP side throughout, are FP64
+  if (a->n_ckpt > 0) {
+    ACK(dfm::convert(a->Wb, a->sf.Wb, d.nfb, s));
+    ACK(dfm::convert(a->Hb, a->sf.Hb, d.nbt, s));
+    ACK(dfm::convert(a->gb, a->sf.gb, d.fnm, s));
+  }
   // reverse sweep, one segment per checkpoint, recomputing the segment's states
   for (int j = a->n_ckpt - 1; j >= 0; --j) {
     const int i0 = j * a->every, len = std::min(a->every, a->n_iter - i0);
@@ -1280,13 +1390,18 @@ int dfmnmf_adjoint_run(dfmnmf_adj* a, int loss, const void* c_true, double* loss
     }
     for (int i = len - 1; i >= 0; --i) {
       std::swap(a->Qb, a->Qb1);
-      std::swap(a->Wb, a->Wb1);
-      std::swap(a->Hb, a->Hb1);
-      std::swap(a->gb, a->gb1);
-      ACK(dfm::load_state(a, d, a->sgQ + (size_t)i * q_n(c), a->sgW + (size_t)i * w_n(c),
-                          a->sgH + (size_t)i * h_n(c), a->sgg + (size_t)i * g_n(c), s));
-      ACK(dfm::reverse_iteration(a, d, s));
+      std::swap(a->sf.Wb, a->sf.Wb1);
+      std::swap(a->sf.Hb, a->sf.Hb1);
+      std::swap(a->sf.gb, a->sf.gb1);
+      ACK(dfm::load_state<float>(a, a->sf, d, a->sgQ + (size_t)i * q_n(c), a->sgW + (size_t)i * w_n(c),
+                                 a->sgH + (size_t)i * h_n(c), a->sgg + (size_t)i * g_n(c), s));
+      ACK(dfm::reverse_iteration<float>(a, a->sf, d, s));
     }
+  }
+  if (a->n_ckpt > 0) {
+    ACK(dfm::convert(a->sf.Wb, a->Wb, d.nfb, s));
+    ACK(dfm::convert(a->sf.Hb, a->Hb, d.nbt, s));
+    ACK(dfm::convert(a->sf.gb, a->gb, d.fnm, s));
   }
   // the context ends at the final state, as after dfmnmf_iterate(n_iter)
   ACK(restore_state(c, a->fnQ, a->fnW, a->fnH, a->fng, s));

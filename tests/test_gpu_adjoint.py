@@ -100,6 +100,7 @@ def check(p, st, n_iter, loss, got, n_dir, n_fd, seed):
         a, scale = dot((dQ, dW, dH, dg), d)
         worst = max(worst, abs(a - fd) / scale)
     errs["dir_vs_fd"] = worst
+    print(f"adjoint {loss}, {n_iter} iterations:", {k: float(f"{v:.2e}") for k, v in errs.items()})
     for k, v in errs.items():
         assert v <= TOL, (k, v, errs)
     return errs
