@@ -155,12 +155,12 @@ def kernel_bytes(F, T, M, N, B, K, MK):
 # `traffic` is null when it no longer matches.
 NCU_TRAFFIC = {
     "paper_4x4_n5": {
-        "k_pstats": (48004352 + 2192128, "kernels_tc.cu", "94eea8ca4bb862b7"),  # k_pstats_tma<0>
+        "k_pstats": (48004352 + 2192128, "kernels_tc.cu", "681d9dac4e7f5a1d"),  # k_pstats_tma<0>
         "k_stats": (27179776 + 1024, "kernels_model.cu", "d019e79f136de230"),
         "k_gupd": (27193344 + 0, "kernels_model.cu", "d019e79f136de230"),
         "k_lambda": (388352 + 0, "kernels_model.cu", "d019e79f136de230"),
-        "k_vtc": (105289984 + 2793216, "kernels_tc.cu", "94eea8ca4bb862b7"),
-        "k_wprep": (6619648 + 0, "kernels_tc.cu", "94eea8ca4bb862b7"),
+        "k_vtc": (105289984 + 2793216, "kernels_tc.cu", "681d9dac4e7f5a1d"),
+        "k_wprep": (6619648 + 0, "kernels_tc.cu", "681d9dac4e7f5a1d"),
         "k_ip": (2701824 + 0, "kernels_ip.cu", "8f14118b76b1c4d8"),
         "k_wupd": (13268736 + 0, "kernels_nmf.cu", "36821db759ba7376"),
         "k_hupd": (13270016 + 0, "kernels_nmf.cu", "36821db759ba7376"),

@@ -18,11 +18,11 @@
 // block of 128 x 64 (R) or 32 x 64 (w) values is contiguous in memory
 // ([tiles][Tr / 64][rows][64], Tr = T rounded up to 64, zero tail), so every
 // tensor copy reads one contiguous 16 KB or 4 KB block instead of 128-byte
-// pieces of rows 2 Tr bytes apart.  k_vtc then only moves and
-// multiplies: one thread streams the four operand tiles of each 64-frame
-// chunk with TMA (128-byte swizzled; R with an evict-first L2 policy, since
-// it is read once per iteration and would otherwise push the streaming
-// kernels' operands out of L2) into a
+// pieces of rows 2 Tr bytes apart.  k_vtc then only moves and multiplies:
+// one thread streams the four operand tiles of each 64-frame chunk with TMA
+// (128-byte swizzled, with an evict-first L2 policy: R and w are read once
+// per iteration, and R, 84 MB on the paper-sized workload, would otherwise
+// push the streaming kernels' operands out of L2) into a
 // 2-stage shared-memory ring (two CTAs per SM), one thread issues
 // tcgen05.mma (M = 128 rows = 128 / (16 K) frequencies, N = 32 weights,
 // K = 16 frames per instruction, FP32 accumulators in tensor memory) and the
