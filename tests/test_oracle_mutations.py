@@ -1,0 +1,147 @@
+"""Planted mistakes in the oracle, each caught by at least one independent pin.
+
+Every mutation below is a plausible one-line slip in a step of the method: a
+dropped factor, a wrong sign, a missing power or square root, a transposed or
+conjugated operand, an inverse left out.  The test plants it by replacing one
+oracle function (in the package namespace the pins call and in the module
+namespace the oracle's own functions call), runs the independent pins -- every
+test of ``test_oracle_pins.py`` and the closed-form test of
+``test_oracle_golden.py`` -- and requires at least one of them to fail.  The
+stored-trajectory regression is left out: the oracle wrote it itself.
+"""
+import contextlib
+import inspect
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle.dfmnmf_oracle as OM
+from tests import test_oracle_golden as golden
+from tests import test_oracle_pins as pins
+
+ORIG = {name: getattr(OM, name) for name in (
+    "weighted_covariances", "model_variance", "ip_update_row", "projected_power", "_mu_statistics",
+    "update_W", "update_g", "neg_loglik", "wiener_filter")}
+
+
+def _ip_row(Qk, Vk, mu, eps=OM.EPS, rtol=OM.SINGULAR_RTOL, *, normalise=True, conj_row=True, order="QV"):
+    """Eqs. (14)-(15) for row mu, with switches that plant the slips below."""
+    F, mk, _ = Qk.shape
+    Vmu = Vk[:, mu]
+    A = np.matmul(Qk, Vmu) if order == "QV" else np.matmul(Vmu, Qk)
+    e = np.zeros((F, mk), dtype=np.complex128)
+    e[:, mu] = 1.0
+    q, _ = OM.solve_or_pinv(A, e, rtol)
+    if normalise:
+        s = np.real(np.einsum("fa,fab,fb->f", np.conj(q), Vmu, q))
+        q = q / np.sqrt(np.maximum(s, eps))[:, None]
+    Qn = Qk.copy()
+    Qn[:, mu, :] = np.conj(q) if conj_row else q
+    return Qn
+
+
+def _mu_statistics_power1(W, H, g, P, eps):
+    lam = OM.source_psd(W, H)
+    y = OM.model_variance(lam, g, eps)
+    A = np.einsum("fnm,ftm->nft", g, P / y)  # slip: yhat^-1 where Eqs. (8)-(9) have yhat^-2
+    D = np.einsum("fnm,ftm->nft", g, 1.0 / y)
+    return A, D
+
+
+def _neg_loglik_flipped(x, mics, st, eps=OM.EPS):
+    T = x.shape[1]
+    P = OM.projected_power(x, st.Q, mics)
+    y = OM.model_variance(OM.source_psd(st.W, st.H), st.g, eps)
+    data = float(np.sum(P / y + np.log(y)))
+    logdet = float(sum(np.sum(OM.log_abs_det_sq(Qk)) for Qk in st.Q))
+    return data + T * logdet  # slip: the sign of the log-determinant term
+
+
+def _wiener_without_inverse(x, mics, st, eps=OM.EPS):
+    x = np.asarray(x, dtype=np.complex128)
+    F, T, M = x.shape
+    lam = OM.source_psd(st.W, st.H)
+    y = OM.model_variance(lam, st.g, eps)
+    off = OM.mic_offsets(mics)
+    N = st.W.shape[0]
+    out = np.empty((N, F, T, M), dtype=np.complex128)
+    for k, mk in enumerate(mics):
+        sl = slice(off[k], off[k] + mk)
+        Qk = st.Q[k]
+        yk = np.einsum("fuv,ftv->ftu", Qk, x[:, :, sl])
+        for n in range(N):
+            gain = lam[n][:, :, None] * st.g[:, n, None, sl] / y[:, :, sl]
+            out[n][:, :, sl] = np.einsum("fuv,ftv->ftu", Qk, gain * yk)  # slip: Q where Q^-1 belongs
+    return out
+
+
+MUTATIONS = {
+    "covariance without the 1/T of Eq. (13)":
+        ("weighted_covariances", lambda x, y, mics: [V * x.shape[1] for V in ORIG["weighted_covariances"](x, y, mics)]),
+    "covariance with the conjugate on the other factor":
+        ("weighted_covariances", lambda x, y, mics: [np.conj(V) for V in ORIG["weighted_covariances"](x, y, mics)]),
+    "model variance with the microphones of g reversed":
+        ("model_variance", lambda lam, g, eps=OM.EPS: ORIG["model_variance"](lam, g[:, :, ::-1], eps)),
+    "IP row without the normalisation of Eq. (15)":
+        ("ip_update_row", lambda Qk, Vk, mu, eps=OM.EPS, rtol=OM.SINGULAR_RTOL:
+            _ip_row(Qk, Vk, mu, eps, rtol, normalise=False)),
+    "IP row stored without the conjugate":
+        ("ip_update_row", lambda Qk, Vk, mu, eps=OM.EPS, rtol=OM.SINGULAR_RTOL:
+            _ip_row(Qk, Vk, mu, eps, rtol, conj_row=False)),
+    "IP system V Q instead of Q V":
+        ("ip_update_row", lambda Qk, Vk, mu, eps=OM.EPS, rtol=OM.SINGULAR_RTOL:
+            _ip_row(Qk, Vk, mu, eps, rtol, order="VQ")),
+    "projected power with Q^H instead of Q":
+        ("projected_power", lambda x, Q, mics: ORIG["projected_power"](
+            x, [np.conj(np.swapaxes(q, 1, 2)) for q in Q], mics)),
+    "MU statistic with yhat^-1 instead of yhat^-2":
+        ("_mu_statistics", _mu_statistics_power1),
+    "W update with numerator and denominator exchanged":
+        ("update_W", lambda W, H, g, P, eps=OM.EPS: W ** 2 / ORIG["update_W"](W, H, g, P, eps)),
+    "g update without the square root":
+        ("update_g", lambda W, H, g, P, eps=OM.EPS: ORIG["update_g"](W, H, g, P, eps) ** 2 / g),
+    "cost with the sign of the log-determinant flipped":
+        ("neg_loglik", _neg_loglik_flipped),
+    "Wiener filter without Q^-1":
+        ("wiener_filter", _wiener_without_inverse),
+}
+
+
+def _pins():
+    fs = [f for name, f in inspect.getmembers(pins, inspect.isfunction) if name.startswith("test_")]
+    fs.append(golden.test_cost_closed_form_identity_and_constant_model)
+    return fs
+
+
+@contextlib.contextmanager
+def _planted(name, fn):
+    had_pkg = hasattr(oracle, name)
+    try:
+        setattr(OM, name, fn)
+        if had_pkg:
+            setattr(oracle, name, fn)
+        yield
+    finally:
+        setattr(OM, name, ORIG[name])
+        if had_pkg:
+            setattr(oracle, name, ORIG[name])
+
+
+def test_unmutated_oracle_passes_every_pin():
+    for f in _pins():
+        with np.errstate(all="ignore"):
+            f()
+
+
+@pytest.mark.parametrize("slip", list(MUTATIONS))
+def test_planted_mistake_is_caught(slip):
+    name, fn = MUTATIONS[slip]
+    caught = []
+    with _planted(name, fn), np.errstate(all="ignore"):
+        for f in _pins():
+            try:
+                f()
+            except Exception:  # an assertion, or a numerical error the slip provokes
+                caught.append(f.__name__)
+    assert caught, f"no pin fails with the planted mistake: {slip}"
