@@ -82,3 +82,39 @@ def test_null_arguments_rejected(lib):
     lib.dfmnmf_batch_destroy(None)  # no-op
     lib.dfmnmf_destroy(None)
     assert lib.dfmnmf_launches_per_iteration(None) == -1
+
+
+def test_tensor_core_form_rejects_unbuilt_layouts_and_tf32(lib):
+    """The tensor-core covariances are built for M_k = 4 with K in {1, 2, 4, 8};
+    DFMNMF_TF32_TC is reserved.  Both are rejected before any device work."""
+    for mics, prec in (((2, 2), D.DFMNMF_BF16_TC), ((4, 4, 4), D.DFMNMF_BF16_TC), ((3, 3), D.DFMNMF_BF16_TC),
+                       ((4, 4), D.DFMNMF_TF32_TC)):
+        a = _args(mics=mics)
+        with pytest.raises(D.DfmnmfError) as ei:
+            D.dfmnmf_init(a["F"], a["T"], a["mics"], a["N"], a["B"], a["x"], a["W0"], a["H0"], a["g0"],
+                          precision=prec)
+        assert ei.value.code == D.DFMNMF_EINVAL, (mics, prec)
+
+
+def test_noalloc_rejects_sizes_beyond_its_static_scratch(lib):
+    """The allocation-free cost keeps F*ceil(T/128) + F*K + 1 partial sums in a
+    static array of DFMNMF_NOALLOC_SCRATCH_DOUBLES; larger problems, bad layouts
+    and null pointers are refused on the host, before any device call."""
+    import ctypes
+    dummy = ctypes.c_void_p(1)  # never dereferenced: every case below fails validation first
+    out = ctypes.c_double()
+
+    def call(F, T, mics, N=2, B_=3, ptr=dummy):
+        m = (ctypes.c_int * len(mics))(*mics)
+        d = D.dfmnmf_desc(F, T, len(mics), m, N, B_, 0, 0, 0.0)
+        return lib.dfmnmf_loglik_noalloc(ctypes.byref(d), ptr, ptr, ptr, ptr, ptr, ctypes.byref(out), None)
+
+    scratch = 65536
+    F = 4000  # 4000 * ceil(2000 / 128) + 4000 * 2 + 1 = 72001 > scratch
+    assert F * ((2000 + 127) // 128) + F * 2 + 1 > scratch
+    assert call(F, 2000, (4, 4)) == D.DFMNMF_EINVAL
+    assert b"exceeds the maximum" in lib.dfmnmf_last_error()
+    assert call(3, 20, (4, 3)) == D.DFMNMF_EINVAL      # unequal subarrays
+    assert call(3, 20, (4, 4), N=17) == D.DFMNMF_EINVAL
+    assert call(0, 20, (4, 4)) == D.DFMNMF_EINVAL
+    assert call(3, 20, (4, 4), ptr=None) == D.DFMNMF_EINVAL
