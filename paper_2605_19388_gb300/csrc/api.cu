@@ -59,7 +59,7 @@ void free_ctx(dfmnmf_ctx* c) {
   if (c->fork_ev) cudaEventDestroy(c->fork_ev);
   if (c->join_ev) cudaEventDestroy(c->join_ev);
   void* ptrs[] = {c->x, c->Q64, c->Q32, c->Qinv32, c->V, c->Vdd, c->W, c->H, c->g, c->lam,
-                  c->P, c->A, c->D, c->red, c->nll_dev, c->flags, c->nmf_part, c->nmf_ticket, c->Rhi, c->Rlo, c->wy_hi, c->wy_lo, c->gQ, c->gW, c->gH, c->gg};
+                  c->P, c->A, c->D, c->red, c->nll_dev, c->flags, c->nmf_part, c->nmf_ticket, c->tc_part, c->tc_ticket, c->gQ, c->gW, c->gH, c->gg};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -113,10 +113,8 @@ struct Launch {
 
 int iteration_launches(const dfmnmf_ctx* c, Launch* out) {
   int n = 0;
-  if (c->precision == DFMNMF_BF16_TC) {
-    out[n++] = {DFMNMF_STAGE_COV, "k_wprep", dfm::launch_wprep, true};
-    out[n++] = {DFMNMF_STAGE_COV, "k_vtc", dfm::launch_vtc, true};
-  } else out[n++] = {DFMNMF_STAGE_COV, "k_cov", dfm::launch_cov, true};
+  if (c->precision == DFMNMF_BF16_TC) out[n++] = {DFMNMF_STAGE_COV, "k_vtc", dfm::launch_vtc, true};
+  else out[n++] = {DFMNMF_STAGE_COV, "k_cov", dfm::launch_cov, true};
   out[n++] = {DFMNMF_STAGE_IP, "k_ip", dfm::launch_ip, true};
   out[n++] = {DFMNMF_STAGE_W, "k_pstats", dfm::launch_power_stats, true};
   out[n++] = {DFMNMF_STAGE_W, "k_wupd", [](const dfmnmf_ctx* c, cudaStream_t s, int, int) { return dfm::launch_wupd(c, s); }, false};
@@ -141,9 +139,11 @@ int enqueue_stage(dfmnmf_ctx* c, int stage, cudaStream_t s) {
   return DFMNMF_OK;
 }
 
-// Split point of the band: a multiple of 8 frequencies (whole tensor-core tiles).
+// Split point of the band: a multiple of 8 frequencies.  The tensor-core
+// form is not split: its covariance kernel is persistent over the whole band
+// and its partial-sum slots serve one launch at a time.
 int band_split(const dfmnmf_ctx* c) {
-  if (c->cfg_branches == 1) return 0;
+  if (c->cfg_branches == 1 || c->precision == DFMNMF_BF16_TC) return 0;
   const int h = ((c->F / 2) + 7) & ~7;
   return (h > 0 && h < c->F) ? h : 0;
 }
@@ -257,6 +257,9 @@ int dfmnmf_init(dfmnmf_ctx** out, const dfmnmf_desc* d, const void* x, const flo
     return fail(DFMNMF_ECUDA, "no CUDA device");
   }
   if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) c->num_sms = 152;
+  if (cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device) != cudaSuccess)
+    c->smem_optin = 232448;
+  c->cfg_vx_groups = 2;
   c->cfg_branches = 2;
   c->cfg_nmf_ctas = 4;
   int r = 0;
@@ -276,28 +279,15 @@ int dfmnmf_init(dfmnmf_ctx** out, const dfmnmf_desc* d, const void* x, const flo
     return r;
   }
   if (c->precision == DFMNMF_BF16_TC) {
-    size_t nr = 0, nw = 0;
-    dfm::tc_operand_elems(c, &nr, &nw);
-    unsigned short *rh = nullptr, *rl = nullptr, *wh = nullptr, *wl = nullptr;
-    r = dalloc(&rh, nr, "R hi");
-    if (!r) r = dalloc(&rl, nr, "R lo");
-    if (!r) r = dalloc(&wh, nw, "w hi");
-    if (!r) r = dalloc(&wl, nw, "w lo");
-    c->Rhi = rh;
-    c->Rlo = rl;
-    c->wy_hi = wh;
-    c->wy_lo = wl;
-    // the padding rows of a partial last tile are never written: zero them once
-    if (!r && (cudaMemset(rh, 0, nr * 2) != cudaSuccess || cudaMemset(rl, 0, nr * 2) != cudaSuccess ||
-               cudaMemset(wh, 0, nw * 2) != cudaSuccess || cudaMemset(wl, 0, nw * 2) != cudaSuccess))
-      r = fail(DFMNMF_ECUDA, "clearing the tensor-core operands failed");
-    if (r) {
+    if ((r = dalloc(&c->tc_part, dfm::tc_part_float4s(c), "tensor-core partial sums")) ||
+        (r = dalloc(&c->tc_ticket, dfm::tc_ticket_count(c), "tensor-core tickets"))) {
       free_ctx(c);
       return r;
     }
-    if (dfm::tc_make_maps(c) != cudaSuccess) {
+    if (dfm::tc_raw_stages(c) == 0) {
       free_ctx(c);
-      return fail(DFMNMF_ECUDA, "tensor map creation failed (cuTensorMapEncodeTiled unavailable or rejected)");
+      return fail(DFMNMF_EINVAL, "the tensor-core form needs more shared memory than the device offers (N=%d K=%d)",
+                  c->N, c->K);
     }
   }
   cudaStream_t s = as_stream(stream);
@@ -329,8 +319,8 @@ int dfmnmf_init(dfmnmf_ctx** out, const dfmnmf_desc* d, const void* x, const flo
   CKI(cudaMemsetAsync(c->lam, 0, (size_t)c->N * c->F * c->Tp * sizeof(float), s));
   CKI(cudaMemsetAsync(c->A, 0, (size_t)c->N * c->F * c->Tp * sizeof(float), s));
   CKI(cudaMemsetAsync(c->D, 0, (size_t)c->N * c->F * c->Tp * sizeof(float), s));
+  if (c->tc_ticket) CKI(cudaMemsetAsync(c->tc_ticket, 0, dfm::tc_ticket_count(c) * sizeof(unsigned), s));
   if ((r = refresh_derived(c, s))) return bail(r);
-  if (c->precision == DFMNMF_BF16_TC) CKI(dfm::launch_rprep(c, s));
 #undef CKI
   *out = c;
   return DFMNMF_OK;
@@ -340,7 +330,6 @@ int dfmnmf_set_observation(dfmnmf_ctx* c, const void* x, void* stream) {
   if (!c || !x) return fail(DFMNMF_EINVAL, "null argument");
   CK(cudaSetDevice(c->device));
   CK(cudaMemcpyAsync(c->x, x, nx(c) * sizeof(float2), cudaMemcpyDefault, as_stream(stream)));
-  if (c->precision == DFMNMF_BF16_TC) CK(dfm::launch_rprep(c, as_stream(stream)));
   return DFMNMF_OK;
 }
 
@@ -488,8 +477,11 @@ int dfmnmf_autotune(dfmnmf_ctx* c, int iters_per_trial, int* branches, int* nmf_
     return e;
   };
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  const int old_br = c->cfg_branches, old_ct = c->cfg_nmf_ctas;
-  int best_br = old_br, best_ct = old_ct;
+  // first option: graph branches of the per-frequency kernels (FP32 form) or converter warp groups of the
+  // persistent covariance kernel (tensor-core form, one branch); second: CTAs per SM of the NMF products
+  const bool tc = c->precision == DFMNMF_BF16_TC;
+  const int old_br = c->cfg_branches, old_ct = c->cfg_nmf_ctas, old_vx = c->cfg_vx_groups;
+  int best_br = old_br, best_ct = old_ct, best_vx = old_vx;
   float best = INFINITY;
   cudaError_t e = copy_state(true);
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
@@ -497,9 +489,10 @@ int dfmnmf_autotune(dfmnmf_ctx* c, int iters_per_trial, int* branches, int* nmf_
   const int br_opts[2] = {1, 2}, ct_opts[3] = {2, 4, 8};
   for (int ib = 0; ib < 2 && e == cudaSuccess && !r; ++ib)
     for (int ic = 0; ic < 3 && e == cudaSuccess && !r; ++ic) {
-      c->cfg_branches = br_opts[ib];
+      c->cfg_branches = tc ? 1 : br_opts[ib];
+      c->cfg_vx_groups = tc ? br_opts[ib] : old_vx;
       c->cfg_nmf_ctas = ct_opts[ic];
-      if (c->cfg_branches == 2 && band_split(c) == 0) continue;  // band too small to split
+      if (!tc && c->cfg_branches == 2 && band_split(c) == 0) continue;  // band too small to split
       drop_graph(c);
       if ((r = ensure_graph(c))) break;
       e = cudaGraphLaunch(c->gexec, s);  // warm-up
@@ -513,11 +506,13 @@ int dfmnmf_autotune(dfmnmf_ctx* c, int iters_per_trial, int* branches, int* nmf_
         best = ms;
         best_br = c->cfg_branches;
         best_ct = c->cfg_nmf_ctas;
+        best_vx = c->cfg_vx_groups;
       }
       if (e == cudaSuccess) e = copy_state(false);
     }
   c->cfg_branches = (e == cudaSuccess && !r) ? best_br : old_br;
   c->cfg_nmf_ctas = (e == cudaSuccess && !r) ? best_ct : old_ct;
+  c->cfg_vx_groups = (e == cudaSuccess && !r) ? best_vx : old_vx;
   drop_graph(c);
   if (e == cudaSuccess) e = copy_state(false);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -40,16 +40,11 @@ struct dfmnmf_ctx {
   double2* gQ;
   float *gW, *gH, *gg;
   unsigned* flags; // dfm::FLAG_COUNT words
-  // tensor-core form: x x^H split in two bfloat16 parts and their TMA descriptors; R and w are stored
-  // as contiguous (tile of 8 / K frequencies, 64-frame chunk) blocks, [tiles][Tr / 64][rows][64]
-  void* Rhi;
-  void* Rlo;
-  void* wy_hi;  // 1/yhat split in two bfloat16 parts, 32 rows (f, m) per tile (k_wprep)
-  void* wy_lo;
-  alignas(64) unsigned char tmap_hi[128];
-  alignas(64) unsigned char tmap_lo[128];
-  alignas(64) unsigned char tmap_whi[128];
-  alignas(64) unsigned char tmap_wlo[128];
+  // tensor-core form (k_vtc): FP32 partial sums of tiles shared by two CTAs and one ticket per tile
+  float4* tc_part;
+  unsigned* tc_ticket;
+  int smem_optin;      // opt-in shared memory per block of the device
+  int cfg_vx_groups;   // converter warp groups of k_vtc (1 or 2)
   size_t red_len;
   // CUDA graph of one iteration, captured on first use
   cudaStream_t cap_stream;
@@ -67,11 +62,10 @@ cudaError_t launch_lambda(const dfmnmf_ctx* c, cudaStream_t s);
 // Launchers of the per-frequency kernels take a frequency range [fb, fb + fc).
 cudaError_t launch_cov(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc);
 cudaError_t launch_vtc(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc);  // tensor-core covariances (BF16_TC form)
-cudaError_t launch_rprep(const dfmnmf_ctx* c, cudaStream_t s);   // split-bfloat16 x x^H for the TC form
-cudaError_t launch_wprep(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc);  // split-bfloat16 1/yhat for the TC form
-cudaError_t tc_make_maps(dfmnmf_ctx* c);
-void tc_operand_elems(const dfmnmf_ctx* c, size_t* nr, size_t* nw);  // elements of R (each part) and of w (each part)
 bool tc_supported(int MK, int K);
+size_t tc_part_float4s(const dfmnmf_ctx* c);   // partial-sum slots of launch_vtc (float4 each)
+size_t tc_ticket_count(const dfmnmf_ctx* c);   // tickets of launch_vtc
+int tc_raw_stages(const dfmnmf_ctx* c);        // raw stages of k_vtc that fit in shared memory (0: none)
 cudaError_t launch_ip(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc);
 cudaError_t launch_power_stats(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc);  // P + A/D (current lambda)
 // The NMF updates take `grad`: NULL updates the factor (Eq. 8, 9 or 10);

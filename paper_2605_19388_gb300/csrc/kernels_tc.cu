@@ -1,38 +1,41 @@
 // kernels_tc.cu -- tensor-core form of the weighted covariances (Eq. 13).
 //
 //   V[f][k][mu][a][b] = (1/T) sum_t R[f][k][a,b](t) * w[f][t][k,mu],
-//   R = x_ftk x_ftk^H packed as M_k^2 = 16 reals, w = 1/yhat.
+//   R = x_ftk x_ftk^H packed as M_k^2 = 16 reals, w = 1/yhat (Eq. 2, floored).
 //
-// For every frequency this is an (16 K x T) by (T x 4 K) product.  The
+// For every frequency this is an (16 K x T) by (T x 4 K) product.  Its
 // operands are split into two bfloat16 parts, R = R_hi + R_lo and
-// w = w_hi + w_lo, and three products R_hi w_hi + R_hi w_lo + R_lo w_hi are
-// accumulated in FP32 (the dropped R_lo w_lo term is below 2^-16 relative).
-// A plain bfloat16 contraction loses too much: on the paper-sized workload
-// it moves the IP update by 6e-2 relative, the split form by 1.5e-4.
+// w = w_hi + w_lo, and R_hi w_hi + R_hi w_lo + R_lo w_hi (+ R_lo w_lo) are
+// accumulated in FP32 (the R_lo w_lo term is below 2^-16 relative; a plain
+// bfloat16 contraction moves the IP update by 6e-2 relative on the
+// paper-sized workload, the split form by 1.5e-4).
 //
-// R depends only on the observation, so it is formed once (k_rprep) into
-// two bfloat16 arrays; the weights change every iteration: k_wprep forms
-// w_hi / w_lo from lambda and g in one streaming pass.  Both are stored in
-// the order k_vtc reads them: a tile of FPC = 8 / K frequencies (128 rows of
-// R, 32 rows of w) is cut into chunks of 64 frames, and each (tile, chunk)
-// block of 128 x 64 (R) or 32 x 64 (w) values is contiguous in memory
-// ([tiles][Tr / 64][rows][64], Tr = T rounded up to 64, zero tail), so every
-// tensor copy reads one contiguous 16 KB or 4 KB block instead of 128-byte
-// pieces of rows 2 Tr bytes apart.  k_vtc then only moves and multiplies:
-// one thread streams the four operand tiles of each 64-frame chunk with TMA
-// (128-byte swizzled, with an evict-first L2 policy: R and w are read once
-// per iteration, and R, 84 MB on the paper-sized workload, would otherwise
-// push the streaming kernels' operands out of L2) into a
-// 2-stage shared-memory ring (two CTAs per SM), one thread issues
-// tcgen05.mma (M = 128 rows = 128 / (16 K) frequencies, N = 32 weights,
-// K = 16 frames per instruction, FP32 accumulators in tensor memory) and the
-// four warps read the accumulators back with tcgen05.ld.  (Forming w inside
-// k_vtc, by warps beside the TMA and MMA threads, left the tensor pipe
-// waiting on them for most of every chunk.)
+// k_vtc reads the observation x and lambda, g -- the method's own operands,
+// each once -- and forms the split R and w on chip:
+//   * one persistent CTA per SM walks a contiguous range of the flattened
+//     (tile, 64-frame chunk) work list, so every SM gets the same number of
+//     chunks; a tile is 8 / K frequencies (128 rows (f, k, entry) of R, 32
+//     rows (f, m) of w);
+//   * warp 0 streams each chunk's x tile (16 KB, swizzled), lambda rows and
+//     g rows by TMA into a ring of raw stages;
+//   * converter warps (one (frequency, subarray) pair per warp, lanes over
+//     frame pairs) form R = x x^H and w = 1/max(sum_n lambda g, eps) in
+//     registers, split them into bfloat16 pairs and write the K-major,
+//     128-byte-swizzled operand tiles of the MMA (frames are laid out along
+//     the contraction axis in the order (lane, j) -> 2 lane + j for frame
+//     lane + 32 j; the contraction does not depend on the order, A and B use
+//     the same one);
+//   * one thread issues tcgen05.mma (M = 128, N = 64: w_hi and w_lo side by
+//     side, K = 16 frames per instruction, FP32 accumulators in tensor memory,
+//     two accumulator buffers so the epilogue of one tile overlaps the next);
+//   * four epilogue warps read the accumulators with tcgen05.ld and write V.
+//     A tile whose chunks are split between two CTAs is finished by the CTA
+//     that arrives last: each part is stored in FP32, and the last one adds
+//     the parts in CTA order (deterministic), in FP64.
 //
-// Supported layouts: M_k = 4 and K in {1, 2, 4, 8} (M = 128 / (16 K) * 16 K
-// rows per tile, N = 32 columns).  Every mbarrier wait is bounded; a wait
-// that gives up sets FLAG_TIMEOUT and the CTA skips the rest of its work.
+// Supported layouts: M_k = 4 and K in {1, 2, 4, 8}.  Every mbarrier wait is
+// bounded; a wait that gives up sets FLAG_TIMEOUT, the CTA drains its copies
+// in flight and its tensor-core work, frees its tensor memory and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -42,14 +45,7 @@
 
 namespace dfm {
 
-constexpr int TC_KC = 64;       // frames per chunk (128 bytes of bfloat16 per row)
-constexpr int TC_ROWS = 128;    // MMA M
-constexpr int TC_COLS = 32;     // MMA N
-constexpr int TC_STAGES = 2;
-constexpr int TC_A_BYTES = TC_ROWS * TC_KC * 2;   // 16 KB per operand part
-constexpr int TC_B_BYTES = TC_COLS * TC_KC * 2;   // 4 KB per operand part
-constexpr int TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_B_BYTES;
-constexpr unsigned long long TC_WAIT_CYCLES = 2000000000ull;  // ~1 s at 2 GHz
+constexpr unsigned TC_WAIT_CYCLES = 2000000000u;  // ~1 s at 2 GHz
 
 // ------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -66,9 +62,12 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, u
                : "memory");
 }
 // Wait for the phase with the given parity to complete; false on timeout.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+// Between polls the warp sleeps for about `sleep_ns` (0: poll again at once),
+// so that warps which wait most of the time (the epilogue, the single-thread
+// producer and MMA issuer) leave the issue slots to the converter warps.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, unsigned sleep_ns = 0) {
   const unsigned addr = smem_u32(bar);
-  const unsigned long long start = clock64();
+  const unsigned start = (unsigned)clock();
   while (true) {
     unsigned ok;
     asm volatile(
@@ -77,37 +76,36 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
         : "r"(addr), "r"(parity)
         : "memory");
     if (ok) return true;
-    if (clock64() - start > TC_WAIT_CYCLES) return false;
+    if ((unsigned)clock() - start > TC_WAIT_CYCLES) return false;  // wrap-safe: the budget is below 2^32
+    if (sleep_ns) __nanosleep(sleep_ns);
   }
 }
+// The same wait by every lane of a warp, with one warp-uniform result.
+__device__ __forceinline__ bool mbar_wait_warp(unsigned long long* bar, unsigned parity, unsigned sleep_ns = 0) {
+  return __all_sync(DFM_FULL_MASK, mbar_wait(bar, parity, sleep_ns)) != 0;
+}
 
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1,
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
                                             unsigned long long* bar) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          smem_u32(dst)),
-      "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
       : "memory");
 }
-// The same copy with an L2 cache policy (createpolicy).
-__device__ __forceinline__ void tma_load_2d_hint(void* dst, const CUtensorMap* map, int c0, int c1,
-                                                 unsigned long long* bar, unsigned long long policy) {
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            unsigned long long* bar) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%2, "
-      "%3}], [%4], %5;" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar)), "l"(policy)
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
       : "memory");
 }
-__device__ __forceinline__ unsigned long long l2_evict_first_policy() {
-  unsigned long long p;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-
-// Position of element (row, t) of a tensor-core operand in the tiled layout:
-// rows of tile `tile` (rows_per_tile of them), chunk t / 64 of nch, frame t % 64.
-__host__ __device__ __forceinline__ size_t tc_index(int tile, int row, int t, int nch, int rows_per_tile) {
-  return (((size_t)tile * nch + (t >> 6)) * rows_per_tile + row) * TC_KC + (t & (TC_KC - 1));
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, int c0, int c1, int c2, const void* src) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                   reinterpret_cast<unsigned long long>(map)),
+               "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(src))
+               : "memory");
 }
 
 // Shared-memory matrix descriptor: K-major operand tile with 128-byte
@@ -123,15 +121,30 @@ __device__ __forceinline__ unsigned long long smem_desc_sw128(unsigned addr) {
   return d;
 }
 
-// Instruction descriptor, kind::f16: D FP32, A and B bfloat16, both K-major,
-// N = 32, M = 128.
-constexpr unsigned TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((TC_COLS >> 3) << 17) | ((TC_ROWS >> 4) << 24);
+// ------------------------------------------------------ fused contraction
+constexpr int VX_KC = 64;                         // frames per chunk (one 128-byte bfloat16 row)
+constexpr int VX_ROWS = 128;                      // MMA M: rows (frequency, subarray, packed entry)
+constexpr int VX_WROWS = 32;                      // rows (frequency, microphone) of one weight part
+constexpr int VX_N = 2 * VX_WROWS;                // MMA N: w_hi rows, then w_lo rows
+constexpr int VX_X_BYTES = 16384;                 // raw x tile: 8/K frequencies x 64 frames x 4K complex64
+constexpr int VX_A_BYTES = VX_ROWS * VX_KC * 2;   // 16 KB per R part
+constexpr int VX_B_BYTES = VX_N * VX_KC * 2;      // 8 KB (both w parts)
+constexpr int VX_OP_BYTES = 2 * VX_A_BYTES + VX_B_BYTES;
+constexpr int VX_OS = 3;                          // operand stages (unit i uses i % 3)
+constexpr int VX_MAX_RS = 6;                      // raw stages at most
+constexpr int VX_CW = 8;                          // converter warps per group: the 8 (frequency, subarray) pairs
+constexpr int VX_EPI_WARP = 2;                    // warps 2..5: epilogue
+constexpr int VX_CONV_WARP = 6;                   // warps 6..: converters
+constexpr int VX_ACC_COLS = 64;                   // tensor-memory columns per accumulator buffer
+
+// Instruction descriptor, kind::f16: D FP32, A and B bfloat16, both K-major, N = 64, M = 128.
+constexpr unsigned VX_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((VX_N >> 3) << 17) | ((VX_ROWS >> 4) << 24);
 
 __device__ __forceinline__ void umma_bf16(unsigned tmem_d, unsigned long long a, unsigned long long b, unsigned acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
           tmem_d),
-      "l"(a), "l"(b), "r"(TC_IDESC), "r"(acc)
+      "l"(a), "l"(b), "r"(VX_IDESC), "r"(acc)
       : "memory");
 }
 __device__ __forceinline__ void umma_commit(unsigned long long* bar) {
@@ -139,149 +152,125 @@ __device__ __forceinline__ void umma_commit(unsigned long long* bar) {
                : "memory");
 }
 
-// ------------------------------------------------------------- R prepare
-// Packed entry r of block k of frequency f at frame t, for t < Tr (zero beyond
-// T), in the tiled layout: row (f % FPC) * 16K + 16 k + r of tile f / FPC.
-__global__ void __launch_bounds__(128) k_rprep(const float2* __restrict__ x, __nv_bfloat16* __restrict__ Rhi,
-                                               __nv_bfloat16* __restrict__ Rlo, int F, int T, int Tr, int K) {
-  const int f = blockIdx.y;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= Tr) return;
-  const int M = K * 4;
-  const int FPC = TC_ROWS / (16 * K), nch = Tr / TC_KC;
-  const int tile = f / FPC, frow = (f % FPC) * 16 * K;
-  for (int k = 0; k < K; ++k) {
-    float R[16];
-    if (t < T) {
-      float2 xv[4];
-      load_block<4>(x + ((size_t)f * T + t) * M + k * 4, xv);
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        R[a * 4 + a] = fmaf(xv[a].x, xv[a].x, xv[a].y * xv[a].y);
-#pragma unroll
-        for (int b = a + 1; b < 4; ++b) {
-          R[a * 4 + b] = fmaf(xv[a].x, xv[b].x, xv[a].y * xv[b].y);
-          R[b * 4 + a] = fmaf(xv[a].y, xv[b].x, -xv[a].x * xv[b].y);
-        }
-      }
-    } else {
-#pragma unroll
-      for (int r = 0; r < 16; ++r) R[r] = 0.f;
-    }
-#pragma unroll
-    for (int r = 0; r < 16; ++r) {
-      const __nv_bfloat16 h = __float2bfloat16_rn(R[r]);
-      const __nv_bfloat16 l = __float2bfloat16_rn(R[r] - __bfloat162float(h));
-      const size_t o = tc_index(tile, frow + k * 16 + r, t, nch, TC_ROWS);
-      Rhi[o] = h;
-      Rlo[o] = l;
-    }
-  }
-}
-
-// ------------------------------------------------------------- weights
-// w = 1 / max(yhat, eps), yhat[f][t][m] = sum_n lambda[n][f][t] g[f][n][m]
-// (Eq. 2 with the floor of Sec. IV-A), split into two bfloat16 parts and
-// stored as rows (f % FPC) * M + m of tile f / FPC, Tr frames, zero beyond T:
-// the B operand of the contraction, read by TMA in the same 128-byte swizzled
-// tiles as R.  Each thread forms two adjacent frames of one frequency for
-// every microphone (float2 lambda loads, g[f] from shared memory four
-// microphones per load, 4-byte stores coalesced along t; row m + 1 of a tile
-// block sits 64 frames after row m).  NM is N itself for N <= 8 and 16
-// (guarded) above; MV is M (4, 8, 16 or 32).
-template <int NM, int MV>
-__global__ void __launch_bounds__(128) k_wprep(const float* __restrict__ lam, const float* __restrict__ g,
-                                               __nv_bfloat16* __restrict__ whi, __nv_bfloat16* __restrict__ wlo,
-                                               int F, int T, int Tp, int Tr, int N, float eps, int fb) {
-  extern __shared__ __align__(16) float gw[];  // [N][MV]
-  const int f = fb + blockIdx.y;
-  for (int i = threadIdx.x; i < N * MV; i += blockDim.x) gw[i] = g[(size_t)f * N * MV + i];
-  __syncthreads();
-  const int t = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-  if (t >= Tr) return;
-  constexpr int FPC = TC_COLS / MV;
-  const int nch = Tr / TC_KC;
-  const int tile = f / FPC, frow = (f % FPC) * MV;
-  float2 lv[NM];
-#pragma unroll
-  for (int n = 0; n < NM; ++n) {
-    lv[n] = make_float2(0.f, 0.f);
-    if ((NM <= 8 || n < N) && t < Tp) lv[n] = *reinterpret_cast<const float2*>(lam + ((size_t)n * F + f) * Tp + t);
-  }
-  const bool v0 = t < T, v1 = t + 1 < T;
-  const size_t o0 = tc_index(tile, frow, t, nch, TC_COLS);
-  __nv_bfloat162* ph = reinterpret_cast<__nv_bfloat162*>(whi + o0);
-  __nv_bfloat162* pl = reinterpret_cast<__nv_bfloat162*>(wlo + o0);
-#pragma unroll
-  for (int m4 = 0; m4 < MV; m4 += 4) {
-    float2 y[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) y[j] = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int n = 0; n < NM; ++n)
-      if (NM <= 8 || n < N) {
-        const float4 gv4 = *reinterpret_cast<const float4*>(gw + n * MV + m4);
-        const float gv[4] = {gv4.x, gv4.y, gv4.z, gv4.w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          y[j].x = fmaf(lv[n].x, gv[j], y[j].x);
-          y[j].y = fmaf(lv[n].y, gv[j], y[j].y);
-        }
-      }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const float w0 = v0 ? fast_rcp(fmaxf(y[j].x, eps)) : 0.f;
-      const float w1 = v1 ? fast_rcp(fmaxf(y[j].y, eps)) : 0.f;
-      const __nv_bfloat162 h = __floats2bfloat162_rn(w0, w1);
-      const float2 hf = __bfloat1622float2(h);
-      const __nv_bfloat162 l = __floats2bfloat162_rn(w0 - hf.x, w1 - hf.y);
-      ph[(m4 + j) * (TC_KC / 2)] = h;
-      pl[(m4 + j) * (TC_KC / 2)] = l;
-    }
-  }
-}
-
-// ------------------------------------------------------------ contraction
-struct TcSmem {
-  unsigned long long full[TC_STAGES];
-  unsigned long long empty[TC_STAGES];
+struct VxCtl {
+  unsigned long long raw_full[VX_MAX_RS];
+  unsigned long long raw_empty[VX_MAX_RS];
+  unsigned long long op_full[VX_OS];
+  unsigned long long op_empty[VX_OS];
+  unsigned long long acc_full[2];
+  unsigned long long acc_empty[2];
   unsigned long long done;
   unsigned tmem_base;
   unsigned abort;
+  unsigned last;
 };
 
-__host__ __device__ constexpr size_t tc_ring_bytes() { return (size_t)TC_STAGES * TC_STAGE_BYTES; }
+// CTA b of a G-CTA grid owns units [b U / G, (b + 1) U / G); the CTA owning unit u.
+__host__ __device__ __forceinline__ int vx_cta_of(long long u, int G, long long U) {
+  return (int)(((u + 1) * G - 1) / U);
+}
 
-// One CTA per tile of TC_ROWS / (16 K) frequencies, four warps: lane 0 of
-// warp 0 streams the four operand tiles of every 64-frame chunk (R_hi, R_lo,
-// w_hi, w_lo) into the shared-memory ring, lane 0 of warp 1 issues the three
-// split products per 16 frames, and all four warps read the accumulators back.
-__global__ void __launch_bounds__(128, 2) k_vtc(const __grid_constant__ CUtensorMap map_rhi,
-                                                const __grid_constant__ CUtensorMap map_rlo,
-                                                const __grid_constant__ CUtensorMap map_whi,
-                                                const __grid_constant__ CUtensorMap map_wlo,
-                                                double2* __restrict__ V, float4* __restrict__ Vdd, int T, int Tr,
-                                                int K, unsigned* __restrict__ flags, int fb, int fe) {
-  extern __shared__ __align__(1024) unsigned char tc_raw[];
-  unsigned char* ring = reinterpret_cast<unsigned char*>(((unsigned long long)tc_raw + 1023) & ~1023ull);
-  TcSmem* ctl = reinterpret_cast<TcSmem*>(ring + tc_ring_bytes());
+// Barrier 1 among the 128 epilogue threads, returning the OR of `pred` over them.
+__device__ __forceinline__ bool epi_bar_or(bool pred) {
+  unsigned r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n barrier.red.or.pred q, 1, 128, p;\n selp.u32 %0, 1, 0, q;\n}"
+      : "=r"(r)
+      : "r"((unsigned)pred)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// Entry e = 4a + b of the packed x x^H of block blk (sums over t already
+// scaled by 1/T) into V (FP64) and Vdd (float pairs), all four mu at once:
+// e with a == b is V[a][a]; a < b is Re V[a][b] = Re V[b][a]; a > b is
+// Im(x_b conj x_a) = Im V[b][a] = -Im V[a][b].
+__device__ __forceinline__ void vx_write_v(double2* __restrict__ V, float4* __restrict__ Vdd, size_t blk, int a,
+                                           int b, const double (&dv)[4]) {
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    double2* Vb = V + (blk * 4 + mu) * 16;
+    float4* Vd = Vdd + (blk * 4 + mu) * 16;
+    double* vdbl = reinterpret_cast<double*>(Vb);
+    float* vflt = reinterpret_cast<float*>(Vd);
+    const float fv = (float)dv[mu];
+    if (a == b) {
+      Vb[a * 4 + a] = make_double2(dv[mu], 0.0);
+      Vd[a * 4 + a] = make_float4(fv, 0.f, 0.f, 0.f);
+    } else if (a < b) {
+      vdbl[2 * (a * 4 + b)] = dv[mu];
+      vdbl[2 * (b * 4 + a)] = dv[mu];
+      vflt[4 * (a * 4 + b)] = fv; vflt[4 * (a * 4 + b) + 1] = 0.f;
+      vflt[4 * (b * 4 + a)] = fv; vflt[4 * (b * 4 + a) + 1] = 0.f;
+    } else {
+      vdbl[2 * (b * 4 + a) + 1] = dv[mu];
+      vdbl[2 * (a * 4 + b) + 1] = -dv[mu];
+      vflt[4 * (b * 4 + a) + 2] = fv; vflt[4 * (b * 4 + a) + 3] = 0.f;
+      vflt[4 * (a * 4 + b) + 2] = -fv; vflt[4 * (a * 4 + b) + 3] = 0.f;
+    }
+  }
+}
+
+// r = hi + lo with hi = bfloat16(r) (round to nearest) and lo = bfloat16(r - hi), for two frames at once.
+__device__ __forceinline__ void vx_split_store(unsigned char* hi, unsigned char* lo, float2 r) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(r.x, r.y);
+  const float2 d = __fadd2_rn(r, make_float2(-__low2float(h), -__high2float(h)));
+  *reinterpret_cast<__nv_bfloat162*>(hi) = h;
+  *reinterpret_cast<__nv_bfloat162*>(lo) = __floats2bfloat162_rn(d.x, d.y);
+}
+
+// The fused contraction; see the head of this file.  K subarrays of 4
+// microphones, CG groups of 8 converter warps (each group converts every
+// CG-th chunk of the CTA).  Dynamic shared memory, 1024-byte aligned:
+// VX_OS operand stages (R_hi, R_lo, w_hi | w_lo), RS raw stages of
+// stage_bytes (x tile, lambda [N][8/K][64], g [8/K][N][M]), control block.
+// `part` holds one 128-row block of FP32 partial sums per (tile, CTA) pair
+// that shares a tile (slot tile - tb + CTA), `tickets` one counter per tile,
+// zero between launches (the CTA that completes a tile resets it).
+template <int K, int CG>
+__global__ void __launch_bounds__((VX_CONV_WARP + VX_CW * CG) * 32, 1)
+    k_vtc(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_l,
+          const __grid_constant__ CUtensorMap map_g, double2* __restrict__ V, float4* __restrict__ Vdd,
+          float4* __restrict__ part, unsigned* __restrict__ tickets, int F, int T, int N, float eps, int tb,
+          int ntile, int nch, int RS, int stage_bytes, unsigned* __restrict__ flags) {
+  constexpr int FPC = 8 / K, M = 4 * K;
+  constexpr unsigned SWZ = (K == 1) ? 0x10u : (K == 2) ? 0x30u : 0x70u;  // 32-, 64-, 128-byte swizzle of x
+  extern __shared__ __align__(1024) unsigned char vx_raw[];
+  // 1024-byte alignment by an offset from the shared array (not by integer casts of the pointer), so that
+  // the compiler keeps every derived pointer in the shared window (32-bit shared loads and stores)
+  unsigned char* ops = vx_raw + ((1024u - (smem_u32(vx_raw) & 1023u)) & 1023u);
+  unsigned char* raw = ops + VX_OS * VX_OP_BYTES;
+  VxCtl* ctl = reinterpret_cast<VxCtl*>(raw + (size_t)RS * stage_bytes);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int FPC = TC_ROWS / (16 * K);    // frequencies per CTA
-  const int f0 = fb + blockIdx.x * FPC;  // frequencies f0 .. min(f0 + FPC, fe) - 1 are this CTA's
-  const int M = 4 * K;
-  const int nch = Tr / TC_KC;
+  const long long U = (long long)ntile * nch;  // below 2^31 (checked at launch)
+  const int G = gridDim.x;
+  const int u_begin = (int)((long long)blockIdx.x * U / G);
+  const int nloc = (int)((long long)(blockIdx.x + 1) * U / G) - u_begin;
+  const int c_begin = u_begin % nch;  // chunk of the CTA's first unit
+  const int lbytes = FPC * N * VX_KC * 4;  // lambda rows of one stage
+  volatile unsigned* abort_flag = &ctl->abort;
 
   if (tid == 0) {
-    for (int s = 0; s < TC_STAGES; ++s) {
-      mbar_init(&ctl->full[s], 1);
-      mbar_init(&ctl->empty[s], 1);
+    for (int s = 0; s < RS; ++s) {
+      mbar_init(&ctl->raw_full[s], 1);
+      mbar_init(&ctl->raw_empty[s], VX_CW);
+    }
+    for (int s = 0; s < VX_OS; ++s) {
+      mbar_init(&ctl->op_full[s], VX_CW);
+      mbar_init(&ctl->op_empty[s], 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&ctl->acc_full[s], 1);
+      mbar_init(&ctl->acc_empty[s], 4);
     }
     mbar_init(&ctl->done, 1);
     ctl->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(&ctl->tmem_base))
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ctl->tmem_base)),
+                 "r"(2 * VX_ACC_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -290,105 +279,227 @@ __global__ void __launch_bounds__(128, 2) k_vtc(const __grid_constant__ CUtensor
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const unsigned tmem = ctl->tmem_base;
 
-  if (warp == 0 && lane == 0) {
-    // ---- TMA producer: block (tile, chunk) of R and of w, one contiguous copy each
-    const unsigned long long evict_first = l2_evict_first_policy();
-    const int tile = f0 / FPC;
-    for (int c = 0; c < nch; ++c) {
-      const int s = c % TC_STAGES;
-      if (c >= TC_STAGES && !mbar_wait(&ctl->empty[s], ((c / TC_STAGES) + 1) & 1)) {
-        atomicOr(&ctl->abort, 1u);
-        break;
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- TMA producer
+      const unsigned tx = (unsigned)(VX_X_BYTES + lbytes + FPC * N * M * 4);
+      int issued = 0, tile = tb + u_begin / nch, c = c_begin;
+      for (int i = 0; i < nloc; ++i, c = (c + 1 == nch) ? (++tile, 0) : c + 1) {
+        const int s = i % RS;
+        if (i >= RS && !mbar_wait(&ctl->raw_empty[s], ((i / RS) - 1) & 1, 64)) {
+          atomicOr(&ctl->abort, 1u);
+          break;
+        }
+        if (*abort_flag) break;
+        unsigned char* st = raw + (size_t)s * stage_bytes;
+        mbar_arrive_expect_tx(&ctl->raw_full[s], tx);
+        if (K == 8) tma_load_4d(st, &map_x, 0, 0, c * VX_KC, tile, &ctl->raw_full[s]);
+        else tma_load_3d(st, &map_x, 0, c * VX_KC, tile * FPC, &ctl->raw_full[s]);
+        tma_load_3d(st + VX_X_BYTES, &map_l, c * VX_KC, tile * FPC, 0, &ctl->raw_full[s]);
+        tma_load_3d(st + VX_X_BYTES + lbytes, &map_g, 0, 0, tile * FPC, &ctl->raw_full[s]);
+        issued = i + 1;
       }
-      if (ctl->abort) break;
-      unsigned char* st = ring + s * TC_STAGE_BYTES;
-      mbar_arrive_expect_tx(&ctl->full[s], TC_STAGE_BYTES);
-      const int blk = tile * nch + c;
-      tma_load_2d_hint(st, &map_rhi, 0, blk * TC_ROWS, &ctl->full[s], evict_first);
-      tma_load_2d_hint(st + TC_A_BYTES, &map_rlo, 0, blk * TC_ROWS, &ctl->full[s], evict_first);
-      tma_load_2d_hint(st + 2 * TC_A_BYTES, &map_whi, 0, blk * TC_COLS, &ctl->full[s], evict_first);
-      tma_load_2d_hint(st + 2 * TC_A_BYTES + TC_B_BYTES, &map_wlo, 0, blk * TC_COLS, &ctl->full[s], evict_first);
+      // every copy issued has landed before the CTA moves on (bounded wait)
+      for (int i = issued > RS ? issued - RS : 0; i < issued; ++i)
+        if (!mbar_wait(&ctl->raw_full[i % RS], (i / RS) & 1, 64)) atomicOr(&ctl->abort, 1u);
     }
-  } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer
-    for (int c = 0; c < nch; ++c) {
-      const int s = c % TC_STAGES;
-      if (!mbar_wait(&ctl->full[s], (c / TC_STAGES) & 1)) {
-        atomicOr(&ctl->abort, 1u);
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const unsigned base = smem_u32(ring + s * TC_STAGE_BYTES);
-      const unsigned a_hi = base, a_lo = base + TC_A_BYTES;
-      const unsigned b_hi = base + 2 * TC_A_BYTES, b_lo = b_hi + TC_B_BYTES;
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer: per chunk, R_hi (w_hi | w_lo) then R_lo (w_hi | w_lo), 16 frames per instruction
+      int sg = -1;
+      for (int i = 0, c = c_begin; i < nloc; ++i, c = (c + 1 == nch) ? 0 : c + 1) {
+        const bool first = (i == 0 || c == 0), last = (i == nloc - 1 || c == nch - 1);
+        if (first) {
+          ++sg;
+          if (sg >= 2 && !mbar_wait(&ctl->acc_empty[sg & 1], ((sg >> 1) - 1) & 1, 32)) {
+            atomicOr(&ctl->abort, 1u);
+            break;
+          }
+        }
+        const int os = i % VX_OS;
+        if (!mbar_wait(&ctl->op_full[os], (i / VX_OS) & 1, 32)) {
+          atomicOr(&ctl->abort, 1u);
+          break;
+        }
+        if (*abort_flag) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const unsigned base = smem_u32(ops + os * VX_OP_BYTES);
+        const unsigned d = tmem + (unsigned)((sg & 1) * VX_ACC_COLS);
 #pragma unroll
-      for (int kk = 0; kk < TC_KC / 16; ++kk) {
-        const unsigned off = kk * 32;  // 16 bfloat16 along K inside the 128-byte swizzle atom
-        umma_bf16(tmem, smem_desc_sw128(a_hi + off), smem_desc_sw128(b_hi + off), (c > 0 || kk > 0) ? 1u : 0u);
-        umma_bf16(tmem, smem_desc_sw128(a_hi + off), smem_desc_sw128(b_lo + off), 1u);
-        umma_bf16(tmem, smem_desc_sw128(a_lo + off), smem_desc_sw128(b_hi + off), 1u);
+        for (int kk = 0; kk < VX_KC / 16; ++kk) {
+          const unsigned long long b = smem_desc_sw128(base + 2 * VX_A_BYTES + kk * 32);
+          umma_bf16(d, smem_desc_sw128(base + kk * 32), b, (first && kk == 0) ? 0u : 1u);
+          umma_bf16(d, smem_desc_sw128(base + VX_A_BYTES + kk * 32), b, 1u);
+        }
+        umma_commit(&ctl->op_empty[os]);
+        if (last) umma_commit(&ctl->acc_full[sg & 1]);
       }
-      umma_commit(&ctl->empty[s]);
+      umma_commit(&ctl->done);
     }
-    umma_commit(&ctl->done);
-  }
-
-  // ---- epilogue: the four warps read the accumulators (lane = row)
-  __syncwarp();
-  const bool ok = mbar_wait(&ctl->done, 0);
-  if (!ok) atomicOr(&ctl->abort, 1u);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  unsigned r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(tmem + ((unsigned)(warp * 32) << 16)));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-  {
-    const int row = tid;                      // 0..127
-    const int fj = row / (16 * K), rk = row % (16 * K);
-    const int k = rk / 16, e = rk % 16;       // packed entry e = a * 4 + b
-    const int f = f0 + fj;
-    if (ok && !ctl->abort && f < fe) {
-      const int a = e / 4, b = e % 4;
-      const double invT = 1.0 / (double)T;
+  } else if (warp < VX_CONV_WARP) {
+    // ---- epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (row = lane)
+    const int q = warp & 3, row = q * 32 + lane;
+    const int pair = row >> 4, e = row & 15;
+    const int fj = pair / K, k = pair % K, a = e >> 2, b = e & 3;
+    const bool up = lane >= 16;  // the second (frequency, subarray) pair of the warp
+    const double invT = 1.0 / (double)T;
+    int sg = -1;
+    for (int i0 = 0; i0 < nloc;) {
+      const int u0 = u_begin + i0;
+      const int tl = u0 / nch, c0 = u0 % nch;
+      const int len = min(nch - c0, nloc - i0);
+      const bool full = (c0 == 0 && len == nch);
+      ++sg;
+      const bool okw = mbar_wait(&ctl->acc_full[sg & 1], (sg >> 1) & 1, 256);
+      if (!okw) atomicOr(&ctl->abort, 1u);
+      if (epi_bar_or(!okw || *abort_flag)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      unsigned h[8], l[8];
+      const unsigned ta = tmem + ((unsigned)(q * 32) << 16) + (unsigned)((sg & 1) * VX_ACC_COLS + 8 * q);
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                   : "=r"(h[0]), "=r"(h[1]), "=r"(h[2]), "=r"(h[3]), "=r"(h[4]), "=r"(h[5]), "=r"(h[6]), "=r"(h[7])
+                   : "r"(ta));
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                   : "=r"(l[0]), "=r"(l[1]), "=r"(l[2]), "=r"(l[3]), "=r"(l[4]), "=r"(l[5]), "=r"(l[6]), "=r"(l[7])
+                   : "r"(ta + VX_WROWS));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&ctl->acc_empty[sg & 1]);
+      float v[4];
+#pragma unroll
+      for (int mu = 0; mu < 4; ++mu)
+        v[mu] = __uint_as_float(up ? h[4 + mu] : h[mu]) + __uint_as_float(up ? l[4 + mu] : l[mu]);
+      const int tile = tb + tl, f = tile * FPC + fj;
       const size_t blk = (size_t)f * K + k;
+      if (full) {
+        if (f < F) {
+          double dv[4];
+#pragma unroll
+          for (int mu = 0; mu < 4; ++mu) dv[mu] = (double)v[mu] * invT;
+          vx_write_v(V, Vdd, blk, a, b, dv);
+        }
+      } else {
+        // tile shared with other CTAs: publish this part, the last CTA to arrive adds them in CTA order
+        const int bfirst = vx_cta_of((long long)tl * nch, G, U);
+        const int blast = vx_cta_of((long long)tl * nch + nch - 1, G, U);
+        part[((size_t)tl + blockIdx.x) * VX_ROWS + row] = make_float4(v[0], v[1], v[2], v[3]);
+        __threadfence();
+        epi_bar();
+        if (tid == VX_EPI_WARP * 32) ctl->last = (atomicAdd(&tickets[tile], 1u) == (unsigned)(blast - bfirst));
+        epi_bar();
+        if (ctl->last) {
+          __threadfence();
+          double dv[4] = {0.0, 0.0, 0.0, 0.0};
+          for (int bb = bfirst; bb <= blast; ++bb) {
+            const float4 p = __ldcg(part + ((size_t)tl + bb) * VX_ROWS + row);
+            dv[0] += (double)p.x;
+            dv[1] += (double)p.y;
+            dv[2] += (double)p.z;
+            dv[3] += (double)p.w;
+          }
+          if (f < F) {
+#pragma unroll
+            for (int mu = 0; mu < 4; ++mu) dv[mu] *= invT;
+            vx_write_v(V, Vdd, blk, a, b, dv);
+          }
+          if (tid == VX_EPI_WARP * 32) tickets[tile] = 0u;
+        }
+        epi_bar();
+      }
+      i0 += len;
+    }
+  } else {
+    // ---- converters: warp cw of group grp forms rows 16 cw .. 16 cw + 15 of R (pair cw) and the w rows of
+    // its four microphones for frames lane and lane + 32 of every CG-th chunk
+    const int cw = (warp - VX_CONV_WARP) % VX_CW, grp = (warp - VX_CONV_WARP) / VX_CW;
+    const int fj = cw / K, k = cw % K;
+    const unsigned lo4 = (unsigned)(lane & 3) * 4, c8 = (unsigned)(lane >> 2);
+    const int wrow = fj * M + 4 * k;  // first w row of this pair
+    int c = (u_begin + grp) % nch;  // chunk of unit i, advanced by CG per step
+    for (int i = grp; i < nloc; i += CG) {
+      const int s = i % RS, os = i % VX_OS;
+      bool ok = mbar_wait_warp(&ctl->raw_full[s], (i / RS) & 1, 32);
+      if (ok && i >= VX_OS) ok = mbar_wait_warp(&ctl->op_empty[os], ((i / VX_OS) - 1) & 1, 32);
+      if (!ok) {
+        if (lane == 0) atomicOr(&ctl->abort, 1u);
+        break;
+      }
+      if (__any_sync(DFM_FULL_MASK, *abort_flag != 0)) break;
+      const unsigned char* st = raw + (size_t)s * stage_bytes;
+      const float* ls = reinterpret_cast<const float*>(st + VX_X_BYTES);
+      const float* gs = reinterpret_cast<const float*>(st + VX_X_BYTES + lbytes);
+      unsigned char* op = ops + os * VX_OP_BYTES;
+      // x of frames lane (.x) and lane + 32 (.y), real and imaginary parts, microphones 0..3 of the pair
+      float2 xr[4], xi[4];
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const unsigned l0 = (unsigned)((fj * VX_KC + lane) * (8 * M) + k * 32 + hh * 16);
+        const unsigned l1 = l0 + 32u * (8 * M);
+        const float4 q0 = *reinterpret_cast<const float4*>(st + (l0 ^ ((l0 >> 3) & SWZ)));
+        const float4 q1 = *reinterpret_cast<const float4*>(st + (l1 ^ ((l1 >> 3) & SWZ)));
+        xr[2 * hh] = make_float2(q0.x, q1.x);
+        xi[2 * hh] = make_float2(q0.y, q1.y);
+        xr[2 * hh + 1] = make_float2(q0.z, q1.z);
+        xi[2 * hh + 1] = make_float2(q0.w, q1.w);
+      }
+      // R = x x^H, entry 4a + b: |x_a|^2 (a == b), Re x_a conj x_b (a < b), Im x_b conj x_a (a > b);
+      // both frames at once (packed single-precision pairs)
+      unsigned char* arow = op + cw * 16 * 128 + lo4;
+#pragma unroll
+      for (int aa = 0; aa < 4; ++aa)
+#pragma unroll
+        for (int bb = 0; bb < 4; ++bb) {
+          float2 r;
+          if (aa == bb) r = __ffma2_rn(xr[aa], xr[aa], __fmul2_rn(xi[aa], xi[aa]));
+          else if (aa < bb) r = __ffma2_rn(xr[aa], xr[bb], __fmul2_rn(xi[aa], xi[bb]));
+          else r = __ffma2_rn(xi[bb], xr[aa], __fmul2_rn(make_float2(-xr[bb].x, -xr[bb].y), xi[aa]));
+          const int e = aa * 4 + bb;
+          const unsigned off = (unsigned)(e * 128) + ((c8 ^ (unsigned)(e & 7)) << 4);
+          vx_split_store(arow + off, arow + VX_A_BYTES + off, r);
+        }
+      // w = 1 / max(yhat, eps) for the pair's four microphones, zero past T
+      float y[2][4];
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) y[j][mu] = 0.f;
+      for (int n = 0; n < N; ++n) {
+        const float l0 = ls[(n * FPC + fj) * VX_KC + lane], l1 = ls[(n * FPC + fj) * VX_KC + lane + 32];
+        const float4 gv = *reinterpret_cast<const float4*>(gs + (fj * N + n) * M + 4 * k);
+        y[0][0] = fmaf(l0, gv.x, y[0][0]); y[0][1] = fmaf(l0, gv.y, y[0][1]);
+        y[0][2] = fmaf(l0, gv.z, y[0][2]); y[0][3] = fmaf(l0, gv.w, y[0][3]);
+        y[1][0] = fmaf(l1, gv.x, y[1][0]); y[1][1] = fmaf(l1, gv.y, y[1][1]);
+        y[1][2] = fmaf(l1, gv.z, y[1][2]); y[1][3] = fmaf(l1, gv.w, y[1][3]);
+      }
+      const bool v0 = c * VX_KC + lane < T, v1 = c * VX_KC + lane + 32 < T;
+      unsigned char* bt = op + 2 * VX_A_BYTES + lo4;
 #pragma unroll
       for (int mu = 0; mu < 4; ++mu) {
-        const float v = __uint_as_float(r[fj * M + k * 4 + mu]);
-        const double dv = (double)v * invT;
-        double2* Vb = V + (blk * 4 + mu) * 16;
-        float4* Vd = Vdd + (blk * 4 + mu) * 16;
-        double* vdbl = reinterpret_cast<double*>(Vb);
-        float* vflt = reinterpret_cast<float*>(Vd);
-        const float fv = (float)dv;
-        if (a == b) {
-          Vb[a * 4 + a] = make_double2(dv, 0.0);
-          Vd[a * 4 + a] = make_float4(fv, 0.f, 0.f, 0.f);
-        } else if (a < b) {  // real part of V[a][b] and V[b][a]
-          vdbl[2 * (a * 4 + b)] = dv;
-          vdbl[2 * (b * 4 + a)] = dv;
-          vflt[4 * (a * 4 + b)] = fv; vflt[4 * (a * 4 + b) + 1] = 0.f;
-          vflt[4 * (b * 4 + a)] = fv; vflt[4 * (b * 4 + a) + 1] = 0.f;
-        } else {  // e = a*4+b with a > b holds Im(x_b conj x_a) = Im V[b][a]
-          vdbl[2 * (b * 4 + a) + 1] = dv;
-          vdbl[2 * (a * 4 + b) + 1] = -dv;
-          vflt[4 * (b * 4 + a) + 2] = fv; vflt[4 * (b * 4 + a) + 3] = 0.f;
-          vflt[4 * (a * 4 + b) + 2] = -fv; vflt[4 * (a * 4 + b) + 3] = 0.f;
-        }
+        const int rw = wrow + mu;
+        const unsigned off = (unsigned)(rw * 128) + ((c8 ^ (unsigned)(rw & 7)) << 4);
+        vx_split_store(bt + off, bt + VX_WROWS * 128 + off,
+                       make_float2(v0 ? fast_rcp(fmaxf(y[0][mu], eps)) : 0.f, v1 ? fast_rcp(fmaxf(y[1][mu], eps)) : 0.f));
       }
+      // generic-proxy writes of the operand tiles, then hand the stages over
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&ctl->raw_empty[s]);
+        mbar_arrive(&ctl->op_full[os]);
+      }
+      for (c += CG; c >= nch;) c -= nch;
     }
   }
+
   __syncthreads();
-  if (ctl->abort && tid == 0) atomicOr(flags + FLAG_TIMEOUT, 1u);
   if (warp == 0) {
+    // all tensor-core work of the CTA has completed before its tensor memory is freed (bounded wait)
+    if (!mbar_wait_warp(&ctl->done, 0, 64) && lane == 0) atomicOr(&ctl->abort, 1u);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * VX_ACC_COLS) : "memory");
   }
+  if (tid == 0 && *abort_flag) atomicOr(flags + FLAG_TIMEOUT, 1u);
 }
 
 // ------------------------------------------------- projections and MU statistics through TMA
@@ -406,20 +517,6 @@ constexpr int PT_ROWS = 128;
 constexpr int PT_X_BYTES = PT_ROWS * 128;  // 16 complex64 per frame
 constexpr int PT_P_BYTES = PT_ROWS * 64;   // 16 float per frame
 
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
-                                            unsigned long long* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-      "[%5];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, int c0, int c1, int c2, const void* src) {
-  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
-                   reinterpret_cast<unsigned long long>(map)),
-               "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(src))
-               : "memory");
-}
 
 template <bool COMP>
 __global__ void __launch_bounds__(128) k_pstats_tma(const __grid_constant__ CUtensorMap map_x,
@@ -431,7 +528,7 @@ __global__ void __launch_bounds__(128) k_pstats_tma(const __grid_constant__ CUte
                                                     int Tp, int N, float eps, int fb, unsigned* __restrict__ flags) {
   constexpr int K = 4, MK = 4, M = 16;
   extern __shared__ __align__(16) unsigned char pt_raw[];
-  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(pt_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* base = pt_raw + ((1024u - (smem_u32(pt_raw) & 1023u)) & 1023u);  // stays in the shared window
   unsigned char* xs = base;                                    // [128][128 B], 128-byte swizzle
   unsigned char* ps = base + PT_X_BYTES;                       // [128][64 B], 64-byte swizzle
   float* ls = reinterpret_cast<float*>(ps + PT_P_BYTES);       // [N][128]
@@ -571,80 +668,107 @@ static EncodeTiledFn encode_fn() {
 
 bool tc_supported(int MK, int K) { return MK == 4 && (K == 1 || K == 2 || K == 4 || K == 8); }
 
-size_t tc_smem_bytes(const dfmnmf_ctx*) { return 1024 + tc_ring_bytes() + sizeof(TcSmem); }
-
-// Tiles of FPC = 8 / K frequencies of the tiled operand layout (the last one
-// padded with zero rows), and the elements of R (each part) and w (each part).
+// Tiles of 8 / K frequencies; slots of partial sums (one per (tile, CTA) pair
+// that can share a tile: tiles + CTAs) and tickets (one per tile).
 int tc_tiles(const dfmnmf_ctx* c) {
-  const int FPC = TC_ROWS / (16 * c->K);
+  const int FPC = 8 / c->K;
   return (c->F + FPC - 1) / FPC;
 }
-void tc_operand_elems(const dfmnmf_ctx* c, size_t* nr, size_t* nw) {
-  *nr = (size_t)tc_tiles(c) * TC_ROWS * c->Tr;
-  *nw = (size_t)tc_tiles(c) * TC_COLS * c->Tr;
+size_t tc_part_float4s(const dfmnmf_ctx* c) { return ((size_t)tc_tiles(c) + (size_t)c->num_sms) * VX_ROWS; }
+size_t tc_ticket_count(const dfmnmf_ctx* c) { return (size_t)tc_tiles(c); }
+
+// Raw stage of the fused contraction: x tile, lambda rows, g rows, rounded to 1 KB.
+static int vx_stage_bytes(int K, int N) {
+  const int FPC = 8 / K;
+  const int b = VX_X_BYTES + FPC * N * VX_KC * 4 + FPC * N * 4 * K * 4;
+  return (b + 1023) & ~1023;
 }
 
-// Four 2-D bfloat16 maps with 128-byte swizzle over the tiled layout viewed as
-// rows of 64 frames: R_hi / R_lo (boxes of 128 rows, one (tile, chunk) block)
-// and w_hi / w_lo (boxes of 32 rows).  The x coordinate of every copy is 0.
-cudaError_t tc_make_maps(dfmnmf_ctx* c) {
+// Raw stages that fit beside the operand stages (at most VX_MAX_RS, at least 2; 0 if none fit).
+int tc_raw_stages(const dfmnmf_ctx* c) {
+  const long avail = (long)c->smem_optin - 1024 - (long)VX_OS * VX_OP_BYTES - (long)sizeof(VxCtl);
+  const long rs = avail / vx_stage_bytes(c->K, c->N);
+  return rs < 2 ? 0 : (int)(rs > VX_MAX_RS ? VX_MAX_RS : rs);
+}
+
+template <int K, int CG>
+static cudaError_t launch_vtc_k(const dfmnmf_ctx* c, cudaStream_t s, const CUtensorMap& mx, const CUtensorMap& ml,
+                                const CUtensorMap& mg, int tb, int ntile, int nch, int G, int RS, int stage,
+                                size_t smem) {
+  auto kern = k_vtc<K, CG>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<G, (VX_CONV_WARP + VX_CW * CG) * 32, smem, s>>>(mx, ml, mg, c->V, c->Vdd, c->tc_part, c->tc_ticket, c->F,
+                                                          c->T, c->N, c->eps, tb, ntile, nch, RS, stage, c->flags);
+  return cudaGetLastError();
+}
+
+// The fused contraction for frequencies [fb, fb + fc), fb a multiple of 8 / K.
+// x as floats [F][T][2M] (boxes of 64 frames x 8/K frequencies; for K = 8 the
+// 256-byte frame rows as two 128-byte halves), lambda [N][F][Tp] (64 frames x
+// 8/K frequencies x N), g [F][N][M] (8/K frequencies); frames past T and
+// frequencies past F read as zeros.  The maps are encoded at launch and
+// passed by value, so a captured graph keeps them.
+cudaError_t launch_vtc(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
   EncodeTiledFn fn = encode_fn();
-  if (!fn) return cudaErrorNotSupported;
-  const cuuint64_t strides[1] = {(cuuint64_t)TC_KC * 2};
-  const cuuint32_t estr[2] = {1, 1};
-  const cuuint64_t blocks = (cuuint64_t)tc_tiles(c) * (c->Tr / TC_KC);
-  struct { unsigned char* map; void* base; cuuint64_t rows; cuuint32_t box_rows; } m[4] = {
-      {c->tmap_hi, c->Rhi, blocks * TC_ROWS, TC_ROWS},
-      {c->tmap_lo, c->Rlo, blocks * TC_ROWS, TC_ROWS},
-      {c->tmap_whi, c->wy_hi, blocks * TC_COLS, TC_COLS},
-      {c->tmap_wlo, c->wy_lo, blocks * TC_COLS, TC_COLS}};
-  for (int i = 0; i < 4; ++i) {
-    const cuuint64_t dims[2] = {(cuuint64_t)TC_KC, m[i].rows};
-    const cuuint32_t box[2] = {TC_KC, m[i].box_rows};
-    const CUresult r = fn(reinterpret_cast<CUtensorMap*>(m[i].map), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, m[i].base,
-                          dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  if (!fn || !tc_supported(c->MK, c->K) || !c->tc_part) return cudaErrorNotSupported;
+  const int K = c->K, FPC = 8 / K, M = c->M;
+  if (fc <= 0) return cudaSuccess;
+  if (fb % FPC) return cudaErrorInvalidValue;
+  const int tb = fb / FPC, ntile = (fb + fc + FPC - 1) / FPC - tb;
+  const int nch = (c->T + VX_KC - 1) / VX_KC;
+  const long long U = (long long)ntile * nch;
+  const int G = (int)(U < c->num_sms ? U : c->num_sms);
+  const int RS = tc_raw_stages(c), stage = vx_stage_bytes(K, c->N);
+  if (RS == 0 || U >= (1ll << 31) / (c->num_sms + 1)) return cudaErrorInvalidValue;  // unit indices stay 32-bit
+  const size_t smem = 1024 + (size_t)VX_OS * VX_OP_BYTES + (size_t)RS * stage + sizeof(VxCtl);
+  CUtensorMap mx, ml, mg;
+  const cuuint32_t e4[4] = {1, 1, 1, 1};
+  CUresult r;
+  if (K == 8) {
+    const cuuint64_t dims[4] = {32, 2, (cuuint64_t)c->T, (cuuint64_t)c->F};
+    const cuuint64_t str[3] = {128, 256, (cuuint64_t)c->T * 256};
+    const cuuint32_t box[4] = {32, 2, VX_KC, 1};
+    r = fn(&mx, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c->x, dims, str, box, e4, CU_TENSOR_MAP_INTERLEAVE_NONE,
+           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  } else {
+    const cuuint64_t dims[3] = {(cuuint64_t)(2 * M), (cuuint64_t)c->T, (cuuint64_t)c->F};
+    const cuuint64_t str[2] = {(cuuint64_t)(8 * M), (cuuint64_t)c->T * 8 * M};
+    const cuuint32_t box[3] = {(cuuint32_t)(2 * M), VX_KC, (cuuint32_t)FPC};
+    const CUtensorMapSwizzle sw =
+        K == 1 ? CU_TENSOR_MAP_SWIZZLE_32B : K == 2 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
+    r = fn(&mx, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->x, dims, str, box, e4, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   }
-  return cudaSuccess;
-}
-
-cudaError_t launch_rprep(const dfmnmf_ctx* c, cudaStream_t s) {
-  dim3 grid((c->Tr + 127) / 128, c->F);
-  k_rprep<<<grid, 128, 0, s>>>(c->x, reinterpret_cast<__nv_bfloat16*>(c->Rhi),
-                               reinterpret_cast<__nv_bfloat16*>(c->Rlo), c->F, c->T, c->Tr, c->K);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_wprep(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
-  dim3 grid((c->Tr / 2 + 127) / 128, fc);
-  const size_t sm = (size_t)c->N * c->M * sizeof(float);
-  auto whi = reinterpret_cast<__nv_bfloat16*>(c->wy_hi);
-  auto wlo = reinterpret_cast<__nv_bfloat16*>(c->wy_lo);
-#define DFM_WPREP(NMV, MV) \
-  k_wprep<NMV, MV><<<grid, 128, sm, s>>>(c->lam, c->g, whi, wlo, c->F, c->T, c->Tp, c->Tr, c->N, c->eps, fb)
-#define DFM_WPREP_N(MV)               \
-  switch (c->N) {                     \
-    case 1: DFM_WPREP(1, MV); break;  \
-    case 2: DFM_WPREP(2, MV); break;  \
-    case 3: DFM_WPREP(3, MV); break;  \
-    case 4: DFM_WPREP(4, MV); break;  \
-    case 5: DFM_WPREP(5, MV); break;  \
-    case 6: DFM_WPREP(6, MV); break;  \
-    case 7: DFM_WPREP(7, MV); break;  \
-    case 8: DFM_WPREP(8, MV); break;  \
-    default: DFM_WPREP(16, MV); break; \
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  {
+    const cuuint64_t dims[3] = {(cuuint64_t)c->Tp, (cuuint64_t)c->F, (cuuint64_t)c->N};
+    const cuuint64_t str[2] = {(cuuint64_t)c->Tp * 4, (cuuint64_t)c->F * c->Tp * 4};
+    const cuuint32_t box[3] = {VX_KC, (cuuint32_t)FPC, (cuuint32_t)c->N};
+    if (fn(&ml, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->lam, dims, str, box, e4, CU_TENSOR_MAP_INTERLEAVE_NONE,
+           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
   }
-  switch (c->M) {
-    case 4: DFM_WPREP_N(4); break;
-    case 8: DFM_WPREP_N(8); break;
-    case 16: DFM_WPREP_N(16); break;
-    case 32: DFM_WPREP_N(32); break;
-    default: return cudaErrorInvalidValue;
+  {
+    const cuuint64_t dims[3] = {(cuuint64_t)M, (cuuint64_t)c->N, (cuuint64_t)c->F};
+    const cuuint64_t str[2] = {(cuuint64_t)M * 4, (cuuint64_t)c->N * M * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)M, (cuuint32_t)c->N, (cuuint32_t)FPC};
+    if (fn(&mg, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->g, dims, str, box, e4, CU_TENSOR_MAP_INTERLEAVE_NONE,
+           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
   }
-#undef DFM_WPREP_N
-#undef DFM_WPREP
-  return cudaGetLastError();
+#define DFM_VTC(KK)                                                                                         \
+  return c->cfg_vx_groups == 1 ? launch_vtc_k<KK, 1>(c, s, mx, ml, mg, tb, ntile, nch, G, RS, stage, smem) \
+                               : launch_vtc_k<KK, 2>(c, s, mx, ml, mg, tb, ntile, nch, G, RS, stage, smem)
+  switch (K) {
+    case 1: DFM_VTC(1);
+    case 2: DFM_VTC(2);
+    case 4: DFM_VTC(4);
+    default: DFM_VTC(8);
+  }
+#undef DFM_VTC
 }
 
 // x as floats [F][T][2M] (boxes of 128 frames x 32 floats, 128-byte swizzle),
@@ -690,17 +814,6 @@ cudaError_t launch_pstats_tma(const dfmnmf_ctx* c, cudaStream_t s, int fb, int f
   dim3 grid(fc, (c->T + PT_ROWS - 1) / PT_ROWS);
   kern<<<grid, 128, sm, s>>>(mx, ml, mp, c->Q64, c->Q32, c->g, c->A, c->D, c->F, c->T, c->Tp, c->N, c->eps, fb,
                              c->flags);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_vtc(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
-  const size_t sm = tc_smem_bytes(c);
-  cudaFuncSetAttribute(k_vtc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  const int FPC = TC_ROWS / (16 * c->K);
-  const int grid = (fc + FPC - 1) / FPC;
-  auto map = [](const unsigned char* p) { return *reinterpret_cast<const CUtensorMap*>(p); };
-  k_vtc<<<grid, 128, sm, s>>>(map(c->tmap_hi), map(c->tmap_lo), map(c->tmap_whi), map(c->tmap_wlo), c->V, c->Vdd,
-                              c->T, c->Tr, c->K, c->flags, fb, fb + fc);
   return cudaGetLastError();
 }
 
