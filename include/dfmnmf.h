@@ -214,10 +214,12 @@ int dfmnmf_cost_gradient(dfmnmf_ctx* ctx, void* dQ, float* dW, float* dH, float*
 
 /*
  * Launch shapes picked by measurement (no counterpart in the paper; a GPU
- * concern): the per-frequency kernels of an iteration run either band-wide
- * on one graph branch or as two halves of the band on two branches
- * (*branches = 1 or 2), and the split NMF products of Eqs. (8)-(9) aim for
- * 2, 4 or 8 CTAs per SM (*nmf_ctas).  Every combination is timed over
+ * concern): in the FP32 form the per-frequency kernels of an iteration run
+ * either band-wide on one graph branch or as two halves of the band on two
+ * branches (*branches = 1 or 2); in the tensor-core form they stay on one
+ * branch (*branches = 1) and the persistent covariance kernel runs with one
+ * or two groups of converter warps instead; the split NMF products of
+ * Eqs. (8)-(9) aim for 2, 4 or 8 CTAs per SM (*nmf_ctas).  Every combination is timed over
  * iters_per_trial >= 1 replays of the captured iteration (after one warm-up
  * replay); the fastest is kept for this context.  The trials advance a copy
  * of the state only: Q, W, H, g and the device flags are restored, so the
@@ -311,25 +313,38 @@ void dfmnmf_adjoint_destroy(dfmnmf_adj* adj);
  * Allocation-free negative log-likelihood.  The paper has no counterpart:
  * this entry point exists for callers that may not allocate device memory
  * when they need the cost -- for example an audio engine's real-time thread,
- * where cudaMalloc can block and synchronise the whole device, or a plug-in
- * whose host application owns the GPU memory budget.  It evaluates exactly
- * the quantity of dfmnmf_loglik (Eq. 12 without the F T M ln(pi) constant)
- * from state the caller already holds in device memory, and needs no context:
- *   desc         sizes and layout as for dfmnmf_init (precision and ip_arith
- *                are ignored; floor_eps <= 0 means 1e-6),
+ * where cudaMalloc can block and synchronise the whole device and so break
+ * the thread's deadline, or a plug-in whose host application owns the GPU
+ * memory budget and forbids allocations by guests.  It returns the same value
+ * dfmnmf_loglik returns for the same state, computed from arrays the caller
+ * already holds in device memory, and needs no context:
+ *   desc         F, T, K, mics, N, B and floor_eps as for dfmnmf_init
+ *                (precision and ip_arith are ignored; floor_eps <= 0 means
+ *                1e-6),
  *   x_dev        complex64 [F][T][M], Q_dev complex128 [F][sum M_k^2],
- *   W_dev, H_dev, g_dev float32 as for dfmnmf_init (all device memory),
+ *   W_dev        float32 [N][F][B], H_dev float32 [N][B][T],
+ *   g_dev        float32 [F][N][M] (all device memory, caller-owned, read
+ *                only),
  *   nll_host     receives the cost (the call synchronises `stream`).
- * Its partial sums live in one static device array of
- * DFMNMF_NOALLOC_SCRATCH_DOUBLES doubles (512 KiB) that every GPU which loads
- * this library keeps until the process exits; sizes with
- * F * ceil(T/128) + F * K + 1 above that return DFMNMF_EINVAL (the
- * 4 x 4-mic, F = 513, T = 626 workload needs 4618).  No cudaMalloc, cudaFree
- * or allocating library routine is called.  The first call on each device
- * (with that device current) looks the array's address up once; make that
- * first call before starting any stream capture.  All calls share the array:
- * calls whose GPU work may overlap (different streams without ordering) race
- * and must be serialised by the caller.  ENUMERIC if the cost is not finite.
+ * Limits, each returning DFMNMF_EINVAL before any device work: all subarrays
+ * of one size M_k in 1..4, K <= 16, N <= 16, B <= 64, F <= 65535, and
+ * F * ceil(T/128) + F * K + 1 <= DFMNMF_NOALLOC_SCRATCH_DOUBLES, because its
+ * partial sums live in one static device array of that many doubles
+ * (512 KiB) that every GPU which loads this library keeps until the process
+ * exits (the 4 x 4-mic, F = 513, T = 626 workload needs 4618).  Null
+ * pointers also return DFMNMF_EINVAL.
+ * No cudaMalloc, cudaFree or allocating library routine is called.  The
+ * first call in each CUDA context (each device's primary context, or any
+ * other context the caller makes current) is a set-up step: it looks the
+ * array's device address up with cudaGetSymbolAddress, which under lazy
+ * module loading (the CUDA default) also loads the module and backs the
+ * array.  Make that first call at set-up time, outside any real-time thread
+ * and before any stream capture; later calls in the same context take no
+ * lock.  All calls share the array, which keeps the last call's partial
+ * sums: every entry a call reads it has written first, but calls whose GPU
+ * work may overlap (different streams without ordering between them) race on
+ * it and must be serialised by the caller.  DFMNMF_ENUMERIC if the cost is
+ * not finite.
  */
 #define DFMNMF_NOALLOC_SCRATCH_DOUBLES 65536
 int dfmnmf_loglik_noalloc(const dfmnmf_desc* desc, const void* x_dev, const void* Q_dev,

@@ -14,31 +14,39 @@
 // file-scope __device__ array of DFMNMF_NOALLOC_SCRATCH_DOUBLES doubles that
 // every GPU loading this library holds until the process exits.  Host code
 // must not use the array's name as a device address (on the host it is only a
-// stand-in symbol), so the first call on each device, with that device
-// current, asks the runtime for the array's device address with
-// cudaGetSymbolAddress and caches it; later calls reuse it.  All calls share
-// the one array: every entry a call reads is written earlier by the same
-// call, so nothing has to be cleared, but two calls whose work overlaps on
-// the GPU (different streams, no ordering between them) race on it.
+// stand-in symbol): the device address is asked of the runtime with
+// cudaGetSymbolAddress, with the device current, and cached per CUDA context.
+// The cache key is the context's unique id (cuCtxGetId), not the device
+// number: after a device reset, or with another context current on the same
+// device, the module is loaded anew and the array may sit elsewhere, so a new
+// id means a new lookup.  The first call in a context does that set-up (under
+// lazy module loading it is also where the module is loaded and the array
+// backed); later calls find the address without taking a lock.  All calls
+// share the one array: every entry a call reads is written earlier by the
+// same call, so nothing has to be cleared, but two calls whose work overlaps
+// on the GPU (different streams, no ordering between them) race on it.
+#include <cuda.h>
 #include <float.h>
 #include <math.h>
+
+#include <atomic>
 #include <mutex>
 
 #include "../../include/dfmnmf.h"
 #include "common.cuh"
 #include "internal.h"
+#include "noalloc_cache.h"
 #include <stdio.h>
 
 namespace {
 
 constexpr int kScratch = DFMNMF_NOALLOC_SCRATCH_DOUBLES;
-constexpr int kMaxDevices = 64;
 constexpr int kNMax = 16;
 
 static __device__ __align__(256) double g_nll_scratch[kScratch];
 
-std::mutex g_scratch_mu;
-double* g_scratch_ptr[kMaxDevices] = {};
+std::mutex g_scratch_mu;                          // serialises set-ups (inserts), never lookups
+dfm::ScratchCache<double*, 64> g_scratch_cache;   // context id -> device address of g_nll_scratch
 
 // Data term of Eq. (12) for one (f, 128-frame chunk): lambda is formed from W
 // and H on the fly, P from the compensated projection Q x.
@@ -163,27 +171,61 @@ int fail(int code, const char* msg) {
   return code;
 }
 
-// Device address of g_nll_scratch on the current device (looked up once per device).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+// Unique id of the CUDA context current on this thread; 0 if none is current
+// yet (the runtime makes the device's primary context current on first use)
+// or the driver cannot tell.
+unsigned long long current_context_id() {
+  static std::atomic<CtxGetCurrentFn> get_cur{nullptr};
+  static std::atomic<CtxGetIdFn> get_id{nullptr};
+  CtxGetCurrentFn gc = get_cur.load(std::memory_order_acquire);
+  CtxGetIdFn gi = get_id.load(std::memory_order_acquire);
+  if (!gc || !gi) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p)
+      return 0;
+    gc = reinterpret_cast<CtxGetCurrentFn>(p);
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p)
+      return 0;
+    gi = reinterpret_cast<CtxGetIdFn>(p);
+    get_cur.store(gc, std::memory_order_release);
+    get_id.store(gi, std::memory_order_release);
+  }
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (gc(&ctx) != CUDA_SUCCESS || !ctx || gi(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// Device address of g_nll_scratch in the current context: a lock-free cache
+// hit, or the set-up (cudaGetSymbolAddress with the device current) whose
+// result is cached under the context's id.
 int scratch_address(double** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
     return fail(DFMNMF_ECUDA, "dfmnmf_loglik_noalloc: no CUDA device");
   }
-  if (dev < 0 || dev >= kMaxDevices) return fail(DFMNMF_EINVAL, "dfmnmf_loglik_noalloc: device index out of range");
+  unsigned long long id = current_context_id();
+  if (id != 0 && g_scratch_cache.find(id, out)) return DFMNMF_OK;
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_nll_scratch);
-    if (e != cudaSuccess || !p) {
-      cudaGetLastError();
-      char msg[256];
-      snprintf(msg, sizeof msg, "dfmnmf_loglik_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-      return fail(DFMNMF_ECUDA, msg);
-    }
-    g_scratch_ptr[dev] = static_cast<double*>(p);
+  if (id != 0 && g_scratch_cache.find(id, out)) return DFMNMF_OK;
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_nll_scratch);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    char msg[256];
+    snprintf(msg, sizeof msg, "dfmnmf_loglik_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+    return fail(DFMNMF_ECUDA, msg);
   }
-  *out = g_scratch_ptr[dev];
+  if (id == 0) id = current_context_id();  // the lookup made the primary context current
+  if (id != 0) g_scratch_cache.insert(id, static_cast<double*>(p));  // a full table only stops caching
+  *out = static_cast<double*>(p);
   return DFMNMF_OK;
 }
 

@@ -331,16 +331,38 @@ def dfmnmf_version() -> int:
     return load_library().dfmnmf_version()
 
 
+def _device_array(a, dtype, numel: int, name: str):
+    """Pointer of a C-contiguous torch CUDA tensor on the current device with `numel` elements of `dtype`
+    (raises ValueError or TypeError otherwise, before the library is called)."""
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        raise ValueError(f"{name} must be a torch CUDA tensor")
+    if not isinstance(a, torch.Tensor) or not a.is_cuda:
+        raise ValueError(f"{name} must be a torch CUDA tensor (device memory), got {type(a).__name__}"
+                         + ("" if not isinstance(a, torch.Tensor) else f" on {a.device}"))
+    if a.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} is on {a.device}, the current device is cuda:{torch.cuda.current_device()}")
+    if a.numel() != numel:
+        raise ValueError(f"{name} has {a.numel()} elements, the sizes need {numel}")
+    return _ptr(a, dtype)
+
+
 def dfmnmf_loglik_noalloc(F: int, T: int, mics: Sequence[int], N: int, B: int, x, Q, W, H, g,
                           floor_eps: float = 1e-6, stream=None) -> float:
-    """Eq. (12) from caller-held device arrays, with no device allocation (see the header)."""
+    """The cost dfmnmf_loglik returns, from caller-held device arrays, with no device allocation (see the
+    header).  x, Q, W, H and g must be CUDA tensors on the current device with exactly the element counts
+    F T M, F sum(M_k^2), N F B, N B T and F N M: the library cannot check device pointers itself."""
     lib = load_library()
-    mic_arr = (ctypes.c_int * len(mics))(*[int(m) for m in mics])
+    mics = [int(m) for m in mics]
+    M, q = sum(mics), sum(m * m for m in mics)
+    ptrs = [_device_array(a, _dt(dt), n, name) for a, dt, n, name in (
+        (x, "c64", F * T * M, "x"), (Q, "c128", F * q, "Q"), (W, "f32", N * F * B, "W"),
+        (H, "f32", N * B * T, "H"), (g, "f32", F * N * M, "g"))]
+    mic_arr = (ctypes.c_int * len(mics))(*mics)
     d = dfmnmf_desc(int(F), int(T), len(mics), mic_arr, int(N), int(B), 0, 0, float(floor_eps))
     v = ctypes.c_double()
-    _check(lib.dfmnmf_loglik_noalloc(ctypes.byref(d), _ptr(x, _dt("c64")), _ptr(Q, _dt("c128")),
-                                     _ptr(W, _dt("f32")), _ptr(H, _dt("f32")), _ptr(g, _dt("f32")),
-                                     ctypes.byref(v), _stream(stream)))
+    _check(lib.dfmnmf_loglik_noalloc(ctypes.byref(d), *ptrs, ctypes.byref(v), _stream(stream)))
     return v.value
 
 

@@ -118,3 +118,65 @@ def test_noalloc_rejects_sizes_beyond_its_static_scratch(lib):
     assert call(3, 20, (4, 4), N=17) == D.DFMNMF_EINVAL
     assert call(0, 20, (4, 4)) == D.DFMNMF_EINVAL
     assert call(3, 20, (4, 4), ptr=None) == D.DFMNMF_EINVAL
+
+
+def test_noalloc_wrapper_refuses_host_and_wrong_sized_arrays(lib):
+    """The binding refuses arrays the library could only read through a host pointer or out of
+    bounds: host arrays, and tensors whose element counts do not match the sizes, before any call."""
+    torch = pytest.importorskip("torch")
+    F, T, mics, N, B_ = 3, 20, (4, 4), 2, 3
+    M = sum(mics)
+    host = dict(x=np.zeros((F, T, M), np.complex64), Q=np.zeros((F, 32), np.complex128),
+                W=np.zeros((N, F, B_), np.float32), H=np.zeros((N, B_, T), np.float32),
+                g=np.zeros((F, N, M), np.float32))
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        D.dfmnmf_loglik_noalloc(F, T, mics, N, B_, **host)
+    cpu = {k: torch.from_numpy(v) for k, v in host.items()}
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        D.dfmnmf_loglik_noalloc(F, T, mics, N, B_, **cpu)
+    if torch.cuda.is_available():  # wrong element counts are refused on the GPU box too
+        dev = {k: v.cuda() for k, v in cpu.items()}
+        dev["H"] = torch.zeros((N, B_, T - 1), dtype=torch.float32, device="cuda")
+        with pytest.raises(ValueError, match="elements"):
+            D.dfmnmf_loglik_noalloc(F, T, mics, N, B_, **dev)
+
+
+CACHE_TEST = r"""
+#include <cstdio>
+#include "noalloc_cache.h"
+int main() {
+  dfm::ScratchCache<double*, 4> c;
+  double a = 0, b = 0;
+  double* out = nullptr;
+  if (c.find(7, &out)) return 1;                   // empty table: miss
+  if (c.insert(0, &a)) return 2;                   // key 0 ("no context") is never stored
+  if (!c.insert(7, &a)) return 3;
+  if (!c.find(7, &out) || out != &a) return 4;     // hit
+  if (c.find(8, &out)) return 5;                   // another context (a reset device, another
+                                                   // context on the same device) misses
+  if (!c.insert(8, &b) || !c.find(8, &out) || out != &b) return 6;
+  if (!c.find(7, &out) || out != &a) return 7;     // entries never change once stored
+  if (!c.insert(9, &a) || !c.insert(10, &a)) return 8;
+  if (c.insert(11, &b) || c.find(11, &out)) return 9;  // full: refused, the caller looks up uncached
+  std::puts("ok");
+  return 0;
+}
+"""
+
+
+def test_noalloc_address_cache_is_keyed_by_context(tmp_path):
+    """The allocation-free entry point caches the scratch array's device address per CUDA context id
+    (not per device number): a new context misses and is looked up anew; stored entries never change;
+    a full table stops caching.  Host-only unit test of the cache (compiled with the host compiler)."""
+    import shutil
+    import subprocess
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no host C++ compiler")
+    src = tmp_path / "cache_test.cpp"
+    src.write_text(CACHE_TEST)
+    exe = tmp_path / "cache_test"
+    inc = os.path.join(ROOT, "paper_2605_19388_gb300", "csrc")
+    subprocess.run([cxx, "-std=c++17", "-O1", "-I", inc, str(src), "-o", str(exe)], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout)
