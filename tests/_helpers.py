@@ -41,3 +41,61 @@ def sdr_db(est, ref, mic=0):
 
 def oracle_state(prob):
     return O.state_from_arrays(prob.Q0, prob.W0, prob.H0, prob.g0, prob.mics)
+
+
+# ----------------------------------------------------------- element-wise checks
+# A normwise error can hide a wrong bin, a wrong partial tile or a wrong small
+# entry under large ones, so every parity check also bounds each element:
+#     |a_i - b_i| <= tol * max(|b_i|, s_i),
+# with a stated scale floor s_i per array (the reference b decides it):
+#   V  (Eq. 13, [F][K][mu][Mk][Mk])  the largest |entry| of the same M_k x M_k block;
+#   Q  ([F][K][Mk][Mk] or per block)  the largest |entry| of the same row q_mu^H;
+#   P, W, H, g, lambda, the Wiener output  the median |entry| of the whole array.
+# Entries far below these scales carry the rounding of the sums they come from
+# (cancellation in off-diagonal covariances and in projections), so they are
+# held to the scale's absolute accuracy, not to their own relative one.
+def elem_err(a, b, floor):
+    """max_i |a_i - b_i| / max(|b_i|, floor_i) (floor broadcastable to b)."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    cplx = np.iscomplexobj(a) or np.iscomplexobj(b)
+    d = np.abs(a.astype(np.complex128 if cplx else np.float64) - b)
+    den = np.maximum(np.abs(b), floor)
+    den = np.where(den > 0, den, 1.0)
+    return float(np.max(d / den)) if d.size else 0.0
+
+
+def floor_median(b):
+    return float(np.median(np.abs(np.asarray(b))))
+
+
+def floor_last_axes(b, naxes):
+    """Largest |entry| over the last `naxes` axes (kept for broadcasting)."""
+    b = np.abs(np.asarray(b))
+    return np.max(b, axis=tuple(range(b.ndim - naxes, b.ndim)), keepdims=True)
+
+
+def elem_err_V(a, b):
+    return elem_err(a, b, floor_last_axes(b, 2))
+
+
+def elem_err_Q(a, b):
+    """Q as [..., Mk, Mk] blocks (rows on the second-to-last axis) or a list of such per subarray."""
+    if isinstance(b, (list, tuple)):
+        return max(elem_err(x, y, floor_last_axes(y, 1)) for x, y in zip(a, b))
+    return elem_err(a, b, floor_last_axes(b, 1))
+
+
+def elem_err_med(a, b):
+    return elem_err(a, b, floor_median(b))
+
+
+def check_both(errs, name, a, b, kind, tol=None):
+    """Record the normwise and the element-wise error of one output under `name` and `name`_elem."""
+    fn = {"V": elem_err_V, "Q": elem_err_Q, "med": elem_err_med}[kind]
+    if isinstance(b, (list, tuple)):
+        errs[name] = max(rel_err(x, y) for x, y in zip(a, b))
+    else:
+        errs[name] = rel_err(a, b)
+    errs[name + "_elem"] = fn(a, b)
+    return errs

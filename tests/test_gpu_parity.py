@@ -9,7 +9,7 @@ import pytest
 
 import oracle as O
 from paper_2605_19388_gb300 import synth
-from tests._helpers import rel_err, v_oracle_layout, sdr_db, oracle_state
+from tests._helpers import rel_err, v_oracle_layout, sdr_db, oracle_state, check_both
 
 pytestmark = pytest.mark.gpu
 
@@ -42,35 +42,35 @@ def stage_parity(p, Q0, ip=D.DFMNMF_IP_F32X2, tol=TOL_UPDATE, tol_ip=TOL_UPDATE)
     D.dfmnmf_run_stage(ctx, D.DFMNMF_STAGE_COV)
     V_gpu = D.buffer_numpy(ctx, D.DFMNMF_BUF_V)
     lam_gpu = D.buffer_numpy(ctx, D.DFMNMF_BUF_LAMBDA)
-    errs["lambda"] = rel_err(lam_gpu, O.source_psd(st.W, st.H))
+    check_both(errs, "lambda", lam_gpu, O.source_psd(st.W, st.H), "med")
     y = O.model_variance(O.source_psd(st.W, st.H), st.g)
     V_ref = O.weighted_covariances(x, y, p.mics)
-    errs["V"] = rel_err(V_gpu, v_oracle_layout(V_ref))
+    check_both(errs, "V", V_gpu, v_oracle_layout(V_ref), "V")
     # stage 2: IP (Eqs. 14-15) on the GPU's V
     D.dfmnmf_run_stage(ctx, D.DFMNMF_STAGE_IP)
     st2 = gpu_state(ctx)
     V_in = [V_gpu[:, k].astype(np.complex128) for k in range(p.K)]
     Q_ref = O.ip_update(st.Q, V_in)
-    errs["Q"] = max(rel_err(st2.Q[k], Q_ref[k]) for k in range(p.K))
+    check_both(errs, "Q", list(st2.Q), list(Q_ref), "Q")
     # stage 3: P and W (Eq. 8) from the GPU's Q
     D.dfmnmf_run_stage(ctx, D.DFMNMF_STAGE_W)
     st3 = gpu_state(ctx)
     P_gpu = D.buffer_numpy(ctx, D.DFMNMF_BUF_P)
     P_ref = O.projected_power(x, st2.Q, p.mics)
-    errs["P"] = rel_err(P_gpu, P_ref)
-    errs["W"] = rel_err(st3.W, O.update_W(st2.W, st2.H, st2.g, P_ref))
+    check_both(errs, "P", P_gpu, P_ref, "med")
+    check_both(errs, "W", st3.W, O.update_W(st2.W, st2.H, st2.g, P_ref), "med")
     # stage 4: H (Eq. 9)
     D.dfmnmf_run_stage(ctx, D.DFMNMF_STAGE_H)
     st4 = gpu_state(ctx)
-    errs["H"] = rel_err(st4.H, O.update_H(st3.W, st3.H, st3.g, P_ref))
+    check_both(errs, "H", st4.H, O.update_H(st3.W, st3.H, st3.g, P_ref), "med")
     # stage 5: g (Eq. 10)
     D.dfmnmf_run_stage(ctx, D.DFMNMF_STAGE_G)
     st5 = gpu_state(ctx)
-    errs["g"] = rel_err(st5.g, O.update_g(st4.W, st4.H, st4.g, P_ref))
+    check_both(errs, "g", st5.g, O.update_g(st4.W, st4.H, st4.g, P_ref), "med")
     lam5 = D.buffer_numpy(ctx, D.DFMNMF_BUF_LAMBDA)
-    errs["lambda_end"] = rel_err(lam5, O.source_psd(st5.W, st5.H))
+    check_both(errs, "lambda_end", lam5, O.source_psd(st5.W, st5.H), "med")
     for k, v in errs.items():
-        lim = tol_ip if k == "Q" else tol
+        lim = tol_ip if k.startswith("Q") else tol
         assert v <= lim, (k, v, errs)
     return errs
 
@@ -122,8 +122,8 @@ def test_singular_systems_use_pseudo_inverse():
     y = O.model_variance(O.source_psd(st.W, st.H), st.g)
     V_ref = O.weighted_covariances(x, y, p.mics)
     Q_ref = O.ip_update(st.Q, V_ref)
-    for k in range(p.K):
-        assert rel_err(Q_gpu[k], Q_ref[k]) < 1e-4, k
+    errs = check_both({}, "Q", list(Q_gpu), list(Q_ref), "Q")
+    assert max(errs.values()) < 1e-4, errs
     assert np.all(np.isfinite(V_gpu))
 
 
@@ -139,8 +139,8 @@ def test_silent_subarray_bin():
     y = O.model_variance(O.source_psd(st.W, st.H), st.g)
     Q_ref = O.ip_update(st.Q, O.weighted_covariances(p.x.astype(np.complex128), y, p.mics))
     assert np.all(Q_gpu[1][2] == 0) and np.all(Q_ref[1][2] == 0)
-    for k in range(p.K):
-        assert rel_err(Q_gpu[k], Q_ref[k]) < TOL_UPDATE
+    errs = check_both({}, "Q", list(Q_gpu), list(Q_ref), "Q")
+    assert max(errs.values()) < TOL_UPDATE, errs
 
 
 def test_loglik_and_wiener_parity():
@@ -157,7 +157,8 @@ def test_loglik_and_wiener_parity():
     D.dfmnmf_separate(ctx, c)
     torch.cuda.synchronize()
     c_ref = O.wiener_filter(x, p.mics, st)
-    assert rel_err(c.cpu().numpy(), c_ref) < 1e-5
+    errs = check_both({}, "c", c.cpu().numpy(), c_ref, "med")
+    assert max(errs.values()) < 1e-5, errs
 
 
 def test_iterate_equals_stages():
@@ -201,12 +202,12 @@ def test_paper_workload_one_iteration_full_size():
     got = gpu_state(ctx)
     rec = {}
     ref = O.mm_iteration(x, p.mics, oracle_state(p), record=rec)
-    for k in range(p.K):
-        assert rel_err(got.Q[k], ref.Q[k]) < TOL_UPDATE
-    assert rel_err(got.W, ref.W) < TOL_UPDATE
-    assert rel_err(got.H, ref.H) < TOL_UPDATE
-    assert rel_err(got.g, ref.g) < TOL_UPDATE
-    assert rel_err(D.buffer_numpy(ctx, D.DFMNMF_BUF_P), rec["P"]) < TOL_UPDATE
+    errs = check_both({}, "Q", list(got.Q), list(ref.Q), "Q")
+    for name in ("W", "H", "g"):
+        check_both(errs, name, getattr(got, name), getattr(ref, name), "med")
+    check_both(errs, "P", D.buffer_numpy(ctx, D.DFMNMF_BUF_P), rec["P"], "med")
+    print("FP32 form, one full-size iteration", errs)
+    assert max(errs.values()) < TOL_UPDATE, errs
 
 
 def test_nonfinite_input_reports_enumeric():

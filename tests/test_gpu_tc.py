@@ -13,7 +13,7 @@ import pytest
 
 import oracle as O
 from paper_2605_19388_gb300 import synth
-from tests._helpers import rel_err, v_oracle_layout, sdr_db, oracle_state
+from tests._helpers import rel_err, v_oracle_layout, sdr_db, oracle_state, check_both
 
 pytestmark = pytest.mark.gpu
 
@@ -49,8 +49,8 @@ def test_tc_covariances_match_oracle(shape):
     V = D.buffer_numpy(ctx, D.DFMNMF_BUF_V)
     y = O.model_variance(O.source_psd(st.W, st.H), st.g)
     V_ref = v_oracle_layout(O.weighted_covariances(p.x.astype(np.complex128), y, p.mics))
-    err = rel_err(V, V_ref)
-    assert err < 1e-4, err
+    errs = check_both({}, "V", V, V_ref, "V")
+    assert max(errs.values()) < 1e-4, errs
 
 
 def tc_stage_errors(p):
@@ -62,22 +62,22 @@ def tc_stage_errors(p):
     D.dfmnmf_run_stage(ctx, D.DFMNMF_STAGE_COV)
     V = D.buffer_numpy(ctx, D.DFMNMF_BUF_V)
     y = O.model_variance(O.source_psd(st.W, st.H), st.g)
-    errs["V"] = rel_err(V, v_oracle_layout(O.weighted_covariances(x, y, p.mics)))
+    check_both(errs, "V", V, v_oracle_layout(O.weighted_covariances(x, y, p.mics)), "V")
     D.dfmnmf_run_stage(ctx, D.DFMNMF_STAGE_IP)
     st2 = state(ctx)
     Q_ref = O.ip_update(st.Q, [V[:, k] for k in range(p.K)])
-    errs["Q"] = max(rel_err(st2.Q[k], Q_ref[k]) for k in range(p.K))
+    check_both(errs, "Q", list(st2.Q), list(Q_ref), "Q")
     D.dfmnmf_run_stage(ctx, D.DFMNMF_STAGE_W)
     st3 = state(ctx)
     P = O.projected_power(x, st2.Q, p.mics)
-    errs["P"] = rel_err(D.buffer_numpy(ctx, D.DFMNMF_BUF_P), P)
-    errs["W"] = rel_err(st3.W, O.update_W(st2.W, st2.H, st2.g, P))
+    check_both(errs, "P", D.buffer_numpy(ctx, D.DFMNMF_BUF_P), P, "med")
+    check_both(errs, "W", st3.W, O.update_W(st2.W, st2.H, st2.g, P), "med")
     D.dfmnmf_run_stage(ctx, D.DFMNMF_STAGE_H)
     st4 = state(ctx)
-    errs["H"] = rel_err(st4.H, O.update_H(st3.W, st3.H, st3.g, P))
+    check_both(errs, "H", st4.H, O.update_H(st3.W, st3.H, st3.g, P), "med")
     D.dfmnmf_run_stage(ctx, D.DFMNMF_STAGE_G)
     st5 = state(ctx)
-    errs["g"] = rel_err(st5.g, O.update_g(st4.W, st4.H, st4.g, P))
+    check_both(errs, "g", st5.g, O.update_g(st4.W, st4.H, st4.g, P), "med")
     return errs
 
 
@@ -132,9 +132,10 @@ def test_tc_paper_workload_one_iteration_full_size(autotune):
     got = state(ctx)
     rec = {}
     ref = O.mm_iteration(x, p.mics, oracle_state(p), record=rec)
-    errs = {"Q": max(rel_err(got.Q[k], ref.Q[k]) for k in range(p.K)), "W": rel_err(got.W, ref.W),
-            "H": rel_err(got.H, ref.H), "g": rel_err(got.g, ref.g),
-            "P": rel_err(D.buffer_numpy(ctx, D.DFMNMF_BUF_P), rec["P"])}
+    errs = check_both({}, "Q", list(got.Q), list(ref.Q), "Q")
+    for name in ("W", "H", "g"):
+        check_both(errs, name, getattr(got, name), getattr(ref, name), "med")
+    check_both(errs, "P", D.buffer_numpy(ctx, D.DFMNMF_BUF_P), rec["P"], "med")
     print("tensor-core form, one full-size iteration, autotune", autotune, errs)
     assert max(errs.values()) < TOL_TC, errs
 
