@@ -131,10 +131,9 @@ class ClockSampler:
 def kernel_bytes(F, T, M, N, B, K, MK):
     """Algorithmic DRAM bytes of one launch of each kernel (each operand once)."""
     q = F * K * MK * MK
-    Tr = (T + 63) // 64 * 64
     return {
-        "k_wprep": 4 * N * F * T + 4 * F * N * M + 2 * F * M * Tr * 2,
-        "k_vtc": 2 * F * 16 * K * Tr * 2 + 2 * F * M * Tr * 2 + 16 * q * MK + 16 * q * MK,
+        # Eq. 13 in either form: x once, lambda and g once, V once (complex64 count)
+        "k_vtc": 8 * F * T * M + 4 * N * F * T + 4 * F * N * M + 8 * q * MK,
         "k_cov": 8 * F * T * M + 4 * N * F * T + 4 * F * N * M + 8 * q * MK,
         "k_ip": 8 * q * MK + 32 * q + 8 * q,
         "k_pstats": 8 * F * T * M + 4 * N * F * T + 4 * F * N * M + 8 * q + 4 * F * T * M + 8 * N * F * T,
@@ -159,8 +158,6 @@ NCU_TRAFFIC = {
         "k_stats": (27179776 + 1024, "kernels_model.cu", "d019e79f136de230"),
         "k_gupd": (27193344 + 0, "kernels_model.cu", "d019e79f136de230"),
         "k_lambda": (388352 + 0, "kernels_model.cu", "d019e79f136de230"),
-        "k_vtc": (105289984 + 2793216, "kernels_tc.cu", "681d9dac4e7f5a1d"),
-        "k_wprep": (6619648 + 0, "kernels_tc.cu", "681d9dac4e7f5a1d"),
         "k_ip": (2701824 + 0, "kernels_ip.cu", "8f14118b76b1c4d8"),
         "k_wupd": (13268736 + 0, "kernels_nmf.cu", "36821db759ba7376"),
         "k_hupd": (13270016 + 0, "kernels_nmf.cu", "36821db759ba7376"),
@@ -269,6 +266,31 @@ print(json.dumps(dict(iters=n, seconds=el)))
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def run_oracle_sample_allcores(workload: str, seconds: float, workers: int | None = None) -> dict:
+    """Time the FP64 oracle's MM iterations on every host core for about `seconds`: its bins are split into
+    one contiguous slice per core, each slice iterated by the oracle's own functions in a worker process,
+    the Eq. 9 sum over bins added in the parent (oracle/parallel.py).  One warm-up iteration is untimed."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import oracle as O
+    from oracle.parallel import SlicedOracle
+    from paper_2605_19388_gb300 import synth
+    p = synth.make_workload(workload, seed=0)
+    workers = workers or os.cpu_count() or 1
+    st = O.state_from_arrays(p.Q0, p.W0, p.H0, p.g0, p.mics)
+    with SlicedOracle(p.x.astype(np.complex128), p.mics, st, workers) as so:
+        so.iterate(1)
+        t0 = time.perf_counter()
+        n = 0
+        while True:
+            so.iterate(1)
+            n += 1
+            el = time.perf_counter() - t0
+            if el >= seconds:
+                break
+        return {"iters": n, "seconds": el, "workers": so.workers}
 
 
 def reference_arm(args, rank, world):
@@ -561,7 +583,7 @@ def main():
         return {n: {"ms": ms, "share": ms / iter_ms, "alg_bytes": kbf.get(base(n)),
                     "GBps": (kbf[base(n)] / (ms * 1e-3) / 1e9) if base(n) in kbf else None} for n, ms in kt}
 
-    launches_step = iters * head["launches_iter"] + 2 + 3 + 2 + (1 if forms[0] == "bf16tc" else 0)
+    launches_step = iters * head["launches_iter"] + 2 + 3 + 2
     out = {
         "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
@@ -596,18 +618,25 @@ def main():
     }
     ctx = ctxs[forms[0]]
 
-    # end to end through the public API with host buffers (pinned)
+    # end to end through the public API with host buffers (pinned): the observation and the initial state
+    # go in, the separated images (Wiener filter output) and the final state come back, every step
     if not args.no_e2e:
         xh = torch.from_numpy(p.x).pin_memory()
         W0h, H0h, g0h = (torch.from_numpy(a).pin_memory() for a in (p.W0, p.H0, p.g0))
         Q0h = torch.from_numpy(p.Q0).pin_memory()
+        c_h = torch.empty((N, F, T, M), dtype=torch.complex64).pin_memory()
+        Q_h = torch.empty_like(Q0h).pin_memory()
+        W_h, H_h, g_h = (torch.empty_like(a).pin_memory() for a in (W0h, H0h, g0h))
+        nll_e2e = []
 
         def step_e2e(c):
             D.dfmnmf_set_observation(c, xh)           # pinned host -> device, inside the timed region
             D.dfmnmf_set_params(c, Q0h, W0h, H0h, g0h)
             D.dfmnmf_iterate(c, iters)
-            D.dfmnmf_loglik(c)
+            nll_e2e.append(D.dfmnmf_loglik(c))        # Eq. 12 to the host (synchronises)
             D.dfmnmf_separate(c, c_out)
+            c_h.copy_(c_out, non_blocking=True)       # separated images, device -> pinned host
+            D.dfmnmf_get_params(c, Q_h, W_h, H_h, g_h)  # final state, device -> pinned host
 
         for _ in range(2):
             step_e2e(ctx)
@@ -621,9 +650,12 @@ def main():
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e2e_ms = float(t.item())
         h2d = xh.numel() * 8 + (W0h.numel() + H0h.numel() + g0h.numel()) * 4 + Q0h.numel() * 16
+        d2h = (8 + 16 + c_h.numel() * 8 + Q_h.numel() * 16 + (W_h.numel() + H_h.numel() + g_h.numel()) * 4)
         out["e2e"] = {"value": replica_value(e2e_ms, world, iters, args.steps), "unit": UNIT,
-                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8 + 16,
-                      "ms_per_step": e2e_ms / args.steps}
+                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                      "ms_per_step": e2e_ms / args.steps,
+                      "d2h": "the cost (8 B) and device flags (16 B), the separated images complex64 [N][F][T][M], "
+                             "the final Q, W, H and g"}
 
     # independent mixtures of the same shape run concurrently, one stream and one context each
     if args.concurrent > 1:
@@ -672,27 +704,39 @@ def main():
     if not args.no_adjoint and world == 1:
         out["adjoint"] = adjoint_measurement(D, synth, torch, timed)
 
-    # variants on the same GPU: native-FP64 and plain-FP32 IP solves (FP32 form)
+    # variants on the same GPU: native-FP64 and plain-FP32 IP solves (FP32 form), and the tensor-core form
+    # with native-FP64 IP solves (the headline tensor-core form solves in float pairs)
     if not args.no_variants:
         var = {}
-        for name, ipv in (("ip_f64", D.DFMNMF_IP_F64), ("ip_f32", D.DFMNMF_IP_F32)):
-            if ipv == ip:
+        for name, ipv, prec in (("ip_f64", D.DFMNMF_IP_F64, D.DFMNMF_FP32), ("ip_f32", D.DFMNMF_IP_F32, D.DFMNMF_FP32),
+                                ("bf16tc_ip_f64", D.DFMNMF_IP_F64, D.DFMNMF_BF16_TC)):
+            if ipv == ip and prec == precisions[forms[0]]:
                 continue
-            c2 = D.dfmnmf_init(F, T, p.mics, N, Bb, x_d, W0_d, H0_d, g0_d, Q0_d, ip_arith=ipv)
+            c2 = D.dfmnmf_init(F, T, p.mics, N, Bb, x_d, W0_d, H0_d, g0_d, Q0_d, ip_arith=ipv, precision=prec)
+            D.dfmnmf_autotune(c2, 3)
             for _ in range(2):
                 step(c2)
             ms = timed(step, c2, max(2, args.steps // 2))
             n2 = max(2, args.steps // 2)
             var[name] = {"value": world * iters * n2 / (ms / 1000.0), "unit": UNIT,
+                         "form": "bf16tc" if prec == D.DFMNMF_BF16_TC else "fp32",
+                         "ip_arith": {D.DFMNMF_IP_F64: "f64", D.DFMNMF_IP_F32: "f32",
+                                      D.DFMNMF_IP_F32X2: "f32x2"}[ipv],
+                         "nll_last": nll_box[-1],
                          "k_ip_ms": dict(D.dfmnmf_kernel_times(c2, 10)).get("k_ip")}
             D.dfmnmf_destroy(c2)
         out["variants"] = var
 
     if rank == 0 and world == 1 and not args.no_cpu:
         s = run_oracle_sample(args.workload, args.cpu_seconds)
-        out["cpu_baseline"] = {"value": s["iters"] / s["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
-                               "sample": f"{s['iters']} MM iterations of the FP64 oracle on the same workload "
-                                         f"({s['seconds']:.1f} s, one thread)"}
+        sa = run_oracle_sample_allcores(args.workload, args.cpu_seconds)
+        out["cpu_baseline"] = {
+            "value": sa["iters"] / sa["seconds"], "unit": UNIT, "cores": sa["workers"], "kind": "oracle",
+            "sample": f"{sa['iters']} MM iterations of the FP64 oracle on the same workload ({sa['seconds']:.1f} s), "
+                      f"its bins split over {sa['workers']} worker processes, one thread each",
+            "single_thread": {"value": s["iters"] / s["seconds"], "unit": UNIT, "cores": 1,
+                              "sample": f"{s['iters']} MM iterations of the FP64 oracle ({s['seconds']:.1f} s, "
+                                        f"one thread)"}}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
