@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--workload", default="paper_4x4_n5")
     ap.add_argument("--iters", type=int, default=None, help="MM iterations per step (default: the workload's)")
     ap.add_argument("--ip", choices=["f32x2", "f64", "f32"], default="f32x2")
-    ap.add_argument("--forms", default="bf16tc,fp32,allmic",
+    ap.add_argument("--forms", default="bf16tc,tf32tc,fp32,allmic",
                     help="comma list of forms to time (allmic: conventional FastMNMF with one full M x M "
                          "diagonaliser, the comparator); the first is the headline value")
     ap.add_argument("--no-e2e", action="store_true")
@@ -138,6 +138,7 @@ def kernel_bytes(F, T, M, N, B, K, MK):
         "k_ip": 8 * q * MK + 32 * q + 8 * q,
         "k_pstats": 8 * F * T * M + 4 * N * F * T + 4 * F * N * M + 8 * q + 4 * F * T * M + 8 * N * F * T,
         "k_wupd": 8 * N * F * T + 4 * N * B * T + 8 * N * F * B + 4 * N * F * T,
+        "k_wupd_tc": 8 * N * F * T + 4 * N * B * T + 8 * N * F * B,
         "k_stats": 4 * F * T * M + 4 * N * F * T + 4 * F * N * M + 8 * N * F * T,
         "k_hupd": 8 * N * F * T + 4 * N * F * B + 8 * N * B * T + 4 * N * F * T,
         "k_gupd": 4 * N * F * T + 4 * F * T * M + 8 * F * N * M,
@@ -460,12 +461,13 @@ def main():
     c_out = torch.empty((N, F, T, M), dtype=torch.complex64, device=dev)
     flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    precisions = {"bf16tc": D.DFMNMF_BF16_TC, "fp32": D.DFMNMF_FP32, "allmic": D.DFMNMF_FP32}
+    precisions = {"bf16tc": D.DFMNMF_BF16_TC, "tf32tc": D.DFMNMF_TF32_TC, "fp32": D.DFMNMF_FP32,
+                  "allmic": D.DFMNMF_FP32}
     # conventional all-microphone FastMNMF on the same observation: one 16 x 16 block per bin
     allmic = (M,)
     Q0_all_d = torch.from_numpy(synth.identity_blocks(F, allmic)).to(dev)
-    form_mics = {"bf16tc": p.mics, "fp32": p.mics, "allmic": allmic}
-    form_q0 = {"bf16tc": Q0_d, "fp32": Q0_d, "allmic": Q0_all_d}
+    form_mics = {"bf16tc": p.mics, "tf32tc": p.mics, "fp32": p.mics, "allmic": allmic}
+    form_q0 = {"bf16tc": Q0_d, "tf32tc": Q0_d, "fp32": Q0_d, "allmic": Q0_all_d}
     ctx_q0 = {}
     shapes = {}
     forms = [f.strip() for f in args.forms.split(",") if f.strip()]
@@ -708,12 +710,16 @@ def main():
     # with native-FP64 IP solves (the headline tensor-core form solves in float pairs)
     if not args.no_variants:
         var = {}
-        for name, ipv, prec in (("ip_f64", D.DFMNMF_IP_F64, D.DFMNMF_FP32), ("ip_f32", D.DFMNMF_IP_F32, D.DFMNMF_FP32),
-                                ("bf16tc_ip_f64", D.DFMNMF_IP_F64, D.DFMNMF_BF16_TC)):
-            if ipv == ip and prec == precisions[forms[0]]:
+        for name, ipv, prec, wtc in (("ip_f64", D.DFMNMF_IP_F64, D.DFMNMF_FP32, 0),
+                                     ("ip_f32", D.DFMNMF_IP_F32, D.DFMNMF_FP32, 0),
+                                     ("bf16tc_ip_f64", D.DFMNMF_IP_F64, D.DFMNMF_BF16_TC, 0),
+                                     ("bf16tc_wupd_tc", ip, D.DFMNMF_BF16_TC, 1)):
+            if ipv == ip and prec == precisions[forms[0]] and not wtc:
                 continue
             c2 = D.dfmnmf_init(F, T, p.mics, N, Bb, x_d, W0_d, H0_d, g0_d, Q0_d, ip_arith=ipv, precision=prec)
             D.dfmnmf_autotune(c2, 3)
+            if wtc:  # W-update products on the tensor cores (tcgen05 kind::tf32) instead of the CUDA cores
+                D.dfmnmf_set_option(c2, D.DFMNMF_OPT_WUPD_TC, 1)
             for _ in range(2):
                 step(c2)
             ms = timed(step, c2, max(2, args.steps // 2))
@@ -723,7 +729,8 @@ def main():
                          "ip_arith": {D.DFMNMF_IP_F64: "f64", D.DFMNMF_IP_F32: "f32",
                                       D.DFMNMF_IP_F32X2: "f32x2"}[ipv],
                          "nll_last": nll_box[-1],
-                         "k_ip_ms": dict(D.dfmnmf_kernel_times(c2, 10)).get("k_ip")}
+                         "k_ip_ms": dict(D.dfmnmf_kernel_times(c2, 10)).get("k_ip"),
+                         "w_update_ms": {k: v for k, v in D.dfmnmf_kernel_times(c2, 10) if k.startswith("k_wupd")}}
             D.dfmnmf_destroy(c2)
         out["variants"] = var
 

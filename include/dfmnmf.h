@@ -69,19 +69,26 @@ typedef enum dfmnmf_status {
   DFMNMF_ENOMEM = 2,   /* device allocation failed */
   DFMNMF_ECUDA = 3,    /* a CUDA runtime call failed (message has the detail) */
   DFMNMF_ENUMERIC = 4, /* a NaN or Inf was produced by an update */
-  DFMNMF_ETIMEOUT = 5  /* a bounded device wait gave up (reserved) */
+  DFMNMF_ETIMEOUT = 5  /* a bounded device wait gave up (see DFMNMF_OPT_WAIT_CYCLES);
+                          destroy the context afterwards                       */
 } dfmnmf_status;
 
 /* Arithmetic of the weighted-covariance contraction (Eq. 13). */
 typedef enum dfmnmf_precision {
   DFMNMF_FP32 = 0,    /* CUDA cores: x x^H and the weights as exact float pairs
                          (float-float sums), for ill-conditioned covariances     */
-  DFMNMF_BF16_TC = 1, /* tensor cores (tcgen05): x x^H and 1/yhat each split in
-                         two bfloat16 parts, three products, FP32 accumulation;
-                         M_k = 4 with K in {1, 2, 4, 8}.  The NMF products stay
-                         FP32 on the CUDA cores in both forms                    */
-  DFMNMF_TF32_TC = 2  /* reserved: returns DFMNMF_EINVAL (TF32 operands miss the
-                         accuracy of the split bfloat16 form)                   */
+  DFMNMF_BF16_TC = 1, /* tensor cores (tcgen05 kind::f16): x x^H and 1/yhat each
+                         split in two bfloat16 parts (hi = round to nearest,
+                         lo = rest), all four products, FP32 accumulation;
+                         M_k = 4 with K in {1, 2, 4, 8}                         */
+  DFMNMF_TF32_TC = 2  /* tensor cores (tcgen05 kind::tf32): the same split with
+                         TF32 parts (hi = round to nearest TF32, lo = rest), the
+                         parts side by side on the contraction axis; same
+                         layouts.  Measured about three times less accurate than
+                         the bfloat16 form on the 4 x 4-mic workload.  In both
+                         tensor-core forms the NMF products run on the CUDA
+                         cores unless DFMNMF_OPT_WUPD_TC moves the W update's
+                         onto the tensor cores                                  */
 } dfmnmf_precision;
 
 /* Arithmetic of the M_k x M_k iterative-projection solves (Eqs. 14-15). */
@@ -229,6 +236,35 @@ int dfmnmf_cost_gradient(dfmnmf_ctx* ctx, void* dQ, float* dW, float* dH, float*
  * rounding (the split changes the order of the NMF sums).
  */
 int dfmnmf_autotune(dfmnmf_ctx* ctx, int iters_per_trial, int* branches, int* nmf_ctas, void* stream);
+
+/*
+ * Launch options of a context, set by hand (no counterpart in the paper; a
+ * GPU concern).  dfmnmf_autotune sets the first three by measurement.
+ *   DFMNMF_OPT_BRANCHES    1 or 2 graph branches for the per-frequency kernels
+ *                          (FP32 form; the tensor-core forms use 1)
+ *   DFMNMF_OPT_NMF_CTAS    2, 4 or 8: CTAs per SM the split NMF products aim for
+ *   DFMNMF_OPT_VX_GROUPS   1 or 2 groups of converter warps in the tensor-core
+ *                          covariance kernel
+ *   DFMNMF_OPT_WUPD_TC     0: the W-update products (Eq. 8) on the CUDA cores;
+ *                          1: on the tensor cores (tcgen05 kind::tf32), for the
+ *                          tensor-core forms only
+ *   DFMNMF_OPT_WAIT_CYCLES budget, in SM clock cycles (default 2e9, ~1 s), of
+ *                          the pipeline waits of the tensor-core covariance
+ *                          kernel; a wait that runs out ends the kernel with
+ *                          DFMNMF_ETIMEOUT reported by the next synchronising
+ *                          call (the kernel still waits, with the full budget,
+ *                          for its copies and tensor-core work in flight before
+ *                          it exits).  A small value makes the failure path
+ *                          testable; the context is not usable afterwards.
+ * Results are identical under every choice up to rounding.  Takes effect at the
+ * next captured iteration (the captured graph is rebuilt).  DFMNMF_EINVAL for
+ * an unknown option or value; DFMNMF_OPT_WUPD_TC = 1 on the FP32 form is
+ * EINVAL.  dfmnmf_get_option returns the value, or -1.
+ */
+enum { DFMNMF_OPT_BRANCHES = 1, DFMNMF_OPT_NMF_CTAS = 2, DFMNMF_OPT_VX_GROUPS = 3, DFMNMF_OPT_WUPD_TC = 4,
+       DFMNMF_OPT_WAIT_CYCLES = 5 };
+int dfmnmf_set_option(dfmnmf_ctx* ctx, int option, int value);
+int dfmnmf_get_option(const dfmnmf_ctx* ctx, int option);
 
 /*
  * Many mixtures, one CUDA graph launch per iteration (no counterpart in the

@@ -59,7 +59,7 @@ void free_ctx(dfmnmf_ctx* c) {
   if (c->fork_ev) cudaEventDestroy(c->fork_ev);
   if (c->join_ev) cudaEventDestroy(c->join_ev);
   void* ptrs[] = {c->x, c->Q64, c->Q32, c->Qinv32, c->V, c->Vdd, c->W, c->H, c->g, c->lam,
-                  c->P, c->A, c->D, c->red, c->nll_dev, c->flags, c->nmf_part, c->nmf_ticket, c->tc_part, c->tc_ticket, c->gQ, c->gW, c->gH, c->gg};
+                  c->P, c->A, c->D, c->red, c->nll_dev, c->flags, c->nmf_part, c->nmf_ticket, c->tc_part, c->tc_ticket, c->wtc_part, c->wtc_ticket, c->gQ, c->gW, c->gH, c->gg};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -113,11 +113,14 @@ struct Launch {
 
 int iteration_launches(const dfmnmf_ctx* c, Launch* out) {
   int n = 0;
-  if (c->precision == DFMNMF_BF16_TC) out[n++] = {DFMNMF_STAGE_COV, "k_vtc", dfm::launch_vtc, true};
+  if (dfm::is_tc(c->precision)) out[n++] = {DFMNMF_STAGE_COV, "k_vtc", dfm::launch_vtc, true};
   else out[n++] = {DFMNMF_STAGE_COV, "k_cov", dfm::launch_cov, true};
   out[n++] = {DFMNMF_STAGE_IP, "k_ip", dfm::launch_ip, true};
   out[n++] = {DFMNMF_STAGE_W, "k_pstats", dfm::launch_power_stats, true};
-  out[n++] = {DFMNMF_STAGE_W, "k_wupd", [](const dfmnmf_ctx* c, cudaStream_t s, int, int) { return dfm::launch_wupd(c, s); }, false};
+  if (dfm::is_tc(c->precision) && c->cfg_wupd_tc)
+    out[n++] = {DFMNMF_STAGE_W, "k_wupd_tc", [](const dfmnmf_ctx* c, cudaStream_t s, int, int) { return dfm::launch_wupd_tc(c, s); }, false};
+  else
+    out[n++] = {DFMNMF_STAGE_W, "k_wupd", [](const dfmnmf_ctx* c, cudaStream_t s, int, int) { return dfm::launch_wupd(c, s); }, false};
   out[n++] = {DFMNMF_STAGE_W, "k_lambda", [](const dfmnmf_ctx* c, cudaStream_t s, int, int) { return dfm::launch_lambda(c, s); }, false};
   out[n++] = {DFMNMF_STAGE_H, "k_stats", [](const dfmnmf_ctx* c, cudaStream_t s, int, int) { return dfm::launch_stats(c, s); }, false};
   out[n++] = {DFMNMF_STAGE_H, "k_hupd", [](const dfmnmf_ctx* c, cudaStream_t s, int, int) { return dfm::launch_hupd(c, s); }, false};
@@ -143,7 +146,7 @@ int enqueue_stage(dfmnmf_ctx* c, int stage, cudaStream_t s) {
 // form is not split: its covariance kernel is persistent over the whole band
 // and its partial-sum slots serve one launch at a time.
 int band_split(const dfmnmf_ctx* c) {
-  if (c->cfg_branches == 1 || c->precision == DFMNMF_BF16_TC) return 0;
+  if (c->cfg_branches == 1 || dfm::is_tc(c->precision)) return 0;
   const int h = ((c->F / 2) + 7) & ~7;
   return (h > 0 && h < c->F) ? h : 0;
 }
@@ -237,9 +240,9 @@ int dfmnmf_init(dfmnmf_ctx** out, const dfmnmf_desc* d, const void* x, const flo
   if (MK > 4 && !(MK == 16 && d->K == 1))
     return fail(DFMNMF_EINVAL, "subarray size M_k=%d: this release supports 1..4, or 16 with K = 1 (all-microphone form)",
                 MK);
-  if (d->precision != DFMNMF_FP32 && d->precision != DFMNMF_BF16_TC)
+  if (d->precision != DFMNMF_FP32 && !dfm::is_tc(d->precision))
     return fail(DFMNMF_EINVAL, "precision %d is not built in this release", d->precision);
-  if (d->precision == DFMNMF_BF16_TC && !dfm::tc_supported(MK, d->K))
+  if (dfm::is_tc(d->precision) && !dfm::tc_supported(MK, d->K))
     return fail(DFMNMF_EINVAL, "the tensor-core form needs M_k = 4 and K in {1, 2, 4, 8} (M_k=%d K=%d)", MK, d->K);
   if (d->ip_arith < 0 || d->ip_arith > 2) return fail(DFMNMF_EINVAL, "unknown ip_arith %d", d->ip_arith);
 
@@ -260,6 +263,7 @@ int dfmnmf_init(dfmnmf_ctx** out, const dfmnmf_desc* d, const void* x, const flo
   if (cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device) != cudaSuccess)
     c->smem_optin = 232448;
   c->cfg_vx_groups = 2;
+  c->wait_cycles = 2000000000u;  // ~1 s at 2 GHz
   c->cfg_branches = 2;
   c->cfg_nmf_ctas = 4;
   int r = 0;
@@ -278,9 +282,11 @@ int dfmnmf_init(dfmnmf_ctx** out, const dfmnmf_desc* d, const void* x, const flo
     free_ctx(c);
     return r;
   }
-  if (c->precision == DFMNMF_BF16_TC) {
+  if (dfm::is_tc(c->precision)) {
     if ((r = dalloc(&c->tc_part, dfm::tc_part_float4s(c), "tensor-core partial sums")) ||
-        (r = dalloc(&c->tc_ticket, dfm::tc_ticket_count(c), "tensor-core tickets"))) {
+        (r = dalloc(&c->tc_ticket, dfm::tc_ticket_count(c), "tensor-core tickets")) ||
+        (r = dalloc(&c->wtc_part, dfm::wupd_tc_scratch_float2s(c), "tensor-core W-update parts")) ||
+        (r = dalloc(&c->wtc_ticket, dfm::wupd_tc_ticket_count(c), "tensor-core W-update tickets"))) {
       free_ctx(c);
       return r;
     }
@@ -320,6 +326,7 @@ int dfmnmf_init(dfmnmf_ctx** out, const dfmnmf_desc* d, const void* x, const flo
   CKI(cudaMemsetAsync(c->A, 0, (size_t)c->N * c->F * c->Tp * sizeof(float), s));
   CKI(cudaMemsetAsync(c->D, 0, (size_t)c->N * c->F * c->Tp * sizeof(float), s));
   if (c->tc_ticket) CKI(cudaMemsetAsync(c->tc_ticket, 0, dfm::tc_ticket_count(c) * sizeof(unsigned), s));
+  if (c->wtc_ticket) CKI(cudaMemsetAsync(c->wtc_ticket, 0, dfm::wupd_tc_ticket_count(c) * sizeof(unsigned), s));
   if ((r = refresh_derived(c, s))) return bail(r);
 #undef CKI
   *out = c;
@@ -349,6 +356,50 @@ int dfmnmf_run_stage(dfmnmf_ctx* c, int stage, void* stream) {
   if (stage < DFMNMF_STAGE_COV || stage > DFMNMF_STAGE_G) return fail(DFMNMF_EINVAL, "unknown stage %d", stage);
   CK(cudaSetDevice(c->device));
   return enqueue_stage(c, stage, as_stream(stream));
+}
+
+int dfmnmf_set_option(dfmnmf_ctx* c, int option, int value) {
+  if (!c) return fail(DFMNMF_EINVAL, "null context");
+  switch (option) {
+    case DFMNMF_OPT_BRANCHES:
+      if (value != 1 && value != 2) return fail(DFMNMF_EINVAL, "branches must be 1 or 2 (got %d)", value);
+      c->cfg_branches = value;
+      break;
+    case DFMNMF_OPT_NMF_CTAS:
+      if (value != 2 && value != 4 && value != 8) return fail(DFMNMF_EINVAL, "nmf_ctas must be 2, 4 or 8 (got %d)", value);
+      c->cfg_nmf_ctas = value;
+      break;
+    case DFMNMF_OPT_VX_GROUPS:
+      if (value != 1 && value != 2) return fail(DFMNMF_EINVAL, "vx_groups must be 1 or 2 (got %d)", value);
+      c->cfg_vx_groups = value;
+      break;
+    case DFMNMF_OPT_WUPD_TC:
+      if (value != 0 && value != 1) return fail(DFMNMF_EINVAL, "wupd_tc must be 0 or 1 (got %d)", value);
+      if (value == 1 && !dfm::is_tc(c->precision))
+        return fail(DFMNMF_EINVAL, "the tensor-core W update belongs to the tensor-core forms");
+      c->cfg_wupd_tc = value;
+      break;
+    case DFMNMF_OPT_WAIT_CYCLES:
+      if (value < 1) return fail(DFMNMF_EINVAL, "wait_cycles must be positive (got %d)", value);
+      c->wait_cycles = (unsigned)value;
+      break;
+    default:
+      return fail(DFMNMF_EINVAL, "unknown option %d", option);
+  }
+  drop_graph(c);
+  return DFMNMF_OK;
+}
+
+int dfmnmf_get_option(const dfmnmf_ctx* c, int option) {
+  if (!c) return -1;
+  switch (option) {
+    case DFMNMF_OPT_BRANCHES: return c->cfg_branches;
+    case DFMNMF_OPT_NMF_CTAS: return c->cfg_nmf_ctas;
+    case DFMNMF_OPT_VX_GROUPS: return c->cfg_vx_groups;
+    case DFMNMF_OPT_WUPD_TC: return c->cfg_wupd_tc;
+    case DFMNMF_OPT_WAIT_CYCLES: return c->wait_cycles > 0x7fffffffu ? 0x7fffffff : (int)c->wait_cycles;
+    default: return -1;
+  }
 }
 
 int dfmnmf_launches_per_iteration(const dfmnmf_ctx* c) {
@@ -479,7 +530,7 @@ int dfmnmf_autotune(dfmnmf_ctx* c, int iters_per_trial, int* branches, int* nmf_
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   // first option: graph branches of the per-frequency kernels (FP32 form) or converter warp groups of the
   // persistent covariance kernel (tensor-core form, one branch); second: CTAs per SM of the NMF products
-  const bool tc = c->precision == DFMNMF_BF16_TC;
+  const bool tc = dfm::is_tc(c->precision);
   const int old_br = c->cfg_branches, old_ct = c->cfg_nmf_ctas, old_vx = c->cfg_vx_groups;
   int best_br = old_br, best_ct = old_ct, best_vx = old_vx;
   float best = INFINITY;

@@ -43,8 +43,12 @@ struct dfmnmf_ctx {
   // tensor-core form (k_vtc): FP32 partial sums of tiles shared by two CTAs and one ticket per tile
   float4* tc_part;
   unsigned* tc_ticket;
+  float2* wtc_part;    // tensor-core forms: FP32 parts of the W-update products (k_wupd_tc) ...
+  unsigned* wtc_ticket;  // ... and one ticket per (source, 128-bin tile)
   int smem_optin;      // opt-in shared memory per block of the device
   int cfg_vx_groups;   // converter warp groups of k_vtc (1 or 2)
+  int cfg_wupd_tc;     // tensor-core forms: W-update products on the tensor cores (k_wupd_tc) when 1
+  unsigned wait_cycles;  // budget of the pipeline waits of the tensor-core covariance kernel
   size_t red_len;
   // CUDA graph of one iteration, captured on first use
   cudaStream_t cap_stream;
@@ -56,6 +60,9 @@ struct dfmnmf_ctx {
 };
 
 namespace dfm {
+
+// The tensor-core forms (bfloat16 or TF32 split operands of the covariance contraction).
+inline bool is_tc(int precision) { return precision == 1 || precision == 2; }
 
 // All launchers return cudaGetLastError() after enqueueing.
 cudaError_t launch_lambda(const dfmnmf_ctx* c, cudaStream_t s);
@@ -72,6 +79,9 @@ cudaError_t launch_power_stats(const dfmnmf_ctx* c, cudaStream_t s, int fb, int 
 // otherwise the gradient of Eq. (12) with respect to it (den - num of the
 // rule) is written there and the factor is left unchanged.
 cudaError_t launch_wupd(const dfmnmf_ctx* c, cudaStream_t s, float* grad = nullptr);  // Eq. 8
+cudaError_t launch_wupd_tc(const dfmnmf_ctx* c, cudaStream_t s, float* grad = nullptr);  // Eq. 8, tcgen05 TF32
+size_t wupd_tc_scratch_float2s(const dfmnmf_ctx* c);
+size_t wupd_tc_ticket_count(const dfmnmf_ctx* c);
 cudaError_t launch_stats(const dfmnmf_ctx* c, cudaStream_t s);        // A/D from stored P
 cudaError_t launch_hupd(const dfmnmf_ctx* c, cudaStream_t s, float* grad = nullptr);  // Eq. 9
 cudaError_t launch_gupd(const dfmnmf_ctx* c, cudaStream_t s, float* grad = nullptr);  // Eq. 10

@@ -168,17 +168,14 @@ __global__ void __launch_bounds__(128) k_ip(const double2* __restrict__ V, const
       float mpf = INFINITY;
 #pragma unroll
       for (int c = 0; c < MK; ++c) {
-        float key = (act && j == c && i >= c) ? cabs2_f(af) : -1.f;
-        int prow = i;
+        // pivot row: the largest |a_ic|, i >= c, among the M_k lanes of column c (xor steps of M_k lanes),
+        // magnitude and row packed in one word (low three bits 7 - i: the lower row wins a tie), then
+        // broadcast from lane (0, c); the singularity decision of this path does not depend on near ties
+        unsigned key = (act && j == c && i >= c) ? ((__float_as_uint(cabs2_f(af)) & ~7u) | (unsigned)(7 - i)) : 0u;
 #pragma unroll
-        for (int o = 8; o > 0; o >>= 1) {
-          const float ok = __shfl_xor_sync(DFM_FULL_MASK, key, o);
-          const int orow = __shfl_xor_sync(DFM_FULL_MASK, prow, o);
-          if (ok > key || (ok == key && orow < prow)) {
-            key = ok;
-            prow = orow;
-          }
-        }
+        for (int o = MK; o < MK * MK; o <<= 1) key = max(key, __shfl_xor_sync(DFM_FULL_MASK, key, o));
+        key = __shfl_sync(DFM_FULL_MASK, key, L(0, c));
+        const int prow = 7 - (int)(key & 7u);
         int src = lane;
         if (act && i == c) src = L(prow, j);
         else if (act && i == prow) src = L(c, j);
@@ -633,7 +630,7 @@ cudaError_t launch_ip(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
     switch (c->ip_arith) {
       case 0: k_ip<MK_, double><<<grid, 128, 0, s>>>(c->V + o * MK_ * MK_ * MK_, c->Vdd + o * MK_ * MK_ * MK_, c->Q64 + o * MK_ * MK_, c->Q32 + o * MK_ * MK_, nblocks, c->eps, c->singular_rtol, c->flags); break;
       case 1:
-        if (c->precision == DFMNMF_BF16_TC)
+        if (is_tc(c->precision))
           k_ip<MK_, dd, 1><<<grid, 128, 0, s>>>(c->V + o * MK_ * MK_ * MK_, c->Vdd + o * MK_ * MK_ * MK_, c->Q64 + o * MK_ * MK_, c->Q32 + o * MK_ * MK_, nblocks, c->eps, c->singular_rtol, c->flags);
         else
           k_ip<MK_, dd><<<grid, 128, 0, s>>>(c->V + o * MK_ * MK_ * MK_, c->Vdd + o * MK_ * MK_ * MK_, c->Q64 + o * MK_ * MK_, c->Q32 + o * MK_ * MK_, nblocks, c->eps, c->singular_rtol, c->flags);

@@ -36,120 +36,54 @@
 // Supported layouts: M_k = 4 and K in {1, 2, 4, 8}.  Every mbarrier wait is
 // bounded; a wait that gives up sets FLAG_TIMEOUT, the CTA drains its copies
 // in flight and its tensor-core work, frees its tensor memory and returns.
+// The pipeline waits use the context's budget (`budget` cycles, ~1 s unless
+// set otherwise); the waits that drain copies and tensor-core work before the
+// CTA exits always use the full ~1 s budget, so no copy or MMA can outlive it.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "../../include/dfmnmf.h"
 #include "common.cuh"
 #include "internal.h"
+#include "tc_ptx.cuh"
 
 namespace dfm {
 
-constexpr unsigned TC_WAIT_CYCLES = 2000000000u;  // ~1 s at 2 GHz
-
-// ------------------------------------------------------------ PTX helpers
-__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
-  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
-  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-// Wait for the phase with the given parity to complete; false on timeout.
-// Between polls the warp sleeps for about `sleep_ns` (0: poll again at once),
-// so that warps which wait most of the time (the epilogue, the single-thread
-// producer and MMA issuer) leave the issue slots to the converter warps.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, unsigned sleep_ns = 0) {
-  const unsigned addr = smem_u32(bar);
-  const unsigned start = (unsigned)clock();
-  while (true) {
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(addr), "r"(parity)
-        : "memory");
-    if (ok) return true;
-    if ((unsigned)clock() - start > TC_WAIT_CYCLES) return false;  // wrap-safe: the budget is below 2^32
-    if (sleep_ns) __nanosleep(sleep_ns);
-  }
-}
-// The same wait by every lane of a warp, with one warp-uniform result.
-__device__ __forceinline__ bool mbar_wait_warp(unsigned long long* bar, unsigned parity, unsigned sleep_ns = 0) {
-  return __all_sync(DFM_FULL_MASK, mbar_wait(bar, parity, sleep_ns)) != 0;
-}
-
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
-                                            unsigned long long* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-      "[%5];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
-                                            unsigned long long* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
-      "[%6];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, int c0, int c1, int c2, const void* src) {
-  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
-                   reinterpret_cast<unsigned long long>(map)),
-               "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(src))
-               : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major operand tile with 128-byte
-// swizzle, 8-row groups 1024 bytes apart (stride byte offset), descriptor
-// version 1, base offset 0.
-__device__ __forceinline__ unsigned long long smem_desc_sw128(unsigned addr) {
-  unsigned long long d = 0;
-  d |= (unsigned long long)((addr >> 4) & 0x3FFF);
-  d |= (unsigned long long)(1) << 16;              // leading byte offset (unused by swizzled K-major)
-  d |= (unsigned long long)((1024 >> 4) & 0x3FFF) << 32;
-  d |= 1ull << 46;                                 // version
-  d |= 2ull << 61;                                 // 128-byte swizzle
-  return d;
-}
-
 // ------------------------------------------------------ fused contraction
-constexpr int VX_KC = 64;                         // frames per chunk (one 128-byte bfloat16 row)
 constexpr int VX_ROWS = 128;                      // MMA M: rows (frequency, subarray, packed entry)
 constexpr int VX_WROWS = 32;                      // rows (frequency, microphone) of one weight part
 constexpr int VX_N = 2 * VX_WROWS;                // MMA N: w_hi rows, then w_lo rows
-constexpr int VX_X_BYTES = 16384;                 // raw x tile: 8/K frequencies x 64 frames x 4K complex64
-constexpr int VX_A_BYTES = VX_ROWS * VX_KC * 2;   // 16 KB per R part
-constexpr int VX_B_BYTES = VX_N * VX_KC * 2;      // 8 KB (both w parts)
-constexpr int VX_OP_BYTES = 2 * VX_A_BYTES + VX_B_BYTES;
+constexpr int VX_A_BYTES = VX_ROWS * 128;         // 16 KB: one 128-row region of 128-byte rows
+// Per operand type.  bfloat16 (TF = false): chunks of 64 frames, R_hi and R_lo in two A regions, the
+// B tile 64 rows of 64 frames.  TF32 (TF = true): chunks of 32 frames, the split kept along the
+// contraction axis -- position 2 t holds the high part of frame t, 2 t + 1 its low part, and both
+// positions of B hold w(t) -- so a row of A is 64 values in two 128-byte regions (frames 0..15,
+// 16..31), and B is two 64-row regions.
+template <bool TF> struct VxCfg {
+  static constexpr int KC = TF ? 32 : 64;                         // frames per chunk
+  static constexpr int X_BYTES = TF ? 8192 : 16384;               // raw x tile: 8/K frequencies x KC frames x 4K complex64
+  static constexpr int B_BYTES = TF ? 2 * VX_N * 128 : VX_N * 128;
+  static constexpr int OP_BYTES = 2 * VX_A_BYTES + B_BYTES;       // 40 KB (bfloat16), 48 KB (TF32)
+};
 constexpr int VX_OS = 3;                          // operand stages (unit i uses i % 3)
 constexpr int VX_MAX_RS = 6;                      // raw stages at most
 constexpr int VX_CW = 8;                          // converter warps per group: the 8 (frequency, subarray) pairs
-constexpr int VX_EPI_WARP = 2;                    // warps 2..5: epilogue
+constexpr int VX_PROD_WARP = 0;                   // TMA producer
+constexpr int VX_MMA_WARP = 1;                    // MMA issuer
+constexpr int VX_EPI_WARP = 2;                    // warps 2..5: epilogue (four consecutive warps: every lane quadrant)
 constexpr int VX_CONV_WARP = 6;                   // warps 6..: converters
 constexpr int VX_ACC_COLS = 64;                   // tensor-memory columns per accumulator buffer
 
-// Instruction descriptor, kind::f16: D FP32, A and B bfloat16, both K-major, N = 64, M = 128.
+// Instruction descriptors: D FP32 (bits 4-5 = 1), A and B of one type (bits 7-9, 10-12: bfloat16 = 1 under
+// kind::f16, TF32 = 2 under kind::tf32), both K-major, N = 64 (bits 17-22: N / 8), M = 128 (bits 24-28: M / 16).
 constexpr unsigned VX_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((VX_N >> 3) << 17) | ((VX_ROWS >> 4) << 24);
+constexpr unsigned VX_IDESC_TF32 = (1u << 4) | (2u << 7) | (2u << 10) | ((VX_N >> 3) << 17) | ((VX_ROWS >> 4) << 24);
 
 __device__ __forceinline__ void umma_bf16(unsigned tmem_d, unsigned long long a, unsigned long long b, unsigned acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
-          tmem_d),
-      "l"(a), "l"(b), "r"(VX_IDESC), "r"(acc)
-      : "memory");
+  umma_f16_id(tmem_d, a, b, VX_IDESC, acc);
 }
-__device__ __forceinline__ void umma_commit(unsigned long long* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
+__device__ __forceinline__ void umma_tf32(unsigned tmem_d, unsigned long long a, unsigned long long b, unsigned acc) {
+  umma_tf32_id(tmem_d, a, b, VX_IDESC_TF32, acc);
 }
 
 struct VxCtl {
@@ -212,12 +146,20 @@ __device__ __forceinline__ void vx_write_v(double2* __restrict__ V, float4* __re
   }
 }
 
+// Nearest TF32 value of x (round half away from zero), as an FP32 number with the low 13 bits zero.
+__device__ __forceinline__ float tf32_rna(float x) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
 // r = hi + lo with hi = bfloat16(r) (round to nearest) and lo = bfloat16(r - hi), for two frames at once.
-__device__ __forceinline__ void vx_split_store(unsigned char* hi, unsigned char* lo, float2 r) {
-  const __nv_bfloat162 h = __floats2bfloat162_rn(r.x, r.y);
-  const float2 d = __fadd2_rn(r, make_float2(-__low2float(h), -__high2float(h)));
+__device__ __forceinline__ void vx_split_store(unsigned char* hi, unsigned char* lo, float r0, float r1) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(r0, r1);
+  const float h0 = __uint_as_float((unsigned)__bfloat16_as_ushort(h.x) << 16);
+  const float h1 = __uint_as_float((unsigned)__bfloat16_as_ushort(h.y) << 16);
   *reinterpret_cast<__nv_bfloat162*>(hi) = h;
-  *reinterpret_cast<__nv_bfloat162*>(lo) = __floats2bfloat162_rn(d.x, d.y);
+  *reinterpret_cast<__nv_bfloat162*>(lo) = __floats2bfloat162_rn(r0 - h0, r1 - h1);
 }
 
 // The fused contraction; see the head of this file.  K subarrays of 4
@@ -228,19 +170,21 @@ __device__ __forceinline__ void vx_split_store(unsigned char* hi, unsigned char*
 // `part` holds one 128-row block of FP32 partial sums per (tile, CTA) pair
 // that shares a tile (slot tile - tb + CTA), `tickets` one counter per tile,
 // zero between launches (the CTA that completes a tile resets it).
-template <int K, int CG>
+template <int K, int CG, bool TF>
 __global__ void __launch_bounds__((VX_CONV_WARP + VX_CW * CG) * 32, 1)
     k_vtc(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_l,
           const __grid_constant__ CUtensorMap map_g, double2* __restrict__ V, float4* __restrict__ Vdd,
           float4* __restrict__ part, unsigned* __restrict__ tickets, int F, int T, int N, float eps, int tb,
-          int ntile, int nch, int RS, int stage_bytes, unsigned* __restrict__ flags) {
+          int ntile, int nch, int RS, int stage_bytes, unsigned budget, unsigned* __restrict__ flags) {
   constexpr int FPC = 8 / K, M = 4 * K;
   constexpr unsigned SWZ = (K == 1) ? 0x10u : (K == 2) ? 0x30u : 0x70u;  // 32-, 64-, 128-byte swizzle of x
   extern __shared__ __align__(1024) unsigned char vx_raw[];
   // 1024-byte alignment by an offset from the shared array (not by integer casts of the pointer), so that
   // the compiler keeps every derived pointer in the shared window (32-bit shared loads and stores)
   unsigned char* ops = vx_raw + ((1024u - (smem_u32(vx_raw) & 1023u)) & 1023u);
-  unsigned char* raw = ops + VX_OS * VX_OP_BYTES;
+  using Cfg = VxCfg<TF>;
+  constexpr int KC = Cfg::KC, X_BYTES = Cfg::X_BYTES, OP_BYTES = Cfg::OP_BYTES;
+  unsigned char* raw = ops + VX_OS * OP_BYTES;
   VxCtl* ctl = reinterpret_cast<VxCtl*>(raw + (size_t)RS * stage_bytes);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long U = (long long)ntile * nch;  // below 2^31 (checked at launch)
@@ -248,7 +192,7 @@ __global__ void __launch_bounds__((VX_CONV_WARP + VX_CW * CG) * 32, 1)
   const int u_begin = (int)((long long)blockIdx.x * U / G);
   const int nloc = (int)((long long)(blockIdx.x + 1) * U / G) - u_begin;
   const int c_begin = u_begin % nch;  // chunk of the CTA's first unit
-  const int lbytes = FPC * N * VX_KC * 4;  // lambda rows of one stage
+  const int lbytes = FPC * N * KC * 4;  // lambda rows of one stage
   volatile unsigned* abort_flag = &ctl->abort;
 
   if (tid == 0) {
@@ -279,64 +223,83 @@ __global__ void __launch_bounds__((VX_CONV_WARP + VX_CW * CG) * 32, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const unsigned tmem = ctl->tmem_base;
 
-  if (warp == 0) {
-    if (lane == 0) {
-      // ---- TMA producer
-      const unsigned tx = (unsigned)(VX_X_BYTES + lbytes + FPC * N * M * 4);
-      int issued = 0, tile = tb + u_begin / nch, c = c_begin;
-      for (int i = 0; i < nloc; ++i, c = (c + 1 == nch) ? (++tile, 0) : c + 1) {
-        const int s = i % RS;
-        if (i >= RS && !mbar_wait(&ctl->raw_empty[s], ((i / RS) - 1) & 1, 64)) {
-          atomicOr(&ctl->abort, 1u);
-          break;
-        }
-        if (*abort_flag) break;
-        unsigned char* st = raw + (size_t)s * stage_bytes;
-        mbar_arrive_expect_tx(&ctl->raw_full[s], tx);
-        if (K == 8) tma_load_4d(st, &map_x, 0, 0, c * VX_KC, tile, &ctl->raw_full[s]);
-        else tma_load_3d(st, &map_x, 0, c * VX_KC, tile * FPC, &ctl->raw_full[s]);
-        tma_load_3d(st + VX_X_BYTES, &map_l, c * VX_KC, tile * FPC, 0, &ctl->raw_full[s]);
-        tma_load_3d(st + VX_X_BYTES + lbytes, &map_g, 0, 0, tile * FPC, &ctl->raw_full[s]);
-        issued = i + 1;
+  if (warp == VX_PROD_WARP) {
+    // ---- TMA producer: the whole warp walks the units (warp-uniform control flow), one elected lane
+    // issues the copies
+    const unsigned tx = (unsigned)(X_BYTES + lbytes + FPC * N * M * 4);
+    int issued = 0, tile = tb + u_begin / nch, c = c_begin;
+    for (int i = 0; i < nloc; ++i, c = (c + 1 == nch) ? (++tile, 0) : c + 1) {
+      const int s = i % RS;
+      if (i >= RS && !mbar_wait_warp(&ctl->raw_empty[s], ((i / RS) - 1) & 1, 128, budget)) {
+        if (lane == 0) atomicOr(&ctl->abort, 1u);
+        break;
       }
-      // every copy issued has landed before the CTA moves on (bounded wait)
-      for (int i = issued > RS ? issued - RS : 0; i < issued; ++i)
-        if (!mbar_wait(&ctl->raw_full[i % RS], (i / RS) & 1, 64)) atomicOr(&ctl->abort, 1u);
+      if (__any_sync(DFM_FULL_MASK, *abort_flag != 0)) break;
+      unsigned char* st = raw + (size_t)s * stage_bytes;
+      if (elect_one()) {
+        mbar_arrive_expect_tx(&ctl->raw_full[s], tx);
+        if (K == 8) tma_load_4d(st, &map_x, 0, 0, c * KC, tile, &ctl->raw_full[s]);
+        else tma_load_3d(st, &map_x, 0, c * KC, tile * FPC, &ctl->raw_full[s]);
+        tma_load_3d(st + X_BYTES, &map_l, c * KC, tile * FPC, 0, &ctl->raw_full[s]);
+        tma_load_3d(st + X_BYTES + lbytes, &map_g, 0, 0, tile * FPC, &ctl->raw_full[s]);
+      }
+      __syncwarp();
+      issued = i + 1;
     }
-  } else if (warp == 1) {
-    if (lane == 0) {
-      // ---- MMA issuer: per chunk, R_hi (w_hi | w_lo) then R_lo (w_hi | w_lo), 16 frames per instruction
-      int sg = -1;
-      for (int i = 0, c = c_begin; i < nloc; ++i, c = (c + 1 == nch) ? 0 : c + 1) {
-        const bool first = (i == 0 || c == 0), last = (i == nloc - 1 || c == nch - 1);
-        if (first) {
-          ++sg;
-          if (sg >= 2 && !mbar_wait(&ctl->acc_empty[sg & 1], ((sg >> 1) - 1) & 1, 32)) {
-            atomicOr(&ctl->abort, 1u);
-            break;
-          }
-        }
-        const int os = i % VX_OS;
-        if (!mbar_wait(&ctl->op_full[os], (i / VX_OS) & 1, 32)) {
-          atomicOr(&ctl->abort, 1u);
+    // every copy issued has landed before the CTA moves on (bounded wait)
+    for (int i = issued > RS ? issued - RS : 0; i < issued; ++i)
+      if (!mbar_wait_warp(&ctl->raw_full[i % RS], (i / RS) & 1, 128) && lane == 0) atomicOr(&ctl->abort, 1u);
+  } else if (warp == VX_MMA_WARP) {
+    // ---- MMA issuer: the whole warp walks the units, one elected lane issues per chunk R_hi (w_hi | w_lo)
+    // then R_lo (w_hi | w_lo), 16 frames per instruction
+    const unsigned long long dstage0 = smem_desc_sw128(smem_u32(ops));
+    int sg = -1;
+    for (int i = 0, c = c_begin; i < nloc; ++i, c = (c + 1 == nch) ? 0 : c + 1) {
+      const bool first = (i == 0 || c == 0), last = (i == nloc - 1 || c == nch - 1);
+      if (first) {
+        ++sg;
+        if (sg >= 2 && !mbar_wait_warp(&ctl->acc_empty[sg & 1], ((sg >> 1) - 1) & 1, 32, budget)) {
+          if (lane == 0) atomicOr(&ctl->abort, 1u);
           break;
         }
-        if (*abort_flag) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const unsigned base = smem_u32(ops + os * VX_OP_BYTES);
-        const unsigned d = tmem + (unsigned)((sg & 1) * VX_ACC_COLS);
+      }
+      const int os = i % VX_OS;
+      if (!mbar_wait_warp(&ctl->op_full[os], (i / VX_OS) & 1, 32, budget)) {
+        if (lane == 0) atomicOr(&ctl->abort, 1u);
+        break;
+      }
+      if (__any_sync(DFM_FULL_MASK, *abort_flag != 0)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // descriptors of the stage: the start-address field (address / 16, 14 bits, no carry below 256 KB)
+      // advances by the byte offset / 16 of each tile and of each 16-frame step (32 bytes)
+      const unsigned long long da = dstage0 + (unsigned long long)((os * OP_BYTES) >> 4);
+      const unsigned d = tmem + (unsigned)((sg & 1) * VX_ACC_COLS);
+      if (elect_one()) {
+        if constexpr (TF) {
+          // 8 steps of 8 positions (4 frames, high and low parts): region s / 4, 32 bytes per step in it
 #pragma unroll
-        for (int kk = 0; kk < VX_KC / 16; ++kk) {
-          const unsigned long long b = smem_desc_sw128(base + 2 * VX_A_BYTES + kk * 32);
-          umma_bf16(d, smem_desc_sw128(base + kk * 32), b, (first && kk == 0) ? 0u : 1u);
-          umma_bf16(d, smem_desc_sw128(base + VX_A_BYTES + kk * 32), b, 1u);
+          for (int st8 = 0; st8 < 8; ++st8) {
+            const unsigned long long a = da + (unsigned long long)(((st8 >> 2) * VX_A_BYTES) >> 4) + 2 * (st8 & 3);
+            const unsigned long long b =
+                da + (unsigned long long)((2 * VX_A_BYTES + (st8 >> 2) * VX_N * 128) >> 4) + 2 * (st8 & 3);
+            umma_tf32(d, a, b, (first && st8 == 0) ? 0u : 1u);
+          }
+        } else {
+#pragma unroll
+          for (int kk = 0; kk < KC / 16; ++kk) {
+            const unsigned long long b = da + (unsigned long long)(((2 * VX_A_BYTES) >> 4) + 2 * kk);
+            umma_bf16(d, da + (unsigned long long)(2 * kk), b, (first && kk == 0) ? 0u : 1u);
+            umma_bf16(d, da + (unsigned long long)((VX_A_BYTES >> 4) + 2 * kk), b, 1u);
+          }
         }
         umma_commit(&ctl->op_empty[os]);
         if (last) umma_commit(&ctl->acc_full[sg & 1]);
       }
-      umma_commit(&ctl->done);
+      __syncwarp();
     }
-  } else if (warp < VX_CONV_WARP) {
+    if (elect_one()) umma_commit(&ctl->done);
+    __syncwarp();
+  } else if (warp >= VX_EPI_WARP && warp < VX_EPI_WARP + 4) {
     // ---- epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (row = lane)
     const int q = warp & 3, row = q * 32 + lane;
     const int pair = row >> 4, e = row & 15;
@@ -350,7 +313,7 @@ __global__ void __launch_bounds__((VX_CONV_WARP + VX_CW * CG) * 32, 1)
       const int len = min(nch - c0, nloc - i0);
       const bool full = (c0 == 0 && len == nch);
       ++sg;
-      const bool okw = mbar_wait(&ctl->acc_full[sg & 1], (sg >> 1) & 1, 256);
+      const bool okw = mbar_wait(&ctl->acc_full[sg & 1], (sg >> 1) & 1, 512, budget);
       if (!okw) atomicOr(&ctl->abort, 1u);
       if (epi_bar_or(!okw || *abort_flag)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -409,7 +372,7 @@ __global__ void __launch_bounds__((VX_CONV_WARP + VX_CW * CG) * 32, 1)
       }
       i0 += len;
     }
-  } else {
+  } else if (warp >= VX_CONV_WARP) {
     // ---- converters: warp cw of group grp forms rows 16 cw .. 16 cw + 15 of R (pair cw) and the w rows of
     // its four microphones for frames lane and lane + 32 of every CG-th chunk
     const int cw = (warp - VX_CONV_WARP) % VX_CW, grp = (warp - VX_CONV_WARP) / VX_CW;
@@ -419,67 +382,118 @@ __global__ void __launch_bounds__((VX_CONV_WARP + VX_CW * CG) * 32, 1)
     int c = (u_begin + grp) % nch;  // chunk of unit i, advanced by CG per step
     for (int i = grp; i < nloc; i += CG) {
       const int s = i % RS, os = i % VX_OS;
-      bool ok = mbar_wait_warp(&ctl->raw_full[s], (i / RS) & 1, 32);
-      if (ok && i >= VX_OS) ok = mbar_wait_warp(&ctl->op_empty[os], ((i / VX_OS) - 1) & 1, 32);
+      bool ok = mbar_wait_warp(&ctl->raw_full[s], (i / RS) & 1, 32, budget);
+      if (ok && i >= VX_OS) ok = mbar_wait_warp(&ctl->op_empty[os], ((i / VX_OS) - 1) & 1, 32, budget);
       if (!ok) {
         if (lane == 0) atomicOr(&ctl->abort, 1u);
         break;
       }
       if (__any_sync(DFM_FULL_MASK, *abort_flag != 0)) break;
       const unsigned char* st = raw + (size_t)s * stage_bytes;
-      const float* ls = reinterpret_cast<const float*>(st + VX_X_BYTES);
-      const float* gs = reinterpret_cast<const float*>(st + VX_X_BYTES + lbytes);
-      unsigned char* op = ops + os * VX_OP_BYTES;
-      // x of frames lane (.x) and lane + 32 (.y), real and imaginary parts, microphones 0..3 of the pair
-      float2 xr[4], xi[4];
+      const float* ls = reinterpret_cast<const float*>(st + X_BYTES);
+      const float* gs = reinterpret_cast<const float*>(st + X_BYTES + lbytes);
+      unsigned char* op = ops + os * OP_BYTES;
+      if constexpr (TF) {
+        // TF32: frame `lane` of the chunk.  R and w each split as hi = the value rounded to TF32 (cvt.rna)
+        // and lo = value - hi (exact); hi and lo of a frame are adjacent on the contraction axis, so each
+        // entry is one 8-byte store: region lane / 16, 16-byte chunk (lane % 16) / 2 of the row (swizzled
+        // with the row), half lane % 2.
+        float2 xv[4];
 #pragma unroll
-      for (int hh = 0; hh < 2; ++hh) {
-        const unsigned l0 = (unsigned)((fj * VX_KC + lane) * (8 * M) + k * 32 + hh * 16);
-        const unsigned l1 = l0 + 32u * (8 * M);
-        const float4 q0 = *reinterpret_cast<const float4*>(st + (l0 ^ ((l0 >> 3) & SWZ)));
-        const float4 q1 = *reinterpret_cast<const float4*>(st + (l1 ^ ((l1 >> 3) & SWZ)));
-        xr[2 * hh] = make_float2(q0.x, q1.x);
-        xi[2 * hh] = make_float2(q0.y, q1.y);
-        xr[2 * hh + 1] = make_float2(q0.z, q1.z);
-        xi[2 * hh + 1] = make_float2(q0.w, q1.w);
-      }
-      // R = x x^H, entry 4a + b: |x_a|^2 (a == b), Re x_a conj x_b (a < b), Im x_b conj x_a (a > b);
-      // both frames at once (packed single-precision pairs)
-      unsigned char* arow = op + cw * 16 * 128 + lo4;
-#pragma unroll
-      for (int aa = 0; aa < 4; ++aa)
-#pragma unroll
-        for (int bb = 0; bb < 4; ++bb) {
-          float2 r;
-          if (aa == bb) r = __ffma2_rn(xr[aa], xr[aa], __fmul2_rn(xi[aa], xi[aa]));
-          else if (aa < bb) r = __ffma2_rn(xr[aa], xr[bb], __fmul2_rn(xi[aa], xi[bb]));
-          else r = __ffma2_rn(xi[bb], xr[aa], __fmul2_rn(make_float2(-xr[bb].x, -xr[bb].y), xi[aa]));
-          const int e = aa * 4 + bb;
-          const unsigned off = (unsigned)(e * 128) + ((c8 ^ (unsigned)(e & 7)) << 4);
-          vx_split_store(arow + off, arow + VX_A_BYTES + off, r);
+        for (int hh = 0; hh < 2; ++hh) {
+          const unsigned lin = (unsigned)((fj * KC + lane) * (8 * M) + k * 32 + hh * 16);
+          const float4 qv = *reinterpret_cast<const float4*>(st + (lin ^ ((lin >> 3) & SWZ)));
+          xv[2 * hh] = make_float2(qv.x, qv.y);
+          xv[2 * hh + 1] = make_float2(qv.z, qv.w);
         }
-      // w = 1 / max(yhat, eps) for the pair's four microphones, zero past T
-      float y[2][4];
+        const unsigned kq = (unsigned)(lane & 15);
+        const unsigned tfoff = (unsigned)(lane >> 4) * VX_A_BYTES + (kq & 1u) * 8u;
+        unsigned char* arow = op + cw * 16 * 128 + tfoff;
 #pragma unroll
-      for (int j = 0; j < 2; ++j)
+        for (int aa = 0; aa < 4; ++aa)
 #pragma unroll
-        for (int mu = 0; mu < 4; ++mu) y[j][mu] = 0.f;
-      for (int n = 0; n < N; ++n) {
-        const float l0 = ls[(n * FPC + fj) * VX_KC + lane], l1 = ls[(n * FPC + fj) * VX_KC + lane + 32];
-        const float4 gv = *reinterpret_cast<const float4*>(gs + (fj * N + n) * M + 4 * k);
-        y[0][0] = fmaf(l0, gv.x, y[0][0]); y[0][1] = fmaf(l0, gv.y, y[0][1]);
-        y[0][2] = fmaf(l0, gv.z, y[0][2]); y[0][3] = fmaf(l0, gv.w, y[0][3]);
-        y[1][0] = fmaf(l1, gv.x, y[1][0]); y[1][1] = fmaf(l1, gv.y, y[1][1]);
-        y[1][2] = fmaf(l1, gv.z, y[1][2]); y[1][3] = fmaf(l1, gv.w, y[1][3]);
-      }
-      const bool v0 = c * VX_KC + lane < T, v1 = c * VX_KC + lane + 32 < T;
-      unsigned char* bt = op + 2 * VX_A_BYTES + lo4;
+          for (int bb = 0; bb < 4; ++bb) {
+            const float2 xa = xv[aa], xb = xv[bb];
+            const float r = (aa == bb) ? fmaf(xa.x, xa.x, xa.y * xa.y)
+                            : (aa < bb) ? fmaf(xa.x, xb.x, xa.y * xb.y)
+                                        : fmaf(xb.y, xa.x, -xb.x * xa.y);
+            const int e = aa * 4 + bb;
+            const unsigned off = (unsigned)(e * 128) + (((kq >> 1) ^ (unsigned)(e & 7)) << 4);
+            const float h = tf32_rna(r);
+            *reinterpret_cast<float2*>(arow + off) = make_float2(h, r - h);
+          }
+        float y[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int n = 0; n < N; ++n) {
+          const float l0 = ls[(n * FPC + fj) * KC + lane];
+          const float4 gv = *reinterpret_cast<const float4*>(gs + (fj * N + n) * M + 4 * k);
+          y[0] = fmaf(l0, gv.x, y[0]); y[1] = fmaf(l0, gv.y, y[1]);
+          y[2] = fmaf(l0, gv.z, y[2]); y[3] = fmaf(l0, gv.w, y[3]);
+        }
+        const bool v0 = c * KC + lane < T;
+        unsigned char* bt = op + 2 * VX_A_BYTES + (unsigned)(lane >> 4) * (VX_N * 128) + (kq & 1u) * 8u;
 #pragma unroll
-      for (int mu = 0; mu < 4; ++mu) {
-        const int rw = wrow + mu;
-        const unsigned off = (unsigned)(rw * 128) + ((c8 ^ (unsigned)(rw & 7)) << 4);
-        vx_split_store(bt + off, bt + VX_WROWS * 128 + off,
-                       make_float2(v0 ? fast_rcp(fmaxf(y[0][mu], eps)) : 0.f, v1 ? fast_rcp(fmaxf(y[1][mu], eps)) : 0.f));
+        for (int mu = 0; mu < 4; ++mu) {
+          const int rw = wrow + mu;
+          const unsigned off = (unsigned)(rw * 128) + (((kq >> 1) ^ (unsigned)(rw & 7)) << 4);
+          const float w = v0 ? fast_rcp(fmaxf(y[mu], eps)) : 0.f;
+          const float h = tf32_rna(w), l = w - h;
+          *reinterpret_cast<float2*>(bt + off) = make_float2(h, h);
+          *reinterpret_cast<float2*>(bt + VX_WROWS * 128 + off) = make_float2(l, l);
+        }
+      } else {
+        // x of frames lane and lane + 32, microphones 0..3 of the pair
+        float2 xv[2][4];
+  #pragma unroll
+        for (int j = 0; j < 2; ++j)
+  #pragma unroll
+          for (int hh = 0; hh < 2; ++hh) {
+            const unsigned lin = (unsigned)((fj * KC + lane + 32 * j) * (8 * M) + k * 32 + hh * 16);
+            const float4 qv = *reinterpret_cast<const float4*>(st + (lin ^ ((lin >> 3) & SWZ)));
+            xv[j][2 * hh] = make_float2(qv.x, qv.y);
+            xv[j][2 * hh + 1] = make_float2(qv.z, qv.w);
+          }
+        // R = x x^H, entry 4a + b: |x_a|^2 (a == b), Re x_a conj x_b (a < b), Im x_b conj x_a (a > b)
+        // (scalar single precision: packed pairs cost more register moves than they save)
+        unsigned char* arow = op + cw * 16 * 128 + lo4;
+  #pragma unroll
+        for (int aa = 0; aa < 4; ++aa)
+  #pragma unroll
+          for (int bb = 0; bb < 4; ++bb) {
+            float r[2];
+  #pragma unroll
+            for (int j = 0; j < 2; ++j) {
+              const float2 xa = xv[j][aa], xb = xv[j][bb];
+              if (aa == bb) r[j] = fmaf(xa.x, xa.x, xa.y * xa.y);
+              else if (aa < bb) r[j] = fmaf(xa.x, xb.x, xa.y * xb.y);
+              else r[j] = fmaf(xb.y, xa.x, -xb.x * xa.y);
+            }
+            const int e = aa * 4 + bb;
+            const unsigned off = (unsigned)(e * 128) + ((c8 ^ (unsigned)(e & 7)) << 4);
+            vx_split_store(arow + off, arow + VX_A_BYTES + off, r[0], r[1]);
+          }
+        // w = 1 / max(yhat, eps) for the pair's four microphones, zero past T
+        float y[2][4];
+  #pragma unroll
+        for (int j = 0; j < 2; ++j)
+  #pragma unroll
+          for (int mu = 0; mu < 4; ++mu) y[j][mu] = 0.f;
+        for (int n = 0; n < N; ++n) {
+          const float l0 = ls[(n * FPC + fj) * KC + lane], l1 = ls[(n * FPC + fj) * KC + lane + 32];
+          const float4 gv = *reinterpret_cast<const float4*>(gs + (fj * N + n) * M + 4 * k);
+          y[0][0] = fmaf(l0, gv.x, y[0][0]); y[0][1] = fmaf(l0, gv.y, y[0][1]);
+          y[0][2] = fmaf(l0, gv.z, y[0][2]); y[0][3] = fmaf(l0, gv.w, y[0][3]);
+          y[1][0] = fmaf(l1, gv.x, y[1][0]); y[1][1] = fmaf(l1, gv.y, y[1][1]);
+          y[1][2] = fmaf(l1, gv.z, y[1][2]); y[1][3] = fmaf(l1, gv.w, y[1][3]);
+        }
+        const bool v0 = c * KC + lane < T, v1 = c * KC + lane + 32 < T;
+        unsigned char* bt = op + 2 * VX_A_BYTES + lo4;
+  #pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+          const int rw = wrow + mu;
+          const unsigned off = (unsigned)(rw * 128) + ((c8 ^ (unsigned)(rw & 7)) << 4);
+          vx_split_store(bt + off, bt + VX_WROWS * 128 + off, v0 ? fast_rcp(fmaxf(y[0][mu], eps)) : 0.f,
+                         v1 ? fast_rcp(fmaxf(y[1][mu], eps)) : 0.f);
+        }
       }
       // generic-proxy writes of the operand tiles, then hand the stages over
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -495,7 +509,7 @@ __global__ void __launch_bounds__((VX_CONV_WARP + VX_CW * CG) * 32, 1)
   __syncthreads();
   if (warp == 0) {
     // all tensor-core work of the CTA has completed before its tensor memory is freed (bounded wait)
-    if (!mbar_wait_warp(&ctl->done, 0, 64) && lane == 0) atomicOr(&ctl->abort, 1u);
+    if (!mbar_wait_warp(&ctl->done, 0, 256) && lane == 0) atomicOr(&ctl->abort, 1u);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * VX_ACC_COLS) : "memory");
   }
@@ -678,35 +692,41 @@ size_t tc_part_float4s(const dfmnmf_ctx* c) { return ((size_t)tc_tiles(c) + (siz
 size_t tc_ticket_count(const dfmnmf_ctx* c) { return (size_t)tc_tiles(c); }
 
 // Raw stage of the fused contraction: x tile, lambda rows, g rows, rounded to 1 KB.
-static int vx_stage_bytes(int K, int N) {
+static bool vx_tf32(const dfmnmf_ctx* c) { return c->precision == DFMNMF_TF32_TC; }
+static int vx_kc(bool tf) { return tf ? VxCfg<true>::KC : VxCfg<false>::KC; }
+static int vx_op_bytes(bool tf) { return tf ? VxCfg<true>::OP_BYTES : VxCfg<false>::OP_BYTES; }
+static int vx_stage_bytes(int K, int N, bool tf) {
   const int FPC = 8 / K;
-  const int b = VX_X_BYTES + FPC * N * VX_KC * 4 + FPC * N * 4 * K * 4;
+  const int b = (tf ? VxCfg<true>::X_BYTES : VxCfg<false>::X_BYTES) + FPC * N * vx_kc(tf) * 4 + FPC * N * 4 * K * 4;
   return (b + 1023) & ~1023;
 }
 
 // Raw stages that fit beside the operand stages (at most VX_MAX_RS, at least 2; 0 if none fit).
 int tc_raw_stages(const dfmnmf_ctx* c) {
-  const long avail = (long)c->smem_optin - 1024 - (long)VX_OS * VX_OP_BYTES - (long)sizeof(VxCtl);
-  const long rs = avail / vx_stage_bytes(c->K, c->N);
+  const bool tf = vx_tf32(c);
+  const long avail = (long)c->smem_optin - 1024 - (long)VX_OS * vx_op_bytes(tf) - (long)sizeof(VxCtl);
+  const long rs = avail / vx_stage_bytes(c->K, c->N, tf);
   return rs < 2 ? 0 : (int)(rs > VX_MAX_RS ? VX_MAX_RS : rs);
 }
 
-template <int K, int CG>
+template <int K, int CG, bool TF>
 static cudaError_t launch_vtc_k(const dfmnmf_ctx* c, cudaStream_t s, const CUtensorMap& mx, const CUtensorMap& ml,
                                 const CUtensorMap& mg, int tb, int ntile, int nch, int G, int RS, int stage,
                                 size_t smem) {
-  auto kern = k_vtc<K, CG>;
+  auto kern = k_vtc<K, CG, TF>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<G, (VX_CONV_WARP + VX_CW * CG) * 32, smem, s>>>(mx, ml, mg, c->V, c->Vdd, c->tc_part, c->tc_ticket, c->F,
-                                                          c->T, c->N, c->eps, tb, ntile, nch, RS, stage, c->flags);
+                                                          c->T, c->N, c->eps, tb, ntile, nch, RS, stage,
+                                                          c->wait_cycles, c->flags);
   return cudaGetLastError();
 }
 
 // The fused contraction for frequencies [fb, fb + fc), fb a multiple of 8 / K.
-// x as floats [F][T][2M] (boxes of 64 frames x 8/K frequencies; for K = 8 the
-// 256-byte frame rows as two 128-byte halves), lambda [N][F][Tp] (64 frames x
-// 8/K frequencies x N), g [F][N][M] (8/K frequencies); frames past T and
+// x as floats [F][T][2M] (boxes of KC frames x 8/K frequencies, KC = 64 for
+// bfloat16 operands and 32 for TF32; for K = 8 the 256-byte frame rows as two
+// 128-byte halves), lambda [N][F][Tp] (KC frames x 8/K frequencies x N),
+// g [F][N][M] (8/K frequencies); frames past T and
 // frequencies past F read as zeros.  The maps are encoded at launch and
 // passed by value, so a captured graph keeps them.
 cudaError_t launch_vtc(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
@@ -716,25 +736,27 @@ cudaError_t launch_vtc(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
   if (fc <= 0) return cudaSuccess;
   if (fb % FPC) return cudaErrorInvalidValue;
   const int tb = fb / FPC, ntile = (fb + fc + FPC - 1) / FPC - tb;
-  const int nch = (c->T + VX_KC - 1) / VX_KC;
+  const bool tf = vx_tf32(c);
+  const int KC = vx_kc(tf);
+  const int nch = (c->T + KC - 1) / KC;
   const long long U = (long long)ntile * nch;
   const int G = (int)(U < c->num_sms ? U : c->num_sms);
-  const int RS = tc_raw_stages(c), stage = vx_stage_bytes(K, c->N);
+  const int RS = tc_raw_stages(c), stage = vx_stage_bytes(K, c->N, tf);
   if (RS == 0 || U >= (1ll << 31) / (c->num_sms + 1)) return cudaErrorInvalidValue;  // unit indices stay 32-bit
-  const size_t smem = 1024 + (size_t)VX_OS * VX_OP_BYTES + (size_t)RS * stage + sizeof(VxCtl);
+  const size_t smem = 1024 + (size_t)VX_OS * vx_op_bytes(tf) + (size_t)RS * stage + sizeof(VxCtl);
   CUtensorMap mx, ml, mg;
   const cuuint32_t e4[4] = {1, 1, 1, 1};
   CUresult r;
   if (K == 8) {
     const cuuint64_t dims[4] = {32, 2, (cuuint64_t)c->T, (cuuint64_t)c->F};
     const cuuint64_t str[3] = {128, 256, (cuuint64_t)c->T * 256};
-    const cuuint32_t box[4] = {32, 2, VX_KC, 1};
+    const cuuint32_t box[4] = {32, 2, (cuuint32_t)KC, 1};
     r = fn(&mx, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c->x, dims, str, box, e4, CU_TENSOR_MAP_INTERLEAVE_NONE,
            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   } else {
     const cuuint64_t dims[3] = {(cuuint64_t)(2 * M), (cuuint64_t)c->T, (cuuint64_t)c->F};
     const cuuint64_t str[2] = {(cuuint64_t)(8 * M), (cuuint64_t)c->T * 8 * M};
-    const cuuint32_t box[3] = {(cuuint32_t)(2 * M), VX_KC, (cuuint32_t)FPC};
+    const cuuint32_t box[3] = {(cuuint32_t)(2 * M), (cuuint32_t)KC, (cuuint32_t)FPC};
     const CUtensorMapSwizzle sw =
         K == 1 ? CU_TENSOR_MAP_SWIZZLE_32B : K == 2 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
     r = fn(&mx, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->x, dims, str, box, e4, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
@@ -744,7 +766,7 @@ cudaError_t launch_vtc(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
   {
     const cuuint64_t dims[3] = {(cuuint64_t)c->Tp, (cuuint64_t)c->F, (cuuint64_t)c->N};
     const cuuint64_t str[2] = {(cuuint64_t)c->Tp * 4, (cuuint64_t)c->F * c->Tp * 4};
-    const cuuint32_t box[3] = {VX_KC, (cuuint32_t)FPC, (cuuint32_t)c->N};
+    const cuuint32_t box[3] = {(cuuint32_t)KC, (cuuint32_t)FPC, (cuuint32_t)c->N};
     if (fn(&ml, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->lam, dims, str, box, e4, CU_TENSOR_MAP_INTERLEAVE_NONE,
            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
         CUDA_SUCCESS)
@@ -759,9 +781,12 @@ cudaError_t launch_vtc(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
         CUDA_SUCCESS)
       return cudaErrorInvalidValue;
   }
-#define DFM_VTC(KK)                                                                                         \
-  return c->cfg_vx_groups == 1 ? launch_vtc_k<KK, 1>(c, s, mx, ml, mg, tb, ntile, nch, G, RS, stage, smem) \
-                               : launch_vtc_k<KK, 2>(c, s, mx, ml, mg, tb, ntile, nch, G, RS, stage, smem)
+#define DFM_VTC_TF(KK, TFV)                                                                                      \
+  return c->cfg_vx_groups == 1 ? launch_vtc_k<KK, 1, TFV>(c, s, mx, ml, mg, tb, ntile, nch, G, RS, stage, smem) \
+                               : launch_vtc_k<KK, 2, TFV>(c, s, mx, ml, mg, tb, ntile, nch, G, RS, stage, smem)
+#define DFM_VTC(KK)                \
+  if (tf) DFM_VTC_TF(KK, true);    \
+  else DFM_VTC_TF(KK, false)
   switch (K) {
     case 1: DFM_VTC(1);
     case 2: DFM_VTC(2);
@@ -769,6 +794,7 @@ cudaError_t launch_vtc(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
     default: DFM_VTC(8);
   }
 #undef DFM_VTC
+#undef DFM_VTC_TF
 }
 
 // x as floats [F][T][2M] (boxes of 128 frames x 32 floats, 128-byte swizzle),

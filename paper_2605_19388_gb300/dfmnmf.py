@@ -24,6 +24,7 @@ DFMNMF_IP_F64, DFMNMF_IP_F32X2, DFMNMF_IP_F32 = 0, 1, 2
 DFMNMF_STAGE_COV, DFMNMF_STAGE_IP, DFMNMF_STAGE_W, DFMNMF_STAGE_H, DFMNMF_STAGE_G = 1, 2, 3, 4, 5
 DFMNMF_BUF_V, DFMNMF_BUF_P, DFMNMF_BUF_LAMBDA = 1, 2, 3
 DFMNMF_LOSS_NLL, DFMNMF_LOSS_WIENER_MSE = 1, 2
+DFMNMF_OPT_BRANCHES, DFMNMF_OPT_NMF_CTAS, DFMNMF_OPT_VX_GROUPS, DFMNMF_OPT_WUPD_TC, DFMNMF_OPT_WAIT_CYCLES = 1, 2, 3, 4, 5
 
 # Every symbol include/dfmnmf.h declares.
 EXPORTED = ("dfmnmf_init", "dfmnmf_set_observation", "dfmnmf_iterate", "dfmnmf_run_stage",
@@ -32,7 +33,8 @@ EXPORTED = ("dfmnmf_init", "dfmnmf_set_observation", "dfmnmf_iterate", "dfmnmf_r
             "dfmnmf_last_error", "dfmnmf_version", "dfmnmf_loglik_noalloc", "dfmnmf_autotune",
             "dfmnmf_cost_gradient", "dfmnmf_init_from_images",
             "dfmnmf_batch_create", "dfmnmf_batch_iterate", "dfmnmf_batch_destroy",
-            "dfmnmf_adjoint_create", "dfmnmf_adjoint_run", "dfmnmf_adjoint_destroy")
+            "dfmnmf_adjoint_create", "dfmnmf_adjoint_run", "dfmnmf_adjoint_destroy",
+            "dfmnmf_set_option", "dfmnmf_get_option")
 
 
 class DfmnmfError(RuntimeError):
@@ -86,6 +88,8 @@ def load_library(path: Optional[str] = None):
         "dfmnmf_adjoint_create": (ci, [ctypes.POINTER(vp), vp, ci, ci]),
         "dfmnmf_adjoint_run": (ci, [vp, ci, vp, ctypes.POINTER(cd), vp, vp, vp, vp, vp]),
         "dfmnmf_adjoint_destroy": (None, [vp]),
+        "dfmnmf_set_option": (ci, [vp, ci, ci]),
+        "dfmnmf_get_option": (ci, [vp, ci]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -257,6 +261,14 @@ def dfmnmf_autotune(ctx: Context, iters_per_trial: int = 5, stream=None):
     _check(load_library().dfmnmf_autotune(ctx.handle, int(iters_per_trial), ctypes.byref(br), ctypes.byref(ct),
                                           _stream(stream)))
     return br.value, ct.value
+
+
+def dfmnmf_set_option(ctx: Context, option: int, value: int):
+    _check(load_library().dfmnmf_set_option(ctx.handle, int(option), int(value)))
+
+
+def dfmnmf_get_option(ctx: Context, option: int) -> int:
+    return load_library().dfmnmf_get_option(ctx.handle, int(option))
 
 
 class Batch:

@@ -82,18 +82,20 @@ def test_null_arguments_rejected(lib):
     lib.dfmnmf_batch_destroy(None)  # no-op
     lib.dfmnmf_destroy(None)
     assert lib.dfmnmf_launches_per_iteration(None) == -1
+    assert lib.dfmnmf_set_option(None, 1, 1) == D.DFMNMF_EINVAL
+    assert lib.dfmnmf_get_option(None, 1) == -1
 
 
-def test_tensor_core_form_rejects_unbuilt_layouts_and_tf32(lib):
-    """The tensor-core covariances are built for M_k = 4 with K in {1, 2, 4, 8};
-    DFMNMF_TF32_TC is reserved.  Both are rejected before any device work."""
-    for mics, prec in (((2, 2), D.DFMNMF_BF16_TC), ((4, 4, 4), D.DFMNMF_BF16_TC), ((3, 3), D.DFMNMF_BF16_TC),
-                       ((4, 4), D.DFMNMF_TF32_TC)):
-        a = _args(mics=mics)
-        with pytest.raises(D.DfmnmfError) as ei:
-            D.dfmnmf_init(a["F"], a["T"], a["mics"], a["N"], a["B"], a["x"], a["W0"], a["H0"], a["g0"],
-                          precision=prec)
-        assert ei.value.code == D.DFMNMF_EINVAL, (mics, prec)
+def test_tensor_core_forms_reject_unbuilt_layouts(lib):
+    """The tensor-core covariances (bfloat16 or TF32 split operands) are built for M_k = 4 with K in
+    {1, 2, 4, 8}; other layouts are rejected before any device work."""
+    for mics in ((2, 2), (4, 4, 4), (3, 3)):
+        for prec in (D.DFMNMF_BF16_TC, D.DFMNMF_TF32_TC):
+            a = _args(mics=mics)
+            with pytest.raises(D.DfmnmfError) as ei:
+                D.dfmnmf_init(a["F"], a["T"], a["mics"], a["N"], a["B"], a["x"], a["W0"], a["H0"], a["g0"],
+                              precision=prec)
+            assert ei.value.code == D.DFMNMF_EINVAL, (mics, prec)
 
 
 def test_noalloc_rejects_sizes_beyond_its_static_scratch(lib):

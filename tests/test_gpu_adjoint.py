@@ -28,6 +28,7 @@ from paper_2605_19388_gb300 import autograd as AG  # noqa: E402
 from paper_2605_19388_gb300 import dfmnmf as D  # noqa: E402
 
 TOL = 1e-4
+DIR_FLOOR = 1e-2  # stated floor of the directional checks, as a fraction of sum_i |g_i d_i|
 LOSSES = {"nll": D.DFMNMF_LOSS_NLL, "wiener_mse": D.DFMNMF_LOSS_WIENER_MSE}
 
 
@@ -85,11 +86,13 @@ def check(p, st, n_iter, loss, got, n_dir, n_fd, seed):
         errs["Q"] = max(rel_err(dQ[k], rQ[k]) for k in range(len(p.mics)))
     else:  # one microphone per subarray: Q' = e^{i arg Q} / sqrt(V), no loss depends on Q0
         errs["Q"] = sum(nrm(dQ[k]) * nrm(st.Q[k]) for k in range(len(p.mics))) / scale_all
+    # a directional derivative is compared relative to itself; where it cancels below DIR_FLOOR times
+    # sum_i |g_i d_i| (the size of its terms), relative to that floor instead
     worst = 0.0
     for d in directions(st, n_dir, seed):
         a, scale = dot((dQ, dW, dH, dg), d)
         b, _ = dot((rQ, rW, rH, rg), d)
-        worst = max(worst, abs(a - b) / scale)
+        worst = max(worst, abs(a - b) / max(abs(b), DIR_FLOOR * scale))
     errs["dir_vs_oracle"] = worst
     h, worst = 1e-6, 0.0
     for d in directions(st, n_fd, seed + 1):
@@ -98,7 +101,7 @@ def check(p, st, n_iter, loss, got, n_dir, n_fd, seed):
         sm = O.State([q - h * e for q, e in zip(st.Q, eQ)], st.W - h * eW, st.H - h * eH, st.g - h * eg)
         fd = (torch_loss(p, sp, n_iter, loss) - torch_loss(p, sm, n_iter, loss)) / (2 * h)
         a, scale = dot((dQ, dW, dH, dg), d)
-        worst = max(worst, abs(a - fd) / scale)
+        worst = max(worst, abs(a - fd) / max(abs(fd), DIR_FLOOR * scale))
     errs["dir_vs_fd"] = worst
     print(f"adjoint {loss}, {n_iter} iterations:", {k: float(f"{v:.2e}") for k, v in errs.items()})
     for k, v in errs.items():
@@ -184,7 +187,7 @@ def test_rejects_bad_arguments():
         assert ei.value.code == D.DFMNMF_EINVAL
 
 
-@pytest.mark.parametrize("loss,n_fd", [("nll", 32), ("wiener_mse", 8)])
+@pytest.mark.parametrize("loss,n_fd", [("nll", 32), ("wiener_mse", 32)])
 def test_differentiation_workload_20_iterations(loss, n_fd):
     """4 x 4 mics, N = 5, B = 16, F = 257, T = 313; 20 iterations, checkpoints every 5;
     32 random directions against the oracle gradient, n_fd against FP64 central differences."""

@@ -218,3 +218,27 @@ def test_nonfinite_input_reports_enumeric():
     with pytest.raises(D.DfmnmfError) as ei:
         D.dfmnmf_loglik(ctx)
     assert ei.value.code == D.DFMNMF_ENUMERIC
+
+
+def test_fp32_form_200_iterations_paper_workload():
+    """The 4 x 4-mic, N = 5, F = 513, T = 626 workload for its full 200 iterations in the FP32 form:
+    Eq. (12) within 1e-3 relative and the SDR within 0.1 dB of the oracle's.  The oracle runs on
+    every host core (its bins split over worker processes; oracle/parallel.py)."""
+    import os
+    from oracle.parallel import SlicedOracle
+    p = synth.make_workload("paper_4x4_n5", seed=0, with_images=True)
+    x = p.x.astype(np.complex128)
+    ctx = make_ctx(p)
+    D.dfmnmf_iterate(ctx, 200)
+    nll_gpu = D.dfmnmf_loglik(ctx)
+    c_gpu = torch.empty((p.N, p.F, p.T, p.M), dtype=torch.complex64, device="cuda")
+    D.dfmnmf_separate(ctx, c_gpu)
+    with SlicedOracle(x, p.mics, oracle_state(p), workers=os.cpu_count() or 1) as so:
+        so.iterate(200)
+        st = so.state()
+    nll_ref = O.neg_loglik(x, p.mics, st)
+    sdr_gpu, _ = sdr_db(c_gpu.cpu().numpy(), p.c)
+    sdr_ref, _ = sdr_db(O.wiener_filter(x, p.mics, st), p.c)
+    print("FP32 form, 200 iterations: nll", nll_gpu, nll_ref, "SDR", sdr_gpu, sdr_ref)
+    assert abs(nll_gpu - nll_ref) <= 1e-3 * abs(nll_ref), (nll_gpu, nll_ref)
+    assert np.max(np.abs(np.sort(sdr_gpu) - np.sort(sdr_ref))) <= 0.1, (sdr_gpu, sdr_ref)
