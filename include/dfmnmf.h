@@ -196,6 +196,18 @@ int dfmnmf_launches_per_iteration(const dfmnmf_ctx* ctx);
 int dfmnmf_kernel_times(dfmnmf_ctx* ctx, int n_iter, double* avg_ms, const char** names, int cap,
                         int* count, void* stream);
 
+/*
+ * Profiling aid: each kernel of the iteration alone, `reps` >= 1 band-wide
+ * launches back to back in one CUDA graph timed by two events (after one
+ * warm-up replay); avg_ms[i] is the mean duration of one launch, including
+ * the gap between launches but no timing event.  Names and counts as for
+ * dfmnmf_kernel_times.  The repeated launches change the state (an IP or MU
+ * kernel applied reps times): restore it with dfmnmf_set_params afterwards.
+ * Synchronises `stream`.
+ */
+int dfmnmf_kernel_times_isolated(dfmnmf_ctx* ctx, int reps, double* avg_ms, const char** names, int cap,
+                                 int* count, void* stream);
+
 void dfmnmf_destroy(dfmnmf_ctx* ctx);
 
 /*

@@ -463,6 +463,48 @@ int dfmnmf_kernel_times(dfmnmf_ctx* c, int n_iter, double* avg_ms, const char** 
   return rc;
 }
 
+int dfmnmf_kernel_times_isolated(dfmnmf_ctx* c, int reps, double* avg_ms, const char** names, int cap, int* count,
+                                 void* stream) {
+  if (!c || !avg_ms || !count || reps < 1) return fail(DFMNMF_EINVAL, "bad argument");
+  CK(cudaSetDevice(c->device));
+  Launch L[kMaxLaunches];
+  const int n = iteration_launches(c, L);
+  *count = n;
+  if (cap < n) return fail(DFMNMF_EINVAL, "capacity %d < %d kernels", cap, n);
+  cudaStream_t s = as_stream(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+               ? fail(DFMNMF_ECUDA, "event creation failed")
+               : DFMNMF_OK;
+  // Each kernel of the iteration alone: `reps` band-wide launches back to back in one graph, timed by
+  // two events around the graph (so neither host latency nor per-launch events enter the time).
+  for (int i = 0; i < n && !rc; ++i) {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = L[i].fn(c, c->cap_stream, 0, c->F);
+    const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &graph);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec, graph, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(gexec, s);  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) e = cudaGraphLaunch(gexec, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    avg_ms[i] = ms / reps;
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) rc = fail(DFMNMF_ECUDA, "isolated timing of %s failed: %s", L[i].name, cudaGetErrorString(e));
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (names)
+    for (int i = 0; i < n; ++i) names[i] = L[i].name;
+  return rc;
+}
+
 int dfmnmf_cost_gradient(dfmnmf_ctx* c, void* dQ, float* dW, float* dH, float* dg, double* nll_host, void* stream) {
   if (!c) return fail(DFMNMF_EINVAL, "null context");
   CK(cudaSetDevice(c->device));

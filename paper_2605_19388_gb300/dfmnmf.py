@@ -34,7 +34,7 @@ EXPORTED = ("dfmnmf_init", "dfmnmf_set_observation", "dfmnmf_iterate", "dfmnmf_r
             "dfmnmf_cost_gradient", "dfmnmf_init_from_images",
             "dfmnmf_batch_create", "dfmnmf_batch_iterate", "dfmnmf_batch_destroy",
             "dfmnmf_adjoint_create", "dfmnmf_adjoint_run", "dfmnmf_adjoint_destroy",
-            "dfmnmf_set_option", "dfmnmf_get_option")
+            "dfmnmf_set_option", "dfmnmf_get_option", "dfmnmf_kernel_times_isolated")
 
 
 class DfmnmfError(RuntimeError):
@@ -89,6 +89,8 @@ def load_library(path: Optional[str] = None):
         "dfmnmf_adjoint_run": (ci, [vp, ci, vp, ctypes.POINTER(cd), vp, vp, vp, vp, vp]),
         "dfmnmf_adjoint_destroy": (None, [vp]),
         "dfmnmf_set_option": (ci, [vp, ci, ci]),
+        "dfmnmf_kernel_times_isolated": (ci, [vp, ci, ctypes.POINTER(cd), ctypes.POINTER(ctypes.c_char_p), ci,
+                                             ctypes.POINTER(ci), vp]),
         "dfmnmf_get_option": (ci, [vp, ci]),
     }
     for name, (res, args) in sig.items():
@@ -230,6 +232,17 @@ def dfmnmf_kernel_times(ctx: Context, n_iter: int, stream=None):
     for i in range(cnt.value):
         out.append((names[i].decode(), ms[i]))
     return out
+
+
+def dfmnmf_kernel_times_isolated(ctx: Context, reps: int, stream=None):
+    """[(kernel name, mean milliseconds per launch)], each kernel alone, reps launches back to back."""
+    cap = 32
+    ms = (ctypes.c_double * cap)()
+    names = (ctypes.c_char_p * cap)()
+    cnt = ctypes.c_int()
+    _check(load_library().dfmnmf_kernel_times_isolated(ctx.handle, int(reps), ms, names, cap, ctypes.byref(cnt),
+                                                       _stream(stream)))
+    return [(names[i].decode(), ms[i]) for i in range(cnt.value)]
 
 
 def dfmnmf_destroy(ctx: Context):
