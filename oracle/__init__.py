@@ -2,6 +2,10 @@
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  The library never does.
+
+Two independent restatements of the method live here: ``dfmnmf_oracle`` in
+NumPy and ``c/dfmnmf_loop.c`` in plain C loops (binding: ``oracle.loop``);
+``tests/test_oracle_loop.py`` holds them against each other.
 """
 from .dfmnmf_oracle import *  # noqa: F401,F403
 from .dfmnmf_oracle import (EPS, SINGULAR_RTOL, State, state_from_arrays, unpack_Q, pack_Q,

@@ -135,6 +135,48 @@ def test_tc_trajectory_50_iterations_paper_workload(form, paper_oracle_50):
     assert np.max(np.abs(np.sort(s_gpu) - np.sort(s_ref))) <= 0.2, (s_gpu, s_ref)
 
 
+def block_errors(a, b):
+    """Per-(f, k) normwise relative error of [F][K][...] arrays (b is the reference)."""
+    F, K = b.shape[:2]
+    d = np.linalg.norm((np.asarray(a, np.complex128) - b).reshape(F, K, -1), axis=2)
+    return d / np.maximum(np.linalg.norm(b.reshape(F, K, -1), axis=2), 1e-300)
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_tc_error_distribution_per_block_paper_workload(form, paper_oracle_50):
+    """The distribution over the F x K = 2052 blocks of the 4 x 4-mic, N = 5, F = 513, T = 626 workload,
+    at the oracle's state after 50 iterations: the covariances' error (Eq. 13, block-wise relative to the
+    oracle's FP64 V on the same state), the IP update's error (Eqs. 14-15: the GPU's rows from its own V
+    against the oracle's rows from the exact V, so the covariance error enters amplified by cond(Q V_mu)),
+    and that condition number.  Every block's IP update stays within the 3e-3 bar."""
+    p, x, st = paper_oracle_50
+    ctx = ctx_for(p, form, Q0=O.pack_Q(st.Q))
+    D.dfmnmf_set_params(ctx, O.pack_Q(st.Q), st.W.astype(np.float32), st.H.astype(np.float32),
+                        st.g.astype(np.float32))
+    g_st = state(ctx)  # the state as the GPU holds it (W, H, g rounded to FP32)
+    D.dfmnmf_run_stage(ctx, D.DFMNMF_STAGE_COV)
+    V = D.buffer_numpy(ctx, D.DFMNMF_BUF_V)
+    y = O.model_variance(O.source_psd(g_st.W, g_st.H), g_st.g)
+    V_list = O.weighted_covariances(x, y, p.mics)
+    V_ref = v_oracle_layout(V_list)
+    D.dfmnmf_run_stage(ctx, D.DFMNMF_STAGE_IP)
+    Q_gpu = np.stack(state(ctx).Q, axis=1)
+    Q_ref = np.stack(O.ip_update(g_st.Q, V_list), axis=1)
+    ev = block_errors(V, V_ref)
+    eq = block_errors(Q_gpu, Q_ref)
+    cond = np.stack([np.max(np.linalg.cond(np.matmul(g_st.Q[k][:, None], V_list[k])), axis=1)
+                     for k in range(p.K)], axis=1)  # [F][K]: the largest over mu
+    stats = {}
+    for name, e in (("V", ev), ("Q", eq), ("cond_QV", cond)):
+        stats[name] = {"max": float(e.max()), "p99": float(np.quantile(e, 0.99)),
+                       "median": float(np.median(e))}
+    worst = np.unravel_index(np.argmax(eq), eq.shape)
+    print("tensor-core form", form, "per-(f,k) distribution over", eq.size, "blocks:", stats,
+          "worst IP block (f, k) =", tuple(int(i) for i in worst), "cond", float(cond[worst]))
+    assert stats["V"]["max"] < 1e-4, stats
+    assert stats["Q"]["max"] < TOL_TC, stats
+
+
 @pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("autotune", [False, True])
 def test_tc_paper_workload_one_iteration_full_size(autotune, form):

@@ -145,3 +145,20 @@ def test_planted_mistake_is_caught(slip):
             except Exception:  # an assertion, or a numerical error the slip provokes
                 caught.append(f.__name__)
     assert caught, f"no pin fails with the planted mistake: {slip}"
+
+
+@pytest.mark.parametrize("slip", list(MUTATIONS))
+def test_planted_mistake_is_caught_by_the_loop_oracle(slip):
+    """The plain-C loop oracle alone catches each planted mistake too (one layout, one trajectory)."""
+    from tests import test_oracle_loop as loop
+    name, fn = MUTATIONS[slip]
+    checks = [lambda: loop.test_every_update_agrees((4, 4), 5, 6),
+              lambda: loop.test_trajectories_agree(dict(F=17, T=60, mics=(4, 4, 4, 4), N=5, B=8), 1e-11)]
+    caught = 0
+    with _planted(name, fn), np.errstate(all="ignore"):
+        for check in checks:
+            try:
+                check()
+            except Exception:
+                caught += 1
+    assert caught, f"the loop oracle agrees with the planted mistake: {slip}"
