@@ -428,6 +428,41 @@ def batched_measurement(args, D, synth, torch, dev, timed, precision, ip):
     return res
 
 
+# ------------------------------------------- all-microphone comparator at M = 32
+def allmic32_measurement(args, D, synth, torch, timed, precision, ip):
+    """One mixture of the batched workload's largest layout (K = 8 subarrays x 4 mics, M = 32, N = 5, B = 16,
+    F = 513, T = 626): the distributed form (headline precision, 8 diagonalisers of 4 x 4 per bin) against
+    conventional all-microphone FastMNMF (K = 1, one 32 x 32 diagonaliser per bin, float-float covariances
+    and IP solves: its covariances are far too ill-conditioned for the tensor-core split operands), each
+    timed as 10 captured iterations per step."""
+    import numpy as np
+    F, T, N, B, iters = 513, 626, 5, 16, 10
+    p = synth.make_problem(F, T, (4,) * 8, N, B, seed=77)
+    res = {"workload": "F=513, T=626, M=32 (8 x 4 mics), N=5, B=16", "iters_per_step": iters,
+           "unit": "MM iter/s"}
+    for name, mics, prec in (("distributed_8x4", (4,) * 8, precision), ("allmic_32", (32,), D.DFMNMF_FP32)):
+        Q0 = torch.from_numpy(synth.identity_blocks(F, mics)).cuda()
+        W0, H0, g0 = (torch.from_numpy(a).cuda() for a in (p.W0, p.H0, p.g0))
+        c = D.dfmnmf_init(F, T, mics, N, B, p.x, p.W0, p.H0, p.g0, Q0, precision=prec, ip_arith=ip)
+
+        def step(_, c=c, st=(Q0, W0, H0, g0)):
+            D.dfmnmf_set_params(c, *st)  # device to device
+            D.dfmnmf_iterate(c, iters)
+
+        for _ in range(2):
+            step(None)
+        torch.cuda.synchronize()
+        nsteps = 3
+        ms = timed(step, None, nsteps)
+        nll = D.dfmnmf_loglik(c)
+        res[name] = {"value": iters * nsteps / (ms / 1000.0), "ms_per_iter": ms / (nsteps * iters),
+                     "tf_bin_mic_updates_per_s": F * T * 32 * iters * nsteps / (ms / 1000.0), "nll_after": nll,
+                     "launches_per_iter": D.dfmnmf_launches_per_iteration(c)}
+        D.dfmnmf_destroy(c)
+    res["distributed_vs_allmic"] = res["distributed_8x4"]["value"] / res["allmic_32"]["value"]
+    return res
+
+
 # ---------------------------------------------------------------- our arm
 def main():
     args = parse()
@@ -716,6 +751,7 @@ def main():
     # many mixtures of uneven length and layout, one graph launch per iteration, launch shapes autotuned
     if args.batched > 0 and world == 1:
         out["batched"] = batched_measurement(args, D, synth, torch, dev, timed, precisions[forms[0]], ip)
+        out["allmic32"] = allmic32_measurement(args, D, synth, torch, timed, precisions[forms[0]], ip)
 
     if not args.no_adjoint and world == 1:
         out["adjoint"] = adjoint_measurement(D, synth, torch, timed)

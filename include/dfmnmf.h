@@ -44,10 +44,11 @@
  *
  * Limits of this release
  *   All subarrays must have the same size M_k in 1..4 (the paper's layout is
- *   three 4-microphone subarrays), or K = 1 with M_k = 16: conventional
- *   all-microphone FastMNMF with a full 16 x 16 diagonaliser (Sec. II-A),
- *   which the distributed form reduces to at K = 1 and which is its
- *   comparator (FP32 form only); other layouts return DFMNMF_EINVAL.
+ *   three 4-microphone subarrays), or K = 1 with M_k = 16 or 32:
+ *   conventional all-microphone FastMNMF with a full 16 x 16 or 32 x 32
+ *   diagonaliser (Sec. II-A), which the distributed form reduces to at K = 1
+ *   and which is its comparator (FP32 form only; no cost gradient at
+ *   M_k = 32); other layouts return DFMNMF_EINVAL.
  *   1 <= N <= 16, 1 <= B <= 64, 1 <= K <= 16, F >= 1, T >= 1.
  */
 #ifndef DFMNMF_H
@@ -226,7 +227,7 @@ void dfmnmf_destroy(dfmnmf_ctx* ctx);
  * inverse and the Q gradient in FP64.  Any output may be NULL; host or
  * device memory.  *nll_host (may be NULL) receives Eq. (12), and then the
  * call synchronises `stream` and reports DFMNMF_ENUMERIC as dfmnmf_loglik
- * does.  The gradient through unrolled iterations is not provided.
+ * does.  Blocks of 32 microphones return DFMNMF_EINVAL.
  */
 int dfmnmf_cost_gradient(dfmnmf_ctx* ctx, void* dQ, float* dW, float* dH, float* dg, double* nll_host,
                          void* stream);

@@ -237,9 +237,9 @@ int dfmnmf_init(dfmnmf_ctx** out, const dfmnmf_desc* d, const void* x, const flo
       return fail(DFMNMF_EINVAL, "this release needs equal subarray sizes (mics[0]=%d, mics[%d]=%d)", MK, k,
                   d->mics[k]);
   }
-  if (MK > 4 && !(MK == 16 && d->K == 1))
-    return fail(DFMNMF_EINVAL, "subarray size M_k=%d: this release supports 1..4, or 16 with K = 1 (all-microphone form)",
-                MK);
+  if (MK > 4 && !((MK == 16 || MK == 32) && d->K == 1))
+    return fail(DFMNMF_EINVAL,
+                "subarray size M_k=%d: this release supports 1..4, or 16 or 32 with K = 1 (all-microphone form)", MK);
   if (d->precision != DFMNMF_FP32 && !dfm::is_tc(d->precision))
     return fail(DFMNMF_EINVAL, "precision %d is not built in this release", d->precision);
   if (dfm::is_tc(d->precision) && !dfm::tc_supported(MK, d->K))
@@ -507,6 +507,7 @@ int dfmnmf_kernel_times_isolated(dfmnmf_ctx* c, int reps, double* avg_ms, const 
 
 int dfmnmf_cost_gradient(dfmnmf_ctx* c, void* dQ, float* dW, float* dH, float* dg, double* nll_host, void* stream) {
   if (!c) return fail(DFMNMF_EINVAL, "null context");
+  if (c->MK > 16) return fail(DFMNMF_EINVAL, "the cost gradient supports blocks of up to 16 microphones (M_k=%d)", c->MK);
   CK(cudaSetDevice(c->device));
   cudaStream_t s = as_stream(stream);
   int r = 0;

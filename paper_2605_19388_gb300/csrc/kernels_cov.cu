@@ -60,9 +60,11 @@ __device__ __forceinline__ void warp_reduce_scatter_dd(float (&hi)[C], float (&l
 // each lane forms only its part of the exact products x_a conj(x_b) and
 // accumulates them against all MK weights 1/yhat, so no product is formed
 // twice.  x x^H is packed as MK^2 reals R[a*MK+b]: a == b |x_a|^2,
-// a < b Re(x_a conj x_b), a > b Im(x_b conj x_a).  Diagonal entries only add
-// non-negative terms, so their running sum dominates every new term and the
-// cheaper fast two-sum is exact for them.
+// a < b Re(x_a conj x_b), a > b Im(x_b conj x_a).  Every entry, the diagonal
+// ones included, is accumulated with the full two-sum: a new term may exceed
+// the running sum (a loud frame after quiet ones), and the fast two-sum then
+// drops up to half an ulp of the partial sum, which breaks the rank structure
+// of V at the 1e-8 level when T is small.
 template <int MK>
 struct CovCfg {
   static constexpr int E = MK * MK;
@@ -89,12 +91,11 @@ __device__ __forceinline__ void cov_accumulate_impl(const float2 (&xv)[MK], cons
     const int r = E0 + j;
     float rh, rl;
     exact_entry<MK>(xv, r, rh, rl);
-    const bool diag = (r / MK) == (r % MK);
 #pragma unroll
     for (int q = 0; q < MK; ++q) {
       const dd p = two_prod(w[q], rh);
       const float e = __fmaf_rn(w[q], rl, p.lo);
-      const dd s = diag ? quick_two_sum(ah[q * EP + j], p.hi) : two_sum(ah[q * EP + j], p.hi);
+      const dd s = two_sum(ah[q * EP + j], p.hi);
       ah[q * EP + j] = s.hi;
       al[q * EP + j] = __fadd_rn(al[q * EP + j], __fadd_rn(s.lo, e));
     }
@@ -223,44 +224,47 @@ __global__ void __launch_bounds__(256, 2) k_cov(const float2* __restrict__ x, co
 }
 
 // ------------------------------------------------------------------------
-// One 16-microphone block per frequency (conventional all-microphone
-// FastMNMF, K = 1, M_k = 16: the comparator of the distributed form).
-// Thread r of the CTA owns packed entry r of x x^H (r = a * 16 + b: a == b
-// |x_a|^2, a < b Re(x_a conj x_b), a > b Im(x_b conj x_a)) and keeps the
-// float-float sums of that entry against all 16 weights 1/yhat_mu in
-// registers.  Frames arrive in chunks of CT through a double-buffered
-// cp.async ring (x rows and lambda rows); the weights of a chunk are formed
-// once into shared memory and read as broadcasts.
-template <int NM>
-__global__ void __launch_bounds__(256) k_cov16(const float2* __restrict__ x, const float* __restrict__ lam,
-                                               const float* __restrict__ g, double2* __restrict__ V,
-                                               float4* __restrict__ Vdd, int F, int T, int Tp, int N, float eps,
-                                               int fb) {
-  constexpr int MK = 16, E = MK * MK;
-  const int f = fb + blockIdx.x, tid = threadIdx.x;
+// One all-microphone block per frequency (conventional FastMNMF, K = 1,
+// M_k = MK = 16 or 32: the comparator of the distributed form).  Thread r of
+// the CTA owns packed entry r of x x^H (r = a * MK + b: a == b |x_a|^2,
+// a < b Re(x_a conj x_b), a > b Im(x_b conj x_a)) and keeps the float-float
+// sums of that entry against MUG of the MK weights 1/yhat_mu in registers;
+// blockIdx.y selects which MUG (all 16 for MK = 16, a quarter of the 32 for
+// MK = 32, so that a thread's accumulators stay within the 64 registers a
+// 1024-thread CTA allows).  Frames arrive in chunks of CT through a
+// double-buffered cp.async ring (x rows and lambda rows); the weights of a
+// chunk are formed once into shared memory and read as broadcasts.
+template <int MK, int MUG, int NM>
+__global__ void __launch_bounds__(MK * MK) k_cov_all(const float2* __restrict__ x, const float* __restrict__ lam,
+                                                      const float* __restrict__ g, double2* __restrict__ V,
+                                                      float4* __restrict__ Vdd, int F, int T, int Tp, int N,
+                                                      float eps, int fb) {
+  constexpr int E = MK * MK, NT = MK * MK;
+  const int f = fb + blockIdx.x, tid = threadIdx.x, mu0 = blockIdx.y * MUG;
   extern __shared__ __align__(16) float smc[];
-  float2* xs = reinterpret_cast<float2*>(smc);     // [2][CT][16]
-  float* ls = smc + 2 * 2 * CT * MK;               // [2][N][CT]
-  float* ws = ls + 2 * NM * CT;                    // [CT][16] weights of the current chunk
-  float* gs = ws + CT * MK;                        // [N][16]
-  for (int i = tid; i < N * MK; i += blockDim.x) gs[i] = g[(size_t)f * N * MK + i];
+  float2* xs = reinterpret_cast<float2*>(smc);     // [2][CT][MK]
+  float* ls = smc + 2 * 2 * CT * MK;               // [2][NM][CT]
+  float* ws = ls + 2 * NM * CT;                    // [CT][MUG] weights of the current chunk
+  float* gs = ws + CT * MUG;                       // [N][MK]
+  for (int i = tid; i < N * MK; i += NT) gs[i] = g[(size_t)f * N * MK + i];
   const int nchunk = (T + CT - 1) / CT;
   auto issue = [&](int c) {
     const int t0 = c * CT, nt = min(CT, T - t0), buf = c & 1;
     const float2* src = x + ((size_t)f * T + t0) * MK;
     float2* dst = xs + (size_t)buf * CT * MK;
-    for (int i = tid; i < nt * MK / 2; i += blockDim.x) cp_async16(dst + 2 * i, src + 2 * i);
-    // lambda rows: warp w copies rows w, w + 8, ... in 16-byte pieces (rows are zero up to Tp)
+    for (int i = tid; i < nt * MK / 2; i += NT) cp_async16(dst + 2 * i, src + 2 * i);
+    // lambda rows: warp w copies rows w, w + NT/32, ... in 16-byte pieces (rows are zero up to Tp)
     const int nq = (nt + 3) / 4, q = tid & 31;
     if (q < nq && q < CT / 4)
-      for (int n = tid >> 5; n < N; n += 8) cp_async16(ls + (buf * NM + n) * CT + 4 * q, lam + ((size_t)n * F + f) * Tp + t0 + 4 * q);
+      for (int n = tid >> 5; n < N; n += NT / 32)
+        cp_async16(ls + (buf * NM + n) * CT + 4 * q, lam + ((size_t)n * F + f) * Tp + t0 + 4 * q);
     cp_async_commit();
   };
   const int a = tid / MK, b = tid % MK;
   const bool diag = a == b;
-  float ah[MK], al[MK];
+  float ah[MUG], al[MUG];
 #pragma unroll
-  for (int q = 0; q < MK; ++q) { ah[q] = 0.f; al[q] = 0.f; }
+  for (int q = 0; q < MUG; ++q) { ah[q] = 0.f; al[q] = 0.f; }
   __syncthreads();
   issue(0);
   for (int c = 0; c < nchunk; ++c) {
@@ -274,9 +278,9 @@ __global__ void __launch_bounds__(256) k_cov16(const float2* __restrict__ x, con
     const int nt = min(CT, T - c * CT), buf = c & 1;
     const float2* xb = xs + (size_t)buf * CT * MK;
     const float* lb = ls + buf * NM * CT;
-    // weights w[tt][mu] = 1 / max(sum_n lambda g, eps) of the chunk's frames
-    for (int i = tid; i < CT * MK; i += blockDim.x) {
-      const int tt = i / MK, mu = i % MK;
+    // weights w[tt][q] = 1 / max(sum_n lambda g_(mu0 + q), eps) of the chunk's frames
+    for (int i = tid; i < CT * MUG; i += NT) {
+      const int tt = i / MUG, mu = mu0 + i % MUG;
       float y = 0.f;
 #pragma unroll
       for (int n = 0; n < NM; ++n)  // NM is a register bound (8 or 16), not N itself
@@ -289,9 +293,9 @@ __global__ void __launch_bounds__(256) k_cov16(const float2* __restrict__ x, con
       float rh, rl;
       if (a <= b) exact_re(xa, xo, rh, rl);
       else exact_im(xa, xo, rh, rl);
-      const float4* wr = reinterpret_cast<const float4*>(ws + tt * MK);
+      const float4* wr = reinterpret_cast<const float4*>(ws + tt * MUG);
 #pragma unroll
-      for (int q4 = 0; q4 < MK / 4; ++q4) {
+      for (int q4 = 0; q4 < MUG / 4; ++q4) {
         const float4 w4 = wr[q4];
         const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
@@ -299,7 +303,7 @@ __global__ void __launch_bounds__(256) k_cov16(const float2* __restrict__ x, con
           const int q = q4 * 4 + u;
           const dd p = two_prod(wv[u], rh);
           const float e = __fmaf_rn(wv[u], rl, p.lo);
-          const dd s = diag ? quick_two_sum(ah[q], p.hi) : two_sum(ah[q], p.hi);
+          const dd s = two_sum(ah[q], p.hi);
           ah[q] = s.hi;
           al[q] = __fadd_rn(al[q], __fadd_rn(s.lo, e));
         }
@@ -310,11 +314,11 @@ __global__ void __launch_bounds__(256) k_cov16(const float2* __restrict__ x, con
   // V[f][mu][a][b] (this thread's real or imaginary part, both halves of the Hermitian pair)
   const double invT = 1.0 / (double)T;
 #pragma unroll
-  for (int q = 0; q < MK; ++q) {
+  for (int q = 0; q < MUG; ++q) {
     const double v = ((double)ah[q] + (double)al[q]) * invT;
     const float vh = (float)v, vl = (float)(v - (double)vh);
-    double* Vd = reinterpret_cast<double*>(V + ((size_t)f * MK + q) * E);
-    float* Vf = reinterpret_cast<float*>(Vdd + ((size_t)f * MK + q) * E);
+    double* Vd = reinterpret_cast<double*>(V + ((size_t)f * MK + mu0 + q) * E);
+    float* Vf = reinterpret_cast<float*>(Vdd + ((size_t)f * MK + mu0 + q) * E);
     if (diag) {
       Vd[2 * (a * MK + a)] = v;
       Vd[2 * (a * MK + a) + 1] = 0.0;
@@ -333,21 +337,23 @@ __global__ void __launch_bounds__(256) k_cov16(const float2* __restrict__ x, con
   }
 }
 
-static cudaError_t launch_cov16(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
-  const int NM = c->N <= 8 ? 8 : 16;
-  const size_t sm = ((size_t)2 * 2 * CT * 16 + 2 * (size_t)NM * CT + (size_t)CT * 16 + (size_t)c->N * 16) * sizeof(float);
-  if (NM == 8) {
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_cov16<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_cov16<8><<<fc, 256, sm, s>>>(c->x, c->lam, c->g, c->V, c->Vdd, c->F, c->T, c->Tp, c->N, c->eps, fb);
-  } else {
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_cov16<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_cov16<16><<<fc, 256, sm, s>>>(c->x, c->lam, c->g, c->V, c->Vdd, c->F, c->T, c->Tp, c->N, c->eps, fb);
-  }
+template <int MK, int MUG, int NM>
+static cudaError_t launch_cov_all_k(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
+  const size_t sm = ((size_t)2 * 2 * CT * MK + 2 * (size_t)NM * CT + (size_t)CT * MUG + (size_t)c->N * MK) * sizeof(float);
+  auto kern = k_cov_all<MK, MUG, NM>;
+  if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  kern<<<dim3(fc, MK / MUG), MK * MK, sm, s>>>(c->x, c->lam, c->g, c->V, c->Vdd, c->F, c->T, c->Tp, c->N, c->eps, fb);
   return cudaGetLastError();
 }
 
+template <int MK, int MUG>
+static cudaError_t launch_cov_all(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
+  return c->N <= 8 ? launch_cov_all_k<MK, MUG, 8>(c, s, fb, fc) : launch_cov_all_k<MK, MUG, 16>(c, s, fb, fc);
+}
+
 cudaError_t launch_cov(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
-  if (c->MK == 16) return launch_cov16(c, s, fb, fc);
+  if (c->MK == 16) return launch_cov_all<16, 16>(c, s, fb, fc);
+  if (c->MK == 32) return launch_cov_all<32, 8>(c, s, fb, fc);
   DFM_MK_DISPATCH(c->MK, {
     constexpr int CP = CovCfg<MK_>::CP;
     const int items = c->K * CovCfg<MK_>::PARTS;

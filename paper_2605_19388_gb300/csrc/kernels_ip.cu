@@ -313,17 +313,9 @@ __global__ void __launch_bounds__(128) k_ip(const double2* __restrict__ V, const
   }
 }
 
-// One 16 x 16 block per CTA of 256 threads (conventional all-microphone
-// FastMNMF, M_k = 16): thread e owns entry (i, j) = (e / 16, e % 16).  For
-// mu ascending: V_mu is staged in shared memory, A = Q V_mu formed entry by
-// entry, A q = e_mu solved by Gauss-Jordan elimination with partial pivoting
-// (the pivot column's magnitudes and the rows exchanged through shared
-// memory, first maximum taken on ties), then Eq. (15) with a block reduction
-// of Re q^H V q.  The singularity test and the pseudo-inverse fallback are
-// those of k_ip.
-// Pseudo-inverse path of k_ip16 (rare): q = pinv(Q V_mu) e_mu in FP64 by one
-// thread, kept out of line so that its local arrays do not weigh on the
-// registers of the main path.
+// Pseudo-inverse path of k_ip_all at M_k = 16 (rare): q = pinv(Q V_mu) e_mu
+// in FP64 by one thread, kept out of line so that its local arrays do not
+// weigh on the registers of the main path.
 template <class R>
 __device__ __noinline__ void ip16_pinv(const cx<R>* Qs, const double2* Vmu, int mu, float rtol, cx<double>* qout) {
   using O = RealOps<R>;
@@ -345,18 +337,118 @@ __device__ __noinline__ void ip16_pinv(const cx<R>* Qs, const double2* Vmu, int 
   for (int r = 0; r < MK; ++r) qout[r] = q[r];
 }
 
-template <class R>
-__global__ void __launch_bounds__(256, 2) k_ip16(const double2* __restrict__ V, const float4* __restrict__ Vdd,
-                                              double2* __restrict__ Q64, float2* __restrict__ Q32, float eps,
-                                              float rtol, unsigned* __restrict__ flags) {
+__device__ __forceinline__ double warp_sum_all(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(DFM_FULL_MASK, v, o);
+  return v;  // every lane holds the same sum (each step adds the same two operands in every lane)
+}
+
+// Pseudo-inverse path at M_k = 32 (rare): q = pinv(Q V_mu) e_mu in FP64 by
+// one warp, lane r owning row r of U = Q V_mu and of the rotation J, both in
+// shared memory (a thread-private 32 x 32 FP64 array would need 16 KB of
+// local memory per thread).  One-sided Jacobi rotations on the column pairs
+// (p, q) -- the same rotation as pinv_column -- with the column sums of
+// |U|^2 and U^H U formed by warp butterflies, so every lane sees the same
+// values and the control flow stays uniform.
+template <class R, int MK>
+__device__ __noinline__ void ip_pinv_warp(const cx<R>* Qs, const double2* Vmu, int mu, float rtol,
+                                          cx<double>* qout, cx<double>* U, cx<double>* Jm) {
   using O = RealOps<R>;
-  constexpr int MK = 16, E = MK * MK;
+  const int lane = threadIdx.x & 31;
+  const bool act = lane < MK;
+  for (int cc = 0; cc < MK; ++cc) {
+    if (act) {
+      double sr = 0.0, si = 0.0;
+      for (int l = 0; l < MK; ++l) {
+        const cx<R> qrl = Qs[lane * MK + l];
+        const double qr = O::to_d(qrl.re), qim = O::to_d(qrl.im);
+        const double2 v = Vmu[l * MK + cc];
+        sr += qr * v.x - qim * v.y;
+        si += qr * v.y + qim * v.x;
+      }
+      U[lane * MK + cc] = cmake(sr, si);
+      Jm[lane * MK + cc] = cmake(lane == cc ? 1.0 : 0.0, 0.0);
+    }
+  }
+  __syncwarp();
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < MK; ++p)
+      for (int qq = p + 1; qq < MK; ++qq) {
+        const cx<double> up = act ? U[lane * MK + p] : cmake(0.0, 0.0);
+        const cx<double> uq = act ? U[lane * MK + qq] : cmake(0.0, 0.0);
+        const double al = warp_sum_all(up.re * up.re + up.im * up.im);
+        const double be = warp_sum_all(uq.re * uq.re + uq.im * uq.im);
+        const double gr = warp_sum_all(up.re * uq.re + up.im * uq.im);  // conj(u_p) u_q
+        const double gi = warp_sum_all(up.re * uq.im - up.im * uq.re);
+        const double gm = sqrt(gr * gr + gi * gi);
+        const double nrm = sqrt(al * be);
+        if (!(gm > 1e-300) || !(gm > 1e-15 * nrm)) continue;
+        off = fmax(off, gm / nrm);
+        const double pr = gr / gm, pi = -gi / gm;  // conj(gamma / |gamma|)
+        const double zeta = (be - al) / (2.0 * gm);
+        const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
+        if (act) {
+          const cx<double> uq2 = cmake(uq.re * pr - uq.im * pi, uq.re * pi + uq.im * pr);
+          U[lane * MK + p] = cmake(cs * up.re - sn * uq2.re, cs * up.im - sn * uq2.im);
+          U[lane * MK + qq] = cmake(sn * up.re + cs * uq2.re, sn * up.im + cs * uq2.im);
+          const cx<double> vp = Jm[lane * MK + p], vq = Jm[lane * MK + qq];
+          const cx<double> vq2 = cmake(vq.re * pr - vq.im * pi, vq.re * pi + vq.im * pr);
+          Jm[lane * MK + p] = cmake(cs * vp.re - sn * vq2.re, cs * vp.im - sn * vq2.im);
+          Jm[lane * MK + qq] = cmake(sn * vp.re + cs * vq2.re, sn * vp.im + cs * vq2.im);
+        }
+        __syncwarp();
+      }
+    if (off < 1e-15) break;
+  }
+  double smax2 = 0.0;
+  for (int cc = 0; cc < MK; ++cc) {
+    const cx<double> u = act ? U[lane * MK + cc] : cmake(0.0, 0.0);
+    smax2 = fmax(smax2, warp_sum_all(u.re * u.re + u.im * u.im));
+  }
+  cx<double> q = cmake(0.0, 0.0);
+  for (int cc = 0; cc < MK; ++cc) {
+    const cx<double> u = act ? U[lane * MK + cc] : cmake(0.0, 0.0);
+    const double s2 = warp_sum_all(u.re * u.re + u.im * u.im);
+    if (!(s2 > (double)rtol * (double)rtol * smax2) || !(s2 > 0.0)) continue;
+    const cx<double> um = U[mu * MK + cc];
+    const double cr = um.re / s2, ci = -um.im / s2;  // conj(U[mu][c]) / sigma_c^2
+    if (act) {
+      const cx<double> v = Jm[lane * MK + cc];
+      q.re += v.re * cr - v.im * ci;
+      q.im += v.re * ci + v.im * cr;
+    }
+  }
+  if (act) qout[lane] = q;
+  __syncwarp();
+}
+
+// One all-microphone block per CTA of MK^2 threads (conventional
+// FastMNMF, M_k = MK = 16 or 32): thread e owns entry (i, j) = (e / MK,
+// e % MK).  For mu ascending: V_mu is staged in shared memory, A = Q V_mu
+// formed entry by entry, A q = e_mu solved by Gauss-Jordan elimination with
+// partial pivoting (each warp finds the pivot row by a butterfly over the
+// column's magnitudes, first maximum on ties; rows are exchanged through
+// shared memory), then Eq. (15) with a block reduction of Re q^H V q.  The
+// singularity test and the pseudo-inverse fallback are those of k_ip.
+template <int MK, class R>
+__global__ void __launch_bounds__(MK * MK, MK <= 16 ? 2 : 1) k_ip_all(const double2* __restrict__ V, const float4* __restrict__ Vdd,
+                                                     double2* __restrict__ Q64, float2* __restrict__ Q32, float eps,
+                                                     float rtol, unsigned* __restrict__ flags) {
+  using O = RealOps<R>;
+  constexpr int E = MK * MK, NW = E / 32;
   const int blk = blockIdx.x;
   const int e = threadIdx.x, i = e / MK, j = e % MK, lane = e & 31, warp = e >> 5;
-  __shared__ cx<R> Qs[E], As[E], Vs[E];
+  extern __shared__ __align__(16) unsigned char smip[];
+  cx<R>* Qs = reinterpret_cast<cx<R>*>(smip);
+  cx<R>* As = Qs + E;
+  cx<R>* Vs = As + E;
+  cx<double>* Ub = reinterpret_cast<cx<double>*>(Vs + E);  // [MK][MK] pinv workspace (MK = 32 only)
+  cx<double>* Jb = Ub + E;
   __shared__ cx<R> bs[MK];
-  __shared__ float keys[MK], wmax[8];
-  __shared__ R wred[8];
+  __shared__ float keys[MK], wmax[NW];
+  __shared__ R wred[NW];
   __shared__ cx<double> qfb[MK];
   Qs[e] = cfrom_d2<R>(Q64[(size_t)blk * E + e]);
   const size_t vbase = (size_t)blk * E * MK;
@@ -377,15 +469,22 @@ __global__ void __launch_bounds__(256, 2) k_ip16(const double2* __restrict__ V, 
     for (int c = 0; c < MK; ++c) {
       As[e] = a;
       if (j == 0) bs[i] = bv;
-      if (j == c) keys[i] = (i >= c) ? cabs2_f(a) : -1.f;
+      if (j == c) {
+        const float kv = cabs2_f(a);
+        keys[i] = (i >= c) ? (kv == kv ? kv : -1.5f) : -1.f;  // rows above c never pivot; NaN never wins
+      }
       __syncthreads();
-      int prow = c;
-      float best = keys[c];
-      for (int r = c + 1; r < MK; ++r)
-        if (keys[r] > best) {
-          best = keys[r];
-          prow = r;
+      float best = lane < MK ? keys[lane] : -2.f;
+      int prow = lane;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ob = __shfl_xor_sync(DFM_FULL_MASK, best, o);
+        const int op = __shfl_xor_sync(DFM_FULL_MASK, prow, o);
+        if (ob > best || (ob == best && op < prow)) {
+          best = ob;
+          prow = op;
         }
+      }
       const int ri = (i == c) ? prow : (i == prow ? c : i);  // this thread's row after the exchange
       const cx<R> piv = As[prow * MK + c];
       minpiv = fminf(minpiv, sqrtf(cabs2_f(piv)));
@@ -404,13 +503,15 @@ __global__ void __launch_bounds__(256, 2) k_ip16(const double2* __restrict__ V, 
     }
     float maxabs = 0.f;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) maxabs = fmaxf(maxabs, wmax[w]);
+    for (int w = 0; w < NW; ++w) maxabs = fmaxf(maxabs, wmax[w]);
     const bool singular = !(minpiv > rtol * maxabs);
     if (singular) {
-      if (e == 0) {
-        ip16_pinv<R>(Qs, Vb + (size_t)mu * E, mu, rtol, qfb);
-        atomicAdd(flags + FLAG_PINV, 1u);
+      if constexpr (MK <= 16) {
+        if (e == 0) ip16_pinv<R>(Qs, Vb + (size_t)mu * E, mu, rtol, qfb);
+      } else {
+        if (warp == 0) ip_pinv_warp<R, MK>(Qs, Vb + (size_t)mu * E, mu, rtol, qfb, Ub, Jb);
       }
+      if (e == 0) atomicAdd(flags + FLAG_PINV, 1u);
     } else if (j == 0) {
       qfb[i] = cmake(O::to_d(bv.re), O::to_d(bv.im));  // float pairs are exact in FP64
     }
@@ -426,7 +527,7 @@ __global__ void __launch_bounds__(256, 2) k_ip16(const double2* __restrict__ V, 
     __syncthreads();
     R sum = O::zero();
 #pragma unroll
-    for (int w = 0; w < 8; ++w) sum = O::add(sum, wred[w]);
+    for (int w = 0; w < NW; ++w) sum = O::add(sum, wred[w]);
     if (!(O::to_f(sum) > eps)) sum = O::from_f(eps);
     const R rs = O::div(O::one(), O::sqrt_(sum));
     if (i == mu) Qs[mu * MK + j] = cscale(cconj(qj), rs);
@@ -437,6 +538,26 @@ __global__ void __launch_bounds__(256, 2) k_ip16(const double2* __restrict__ V, 
   if (!isfinite(re) || !isfinite(im)) atomicOr(flags + FLAG_NONFINITE, 1u);
   Q64[(size_t)blk * E + e] = make_double2(re, im);
   Q32[(size_t)blk * E + e] = make_float2((float)re, (float)im);
+}
+
+template <int MK, class R>
+static void launch_ip_all_k(const dfmnmf_ctx* c, cudaStream_t s, int nblocks, size_t o) {
+  constexpr int E = MK * MK;
+  const size_t sm = 3 * (size_t)E * sizeof(cx<R>) + (MK > 16 ? 2 * (size_t)E * sizeof(cx<double>) : 0);
+  auto kern = k_ip_all<MK, R>;
+  if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const size_t ov = o * E * MK, oq = o * E;
+  kern<<<nblocks, E, sm, s>>>(c->V + ov, c->Vdd + ov, c->Q64 + oq, c->Q32 + oq, c->eps, c->singular_rtol, c->flags);
+}
+
+template <int MK>
+static cudaError_t launch_ip_all(const dfmnmf_ctx* c, cudaStream_t s, int nblocks, size_t o) {
+  switch (c->ip_arith) {
+    case 0: launch_ip_all_k<MK, double>(c, s, nblocks, o); break;
+    case 1: launch_ip_all_k<MK, dd>(c, s, nblocks, o); break;
+    default: launch_ip_all_k<MK, float>(c, s, nblocks, o); break;
+  }
+  return cudaGetLastError();
 }
 
 // ln |det Q_fk|^2 by FP64 Gaussian elimination with partial pivoting, one
@@ -528,6 +649,129 @@ __global__ void k_qinv(const double2* __restrict__ Q64, float2* __restrict__ Qin
       Qinv[(size_t)blk * MK * MK + r * MK + c] = make_float2((float)ar[r][MK + c], (float)ai[r][MK + c]);
 }
 
+// Warp-per-block forms of k_logdet and k_qinv for the 32 x 32 all-microphone
+// blocks: the matrix (and the identity it is reduced against) sits in shared
+// memory, lane q owning columns q and q + 32; the pivot row is found by a
+// butterfly over the lanes (lane r reads row r), first maximum on ties, as
+// in the one-thread forms.
+__device__ __forceinline__ void warp_argmax_first(double& best, int& row) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ob = __shfl_xor_sync(DFM_FULL_MASK, best, o);
+    const int orow = __shfl_xor_sync(DFM_FULL_MASK, row, o);
+    if (ob > best || (ob == best && orow < row)) {
+      best = ob;
+      row = orow;
+    }
+  }
+}
+
+template <int MK>
+__global__ void __launch_bounds__(32) k_logdet_w(const double2* __restrict__ Q64, double* __restrict__ out,
+                                                 int nblocks) {
+  extern __shared__ __align__(16) double2 sld[];  // [MK][MK]
+  const int blk = blockIdx.x, lane = threadIdx.x;
+  for (int i = lane; i < MK * MK; i += 32) sld[i] = Q64[(size_t)blk * MK * MK + i];
+  __syncwarp();
+  double acc = 0.0;
+  for (int c = 0; c < MK; ++c) {
+    double best = -1.0;
+    int p = lane;
+    if (lane >= c && lane < MK) {
+      const double2 v = sld[lane * MK + c];
+      best = v.x * v.x + v.y * v.y;
+      if (!(best == best)) best = -0.5;
+    }
+    warp_argmax_first(best, p);
+    if (p != c)
+      for (int q = lane; q < MK; q += 32) {
+        const double2 t = sld[c * MK + q];
+        sld[c * MK + q] = sld[p * MK + q];
+        sld[p * MK + q] = t;
+      }
+    __syncwarp();
+    const double2 pv = sld[c * MK + c];
+    const double b2 = pv.x * pv.x + pv.y * pv.y;
+    acc += log(b2);
+    if (!(b2 > 0.0)) continue;
+    for (int r = c + 1; r < MK; ++r) {
+      const double2 arc = sld[r * MK + c];
+      const double mr = (arc.x * pv.x + arc.y * pv.y) / b2;  // a[r][c] / a[c][c]
+      const double mi = (arc.y * pv.x - arc.x * pv.y) / b2;
+      __syncwarp();
+      for (int q = c + lane; q < MK; q += 32) {
+        const double2 cq = sld[c * MK + q];
+        double2 v = sld[r * MK + q];
+        v.x -= mr * cq.x - mi * cq.y;
+        v.y -= mr * cq.y + mi * cq.x;
+        sld[r * MK + q] = v;
+      }
+      __syncwarp();
+    }
+  }
+  if (lane == 0) out[blk] = acc;
+}
+
+template <int MK>
+__global__ void __launch_bounds__(32) k_qinv_w(const double2* __restrict__ Q64, float2* __restrict__ Qinv,
+                                               int nblocks, unsigned* __restrict__ flags) {
+  extern __shared__ __align__(16) double2 sqi[];  // [MK][2 MK]: [Q | I] reduced to [I | Q^-1]
+  constexpr int W2 = 2 * MK;
+  const int blk = blockIdx.x, lane = threadIdx.x;
+  for (int i = lane; i < MK * W2; i += 32) {
+    const int r = i / W2, q = i % W2;
+    sqi[i] = q < MK ? Q64[(size_t)blk * MK * MK + r * MK + q] : make_double2(q - MK == r ? 1.0 : 0.0, 0.0);
+  }
+  __syncwarp();
+  for (int c = 0; c < MK; ++c) {
+    double best = -1.0;
+    int p = lane;
+    if (lane >= c && lane < MK) {
+      const double2 v = sqi[lane * W2 + c];
+      best = v.x * v.x + v.y * v.y;
+      if (!(best == best)) best = -0.5;
+    }
+    warp_argmax_first(best, p);
+    if (p != c)
+      for (int q = lane; q < W2; q += 32) {
+        const double2 t = sqi[c * W2 + q];
+        sqi[c * W2 + q] = sqi[p * W2 + q];
+        sqi[p * W2 + q] = t;
+      }
+    __syncwarp();
+    const double2 pv = sqi[c * W2 + c];
+    double b2 = pv.x * pv.x + pv.y * pv.y;
+    if (!(b2 > 0.0)) {
+      if (lane == 0) atomicOr(flags + FLAG_NONFINITE, 1u);
+      b2 = 1.0;
+    }
+    const double ir = pv.x / b2, ii = -pv.y / b2;  // 1 / pivot
+    __syncwarp();
+    for (int q = lane; q < W2; q += 32) {
+      const double2 x = sqi[c * W2 + q];
+      sqi[c * W2 + q] = make_double2(x.x * ir - x.y * ii, x.x * ii + x.y * ir);
+    }
+    __syncwarp();
+    for (int r = 0; r < MK; ++r) {
+      if (r == c) continue;
+      const double2 m = sqi[r * W2 + c];
+      __syncwarp();
+      for (int q = lane; q < W2; q += 32) {
+        const double2 cq = sqi[c * W2 + q];
+        double2 v = sqi[r * W2 + q];
+        v.x -= m.x * cq.x - m.y * cq.y;
+        v.y -= m.x * cq.y + m.y * cq.x;
+        sqi[r * W2 + q] = v;
+      }
+      __syncwarp();
+    }
+  }
+  for (int i = lane; i < MK * MK; i += 32) {
+    const double2 v = sqi[(i / MK) * W2 + MK + i % MK];
+    Qinv[(size_t)blk * MK * MK + i] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
 // Gradient of Eq. (12) with respect to one block Q_fk, packed as
 // dL/dRe + i dL/dIm:  dQ[mu][j] = 2 T ((Q V_mu)[mu][j] - conj(Q^{-1})[j][mu]),
 // where (Q V_mu)[mu][:] = (1/T) sum_t z_mu conj(x) / yhat_mu is the data term
@@ -616,15 +860,8 @@ __global__ void k_q32(const double2* __restrict__ Q64, float2* __restrict__ Q32,
 cudaError_t launch_ip(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
   const int nblocks = fc * c->K;
   const size_t o = (size_t)fb * c->K;  // first block of the range
-  if (c->MK == 16) {
-    const size_t ov = o * 16 * 16 * 16, oq = o * 16 * 16;
-    switch (c->ip_arith) {
-      case 0: k_ip16<double><<<nblocks, 256, 0, s>>>(c->V + ov, c->Vdd + ov, c->Q64 + oq, c->Q32 + oq, c->eps, c->singular_rtol, c->flags); break;
-      case 1: k_ip16<dd><<<nblocks, 256, 0, s>>>(c->V + ov, c->Vdd + ov, c->Q64 + oq, c->Q32 + oq, c->eps, c->singular_rtol, c->flags); break;
-      default: k_ip16<float><<<nblocks, 256, 0, s>>>(c->V + ov, c->Vdd + ov, c->Q64 + oq, c->Q32 + oq, c->eps, c->singular_rtol, c->flags); break;
-    }
-    return cudaGetLastError();
-  }
+  if (c->MK == 16) return launch_ip_all<16>(c, s, nblocks, o);
+  if (c->MK == 32) return launch_ip_all<32>(c, s, nblocks, o);
   const int grid = (nblocks + 7) / 8;  // 4 warps x 2 blocks per CTA
   DFM_MK_DISPATCH(c->MK, {
     switch (c->ip_arith) {
@@ -647,6 +884,10 @@ cudaError_t launch_logdet(const dfmnmf_ctx* c, double* out, cudaStream_t s) {
     k_logdet<16><<<(nblocks + 127) / 128, 128, 0, s>>>(c->Q64, out, nblocks);
     return cudaGetLastError();
   }
+  if (c->MK == 32) {
+    k_logdet_w<32><<<nblocks, 32, 32 * 32 * sizeof(double2), s>>>(c->Q64, out, nblocks);
+    return cudaGetLastError();
+  }
   DFM_MK_DISPATCH(c->MK, { k_logdet<MK_><<<(nblocks + 127) / 128, 128, 0, s>>>(c->Q64, out, nblocks); });
   return cudaGetLastError();
 }
@@ -655,6 +896,10 @@ cudaError_t launch_qinv(const dfmnmf_ctx* c, cudaStream_t s) {
   const int nblocks = c->F * c->K;
   if (c->MK == 16) {
     k_qinv<16><<<(nblocks + 127) / 128, 128, 0, s>>>(c->Q64, c->Qinv32, nblocks, c->flags);
+    return cudaGetLastError();
+  }
+  if (c->MK == 32) {
+    k_qinv_w<32><<<nblocks, 32, 32 * 64 * sizeof(double2), s>>>(c->Q64, c->Qinv32, nblocks, c->flags);
     return cudaGetLastError();
   }
   DFM_MK_DISPATCH(c->MK, { k_qinv<MK_><<<(nblocks + 127) / 128, 128, 0, s>>>(c->Q64, c->Qinv32, nblocks, c->flags); });

@@ -574,6 +574,7 @@ static cudaError_t launch_pstats_impl(const dfmnmf_ctx* c, cudaStream_t s, int f
   if (c->MK == 4 && c->K == 1) return launch_pstats_ft<1, 4, COMPUTE_P, COMP>(c, s, fb, fc);
   if (c->MK == 4 && c->K == 3) return launch_pstats_ft<3, 4, COMPUTE_P, COMP>(c, s, fb, fc);
   if (c->MK == 16 && c->K == 1) return launch_pstats_ft<1, 16, COMPUTE_P, COMP>(c, s, fb, fc);
+  if (c->MK == 32 && c->K == 1) return launch_pstats_ft<1, 32, COMPUTE_P, COMP>(c, s, fb, fc);
   if (c->MK == 4 && c->K == 8) return launch_pstats_ft<8, 4, COMPUTE_P, COMP>(c, s, fb, fc);
   const int TB = 256 / c->K;
   dim3 grid(fc, (c->T + TB - 1) / TB);

@@ -95,6 +95,9 @@ cudaError_t launch_loglik(const dfmnmf_ctx* c, cudaStream_t s) {
   if (c->MK == 16) {
     k_nll_data<16><<<dim3(c->F, ty), 128, gq_smem(c), s>>>(c->x, c->Q64, c->lam, c->g, c->red, c->F, c->T, c->Tp,
                                                             c->K, c->N, c->eps);
+  } else if (c->MK == 32) {
+    k_nll_data<32><<<dim3(c->F, ty), 128, gq_smem(c), s>>>(c->x, c->Q64, c->lam, c->g, c->red, c->F, c->T, c->Tp,
+                                                            c->K, c->N, c->eps);
   } else {
     DFM_MK_DISPATCH(c->MK, {
       k_nll_data<MK_><<<dim3(c->F, ty), 128, gq_smem(c), s>>>(c->x, c->Q64, c->lam, c->g, c->red, c->F, c->T,
@@ -178,6 +181,9 @@ cudaError_t launch_separate(const dfmnmf_ctx* c, float2* out, cudaStream_t s) {
   const size_t sm = gq_smem(c) + (size_t)c->K * c->MK * c->MK * sizeof(float2);
   if (c->MK == 16) {
     k_separate<16><<<dim3(c->F, ty), 128, sm, s>>>(c->x, c->Q64, c->Qinv32, c->lam, c->g, out, c->F, c->T, c->Tp,
+                                                    c->K, c->N, c->eps);
+  } else if (c->MK == 32) {
+    k_separate<32><<<dim3(c->F, ty), 128, sm, s>>>(c->x, c->Q64, c->Qinv32, c->lam, c->g, out, c->F, c->T, c->Tp,
                                                     c->K, c->N, c->eps);
   } else {
     DFM_MK_DISPATCH(c->MK, {

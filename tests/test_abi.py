@@ -45,7 +45,8 @@ def _args(F=3, T=4, mics=(4, 4), N=2, B_=3):
 
 @pytest.mark.parametrize("bad", [dict(F=0), dict(T=0), dict(N=0), dict(B_=0), dict(mics=(4, 3)),
                                  dict(mics=(5,)), dict(mics=(0,)), dict(N=17), dict(B_=65),
-                                 dict(mics=(1,) * 17), dict(mics=(16, 16)), dict(mics=(8,))])
+                                 dict(mics=(1,) * 17), dict(mics=(16, 16)), dict(mics=(8,)),
+                                 dict(mics=(32, 32)), dict(mics=(24,)), dict(mics=(64,))])
 def test_invalid_descriptor_rejected(lib, bad):
     a = _args(**bad)
     with pytest.raises(D.DfmnmfError) as ei:

@@ -1,10 +1,12 @@
-"""Conventional all-microphone FastMNMF (K = 1, one 16 x 16 diagonaliser per
-frequency, Sec. II-A) on the GPU against the FP64 oracle, which runs the same
-equations at K = 1 (the distributed method reduces to it there, Sec. III-B).
+"""Conventional all-microphone FastMNMF (K = 1, one 16 x 16 or 32 x 32
+diagonaliser per frequency, Sec. II-A) on the GPU against the FP64 oracle,
+which runs the same equations at K = 1 (the distributed method reduces to it
+there, Sec. III-B).
 
 Tolerances are those of the FP32 form: every single update within 1e-5
-normwise relative error, Eq. (12) within 1e-3 and the SDR within 0.1 dB after
-the iterations.  With 16 microphones and at most 5 sources the weighted
+normwise relative error (and element by element against the scale floors of
+tests/_helpers.py), Eq. (12) within 1e-3 and the SDR within 0.1 dB after the
+iterations.  With 16 or 32 microphones and at most 5 sources the weighted
 covariances are far more ill-conditioned (cond ~ 1e7) than per-subarray ones,
 which is what the float-float covariances and IP solves are for.
 """
@@ -13,7 +15,7 @@ import pytest
 
 import oracle as O
 from paper_2605_19388_gb300 import synth
-from tests._helpers import rel_err, v_oracle_layout, sdr_db, oracle_state
+from tests._helpers import rel_err, v_oracle_layout, sdr_db, oracle_state, check_both
 
 pytestmark = pytest.mark.gpu
 
@@ -24,7 +26,7 @@ if not torch.cuda.is_available():  # pragma: no cover
 from paper_2605_19388_gb300 import dfmnmf as D  # noqa: E402
 
 TOL = 1e-5
-ALLMIC = (16,)
+LAYOUTS = [(16,), (32,)]
 
 
 def make_ctx(p, Q0=None, ip=D.DFMNMF_IP_F32X2):
@@ -37,10 +39,11 @@ def gpu_state(ctx):
     return O.state_from_arrays(Q, W, H, g, ctx.mics)
 
 
+@pytest.mark.parametrize("mics", LAYOUTS)
 @pytest.mark.parametrize("ip", [D.DFMNMF_IP_F32X2, D.DFMNMF_IP_F64])
-def test_allmic_stage_parity(ip):
+def test_allmic_stage_parity(ip, mics):
     """The five stages once, each against the oracle fed the GPU's own inputs."""
-    p = synth.make_problem(13, 150, ALLMIC, 4, 6, seed=41)
+    p = synth.make_problem(13, 150, mics, 4, 6, seed=41)
     Q0 = synth.random_blocks(p.F, p.mics, seed=42, scale=0.2)
     x = p.x.astype(np.complex128)
     ctx = make_ctx(p, Q0, ip)
@@ -49,57 +52,86 @@ def test_allmic_stage_parity(ip):
     D.dfmnmf_run_stage(ctx, D.DFMNMF_STAGE_COV)
     V_gpu = D.buffer_numpy(ctx, D.DFMNMF_BUF_V)
     y = O.model_variance(O.source_psd(st.W, st.H), st.g)
-    errs["V"] = rel_err(V_gpu, v_oracle_layout(O.weighted_covariances(x, y, p.mics)))
+    check_both(errs, "V", V_gpu, v_oracle_layout(O.weighted_covariances(x, y, p.mics)), "V")
     D.dfmnmf_run_stage(ctx, D.DFMNMF_STAGE_IP)
     st2 = gpu_state(ctx)
-    errs["Q"] = rel_err(st2.Q[0], O.ip_update(st.Q, [V_gpu[:, 0].astype(np.complex128)])[0])
+    check_both(errs, "Q", st2.Q[0], O.ip_update(st.Q, [V_gpu[:, 0].astype(np.complex128)])[0], "Q")
     D.dfmnmf_run_stage(ctx, D.DFMNMF_STAGE_W)
     st3 = gpu_state(ctx)
     P_ref = O.projected_power(x, st2.Q, p.mics)
-    errs["P"] = rel_err(D.buffer_numpy(ctx, D.DFMNMF_BUF_P), P_ref)
-    errs["W"] = rel_err(st3.W, O.update_W(st2.W, st2.H, st2.g, P_ref))
+    check_both(errs, "P", D.buffer_numpy(ctx, D.DFMNMF_BUF_P), P_ref, "med")
+    check_both(errs, "W", st3.W, O.update_W(st2.W, st2.H, st2.g, P_ref), "med")
     D.dfmnmf_run_stage(ctx, D.DFMNMF_STAGE_H)
     st4 = gpu_state(ctx)
-    errs["H"] = rel_err(st4.H, O.update_H(st3.W, st3.H, st3.g, P_ref))
+    check_both(errs, "H", st4.H, O.update_H(st3.W, st3.H, st3.g, P_ref), "med")
     D.dfmnmf_run_stage(ctx, D.DFMNMF_STAGE_G)
-    errs["g"] = rel_err(gpu_state(ctx).g, O.update_g(st4.W, st4.H, st4.g, P_ref))
+    check_both(errs, "g", gpu_state(ctx).g, O.update_g(st4.W, st4.H, st4.g, P_ref), "med")
+    print("all-microphone", mics, "ip", ip, errs)
     for k, v in errs.items():
         assert v <= TOL, (k, v, errs)
 
 
-def test_allmic_covariances_ragged_frames():
+@pytest.mark.parametrize("mics", LAYOUTS)
+def test_allmic_covariances_ragged_frames(mics):
     """Frame counts that leave a partial chunk and odd bin counts."""
-    p = synth.make_problem(5, 97, ALLMIC, 3, 4, seed=43)
+    p = synth.make_problem(5, 97, mics, 3, 4, seed=43)
     ctx = make_ctx(p)
     st = gpu_state(ctx)
     D.dfmnmf_run_stage(ctx, D.DFMNMF_STAGE_COV)
     y = O.model_variance(O.source_psd(st.W, st.H), st.g)
     V_ref = v_oracle_layout(O.weighted_covariances(p.x.astype(np.complex128), y, p.mics))
     # exact float-float sums of exact products; the weights 1/yhat are FP32 (relative 6e-8 each)
-    assert rel_err(D.buffer_numpy(ctx, D.DFMNMF_BUF_V), V_ref) < 1e-6
+    errs = check_both({}, "V", D.buffer_numpy(ctx, D.DFMNMF_BUF_V), V_ref, "V")
+    assert max(errs.values()) < 1e-6, errs
 
 
+@pytest.mark.parametrize("mics", LAYOUTS)
 @pytest.mark.parametrize("ip", [D.DFMNMF_IP_F32X2, D.DFMNMF_IP_F64])
-def test_allmic_singular_uses_pseudo_inverse(ip):
-    """T < 16 frames: every V_mu has rank 6 (the pseudo-inverse rule, Sec. IV-A).
+def test_allmic_singular_uses_pseudo_inverse(ip, mics):
+    """T = 6 frames < M: every V_mu has rank 6 (the pseudo-inverse rule, Sec. IV-A).
 
-    Sixteen successive pseudo-inverse rows on rank-6 covariances amplify any
-    change of V enormously (the FP32 weights' 3e-8 moves the oracle's own
-    result by orders of magnitude), so the oracle is fed the GPU's V, as in
-    the stage-by-stage checks."""
-    p = synth.make_problem(2, 6, ALLMIC, 2, 2, seed=44)
+    A chain of M pseudo-inverse rows on rank-6 covariances amplifies any
+    change of its inputs enormously (a relative change of 1e-13 in V moves
+    the oracle's own final Q by ~4e-7, one of 1e-11 by orders of magnitude),
+    so each row is checked on its own: row mu of the GPU's result against the
+    oracle's Eqs. (14)-(15) applied to the Q that row mu was computed from --
+    the GPU's rows 0..mu-1, the initial rows mu..M-1 -- and the GPU's V.
+    Even one such row is sensitive: a relative change of 1e-13 in V moves
+    the oracle's rows by up to ~9e-7 (measured on this problem); the GPU's
+    V keeps the rank-6 structure to ~1e-15 (its 7th singular value is
+    printed), and its rows come within ~2e-9 (measured), held to 1e-7."""
+    p = synth.make_problem(2, 6, mics, 2, 2, seed=44)
     ctx = make_ctx(p, ip=ip)
     st = gpu_state(ctx)
     D.dfmnmf_run_stage(ctx, D.DFMNMF_STAGE_COV)
     V_gpu = D.buffer_numpy(ctx, D.DFMNMF_BUF_V)[:, 0].astype(np.complex128)
     D.dfmnmf_run_stage(ctx, D.DFMNMF_STAGE_IP)
-    Q_ref = O.ip_update(st.Q, [V_gpu])
-    assert rel_err(gpu_state(ctx).Q[0], Q_ref[0]) < 1e-4
+    Q_gpu = gpu_state(ctx).Q[0]
+    Q_init = st.Q[0]
+    M = p.M
+    # in exact arithmetic every V_mu has rank 6 (the oracle's own V, from the same state)
+    y = O.model_variance(O.source_psd(st.W, st.H), st.g)
+    V_ref = O.weighted_covariances(p.x.astype(np.complex128), y, p.mics)[0]
+    sv_ref = np.linalg.svd(V_ref[0, 0], compute_uv=False)
+    sv_gpu = np.linalg.svd(V_gpu[0, 0], compute_uv=False)
+    print("singular values of V_0 (bin 0), oracle", sv_ref[[0, 5, 6]], "GPU", sv_gpu[[0, 5, 6]])
+    assert sv_ref[6] <= 1e-12 * sv_ref[0]
+    worst = 0.0
+    for mu in range(M):
+        Q_before = Q_gpu.copy()
+        Q_before[:, mu:, :] = Q_init[:, mu:, :]
+        row_ref = O.ip_update_row(Q_before, V_gpu, mu)[:, mu, :]
+        worst = max(worst, rel_err(Q_gpu[:, mu, :], row_ref))
+    chained = rel_err(Q_gpu, O.ip_update(st.Q, [V_gpu])[0])
+    print("all-microphone", mics, "ip", ip, "pseudo-inverse rows: worst row", worst, "chained", chained)
+    assert sv_gpu[6] <= 1e-12 * sv_gpu[0]  # the same pseudo-inverse rank decision as the oracle's
+    assert worst < 1e-7
 
 
-def test_allmic_trajectory_loglik_and_wiener():
+@pytest.mark.parametrize("mics", LAYOUTS)
+def test_allmic_trajectory_loglik_and_wiener(mics):
     """20 iterations, then Eq. (12) and the Wiener filter against the oracle's run."""
-    p = synth.make_problem(17, 200, ALLMIC, 3, 4, seed=45, with_images=True)
+    p = synth.make_problem(17, 200, mics, 3, 4, seed=45, with_images=True)
     x = p.x.astype(np.complex128)
     ctx = make_ctx(p)
     D.dfmnmf_iterate(ctx, 20)
@@ -114,11 +146,13 @@ def test_allmic_trajectory_loglik_and_wiener():
     c_ref = O.wiener_filter(x, p.mics, st)
     sdr_gpu, _ = sdr_db(c_gpu.cpu().numpy(), p.c)
     sdr_ref, _ = sdr_db(c_ref, p.c)
+    print("all-microphone", mics, "20 iterations: nll", nll_gpu, nll_ref, "SDR", sdr_gpu, sdr_ref)
     assert np.max(np.abs(np.sort(sdr_gpu) - np.sort(sdr_ref))) <= 0.1, (sdr_gpu, sdr_ref)
 
 
-def test_allmic_rejects_tensor_core_form_and_two_blocks():
-    p = synth.make_problem(3, 20, ALLMIC, 2, 2, seed=46)
+@pytest.mark.parametrize("mics", LAYOUTS)
+def test_allmic_rejects_tensor_core_form_and_two_blocks(mics):
+    p = synth.make_problem(3, 20, mics, 2, 2, seed=46)
     with pytest.raises(D.DfmnmfError) as ei:
         D.dfmnmf_init(p.F, p.T, p.mics, p.N, p.B, p.x, p.W0, p.H0, p.g0, precision=D.DFMNMF_BF16_TC)
     assert ei.value.code == D.DFMNMF_EINVAL
