@@ -139,6 +139,7 @@ def kernel_bytes(F, T, M, N, B, K, MK):
         "k_pstats": 8 * F * T * M + 4 * N * F * T + 4 * F * N * M + 8 * q + 4 * F * T * M + 8 * N * F * T,
         "k_wupd": 8 * N * F * T + 4 * N * B * T + 8 * N * F * B + 4 * N * F * T,
         "k_wupd_tc": 8 * N * F * T + 4 * N * B * T + 8 * N * F * B,
+        "k_wlam": 12 * N * F * T + 4 * N * B * T + 8 * N * F * B,
         "k_stats": 4 * F * T * M + 4 * N * F * T + 4 * F * N * M + 8 * N * F * T,
         "k_hupd": 8 * N * F * T + 4 * N * F * B + 8 * N * B * T + 4 * N * F * T,
         "k_gupd": 4 * N * F * T + 4 * F * T * M + 8 * F * N * M,
@@ -780,7 +781,8 @@ def main():
                                       D.DFMNMF_IP_F32X2: "f32x2"}[ipv],
                          "nll_last": nll_box[-1],
                          "k_ip_ms": dict(D.dfmnmf_kernel_times(c2, 10)).get("k_ip"),
-                         "w_update_ms": {k: v for k, v in D.dfmnmf_kernel_times(c2, 10) if k.startswith("k_wupd")}}
+                         "w_update_ms": {k: v for k, v in D.dfmnmf_kernel_times(c2, 10)
+                                         if k.startswith(("k_wupd", "k_wlam")) or k == "k_lambda"}}
             D.dfmnmf_destroy(c2)
         out["variants"] = var
 

@@ -117,11 +117,15 @@ int iteration_launches(const dfmnmf_ctx* c, Launch* out) {
   else out[n++] = {DFMNMF_STAGE_COV, "k_cov", dfm::launch_cov, true};
   out[n++] = {DFMNMF_STAGE_IP, "k_ip", dfm::launch_ip, true};
   out[n++] = {DFMNMF_STAGE_W, "k_pstats", dfm::launch_power_stats, true};
-  if (dfm::is_tc(c->precision) && c->cfg_wupd_tc)
-    out[n++] = {DFMNMF_STAGE_W, "k_wupd_tc", [](const dfmnmf_ctx* c, cudaStream_t s, int, int) { return dfm::launch_wupd_tc(c, s); }, false};
-  else
-    out[n++] = {DFMNMF_STAGE_W, "k_wupd", [](const dfmnmf_ctx* c, cudaStream_t s, int, int) { return dfm::launch_wupd(c, s); }, false};
-  out[n++] = {DFMNMF_STAGE_W, "k_lambda", [](const dfmnmf_ctx* c, cudaStream_t s, int, int) { return dfm::launch_lambda(c, s); }, false};
+  if ((dfm::is_tc(c->precision) && c->cfg_wupd_tc) || !dfm::wlam_supported(c)) {
+    if (dfm::is_tc(c->precision) && c->cfg_wupd_tc)
+      out[n++] = {DFMNMF_STAGE_W, "k_wupd_tc", [](const dfmnmf_ctx* c, cudaStream_t s, int, int) { return dfm::launch_wupd_tc(c, s); }, false};
+    else
+      out[n++] = {DFMNMF_STAGE_W, "k_wupd", [](const dfmnmf_ctx* c, cudaStream_t s, int, int) { return dfm::launch_wupd(c, s); }, false};
+    out[n++] = {DFMNMF_STAGE_W, "k_lambda", [](const dfmnmf_ctx* c, cudaStream_t s, int, int) { return dfm::launch_lambda(c, s); }, false};
+  } else {
+    out[n++] = {DFMNMF_STAGE_W, "k_wlam", [](const dfmnmf_ctx* c, cudaStream_t s, int, int) { return dfm::launch_wlam(c, s); }, false};
+  }
   out[n++] = {DFMNMF_STAGE_H, "k_stats", [](const dfmnmf_ctx* c, cudaStream_t s, int, int) { return dfm::launch_stats(c, s); }, false};
   out[n++] = {DFMNMF_STAGE_H, "k_hupd", [](const dfmnmf_ctx* c, cudaStream_t s, int, int) { return dfm::launch_hupd(c, s); }, false};
   out[n++] = {DFMNMF_STAGE_H, "k_lambda", [](const dfmnmf_ctx* c, cudaStream_t s, int, int) { return dfm::launch_lambda(c, s); }, false};

@@ -79,6 +79,8 @@ cudaError_t launch_power_stats(const dfmnmf_ctx* c, cudaStream_t s, int fb, int 
 // otherwise the gradient of Eq. (12) with respect to it (den - num of the
 // rule) is written there and the factor is left unchanged.
 cudaError_t launch_wupd(const dfmnmf_ctx* c, cudaStream_t s, float* grad = nullptr);  // Eq. 8
+cudaError_t launch_wlam(const dfmnmf_ctx* c, cudaStream_t s);  // Eq. 8 and the Eq. 2 refresh, one launch
+bool wlam_supported(const dfmnmf_ctx* c);  // its shared-memory tile fits (B Tp + 16 Tp floats)
 cudaError_t launch_wupd_tc(const dfmnmf_ctx* c, cudaStream_t s, float* grad = nullptr);  // Eq. 8, tcgen05 TF32
 size_t wupd_tc_scratch_float2s(const dfmnmf_ctx* c);
 size_t wupd_tc_ticket_count(const dfmnmf_ctx* c);

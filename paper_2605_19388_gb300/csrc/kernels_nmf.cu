@@ -153,6 +153,143 @@ __global__ void __launch_bounds__(256) k_wupd(const float* __restrict__ A, const
   }
 }
 
+// ------------------------------------------- Eq. (8) with the Eq. (2) refresh
+// One CTA per (source n, WL_F = 10 consecutive frequencies): 52 x 5 CTAs on
+// the paper's 513 bins, two per SM, one wave.  H[n] ([B][Tp]) and the CTA's
+// A and D rows ([10][Tp] each) are staged in shared memory by 16-byte
+// cp.async (all contiguous; the row stride Tp is a multiple of 4).  Warp w
+// takes frequency pair w % 5 and the 128-frame blocks k = w / 5 (mod 2);
+// each lane owns four consecutive frames of a block (16-byte shared-memory
+// reads of A, D and H), accumulates num[b] = sum_t A H[b] and
+// den[b] = sum_t D H[b] for 16 bases of both frequencies, one reduce-scatter
+// gives lane l the warp totals of frequency l / 16, basis l % 16, the second
+// warp's totals are added to the first's through shared memory (fixed
+// order), and that lane updates the W entry.  Then warp w refreshes
+// lambda[n][f][t] = sum_b W[n][f][b] H[n][b][t] (Eq. 2) for frequency w of
+// the CTA, four frames per lane, in the basis order of k_lambda (bit for bit
+// the same refresh).  No partial sums leave the CTA, no second launch.  More
+// than 16 bases are taken 16 at a time.
+constexpr int WL_F = 10;
+constexpr int WL_PAIRS = WL_F / 2;
+constexpr int WL_THREADS = 2 * WL_PAIRS * 32;
+
+size_t wlam_smem_bytes(const dfmnmf_ctx* c) {
+  const int Bq = (c->B + 15) & ~15;
+  return ((size_t)c->B * c->Tp + 2 * (size_t)WL_F * c->Tp + WL_PAIRS * 32 * 2 + (size_t)WL_F * Bq) * sizeof(float);
+}
+
+__global__ void __launch_bounds__(WL_THREADS, 2) k_wlam(const float* __restrict__ A, const float* __restrict__ D,
+                                                        const float* __restrict__ H, float* __restrict__ W,
+                                                        float* __restrict__ lam, int F, int T, int Tp, int B,
+                                                        float eps, unsigned* __restrict__ flags) {
+  extern __shared__ __align__(16) float smw[];
+  const int Bq = (B + 15) & ~15;
+  float* Hs = smw;                          // [B][Tp]
+  float* As = Hs + (size_t)B * Tp;          // [WL_F][Tp]
+  float* Ds = As + (size_t)WL_F * Tp;       // [WL_F][Tp]
+  float* red = Ds + (size_t)WL_F * Tp;      // [WL_PAIRS][32 lanes][2]: the second warp's totals
+  float* wrow = red + WL_PAIRS * 32 * 2;    // [WL_F][Bq]: the new W rows
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n = blockIdx.y, f0 = blockIdx.x * WL_F, nf = min(WL_F, F - f0);
+  {
+    const float* srcH = H + (size_t)n * B * Tp;
+    const float* srcA = A + ((size_t)n * F + f0) * Tp;
+    const float* srcD = D + ((size_t)n * F + f0) * Tp;
+    const int nh = B * Tp / 4, na = nf * Tp / 4;
+    for (int i = tid; i < nh; i += WL_THREADS) cp_async16(Hs + 4 * i, srcH + 4 * i);
+    for (int i = tid; i < na; i += WL_THREADS) {
+      cp_async16(As + 4 * i, srcA + 4 * i);
+      cp_async16(Ds + 4 * i, srcD + 4 * i);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+  }
+  __syncthreads();
+  const int p = warp % WL_PAIRS, second = warp / WL_PAIRS;
+  const int fa = 2 * p, fb = 2 * p + 1;
+  const bool vb = fb < nf;
+  const float* Aa = As + (size_t)fa * Tp;
+  const float* Da = Ds + (size_t)fa * Tp;
+  const float* Ab = As + (size_t)(vb ? fb : fa) * Tp;
+  const float* Db = Ds + (size_t)(vb ? fb : fa) * Tp;
+  const bool va = fa < nf;
+  for (int b0 = 0; b0 < B; b0 += 16) {
+    float acc[64];  // entry 2 (fi 16 + j) + {0: num, 1: den}
+#pragma unroll
+    for (int i = 0; i < 64; ++i) acc[i] = 0.f;
+    if (va) {
+      for (int t = 128 * second + 4 * lane; t < T; t += 256) {
+        // frames t .. t+3; A and D beyond T are read as zero, H is zero there
+        float4 a0 = *reinterpret_cast<const float4*>(Aa + t), d0 = *reinterpret_cast<const float4*>(Da + t);
+        float4 a1 = *reinterpret_cast<const float4*>(Ab + t), d1 = *reinterpret_cast<const float4*>(Db + t);
+        if (t + 3 >= T) {
+          const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (t + 1 >= T) { a0.y = z.y; d0.y = z.y; a1.y = z.y; d1.y = z.y; }
+          if (t + 2 >= T) { a0.z = z.z; d0.z = z.z; a1.z = z.z; d1.z = z.z; }
+          a0.w = z.w; d0.w = z.w; a1.w = z.w; d1.w = z.w;
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const float4 h = (b0 + j < B) ? *reinterpret_cast<const float4*>(Hs + (size_t)(b0 + j) * Tp + t)
+                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+          acc[2 * j] = fmaf(a0.x, h.x, fmaf(a0.y, h.y, fmaf(a0.z, h.z, fmaf(a0.w, h.w, acc[2 * j]))));
+          acc[2 * j + 1] = fmaf(d0.x, h.x, fmaf(d0.y, h.y, fmaf(d0.z, h.z, fmaf(d0.w, h.w, acc[2 * j + 1]))));
+          acc[32 + 2 * j] = fmaf(a1.x, h.x, fmaf(a1.y, h.y, fmaf(a1.z, h.z, fmaf(a1.w, h.w, acc[32 + 2 * j]))));
+          acc[33 + 2 * j] = fmaf(d1.x, h.x, fmaf(d1.y, h.y, fmaf(d1.z, h.z, fmaf(d1.w, h.w, acc[33 + 2 * j]))));
+        }
+      }
+    }
+    warp_reduce_scatter<64>(acc, lane);
+    if (second) {
+      red[(p * 32 + lane) * 2] = acc[0];
+      red[(p * 32 + lane) * 2 + 1] = acc[1];
+    }
+    __syncthreads();
+    if (!second) {
+      const float num = acc[0] + red[(p * 32 + lane) * 2];
+      const float den = acc[1] + red[(p * 32 + lane) * 2 + 1];
+      const int fl = (lane >> 4) ? fb : fa, b = b0 + (lane & 15);
+      if (fl < nf && b < B) {
+        float* wp = W + ((size_t)n * F + f0 + fl) * B + b;
+        const float wn = *wp * sqrtf(num / fmaxf(den, eps));
+        if (!finitef(wn)) atomicOr(flags + FLAG_NONFINITE, 1u);
+        *wp = wn;
+        wrow[fl * Bq + b] = wn;
+      }
+    }
+    __syncthreads();  // wrow complete; red free for the next 16 bases
+  }
+  // warp w: frequency w of the CTA, four consecutive frames per lane (H is zero on T .. Tp-1, so is lambda)
+  for (int fl = warp; fl < nf; fl += WL_THREADS / 32) {
+    float* L = lam + ((size_t)n * F + f0 + fl) * Tp;
+    const float* wr = wrow + fl * Bq;
+    for (int t = 4 * lane; t < Tp; t += 128) {
+      float4 l = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
+      for (int b = 0; b < B; ++b) {
+        const float w = wr[b];
+        const float4 h = *reinterpret_cast<const float4*>(Hs + (size_t)b * Tp + t);
+        l.x = fmaf(w, h.x, l.x);
+        l.y = fmaf(w, h.y, l.y);
+        l.z = fmaf(w, h.z, l.z);
+        l.w = fmaf(w, h.w, l.w);
+      }
+      *reinterpret_cast<float4*>(L + t) = l;
+    }
+  }
+}
+bool wlam_supported(const dfmnmf_ctx* c) {
+  return c->smem_optin > 0 && wlam_smem_bytes(c) <= (size_t)c->smem_optin;
+}
+
+cudaError_t launch_wlam(const dfmnmf_ctx* c, cudaStream_t s) {
+  const size_t sm = wlam_smem_bytes(c);
+  cudaFuncSetAttribute(k_wlam, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  dim3 grid((c->F + WL_F - 1) / WL_F, c->N);
+  k_wlam<<<grid, WL_THREADS, sm, s>>>(c->A, c->D, c->H, c->W, c->lam, c->F, c->T, c->Tp, c->B, c->eps, c->flags);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ Eq. (9)
 // grid (ceil(T/16), N, ceil(B/16) * S); the S CTAs of a tile split the
 // frequencies (chunks of 64) and finish as in k_wupd; lane = (t pair, b quad).

@@ -58,3 +58,39 @@ def test_autotune_restores_state_and_keeps_parity():
     for k in range(len(p.mics)):
         assert rel_err(got.Q[k], ref.Q[k]) < 1e-5
     assert rel_err(got.W, ref.W) < 1e-5 and rel_err(got.H, ref.H) < 1e-5 and rel_err(got.g, ref.g) < 1e-5
+
+
+RAGGED = [dict(T=170, K=2, N=3), dict(T=233, K=4, N=5), dict(T=150, K=8, N=8),
+          dict(T=301, K=2, N=5), dict(T=190, K=8, N=3), dict(T=262, K=4, N=8)]
+
+
+def test_ragged_batch_against_the_oracle():
+    """A batch shaped like the 64-mixture workload (K in {2, 4, 8} subarrays of 4 mics, N in {3, 5, 8}, ragged
+    T, here F = 33): 5 iterations with one graph launch each, every mixture against the oracle's own
+    5 iterations from the same start -- Eq. (12) within 1e-3 (FP32 form, determined mixtures) or 1e-2
+    (tensor-core form, N >= 4) and the SDR of the Wiener output within 0.1 or 0.2 dB."""
+    from tests._helpers import sdr_db
+    probs, ctxs, forms = [], [], []
+    for i, s in enumerate(RAGGED):
+        p = synth.make_problem(33, s["T"], (4,) * s["K"], s["N"], 8, seed=70 + i, with_images=True)
+        form = D.DFMNMF_BF16_TC if s["N"] >= 4 else D.DFMNMF_FP32
+        probs.append(p)
+        forms.append(form)
+        ctxs.append(ctx_of(p, form))
+    b = D.dfmnmf_batch_create(ctxs)
+    D.dfmnmf_batch_iterate(b, 5)
+    torch.cuda.synchronize()
+    for p, c, form in zip(probs, ctxs, forms):
+        x = p.x.astype(np.complex128)
+        st = O.run(x, p.mics, oracle_state(p), 5)
+        nll_ref, nll = O.neg_loglik(x, p.mics, st), D.dfmnmf_loglik(c)
+        out = torch.empty((p.N, p.F, p.T, p.M), dtype=torch.complex64, device="cuda")
+        D.dfmnmf_separate(c, out)
+        s_gpu, _ = sdr_db(out.cpu().numpy(), p.c)
+        s_ref, _ = sdr_db(O.wiener_filter(x, p.mics, st), p.c)
+        tc = form == D.DFMNMF_BF16_TC
+        print("batched mixture T", p.T, "K", p.K, "N", p.N, "tensor-core" if tc else "FP32", "nll", nll, nll_ref,
+              "SDR", s_gpu, s_ref)
+        assert abs(nll - nll_ref) <= (1e-2 if tc else 1e-3) * abs(nll_ref)
+        assert np.max(np.abs(np.sort(s_gpu) - np.sort(s_ref))) <= (0.2 if tc else 0.1)
+    D.dfmnmf_batch_destroy(b)
