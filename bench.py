@@ -147,23 +147,22 @@ def kernel_bytes(F, T, M, N, B, K, MK):
     }
 
 
-# DRAM bytes (read + write) of one band-wide launch, from full-section ncu
-# captures of one iteration of each form (`k_cov` from the FP32 form, the
-# rest from the tensor-core form; band-wide launches: the autotuned launch
-# shapes of those runs put the per-frequency kernels on one graph branch).  A figure holds only while the
+# DRAM bytes (read + write) of one band-wide launch, from a full-section ncu
+# capture of one iteration of the tensor-core form (caches flushed before
+# each launch, so reads are cold).  A figure holds only while the
 # kernel's sources are the ones captured: the digest is the first 16 hex
 # digits of sha256 over csrc/<file>, csrc/common.cuh and csrc/internal.h, and
 # `traffic` is null when it no longer matches.
 NCU_TRAFFIC = {
     "paper_4x4_n5": {
-        "k_pstats": (48004352 + 2192128, "kernels_tc.cu", "681d9dac4e7f5a1d"),  # k_pstats_tma<0>
-        "k_stats": (27179776 + 1024, "kernels_model.cu", "d019e79f136de230"),
-        "k_gupd": (27193344 + 0, "kernels_model.cu", "d019e79f136de230"),
-        "k_lambda": (388352 + 0, "kernels_model.cu", "d019e79f136de230"),
-        "k_ip": (2701824 + 0, "kernels_ip.cu", "8f14118b76b1c4d8"),
-        "k_wupd": (13268736 + 0, "kernels_nmf.cu", "36821db759ba7376"),
-        "k_hupd": (13270016 + 0, "kernels_nmf.cu", "36821db759ba7376"),
-        "k_cov": (47757056 + 43776, "kernels_cov.cu", "b9e9240ac9819186"),  # FP32 form
+        "k_vtc": (47762688 + 119552, "kernels_tc.cu", "8ae7b5d68377161d"),  # k_vtc<4, 2, 0>
+        "k_pstats": (48007680 + 2407680, "kernels_tc.cu", "8ae7b5d68377161d"),  # k_pstats_tma<0>
+        "k_stats": (27179776 + 256, "kernels_model.cu", "94521d8fa885c449"),
+        "k_gupd": (27193344 + 0, "kernels_model.cu", "94521d8fa885c449"),
+        "k_lambda": (388608 + 0, "kernels_model.cu", "94521d8fa885c449"),
+        "k_ip": (2701824 + 0, "kernels_ip.cu", "34f0aab99e2d0c80"),
+        "k_wlam": (13277952 + 0, "kernels_nmf.cu", "adf34c7a08fb1dbe"),
+        "k_hupd": (13270272 + 0, "kernels_nmf.cu", "adf34c7a08fb1dbe"),
     },
 }
 
@@ -176,9 +175,9 @@ NCU_TRAFFIC = {
 ALU_KERNELS = ("k_ip", "k_cov")
 NCU_INST = {  # keyed by (kernel, form): k_ip refines three times in the FP32 form, once in the tensor-core form
     "paper_4x4_n5": {
-        ("k_ip", "bf16tc"): (6995412, "kernels_ip.cu", "8f14118b76b1c4d8"),
-        ("k_ip", "fp32"): (9148758, "kernels_ip.cu", "8f14118b76b1c4d8"),
-        ("k_cov", "fp32"): (54227691, "kernels_cov.cu", "b9e9240ac9819186"),
+        ("k_ip", "bf16tc"): (6633556, "kernels_ip.cu", "34f0aab99e2d0c80"),
+        # the FP32 form's capture ran the per-frequency kernels on two graph branches: the two halves' sum
+        ("k_ip", "fp32"): (4366836 + 4400978, "kernels_ip.cu", "34f0aab99e2d0c80"),
     },
 }
 
@@ -209,7 +208,7 @@ def issue_peak_ginst(sm_count):
 def ncu_traffic(workload, kernel, form):
     import hashlib
     ent = NCU_TRAFFIC.get(workload, {}).get(kernel)
-    if ent is None or (kernel == "k_pstats" and form != "bf16tc"):  # the capture is of the plain projections
+    if ent is None or (kernel in ("k_pstats", "k_vtc") and form != "bf16tc"):  # captured in the bfloat16 form
         return None
     nbytes, src, digest = ent
     h = hashlib.sha256()
@@ -296,21 +295,32 @@ def run_oracle_sample_allcores(workload: str, seconds: float, workers: int | Non
 
 
 def reference_arm(args, rank, world):
+    """The FP64 oracle as it stands, on every host core (its bins split over one worker process per core,
+    oracle/parallel.py); each step is one MM iteration of the workload, a bounded sample of its
+    200-iteration job.  Under torchrun rank 0 alone runs."""
     if rank != 0:
         return
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import oracle as O
+    from oracle.parallel import SlicedOracle
     from paper_2605_19388_gb300 import synth
     w = synth.WORKLOADS[args.workload]
     F, T, M = w["F"], w["T"], sum(w["mics"])
-    per_step = max(2.0, min(args.cpu_seconds, 20.0))
-    for _ in range(args.warmup):
-        run_oracle_sample(args.workload, 0.0, max_iters=1)
-    times, iters = [], 0
-    for _ in range(args.steps):
-        s = run_oracle_sample(args.workload, per_step / 4, max_iters=1)
-        times.append(s["seconds"])
-        iters += s["iters"]
+    p = synth.make_workload(args.workload, seed=0)
+    st = O.state_from_arrays(p.Q0, p.W0, p.H0, p.g0, p.mics)
+    workers = os.cpu_count() or 1
+    times = []
+    with SlicedOracle(p.x.astype(np.complex128), p.mics, st, workers) as so:
+        for _ in range(args.warmup):
+            so.iterate(1)
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            so.iterate(1)
+            times.append(time.perf_counter() - t0)
+        workers = so.workers
     total = sum(times)
-    value = iters / total
+    value = args.steps / total
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
@@ -318,8 +328,9 @@ def reference_arm(args, rank, world):
         "data": "synthetic (seeded STFT mixtures, stand-in for the paper's simulated JNAS rooms)",
         "config": {"workload": args.workload, "F": F, "T": T, "mics": list(w["mics"]), "N": w["N"],
                    "B": w["B"], "step": "one MM iteration of the FP64 oracle (bounded sample of the 200-iteration job)"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{iters} MM iterations of the {args.workload} workload, one per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
+                         "sample": f"{args.steps} MM iterations of the {args.workload} workload, one per step, "
+                                   f"its bins split over {workers} worker processes, one thread each"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "tf_bin_mic_updates_per_s": F * T * M * value,
         "gpu_launches": 0,
