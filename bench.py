@@ -163,6 +163,8 @@ NCU_TRAFFIC = {
         "k_ip": (2701824 + 0, "kernels_ip.cu", "34f0aab99e2d0c80"),
         "k_wlam": (13277952 + 0, "kernels_nmf.cu", "adf34c7a08fb1dbe"),
         "k_hupd": (13270272 + 0, "kernels_nmf.cu", "adf34c7a08fb1dbe"),
+        # FP32 form, the two half-band launches of one iteration added
+        "k_cov": (23855360 + 23948288, "kernels_cov.cu", "451a396ec67f3273"),
     },
 }
 
@@ -178,6 +180,7 @@ NCU_INST = {  # keyed by (kernel, form): k_ip refines three times in the FP32 fo
         ("k_ip", "bf16tc"): (6633556, "kernels_ip.cu", "34f0aab99e2d0c80"),
         # the FP32 form's capture ran the per-frequency kernels on two graph branches: the two halves' sum
         ("k_ip", "fp32"): (4366836 + 4400978, "kernels_ip.cu", "34f0aab99e2d0c80"),
+        ("k_cov", "fp32"): (28044032 + 28153579, "kernels_cov.cu", "451a396ec67f3273"),
     },
 }
 
