@@ -36,7 +36,7 @@ UNIT = "MM iter/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="paper_4x4_n5")
@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the gradient through 20 unrolled iterations (4 x 4 mics, N = 5, F = 257, T = 313)")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="time only the gradient through 20 unrolled iterations and print it (no headline line)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--batched", type=int, default=64,
                     help="also time this many mixtures of mixed length and layout (T in [150, 1250], K in {2, 4, 8} "
@@ -90,7 +92,7 @@ class ClockSampler:
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -499,6 +501,19 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.adjoint_only:
+        def timed_plain(fn, c, nsteps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(nsteps):
+                fn(c)
+            e1.record()
+            e1.synchronize()
+            return e0.elapsed_time(e1)
+        if rank == 0:
+            print(json.dumps({"adjoint": adjoint_measurement(D, synth, torch, timed_plain)}), flush=True)
+        return
     ip = {"f32x2": D.DFMNMF_IP_F32X2, "f64": D.DFMNMF_IP_F64, "f32": D.DFMNMF_IP_F32}[args.ip]
     wl = synth.WORKLOADS[args.workload]
     iters = args.iters or wl["iters"]

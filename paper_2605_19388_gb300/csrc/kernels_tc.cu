@@ -313,7 +313,9 @@ __global__ void __launch_bounds__((VX_CONV_WARP + VX_CW * CG) * 32, 1)
       const int len = min(nch - c0, nloc - i0);
       const bool full = (c0 == 0 && len == nch);
       ++sg;
-      const bool okw = mbar_wait(&ctl->acc_full[sg & 1], (sg >> 1) & 1, 512, budget);
+      // polls are rare while the converters run (they would take their issue slots); the CTA's last tile is
+      // awaited closely, since nothing else is left to run and the launch ends with it
+      const bool okw = mbar_wait(&ctl->acc_full[sg & 1], (sg >> 1) & 1, (i0 + len == nloc) ? 32u : 512u, budget);
       if (!okw) atomicOr(&ctl->abort, 1u);
       if (epi_bar_or(!okw || *abort_flag)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -509,7 +511,7 @@ __global__ void __launch_bounds__((VX_CONV_WARP + VX_CW * CG) * 32, 1)
   __syncthreads();
   if (warp == 0) {
     // all tensor-core work of the CTA has completed before its tensor memory is freed (bounded wait)
-    if (!mbar_wait_warp(&ctl->done, 0, 256) && lane == 0) atomicOr(&ctl->abort, 1u);
+    if (!mbar_wait_warp(&ctl->done, 0, 32) && lane == 0) atomicOr(&ctl->abort, 1u);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * VX_ACC_COLS) : "memory");
   }
