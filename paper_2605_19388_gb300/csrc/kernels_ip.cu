@@ -107,6 +107,83 @@ template <> struct VLoad<float> {
   }
 };
 
+// Eqs. (14)-(15), step 2, in the working precision R: A q = e_mu by Gauss-Jordan elimination with partial
+// pivoting on the 16 lanes of a half warp (lane (i, j) holds A_ij; rows exchanged and pivots broadcast by
+// shuffles, the first maximum taken on ties), then the singularity test of Sec. IV-A; a singular system is
+// solved by lane 0 with the FP64 pseudo-inverse of Q V_mu (Vmu: the FP64 V_mu of the block, qrow: the
+// half warp's shared slot for q).  Returns this lane's q_i.
+template <int MK, class R>
+__device__ __forceinline__ cx<R> ip_gj_solve(cx<R> a, int mu, int i, int j, int e, int sb, bool act, bool valid,
+                                             float maxabs, float rtol, const cx<R>* Qb,
+                                             const double2* __restrict__ Vmu, cx<double>* qrow, unsigned segmask,
+                                             unsigned* __restrict__ flags) {
+  using O = RealOps<R>;
+  const int lane = threadIdx.x & 31;
+  auto L = [&](int r, int c) { return sb + r * MK + c; };
+  cx<R> b = (act && i == mu) ? cmake(O::one(), O::zero()) : czero<R>();
+  float minpiv = INFINITY;
+#pragma unroll
+  for (int c = 0; c < MK; ++c) {
+    float key = (act && j == c && i >= c) ? cabs2_f(a) : -1.f;
+    int prow = i;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+      const float ok = __shfl_xor_sync(DFM_FULL_MASK, key, o);
+      const int orow = __shfl_xor_sync(DFM_FULL_MASK, prow, o);
+      if (ok > key || (ok == key && orow < prow)) {
+        key = ok;
+        prow = orow;
+      }
+    }
+    int src = lane;
+    if (act && i == c) src = L(prow, j);
+    else if (act && i == prow) src = L(c, j);
+    a = cshfl(a, src);
+    b = cshfl(b, src);
+    const cx<R> piv = cshfl(a, L(c, c));
+    minpiv = fminf(minpiv, sqrtf(cabs2_f(piv)));
+    const cx<R> inv = crecip(piv);
+    const cx<R> rowc = cmul(cshfl(a, L(c, j)), inv);
+    const cx<R> bc = cmul(cshfl(b, L(c, 0)), inv);
+    const cx<R> m = cshfl(a, L(i, c));
+    if (i == c) {
+      a = rowc;
+      b = bc;
+    } else {
+      a = csub(a, cmul(m, rowc));
+      b = csub(b, cmul(m, bc));
+    }
+  }
+  if (minpiv > rtol * maxabs) return b;
+  if (e == 0 && valid) {
+    cx<double> U[MK][MK], q[MK];
+    for (int r = 0; r < MK; ++r)
+      for (int c = 0; c < MK; ++c) {
+        double sr = 0.0, si = 0.0;
+        for (int l = 0; l < MK; ++l) {
+          const cx<R> qrl = Qb[r * MK + l];
+          const double qr = O::to_d(qrl.re), qim = O::to_d(qrl.im);
+          const double2 v = Vmu[l * MK + c];
+          sr += qr * v.x - qim * v.y;
+          si += qr * v.y + qim * v.x;
+        }
+        U[r][c] = cmake(sr, si);
+      }
+    pinv_column<MK>(U, mu, (double)rtol, q);
+    for (int r = 0; r < MK; ++r) qrow[r] = q[r];
+    atomicAdd(flags + FLAG_PINV, 1u);
+  }
+  __syncwarp(segmask);
+  return cfrom_d2<R>(make_double2(qrow[i].re, qrow[i].im));
+}
+template <int MK, class R>
+__device__ __noinline__ cx<R> ip_gj_solve_outline(cx<R> a, int mu, int i, int j, int e, int sb, bool act,
+                                                  bool valid, float maxabs, float rtol, const cx<R>* Qb,
+                                                  const double2* __restrict__ Vmu, cx<double>* qrow,
+                                                  unsigned segmask, unsigned* __restrict__ flags) {
+  return ip_gj_solve<MK, R>(a, mu, i, j, e, sb, act, valid, maxabs, rtol, Qb, Vmu, qrow, segmask, flags);
+}
+
 // NREF is the number of float-pair refinement steps of the mixed-precision
 // solve (three for the FP32 form; one for the tensor-core form, whose
 // covariances already carry a relative error near 2^-16).
@@ -228,65 +305,14 @@ __global__ void __launch_bounds__(128) k_ip(const double2* __restrict__ V, const
       }
     }
     if (!solved) {
-    cx<R> b = (act && i == mu) ? cmake(O::one(), O::zero()) : czero<R>();
-    float minpiv = INFINITY;
-    // 2. Gauss-Jordan with partial pivoting
-#pragma unroll
-    for (int c = 0; c < MK; ++c) {
-      float key = (act && j == c && i >= c) ? cabs2_f(a) : -1.f;
-      int prow = i;
-#pragma unroll
-      for (int o = 8; o > 0; o >>= 1) {
-        const float ok = __shfl_xor_sync(DFM_FULL_MASK, key, o);
-        const int orow = __shfl_xor_sync(DFM_FULL_MASK, prow, o);
-        if (ok > key || (ok == key && orow < prow)) {
-          key = ok;
-          prow = orow;
-        }
-      }
-      int src = lane;
-      if (act && i == c) src = L(prow, j);
-      else if (act && i == prow) src = L(c, j);
-      a = cshfl(a, src);
-      b = cshfl(b, src);
-      const cx<R> piv = cshfl(a, L(c, c));
-      minpiv = fminf(minpiv, sqrtf(cabs2_f(piv)));
-      const cx<R> inv = crecip(piv);
-      const cx<R> rowc = cmul(cshfl(a, L(c, j)), inv);
-      const cx<R> bc = cmul(cshfl(b, L(c, 0)), inv);
-      const cx<R> m = cshfl(a, L(i, c));
-      if (i == c) {
-        a = rowc;
-        b = bc;
-      } else {
-        a = csub(a, cmul(m, rowc));
-        b = csub(b, cmul(m, bc));
-      }
-    }
-    const bool singular = !(minpiv > rtol * maxabs);
-    qi = b;
-    if (singular) {
-      if (e == 0 && valid) {
-        cx<double> U[MK][MK], q[MK];
-        for (int r = 0; r < MK; ++r)
-          for (int c = 0; c < MK; ++c) {
-            double sr = 0.0, si = 0.0;
-            for (int l = 0; l < MK; ++l) {
-              const cx<R> qrl = Qb[r * MK + l];
-              const double qr = O::to_d(qrl.re), qim = O::to_d(qrl.im);
-              const double2 v = Vb[mu * E + l * MK + c];
-              sr += qr * v.x - qim * v.y;
-              si += qr * v.y + qim * v.x;
-            }
-            U[r][c] = cmake(sr, si);
-          }
-        pinv_column<MK>(U, mu, (double)rtol, q);
-        for (int r = 0; r < MK; ++r) qfb[warp][seg][r] = q[r];
-        atomicAdd(flags + FLAG_PINV, 1u);
-      }
-      __syncwarp(segmask);
-      qi = cfrom_d2<R>(make_double2(qfb[warp][seg][i].re, qfb[warp][seg][i].im));
-    }
+      // Gauss-Jordan in the working precision (and the pseudo-inverse when singular); out of line where it
+      // is the fallback of the mixed-precision solve, so that the hot path keeps a small code footprint
+      if constexpr (MIXED)
+        qi = ip_gj_solve_outline<MK, R>(a, mu, i, j, e, sb, act, valid, maxabs, rtol, Qb, Vb + mu * E,
+                                        qfb[warp][seg], segmask, flags);
+      else
+        qi = ip_gj_solve<MK, R>(a, mu, i, j, e, sb, act, valid, maxabs, rtol, Qb, Vb + mu * E, qfb[warp][seg],
+                                segmask, flags);
     }
     // 3. normalisation (Eq. 15) and row update
     const cx<R> qj = cshfl(qi, L(j, 0));
