@@ -242,3 +242,18 @@ def test_fp32_form_200_iterations_paper_workload():
     print("FP32 form, 200 iterations: nll", nll_gpu, nll_ref, "SDR", sdr_gpu, sdr_ref)
     assert abs(nll_gpu - nll_ref) <= 1e-3 * abs(nll_ref), (nll_gpu, nll_ref)
     assert np.max(np.abs(np.sort(sdr_gpu) - np.sort(sdr_ref))) <= 0.1, (sdr_gpu, sdr_ref)
+
+
+def test_w_update_fallback_when_the_fused_tile_does_not_fit():
+    """B = 64 bases and T = 1000 frames: H[n] and ten A, D rows (B Tp + 20 Tp floats, 336 KB) exceed the
+    shared memory of one CTA, so the W stage runs the split products (k_wupd) and the separate lambda
+    refresh instead of the fused k_wlam; both paths match the oracle stage by stage."""
+    p = synth.make_problem(9, 1000, (4, 4), 4, 64, seed=81)
+    Q0 = synth.random_blocks(p.F, p.mics, seed=82, scale=0.2)
+    stage_parity(p, Q0)
+    ctx = make_ctx(p, Q0)
+    names = [n for n, _ in D.dfmnmf_kernel_times(ctx, 1)]
+    assert "k_wupd" in names and "k_wlam" not in names, names
+    q = synth.make_problem(9, 300, (4, 4), 4, 16, seed=83)
+    names = [n for n, _ in D.dfmnmf_kernel_times(make_ctx(q), 1)]
+    assert "k_wlam" in names and "k_wupd" not in names, names
