@@ -425,6 +425,7 @@ __global__ void __launch_bounds__((VX_CONV_WARP + VX_CW * CG) * 32, 1)
             *reinterpret_cast<float2*>(arow + off) = make_float2(h, r - h);
           }
         float y[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
         for (int n = 0; n < N; ++n) {
           const float l0 = ls[(n * FPC + fj) * KC + lane];
           const float4 gv = *reinterpret_cast<const float4*>(gs + (fj * N + n) * M + 4 * k);
@@ -479,6 +480,7 @@ __global__ void __launch_bounds__((VX_CONV_WARP + VX_CW * CG) * 32, 1)
         for (int j = 0; j < 2; ++j)
   #pragma unroll
           for (int mu = 0; mu < 4; ++mu) y[j][mu] = 0.f;
+#pragma unroll 4
         for (int n = 0; n < N; ++n) {
           const float l0 = ls[(n * FPC + fj) * KC + lane], l1 = ls[(n * FPC + fj) * KC + lane + 32];
           const float4 gv = *reinterpret_cast<const float4*>(gs + (fj * N + n) * M + 4 * k);
