@@ -6,7 +6,7 @@ import pytest
 
 import oracle as O
 from paper_2605_19388_gb300 import synth
-from tests._helpers import rel_err
+from tests._helpers import rel_err, elem_err_med
 
 pytestmark = pytest.mark.gpu
 
@@ -45,6 +45,12 @@ def test_gradient_matches_oracle(mics):
     assert rel_err(O.unpack_Q(dQ, p.mics)[0], rQ[0]) < 1e-4
     for k in range(len(p.mics)):
         assert rel_err(O.unpack_Q(dQ, p.mics)[k], rQ[k]) < 1e-4
+    # element by element against the median magnitude of each gradient (an entry is a difference of two
+    # sums of positive terms -- den - num of the multiplicative rules -- and carries their absolute rounding)
+    elem = {"W": elem_err_med(dW, rW), "H": elem_err_med(dH, rH), "g": elem_err_med(dg, rg),
+            "Q": max(elem_err_med(O.unpack_Q(dQ, p.mics)[k], rQ[k]) for k in range(len(p.mics)))}
+    print("cost gradient", mics, "element-wise", elem)
+    assert max(elem.values()) < 1e-4, elem
 
 
 def test_directional_derivatives_against_central_differences():

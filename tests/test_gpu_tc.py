@@ -232,7 +232,9 @@ def test_tc_w_update_on_tensor_cores_stage_parity():
     D.dfmnmf_iterate(a, 1)
     D.dfmnmf_iterate(b, 1)
     Wa, Wb = D.params_numpy(a)[1], D.params_numpy(b)[1]
-    assert rel_err(Wb, Wa) < TOL_TC
+    errs = check_both({}, "W", Wb, Wa, "med")
+    print("tensor-core W update against the CUDA-core one, full size", errs)
+    assert max(errs.values()) < TOL_TC, errs
 
 
 def test_launch_options_rejected_values():
