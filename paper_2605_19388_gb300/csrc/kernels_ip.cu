@@ -213,13 +213,25 @@ __global__ void __launch_bounds__(128) k_ip(const double2* __restrict__ V, const
   const size_t vbase = (size_t)(valid ? blk : 0) * E * MK;
   const double2* Vb = V + vbase;
   auto L = [&](int r, int c) { return sb + r * MK + c; };
+  // column j of V_mu for the next mu, requested one row update ahead so that its memory latency is not
+  // on the chain of dependent steps
+  cx<R> vnext[MK];
+#pragma unroll
+  for (int l = 0; l < MK; ++l) vnext[l] = VLoad<R>::get(V, Vdd, vbase + l * MK + j);
 
   for (int mu = 0; mu < MK; ++mu) {
     // 1. A = Q V_mu (lane (i, j)) and V_mu[i][j]
+    cx<R> vcol[MK];
+#pragma unroll
+    for (int l = 0; l < MK; ++l) vcol[l] = vnext[l];
+    if (mu + 1 < MK) {
+#pragma unroll
+      for (int l = 0; l < MK; ++l) vnext[l] = VLoad<R>::get(V, Vdd, vbase + (mu + 1) * E + l * MK + j);
+    }
     cx<R> a = czero<R>(), vij = czero<R>();
 #pragma unroll
     for (int l = 0; l < MK; ++l) {
-      const cx<R> vlj = VLoad<R>::get(V, Vdd, vbase + mu * E + l * MK + j);
+      const cx<R> vlj = vcol[l];
       a = cadd(a, cmul(Qb[i * MK + l], vlj));
       if (l == i) vij = vlj;
     }
