@@ -249,6 +249,7 @@ __global__ void __launch_bounds__(128) k_pstats_ft(const float2* __restrict__ x,
   __syncthreads();
   const int t0 = blockIdx.y * tpc, t1 = min(T, t0 + tpc);
   const float* lt = lam + (size_t)f * Tp;
+#pragma unroll 2
   for (int t = t0 + tid; t < t1; t += blockDim.x) {
     float pv[M];
     float* Pt = P + ((size_t)f * T + t) * M;
@@ -557,12 +558,14 @@ __global__ void __launch_bounds__(128) k_gupd4(const float* __restrict__ lam, co
 
 template <int K, int MK, bool COMPUTE_P, bool COMP>
 static cudaError_t launch_pstats_ft(const dfmnmf_ctx* c, cudaStream_t s, int fb, int fc) {
-  const int tpc = 128;  // one frame per thread: every load of the CTA is in flight at once
+  // one frame per thread where P is formed here; two for the statistics alone, whose loads of both frames
+  // the unrolled loop issues together
+  const int tpc = COMPUTE_P ? 128 : 256;
   dim3 grid(fc, (c->T + tpc - 1) / tpc);
   const size_t sm = ((size_t)((c->N * c->M + 3) & ~3) + (COMPUTE_P ? 4 * (size_t)K * MK * MK : 0)) * sizeof(float);
   auto kern = k_pstats_ft<K, MK, COMPUTE_P, COMP>;
   if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  kern<<<grid, tpc, sm, s>>>(c->x, c->Q64, c->lam, c->g, c->P, c->A, c->D, c->F, c->T, c->Tp, c->N, c->eps, fb, tpc);
+  kern<<<grid, 128, sm, s>>>(c->x, c->Q64, c->lam, c->g, c->P, c->A, c->D, c->F, c->T, c->Tp, c->N, c->eps, fb, tpc);
   return cudaGetLastError();
 }
 
