@@ -157,10 +157,8 @@ def kernel_bytes(F, T, M, N, B, K, MK):
 # `traffic` is null when it no longer matches.
 NCU_TRAFFIC = {
     "paper_4x4_n5": {
-        # k_vtc captured on its one-group launch (k_vtc<4, 1, 0>, the autotuner's other choice): the DRAM
-        # bytes are the operands' and do not depend on the grouping (the two-group launch read 47.76 MB too)
-        "k_vtc": (47762944 + 48384, "kernels_tc.cu", "b47cc1819e46e8ff"),
-        "k_pstats": (48007680 + 413696, "kernels_tc.cu", "b47cc1819e46e8ff"),  # k_pstats_tma<0>
+        "k_vtc": (47761920 + 16896, "kernels_tc.cu", "aa8cbc1fdd39f821"),  # k_vtc<4, 2, 0>
+        "k_pstats": (48007680 + 413696, "kernels_tc.cu", "b47cc1819e46e8ff"),  # k_pstats_tma<0>, earlier source
         "k_stats": (27179776 + 256, "kernels_model.cu", "94521d8fa885c449"),
         "k_gupd": (27193344 + 0, "kernels_model.cu", "94521d8fa885c449"),
         "k_lambda": (388608 + 0, "kernels_model.cu", "94521d8fa885c449"),
