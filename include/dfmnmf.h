@@ -255,12 +255,16 @@ int dfmnmf_autotune(dfmnmf_ctx* ctx, int iters_per_trial, int* branches, int* nm
  * GPU concern).  dfmnmf_autotune sets the first three by measurement.
  *   DFMNMF_OPT_BRANCHES    1 or 2 graph branches for the per-frequency kernels
  *                          (FP32 form; the tensor-core forms use 1)
- *   DFMNMF_OPT_NMF_CTAS    2, 4 or 8: CTAs per SM the split NMF products aim for
+ *   DFMNMF_OPT_NMF_CTAS    2, 4 or 8: CTAs per SM the split NMF products (the H
+ *                          update, and the W update where it is not fused) aim for
  *   DFMNMF_OPT_VX_GROUPS   1 or 2 groups of converter warps in the tensor-core
  *                          covariance kernel
- *   DFMNMF_OPT_WUPD_TC     0: the W-update products (Eq. 8) on the CUDA cores;
- *                          1: on the tensor cores (tcgen05 kind::tf32), for the
- *                          tensor-core forms only
+ *   DFMNMF_OPT_WUPD_TC     0: the W update (Eq. 8) on the CUDA cores, fused with
+ *                          the refresh of lambda where its shared-memory tile
+ *                          fits (otherwise split products and a separate
+ *                          refresh); 1: its products on the tensor cores
+ *                          (tcgen05 kind::tf32) and a separate refresh, for
+ *                          the tensor-core forms only
  *   DFMNMF_OPT_WAIT_CYCLES budget, in SM clock cycles (default 2e9, ~1 s), of
  *                          the pipeline waits of the tensor-core covariance
  *                          kernel; a wait that runs out ends the kernel with
