@@ -157,13 +157,13 @@ def kernel_bytes(F, T, M, N, B, K, MK):
 # `traffic` is null when it no longer matches.
 NCU_TRAFFIC = {
     "paper_4x4_n5": {
-        "k_vtc": (47761920 + 16896, "kernels_tc.cu", "aa8cbc1fdd39f821"),  # k_vtc<4, 2, 0>
-        "k_pstats": (48007680 + 413696, "kernels_tc.cu", "b47cc1819e46e8ff"),  # k_pstats_tma<0>, earlier source
-        "k_stats": (27179776 + 256, "kernels_model.cu", "94521d8fa885c449"),
-        "k_gupd": (27193344 + 0, "kernels_model.cu", "94521d8fa885c449"),
-        "k_lambda": (388608 + 0, "kernels_model.cu", "94521d8fa885c449"),
-        "k_ip": (2701824 + 0, "kernels_ip.cu", "34f0aab99e2d0c80"),
-        "k_wlam": (13277952 + 0, "kernels_nmf.cu", "adf34c7a08fb1dbe"),
+        "k_vtc": (47760896 + 113408, "kernels_tc.cu", "aa8cbc1fdd39f821"),  # k_vtc<4, 2, 0>
+        "k_pstats": (48014592 + 2304256, "kernels_tc.cu", "aa8cbc1fdd39f821"),  # k_pstats_tma<0>
+        "k_stats": (27194112 + 1280, "kernels_model.cu", "2a06519bbda944e8"),
+        "k_gupd": (27193344 + 0, "kernels_model.cu", "2a06519bbda944e8"),
+        "k_lambda": (388096 + 0, "kernels_model.cu", "2a06519bbda944e8"),
+        "k_ip": (2692096 + 0, "kernels_ip.cu", "a29c23b8fb31e383"),
+        "k_wlam": (13277440 + 0, "kernels_nmf.cu", "adf34c7a08fb1dbe"),
         "k_hupd": (13270272 + 0, "kernels_nmf.cu", "adf34c7a08fb1dbe"),
         # FP32 form, the two half-band launches of one iteration added
         "k_cov": (23855360 + 23948288, "kernels_cov.cu", "451a396ec67f3273"),
@@ -179,7 +179,7 @@ NCU_TRAFFIC = {
 ALU_KERNELS = ("k_ip", "k_cov")
 NCU_INST = {  # keyed by (kernel, form): k_ip refines three times in the FP32 form, once in the tensor-core form
     "paper_4x4_n5": {
-        ("k_ip", "bf16tc"): (6633556, "kernels_ip.cu", "34f0aab99e2d0c80"),
+        ("k_ip", "bf16tc"): (6536940, "kernels_ip.cu", "a29c23b8fb31e383"),
         # the FP32 form's capture ran the per-frequency kernels on two graph branches: the two halves' sum
         ("k_ip", "fp32"): (4366836 + 4400978, "kernels_ip.cu", "34f0aab99e2d0c80"),
         ("k_cov", "fp32"): (28044032 + 28153579, "kernels_cov.cu", "451a396ec67f3273"),
