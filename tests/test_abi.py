@@ -32,6 +32,16 @@ def test_header_symbols_exported(lib):
     assert set(syms) == set(D.EXPORTED)
 
 
+def test_header_constants_match_the_binding():
+    """Every enumerator of include/dfmnmf.h has the same value in the Python binding."""
+    text = open(os.path.join(ROOT, "include", "dfmnmf.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    consts = dict((k, int(v)) for k, v in re.findall(r"\b(DFMNMF_[A-Z0-9_]+)\s*=\s*(\d+)", text))
+    assert "DFMNMF_OPT_WAIT_CYCLES" in consts and len(consts) >= 20
+    for k, v in consts.items():
+        assert getattr(D, k) == v, k
+
+
 def test_version(lib):
     assert D.dfmnmf_version() == 100
 
