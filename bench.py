@@ -86,7 +86,8 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
 
     def start(self):
         try:
@@ -196,17 +197,22 @@ NCU_INST = {  # keyed by (kernel, form): k_ip refines three times in the FP32 fo
 }
 
 
-def ncu_inst(workload, kernel, form):
+def source_digest(src):
+    """First 16 hex digits of sha256 over csrc/<src>, csrc/common.cuh and csrc/internal.h."""
     import hashlib
-    ent = NCU_INST.get(workload, {}).get((kernel, form))
-    if ent is None:
-        return None
-    n, src, digest = ent
     h = hashlib.sha256()
     for name in (src, "common.cuh", "internal.h"):
         with open(os.path.join(ROOT, "paper_2605_19388_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
-    return n if h.hexdigest()[:16] == digest else None
+    return h.hexdigest()[:16]
+
+
+def ncu_inst(workload, kernel, form):
+    ent = NCU_INST.get(workload, {}).get((kernel, form))
+    if ent is None:
+        return None
+    n, src, digest = ent
+    return n if source_digest(src) == digest else None
 
 
 def issue_peak_ginst(sm_count):
@@ -220,16 +226,11 @@ def issue_peak_ginst(sm_count):
 
 
 def ncu_traffic(workload, kernel, form):
-    import hashlib
     ent = NCU_TRAFFIC.get(workload, {}).get(kernel)
     if ent is None or (kernel in ("k_pstats", "k_vtc") and form != "bf16tc"):  # captured in the bfloat16 form
         return None
     nbytes, src, digest = ent
-    h = hashlib.sha256()
-    for name in (src, "common.cuh", "internal.h"):
-        with open(os.path.join(ROOT, "paper_2605_19388_gb300", "csrc", name), "rb") as fh:
-            h.update(fh.read())
-    return nbytes if h.hexdigest()[:16] == digest else None
+    return nbytes if source_digest(src) == digest else None
 
 
 def iteration_bytes(F, T, M, N):
@@ -277,7 +278,8 @@ print(json.dumps(dict(iters=n, seconds=el)))
 """
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                NUMEXPR_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=10 * seconds + 300)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])

@@ -57,9 +57,11 @@ def _fake_root(tmp_path):
 
 
 def test_stored_traffic_holds_only_for_the_captured_sources(tmp_path, monkeypatch):
-    csrc = _fake_root(tmp_path)
-    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     nbytes, src, digest = bench.NCU_TRAFFIC["paper_4x4_n5"]["k_vtc"]
+    real = bench.source_digest(src)
+    csrc = _fake_root(tmp_path)
+    assert bench_digest(csrc, src) == real  # the copies hash like the sources
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     monkeypatch.setitem(bench.NCU_TRAFFIC["paper_4x4_n5"], "k_vtc", (nbytes, src, bench_digest(csrc, src)))
     assert bench.ncu_traffic("paper_4x4_n5", "k_vtc", "bf16tc") == nbytes
     assert bench.ncu_traffic("paper_4x4_n5", "k_vtc", "tf32tc") is None  # captured in the bfloat16 form
