@@ -100,6 +100,10 @@ class ClockSampler:
 
     def stop(self):
         if self.proc is None:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
         try:

@@ -108,6 +108,34 @@ def test_clock_samples_parse_reasons_and_skip_bad_lines():
     assert empty == {"sm_mhz": None, "sm_max_mhz": None, "samples": 0, "reasons": []}
 
 
+def test_clock_sampler_runs_the_query_and_parses_its_output(tmp_path, monkeypatch):
+    """start() runs nvidia-smi with the sampling loop, stop() ends it and parses what it wrote
+    (a stand-in nvidia-smi on PATH prints two samples); without nvidia-smi stop() says so."""
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/sh\n"
+                    "echo '0, 2070, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
+                    "echo '0, 2010, 2070, 1400.0, 0x4, Not Active, Not Active, Not Active, Active'\n"
+                    "exec sleep 30\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", f"{tmp_path}{os.pathsep}{os.environ.get('PATH', '')}")
+    cs = bench.ClockSampler(0)
+    cs.start()
+    import time
+    for _ in range(100):  # until both samples are on disk
+        with open(cs.path) as fh:
+            if len(fh.read().splitlines()) >= 2:
+                break
+        time.sleep(0.05)
+    out = cs.stop()
+    assert out == {"sm_mhz": 2040.0, "sm_max_mhz": 2070.0, "samples": 2, "reasons": ["sw_power_cap"]}
+    assert not os.path.exists(cs.path)
+    monkeypatch.setenv("PATH", str(tmp_path / "empty"))
+    cs = bench.ClockSampler(0)
+    cs.start()
+    assert cs.stop()["reasons"] == ["nvidia-smi unavailable"]
+    assert not os.path.exists(cs.path)
+
+
 def test_reference_arm_prints_one_contract_line():
     """`bench.py --impl reference`: the FP64 oracle on the host cores, one JSON line carrying the
     metric, unit and direction of the GPU arm, no host-device bytes and no GPU launches."""
