@@ -136,6 +136,15 @@ def test_clock_sampler_runs_the_query_and_parses_its_output(tmp_path, monkeypatc
     assert not os.path.exists(cs.path)
 
 
+def test_cpu_baseline_samples_time_the_oracle():
+    """The bench's cpu_baseline legs: the FP64 oracle in a single-thread subprocess, and split over
+    worker processes; each reports whole MM iterations and the seconds they took."""
+    one = bench.run_oracle_sample("small_2x4_n3", 0.2, max_iters=2)
+    assert 1 <= one["iters"] <= 2 and one["seconds"] > 0
+    many = bench.run_oracle_sample_allcores("small_2x4_n3", 0.2, workers=2)
+    assert many["iters"] >= 1 and many["seconds"] >= 0.2 and many["workers"] == 2
+
+
 def test_reference_arm_prints_one_contract_line():
     """`bench.py --impl reference`: the FP64 oracle on the host cores, one JSON line carrying the
     metric, unit and direction of the GPU arm, no host-device bytes and no GPU launches."""
