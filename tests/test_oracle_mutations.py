@@ -22,13 +22,14 @@ from tests import test_oracle_pins as pins
 
 ORIG = {name: getattr(OM, name) for name in (
     "weighted_covariances", "model_variance", "ip_update_row", "projected_power", "_mu_statistics",
-    "update_W", "update_g", "neg_loglik", "wiener_filter")}
+    "update_W", "update_H", "update_g", "neg_loglik", "wiener_filter", "log_abs_det_sq", "source_psd")}
 
 
-def _ip_row(Qk, Vk, mu, eps=OM.EPS, rtol=OM.SINGULAR_RTOL, *, normalise=True, conj_row=True, order="QV"):
+def _ip_row(Qk, Vk, mu, eps=OM.EPS, rtol=OM.SINGULAR_RTOL, *, normalise=True, conj_row=True, order="QV",
+            v_shift=0):
     """Eqs. (14)-(15) for row mu, with switches that plant the slips below."""
     F, mk, _ = Qk.shape
-    Vmu = Vk[:, mu]
+    Vmu = Vk[:, (mu + v_shift) % mk]
     A = np.matmul(Qk, Vmu) if order == "QV" else np.matmul(Vmu, Qk)
     e = np.zeros((F, mk), dtype=np.complex128)
     e[:, mu] = 1.0
@@ -92,6 +93,13 @@ MUTATIONS = {
     "IP system V Q instead of Q V":
         ("ip_update_row", lambda Qk, Vk, mu, eps=OM.EPS, rtol=OM.SINGULAR_RTOL:
             _ip_row(Qk, Vk, mu, eps, rtol, order="VQ")),
+    "IP row solved with the next microphone's covariance":
+        ("ip_update_row", lambda Qk, Vk, mu, eps=OM.EPS, rtol=OM.SINGULAR_RTOL:
+            _ip_row(Qk, Vk, mu, eps, rtol, v_shift=1)),
+    "covariance weighted by yhat^-2 instead of yhat^-1":
+        ("weighted_covariances", lambda x, y, mics: ORIG["weighted_covariances"](x, y ** 2, mics)),
+    "source model pairing the bases of W and H in reverse":
+        ("source_psd", lambda W, H: ORIG["source_psd"](W, H[:, ::-1, :])),
     "projected power with Q^H instead of Q":
         ("projected_power", lambda x, Q, mics: ORIG["projected_power"](
             x, [np.conj(np.swapaxes(q, 1, 2)) for q in Q], mics)),
@@ -99,6 +107,10 @@ MUTATIONS = {
         ("_mu_statistics", _mu_statistics_power1),
     "W update with numerator and denominator exchanged":
         ("update_W", lambda W, H, g, P, eps=OM.EPS: W ** 2 / ORIG["update_W"](W, H, g, P, eps)),
+    "H update with numerator and denominator exchanged":
+        ("update_H", lambda W, H, g, P, eps=OM.EPS: H ** 2 / ORIG["update_H"](W, H, g, P, eps)),
+    "log-determinant of Q without its square":
+        ("log_abs_det_sq", lambda Qk: 0.5 * ORIG["log_abs_det_sq"](Qk)),
     "g update without the square root":
         ("update_g", lambda W, H, g, P, eps=OM.EPS: ORIG["update_g"](W, H, g, P, eps) ** 2 / g),
     "cost with the sign of the log-determinant flipped":
