@@ -26,7 +26,7 @@ ORIG = {name: getattr(OM, name) for name in (
 
 
 def _ip_row(Qk, Vk, mu, eps=OM.EPS, rtol=OM.SINGULAR_RTOL, *, normalise=True, conj_row=True, order="QV",
-            v_shift=0):
+            v_shift=0, root=True):
     """Eqs. (14)-(15) for row mu, with switches that plant the slips below."""
     F, mk, _ = Qk.shape
     Vmu = Vk[:, (mu + v_shift) % mk]
@@ -36,7 +36,8 @@ def _ip_row(Qk, Vk, mu, eps=OM.EPS, rtol=OM.SINGULAR_RTOL, *, normalise=True, co
     q, _ = OM.solve_or_pinv(A, e, rtol)
     if normalise:
         s = np.real(np.einsum("fa,fab,fb->f", np.conj(q), Vmu, q))
-        q = q / np.sqrt(np.maximum(s, eps))[:, None]
+        nrm = np.maximum(s, eps)
+        q = q / (np.sqrt(nrm) if root else nrm)[:, None]
     Qn = Qk.copy()
     Qn[:, mu, :] = np.conj(q) if conj_row else q
     return Qn
@@ -93,6 +94,9 @@ MUTATIONS = {
     "IP system V Q instead of Q V":
         ("ip_update_row", lambda Qk, Vk, mu, eps=OM.EPS, rtol=OM.SINGULAR_RTOL:
             _ip_row(Qk, Vk, mu, eps, rtol, order="VQ")),
+    "IP row normalised by q^H V q instead of its square root":
+        ("ip_update_row", lambda Qk, Vk, mu, eps=OM.EPS, rtol=OM.SINGULAR_RTOL:
+            _ip_row(Qk, Vk, mu, eps, rtol, root=False)),
     "IP row solved with the next microphone's covariance":
         ("ip_update_row", lambda Qk, Vk, mu, eps=OM.EPS, rtol=OM.SINGULAR_RTOL:
             _ip_row(Qk, Vk, mu, eps, rtol, v_shift=1)),
@@ -103,6 +107,8 @@ MUTATIONS = {
     "projected power with Q^H instead of Q":
         ("projected_power", lambda x, Q, mics: ORIG["projected_power"](
             x, [np.conj(np.swapaxes(q, 1, 2)) for q in Q], mics)),
+    "projected power |q^H x| without the square":
+        ("projected_power", lambda x, Q, mics: np.sqrt(ORIG["projected_power"](x, Q, mics))),
     "MU statistic with yhat^-1 instead of yhat^-2":
         ("_mu_statistics", _mu_statistics_power1),
     "W update with numerator and denominator exchanged":
