@@ -22,7 +22,8 @@ from tests import test_oracle_pins as pins
 
 ORIG = {name: getattr(OM, name) for name in (
     "weighted_covariances", "model_variance", "ip_update_row", "projected_power", "_mu_statistics",
-    "update_W", "update_H", "update_g", "neg_loglik", "wiener_filter", "log_abs_det_sq", "source_psd")}
+    "update_W", "update_H", "update_g", "neg_loglik", "wiener_filter", "log_abs_det_sq", "source_psd",
+    "init_from_images")}
 
 
 def _ip_row(Qk, Vk, mu, eps=OM.EPS, rtol=OM.SINGULAR_RTOL, *, normalise=True, conj_row=True, order="QV",
@@ -126,6 +127,43 @@ MUTATIONS = {
 }
 
 
+def _init_variant(c, mics, *, per_mic=True, conj_rows=True, swap_pair=False, g_of_last=False):
+    """Steps 3, 5 and 6 of the initialisation (Sec. IV-A) with switches that plant the slips below."""
+    import scipy.linalg
+    c = np.asarray(c, dtype=np.complex128)
+    N, F, T, M = c.shape
+    R = np.einsum("nftm,nftl->nfml", c, np.conj(c)) / T
+    y = np.linalg.solve(R, np.swapaxes(c, 2, 3))
+    h = np.real(np.einsum("nftm,nfmt->nft", np.conj(c), y)) / (M if per_mic else 1)
+    off = OM.mic_offsets(mics)
+    Q, g = [], np.zeros((F, N, M))
+    for k, mk in enumerate(mics):
+        sl = slice(off[k], off[k] + mk)
+        Qk = np.zeros((F, mk, mk), dtype=np.complex128)
+        for f in range(F):
+            a, b = (N - 1, N - 2) if swap_pair else (N - 2, N - 1)
+            _, Wv = scipy.linalg.eigh(R[a, f][sl, sl], R[b, f][sl, sl])
+            Qk[f] = np.conj(Wv.T) if conj_rows else Wv.T
+            for n in range(N):
+                Rn = R[N - 1 if g_of_last else n, f][sl, sl]
+                g[f, n, sl] = np.real(np.einsum("am,ab,bm->m", np.conj(Wv), Rn, Wv))
+        Q.append(Qk)
+    return h, Q, g
+
+
+# Slips in the initialisation, which the loop oracle does not restate: the pins alone must catch them.
+INIT_MUTATIONS = {
+    "initial spectrogram without the 1/M of step 3":
+        ("init_from_images", lambda c, mics: _init_variant(c, mics, per_mic=False)),
+    "initial Q with rows w^T instead of w^H":
+        ("init_from_images", lambda c, mics: _init_variant(c, mics, conj_rows=False)),
+    "initial Q from the pair of the last two sources taken in reverse":
+        ("init_from_images", lambda c, mics: _init_variant(c, mics, swap_pair=True)),
+    "initial g of every source from the last source's covariance":
+        ("init_from_images", lambda c, mics: _init_variant(c, mics, g_of_last=True)),
+}
+
+
 def _pins():
     fs = [f for name, f in inspect.getmembers(pins, inspect.isfunction) if name.startswith("test_")]
     fs.append(golden.test_cost_closed_form_identity_and_constant_model)
@@ -150,6 +188,30 @@ def test_unmutated_oracle_passes_every_pin():
     for f in _pins():
         with np.errstate(all="ignore"):
             f()
+
+
+def test_unmutated_initialisation_variant_is_the_oracle():
+    """The switch-free variant reproduces the oracle's initialisation, so each slip below is one change."""
+    from tests.test_oracle_pins import _images
+    p, c = _images()
+    ref, got = OM.init_from_images(c, p.mics), _init_variant(c, p.mics)
+    np.testing.assert_allclose(got[0], ref[0], rtol=1e-12)
+    for a, b in zip(got[1], ref[1]):
+        np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(got[2], ref[2], rtol=1e-12)
+
+
+@pytest.mark.parametrize("slip", list(INIT_MUTATIONS))
+def test_planted_initialisation_mistake_is_caught(slip):
+    name, fn = INIT_MUTATIONS[slip]
+    caught = []
+    with _planted(name, fn), np.errstate(all="ignore"):
+        for f in _pins():
+            try:
+                f()
+            except AssertionError:
+                caught.append(f.__name__)
+    assert caught, f"no pin fails with the planted mistake: {slip}"
 
 
 @pytest.mark.parametrize("slip", list(MUTATIONS))

@@ -425,10 +425,12 @@ def test_init_gevd_diagonalises_the_last_two_covariances():
 
 def test_init_spectrogram_invariant_to_channel_mixing_and_single_channel_closed_form():
     """Step 3: h = c^H R^{-1} c / M does not change when every frame is mixed by
-    the same invertible matrix (R -> A R A^H), and for one channel it is
+    the same invertible matrix (R -> A R A^H), its mean over the frames is 1
+    (sum_t c^H R^{-1} c / T = trace(R^{-1} R) = M), and for one channel it is
     |c|^2 / mean_t |c|^2."""
     p, c = _images(mics=(4, 4))
     h, _, _ = O.init_from_images(c, p.mics)
+    np.testing.assert_allclose(h.mean(axis=2), 1.0, rtol=1e-8)
     rng = np.random.default_rng(91)
     Amix = rng.standard_normal((8, 8)) + 1j * rng.standard_normal((8, 8))
     h2, _, _ = O.init_from_images(np.einsum("ab,nftb->nfta", Amix, c), p.mics)
