@@ -52,13 +52,18 @@ def _mu_statistics_power1(W, H, g, P, eps):
     return A, D
 
 
-def _neg_loglik_flipped(x, mics, st, eps=OM.EPS):
+def _neg_loglik_variant(x, mics, st, eps=OM.EPS, *, det_sign=-1.0, with_log=True, det_scale="T"):
+    """Eq. (12) with switches that plant the slips below."""
     T = x.shape[1]
     P = OM.projected_power(x, st.Q, mics)
     y = OM.model_variance(OM.source_psd(st.W, st.H), st.g, eps)
-    data = float(np.sum(P / y + np.log(y)))
+    data = float(np.sum(P / y + (np.log(y) if with_log else 0.0)))
     logdet = float(sum(np.sum(OM.log_abs_det_sq(Qk)) for Qk in st.Q))
-    return data + T * logdet  # slip: the sign of the log-determinant term
+    return data + det_sign * (T if det_scale == "T" else 1) * logdet
+
+
+def _neg_loglik_flipped(x, mics, st, eps=OM.EPS):
+    return _neg_loglik_variant(x, mics, st, eps, det_sign=+1.0)  # slip: the sign of the log-determinant term
 
 
 def _wiener_without_inverse(x, mics, st, eps=OM.EPS):
@@ -122,6 +127,10 @@ MUTATIONS = {
         ("update_g", lambda W, H, g, P, eps=OM.EPS: ORIG["update_g"](W, H, g, P, eps) ** 2 / g),
     "cost with the sign of the log-determinant flipped":
         ("neg_loglik", _neg_loglik_flipped),
+    "cost without the ln yhat term":
+        ("neg_loglik", lambda x, mics, st, eps=OM.EPS: _neg_loglik_variant(x, mics, st, eps, with_log=False)),
+    "cost with the log-determinant not multiplied by T":
+        ("neg_loglik", lambda x, mics, st, eps=OM.EPS: _neg_loglik_variant(x, mics, st, eps, det_scale="1")),
     "Wiener filter without Q^-1":
         ("wiener_filter", _wiener_without_inverse),
 }
