@@ -23,7 +23,7 @@ from tests import test_oracle_pins as pins
 ORIG = {name: getattr(OM, name) for name in (
     "weighted_covariances", "model_variance", "ip_update_row", "projected_power", "_mu_statistics",
     "update_W", "update_H", "update_g", "neg_loglik", "wiener_filter", "log_abs_det_sq", "source_psd",
-    "init_from_images")}
+    "init_from_images", "ip_update")}
 
 
 def _ip_row(Qk, Vk, mu, eps=OM.EPS, rtol=OM.SINGULAR_RTOL, *, normalise=True, conj_row=True, order="QV",
@@ -42,6 +42,19 @@ def _ip_row(Qk, Vk, mu, eps=OM.EPS, rtol=OM.SINGULAR_RTOL, *, normalise=True, co
     Qn = Qk.copy()
     Qn[:, mu, :] = np.conj(q) if conj_row else q
     return Qn
+
+
+def _ip_sweep_from_old_block(Q, V, eps=OM.EPS, rtol=OM.SINGULAR_RTOL):
+    """Every row of a block solved from the block as it was before the sweep (all rows at once),
+    where Eqs. (14)-(15) update the rows one after another, each from the block with the rows
+    before it already replaced."""
+    out = []
+    for Qk, Vk in zip(Q, V):
+        Qn = Qk.copy()
+        for mu in range(Qk.shape[1]):
+            Qn[:, mu, :] = OM.ip_update_row(Qk, Vk, mu, eps, rtol)[:, mu, :]  # slip: Qk where Qn belongs
+        out.append(Qn)
+    return out
 
 
 def _mu_statistics_power1(W, H, g, P, eps):
@@ -110,6 +123,8 @@ MUTATIONS = {
         ("weighted_covariances", lambda x, y, mics: ORIG["weighted_covariances"](x, y ** 2, mics)),
     "source model pairing the bases of W and H in reverse":
         ("source_psd", lambda W, H: ORIG["source_psd"](W, H[:, ::-1, :])),
+    "IP sweep solving every row from the block before the sweep":
+        ("ip_update", _ip_sweep_from_old_block),
     "projected power with Q^H instead of Q":
         ("projected_power", lambda x, Q, mics: ORIG["projected_power"](
             x, [np.conj(np.swapaxes(q, 1, 2)) for q in Q], mics)),

@@ -112,6 +112,25 @@ def test_ip_row_stationarity():
             np.testing.assert_allclose(quad, 1.0, atol=1e-10)
 
 
+def test_ip_sweep_updates_rows_in_turn():
+    """A whole sweep (Eq. 13 then Eqs. 14-15 for mu = 0, 1, ... in turn): the last row updated
+    satisfies Q V_mu q = e_mu with the final block, which holds only if every row was solved
+    from the block with the rows before it already replaced."""
+    p, st, x = tiny(mics=(3, 4, 2), F=5, T=30)
+    st.Q = O.unpack_Q(synth.random_blocks(p.F, p.mics, seed=19), p.mics)
+    y = O.model_variance(O.source_psd(st.W, st.H), st.g)
+    V = O.weighted_covariances(x, y, p.mics)
+    Qn = O.ip_update(st.Q, V)
+    for k, mk in enumerate(p.mics):
+        mu = mk - 1
+        q = np.conj(Qn[k][:, mu, :])
+        lhs = np.einsum("fab,fbc,fc->fa", Qn[k], V[k][:, mu], q)
+        e = np.zeros_like(lhs)
+        e[:, mu] = 1
+        np.testing.assert_allclose(lhs, e, atol=1e-10)
+        np.testing.assert_allclose(np.einsum("fa,fab,fb->f", np.conj(q), V[k][:, mu], q), 1.0, atol=1e-10)
+
+
 def test_ip_single_mic_closed_form():
     """M_k = 1: the block becomes exp(i arg Q) / sqrt(V) (scalar case of Eqs. 14-15)."""
     p, st, x = tiny(mics=(1, 1, 1), F=3, T=17)
