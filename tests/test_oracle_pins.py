@@ -329,6 +329,21 @@ def test_wiener_sums_to_mixture_and_matches_dense_posterior_mean():
                 np.testing.assert_allclose(c[n, f, t], ref, rtol=1e-9, atol=1e-11)
 
 
+def test_wiener_invariant_to_row_scaling_of_Q():
+    """c_n = Q^{-1} diag(lambda_n g_n / yhat) Q x: the gain is diagonal and does not involve P,
+    so scaling the rows of every block by nonzero complex factors (Q -> D Q) leaves c unchanged."""
+    p, st, x = tiny(F=3, T=11, mics=(2, 3, 1), N=2, B=2, seed=12)
+    st.Q = O.unpack_Q(synth.random_blocks(p.F, p.mics, seed=13), p.mics)
+    c = O.wiener_filter(x, p.mics, st)
+    rng = np.random.default_rng(14)
+    scaled = []
+    for Qk in st.Q:
+        d = rng.uniform(0.3, 3.0, Qk.shape[:2]) * np.exp(1j * rng.uniform(0, 2 * np.pi, Qk.shape[:2]))
+        scaled.append(d[:, :, None] * Qk)
+    c2 = O.wiener_filter(x, p.mics, O.State(scaled, st.W, st.H, st.g))
+    np.testing.assert_allclose(c2, c, rtol=1e-10, atol=1e-12 * np.abs(c).max())
+
+
 # --------------------------------------------------------------------------- Appendix theorem
 def test_block_joint_diagonalisability_theorem():
     """Appendix: block-diagonal R_n are jointly diagonalisable iff every block family is.
